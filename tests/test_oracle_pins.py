@@ -1,0 +1,447 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+hand-worked values, library routines in special cases, closed forms, invariants
+and brute force on tiny inputs (CPU only)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_08072_gb300 import synth
+
+C = synth.C_LIGHT
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+
+
+def _unit_image(nx, ny, i, j, val=1.0, nband=1):
+    x = np.zeros((nband, nx, ny))
+    x[:, i, j] = val
+    return x
+
+
+# ------------------------------------------------------------------ worked examples
+def test_golden_degrid_values():
+    g = json.load(open(GOLDEN))
+    for case in g["degrid"]:
+        x = _unit_image(4, 4, *case["pixel"], val=case["x"])
+        uvw = np.array([case["uvw"]], dtype=np.float64)
+        v = oracle.degrid(uvw, np.array([C]), np.array([0]), x, 0.6, 0.6)
+        assert abs(v[0, 0] - complex(*case["vis"])) < 1e-12, case
+
+
+def test_golden_grid_values():
+    g = json.load(open(GOLDEN))
+    for case in g["grid"]:
+        uvw = np.array([case["uvw"]], dtype=np.float64)
+        vis = np.array([[complex(*case["vis"])]])
+        wgt = np.array([[case["wgt"]]])
+        img = oracle.grid(uvw, np.array([C]), np.array([0]), vis, wgt, 4, 4, 0.6, 0.6, 1)
+        i, j = case["pixel"]
+        assert abs(img[0, i, j] - case["image"]) < 1e-12, case
+
+
+# ------------------------------------------------------------------ R
+def test_phase_centre_source_gives_unit_visibilities():
+    obs = synth.tiny_observation()
+    x = _unit_image(obs.nx, obs.ny, obs.nx // 2, obs.ny // 2)
+    v = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm)
+    assert np.abs(v - 1.0).max() < 1e-14
+
+
+def test_degrid_equals_numpy_fft_on_regular_grid():
+    """w = 0 and no 1/n: R is a 2-D DFT.  At u = k/(nx dl), v = k'/(ny dm) it equals
+    (-1)^(k+k') fft2(x)[k mod nx, k' mod ny] (numpy's forward FFT, minus sign)."""
+    rng = np.random.default_rng(7)
+    nx, ny, dl = 8, 6, 0.01
+    x = rng.normal(size=(1, nx, ny))
+    ks, kps = np.meshgrid(np.arange(-nx // 2, nx // 2), np.arange(-ny // 2, ny // 2), indexing="ij")
+    ks, kps = ks.ravel(), kps.ravel()
+    uvw = np.stack([ks / (nx * dl), kps / (ny * dl), np.zeros_like(ks, dtype=float)], axis=1)
+    v = oracle.degrid(uvw, np.array([C]), np.array([0]), x, dl, dl, flags=oracle.NO_DIVIDE_BY_N)[:, 0]
+    F = np.fft.fft2(x[0])
+    ref = (-1.0) ** (ks + kps) * F[ks % nx, kps % ny]
+    assert np.abs(v - ref).max() < 1e-12 * np.abs(F).max()
+
+
+def test_hermitian_symmetry():
+    obs = synth.tiny_observation()
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(1, obs.nx, obs.ny))
+    v1 = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm)
+    v2 = oracle.degrid(-obs.uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm)
+    assert np.abs(v2 - np.conj(v1)).max() < 1e-11 * np.abs(v1).max()
+
+
+def test_shift_theorem_w0():
+    """Shifting x by one pixel along l multiplies V by exp(-2 pi i u dl) when w = 0."""
+    obs = synth.tiny_observation()
+    rng = np.random.default_rng(4)
+    x = np.zeros((1, obs.nx, obs.ny))
+    x[0, 10:20, 5:30] = rng.normal(size=(10, 25))
+    xs = np.roll(x, 1, axis=1)
+    f = oracle.NO_DIVIDE_BY_N | oracle.NO_WTERM
+    v = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm, flags=f)
+    vs = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, xs, obs.dl, obs.dm, flags=f)
+    u = obs.uvw[:, 0:1] * obs.freq[None, :] / C
+    assert np.abs(vs - v * np.exp(-2j * np.pi * u * obs.dl)).max() < 1e-10 * np.abs(v).max()
+
+
+def test_linearity_and_row_selection():
+    obs = synth.tiny_observation()
+    rng = np.random.default_rng(5)
+    a, b = rng.normal(size=(2, 1, obs.nx, obs.ny))
+    args = (obs.uvw, obs.freq, obs.band_of_chan)
+    va = oracle.degrid(*args, a, obs.dl, obs.dm)
+    vb = oracle.degrid(*args, b, obs.dl, obs.dm)
+    vab = oracle.degrid(*args, 2.0 * a - 3.0 * b, obs.dl, obs.dm)
+    assert np.abs(vab - (2 * va - 3 * vb)).max() < 1e-10 * np.abs(vab).max()
+    rows = np.array([5, 17, 2000])
+    vr = oracle.degrid(*args, a, obs.dl, obs.dm, rows=rows)
+    assert np.array_equal(vr, va[rows])
+
+
+def test_band_mapping():
+    """Each channel sees only its own band's image."""
+    obs = synth.tiny_observation(nband=2)
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=(2, obs.nx, obs.ny))
+    v = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm)
+    x0 = x.copy(); x0[1] = 0
+    v0 = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x0, obs.dl, obs.dm)
+    b0 = obs.band_of_chan == 0
+    assert np.array_equal(v[:, b0], v0[:, b0])
+    assert np.abs(v0[:, ~b0]).max() == 0.0
+
+
+# ------------------------------------------------------------------ R^dagger
+def test_adjoint_identity():
+    """Re <R x, y> = <x, R^dagger y> with the full w term and 1/n (Eq. 3)."""
+    obs = synth.tiny_observation(nband=2)
+    rng = np.random.default_rng(8)
+    x = rng.normal(size=(2, obs.nx, obs.ny))
+    y = synth.random_vis(rng, (obs.nrow, obs.nchan))
+    rx = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm)
+    ry = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, y, None, obs.nx, obs.ny, obs.dl, obs.dm, 2)
+    lhs = float(np.real(np.vdot(rx, y)))
+    rhs = float(np.sum(x * ry))
+    assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), np.linalg.norm(rx) * np.linalg.norm(y))
+
+
+def test_grid_equals_numpy_ifft_on_regular_grid():
+    rng = np.random.default_rng(9)
+    nx, ny, dl = 6, 8, 0.02
+    ks, kps = np.meshgrid(np.arange(-nx // 2, nx // 2), np.arange(-ny // 2, ny // 2), indexing="ij")
+    ks, kps = ks.ravel(), kps.ravel()
+    uvw = np.stack([ks / (nx * dl), kps / (ny * dl), np.zeros(ks.size)], axis=1)
+    y = synth.random_vis(rng, (ks.size, 1))
+    img = oracle.grid(uvw, np.array([C]), np.array([0]), y, None, nx, ny, dl, dl, 1,
+                      flags=oracle.NO_DIVIDE_BY_N)[0]
+    Y = np.zeros((nx, ny), dtype=complex)
+    Y[ks % nx, kps % ny] = (-1.0) ** (ks + kps) * y[:, 0]
+    ref = np.real(np.fft.ifft2(Y)) * nx * ny
+    assert np.abs(img - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_weights_and_pixel_selection():
+    obs = synth.tiny_observation()
+    rng = np.random.default_rng(10)
+    y = synth.random_vis(rng, (obs.nrow, obs.nchan))
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    a = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, y, w, obs.nx, obs.ny, obs.dl, obs.dm, 1)
+    b = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, y * w, None, obs.nx, obs.ny, obs.dl, obs.dm, 1)
+    assert np.abs(a - b).max() < 1e-10 * np.abs(a).max()
+    pix = np.array([0, 77, 4095])
+    s = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, y, w, obs.nx, obs.ny, obs.dl, obs.dm, 1, pix=pix)
+    assert np.array_equal(s, a.reshape(-1)[pix])
+
+
+def test_dense_matrix_brute_force():
+    """Columns of R from unit images and rows of R^dagger from unit visibilities:
+    the two matrices are transposes under the real inner product."""
+    obs = synth.tiny_observation(nx=8, ny=8, ntime=3, n_ant=5, nchan=2)
+    npx = obs.nx * obs.ny
+    Rm = np.zeros((obs.nvis, npx), dtype=complex)
+    for p in range(npx):
+        e = np.zeros((1, obs.nx, obs.ny)); e.reshape(-1)[p] = 1.0
+        Rm[:, p] = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, e, obs.dl, obs.dm).reshape(-1)
+    Ra = np.zeros((npx, obs.nvis, 2))
+    for k in range(obs.nvis):
+        for part, val in ((0, 1.0), (1, 1.0j)):
+            y = np.zeros(obs.nvis, dtype=complex); y[k] = val
+            Ra[:, k, part] = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, y.reshape(obs.nrow, obs.nchan),
+                                         None, obs.nx, obs.ny, obs.dl, obs.dm, 1).reshape(-1)
+    # Re <R e_p, e_k> = Re R[k,p];  Re <R e_p, i e_k> = Im R[k,p]
+    assert np.abs(Ra[:, :, 0] - Rm.real.T).max() < 1e-12
+    assert np.abs(Ra[:, :, 1] - Rm.imag.T).max() < 1e-12
+
+
+# ------------------------------------------------------------------ I^d, PSF, H
+def test_dirty_of_centre_source_is_psf_crop():
+    obs = synth.tiny_observation()
+    rng = np.random.default_rng(11)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    x = _unit_image(obs.nx, obs.ny, obs.nx // 2, obs.ny // 2)
+    v = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm)
+    d, ws = oracle.dirty(obs.uvw, obs.freq, obs.band_of_chan, v, w, obs.nx, obs.ny, obs.dl, obs.dm, 1)
+    p, ws2 = oracle.psf(obs.uvw, obs.freq, obs.band_of_chan, w, obs.nx, obs.ny, obs.dl, obs.dm, 1)
+    h = obs.nx // 2
+    crop = p[:, h:h + obs.nx, h:h + obs.ny]
+    assert np.abs(d - crop).max() < 1e-10 * ws[0]
+    assert abs(p[0, obs.nx, obs.ny] - w.sum()) < 1e-10 * w.sum()
+    assert np.allclose(ws, [w.sum()]) and np.allclose(ws2, ws)
+    assert p[0, obs.nx, obs.ny] == pytest.approx(p.max(), rel=1e-12)
+
+
+def test_psf_point_symmetric_at_w0():
+    obs = synth.tiny_observation(nx=16, ny=16)
+    uvw = obs.uvw.copy(); uvw[:, 2] = 0.0
+    p, _ = oracle.psf(uvw, obs.freq, obs.band_of_chan, None, obs.nx, obs.ny, obs.dl, obs.dm, 1)
+    n = obs.nx
+    a = p[0, 1:, 1:]
+    assert np.abs(a - a[::-1, ::-1]).max() < 1e-10 * p.max()
+    # with w != 0 the symmetry is broken (the n-1 term)
+    p2, _ = oracle.psf(obs.uvw * 50.0, obs.freq, obs.band_of_chan, None, n, n, obs.dl * 20, obs.dm * 20, 1)
+    b = p2[0, 1:, 1:]
+    assert np.abs(b - b[::-1, ::-1]).max() > 1e-6 * p2.max()
+
+
+def test_hessian_equals_psf_conv_at_w0():
+    obs = synth.tiny_observation(nx=16, ny=16)
+    uvw = obs.uvw.copy(); uvw[:, 2] = 0.0
+    rng = np.random.default_rng(12)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    x = rng.normal(size=(1, obs.nx, obs.ny))
+    a = (uvw, obs.freq, obs.band_of_chan)
+    f = oracle.NO_DIVIDE_BY_N
+    hx = oracle.hessian(*a, w, x, obs.dl, obs.dm, flags=f)
+    p, _ = oracle.psf(*a, w, obs.nx, obs.ny, obs.dl, obs.dm, 1, flags=f)
+    assert np.abs(hx - oracle.psf_conv_direct(p, x)).max() < 1e-10 * np.abs(hx).max()
+    # with 1/n: H x = n^-1 (PSF_raw * (n^-1 x))
+    l = (np.arange(obs.nx) - obs.nx // 2) * obs.dl
+    m = (np.arange(obs.ny) - obs.ny // 2) * obs.dm
+    ninv = 1.0 / np.sqrt(1.0 - l[:, None] ** 2 - m[None, :] ** 2)
+    hx2 = oracle.hessian(*a, w, x, obs.dl, obs.dm)
+    ref = ninv * oracle.psf_conv_direct(p, ninv * x)
+    assert np.abs(hx2 - ref).max() < 1e-10 * np.abs(hx2).max()
+
+
+def test_hessian_differs_from_psf_conv_when_noncoplanar():
+    """Eq. 4 neglects the w term: with w != 0 the PSF convolution is only approximate."""
+    obs = synth.tiny_observation(nx=16, ny=16)
+    rng = np.random.default_rng(13)
+    uvw = obs.uvw * 50.0
+    dl = obs.dl * 20
+    x = rng.uniform(0, 1, (1, 16, 16))
+    hx = oracle.hessian(uvw, obs.freq, obs.band_of_chan, None, x, dl, dl)
+    p, _ = oracle.psf(uvw, obs.freq, obs.band_of_chan, None, 16, 16, dl, dl, 1)
+    rel = np.linalg.norm(hx - oracle.psf_conv(p, x)) / np.linalg.norm(hx)
+    assert rel > 1e-3
+
+
+def test_hessian_symmetric_psd():
+    obs = synth.tiny_observation(nx=16, ny=16)
+    rng = np.random.default_rng(14)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    x, z = rng.normal(size=(2, 1, 16, 16))
+    a = (obs.uvw, obs.freq, obs.band_of_chan, w)
+    hx = oracle.hessian(*a, x, obs.dl, obs.dm)
+    hz = oracle.hessian(*a, z, obs.dl, obs.dm)
+    assert abs(np.sum(hx * z) - np.sum(x * hz)) < 1e-10 * abs(np.sum(hx * z))
+    rx = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm)
+    assert np.sum(x * hx) == pytest.approx(np.sum(w * np.abs(rx) ** 2), rel=1e-11)
+
+
+# ------------------------------------------------------------------ gradient (Eqs. 2-3)
+def test_gradient_central_differences_and_zero_at_truth():
+    obs = synth.tiny_observation(nx=16, ny=16)
+    rng = np.random.default_rng(15)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    a = (obs.uvw, obs.freq, obs.band_of_chan)
+    xt = synth.sparse_random_image(rng, 1, 16, 16, 0.1)
+    V = oracle.degrid(*a, xt, obs.dl, obs.dm)
+    d, _ = oracle.dirty(*a, V, w, 16, 16, obs.dl, obs.dm, 1)
+    g_true = oracle.hessian(*a, w, xt, obs.dl, obs.dm) - d
+    assert np.abs(g_true).max() < 1e-10 * np.abs(d).max()
+    V = V + synth.complex_noise(rng, V.shape)
+    d, _ = oracle.dirty(*a, V, w, 16, 16, obs.dl, obs.dm, 1)
+    x = rng.uniform(0, 1, (1, 16, 16))
+    g = oracle.hessian(*a, w, x, obs.dl, obs.dm) - d
+
+    def f(xx):
+        r = V - oracle.degrid(*a, xx, obs.dl, obs.dm)
+        return 0.5 * float(np.sum(w * np.abs(r) ** 2))
+
+    for p in rng.choice(256, 6, replace=False):
+        e = np.zeros_like(x); e.reshape(-1)[p] = 0.5
+        fd = (f(x + e) - f(x - e)) / 1.0
+        assert fd == pytest.approx(g.reshape(-1)[p], rel=1e-7, abs=1e-9 * np.abs(g).max())
+
+
+# ------------------------------------------------------------------ PSF convolution
+def test_psf_conv_fft_equals_direct_sum():
+    rng = np.random.default_rng(16)
+    psf = rng.normal(size=(2, 24, 20))
+    x = rng.normal(size=(2, 12, 10))
+    a = oracle.psf_conv_direct(psf, x)
+    b = oracle.psf_conv(psf, x)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+
+
+def test_psf_conv_delta_is_identity_and_shift():
+    x = np.random.default_rng(17).normal(size=(1, 8, 8))
+    d = np.zeros((1, 16, 16)); d[0, 8, 8] = 1.0
+    assert np.abs(oracle.psf_conv_direct(d, x) - x).max() == 0.0
+    d2 = np.zeros((1, 16, 16)); d2[0, 9, 8] = 1.0      # centre + one pixel along l
+    y = oracle.psf_conv_direct(d2, x)
+    assert np.abs(y[0, 1:] - x[0, :-1]).max() == 0.0 and np.abs(y[0, 0]).max() == 0.0
+
+
+# ------------------------------------------------------------------ CG on U (Eq. 8)
+def _test_psf(nx, ny, seed=18):
+    obs = synth.tiny_observation(nx=nx, ny=ny, seed=seed)
+    p, ws = oracle.psf(obs.uvw, obs.freq, obs.band_of_chan, None, nx, ny, obs.dl, obs.dm, 1)
+    return p / ws[0]
+
+
+def test_cg_matches_dense_solve():
+    nx = ny = 8
+    p = _test_psf(nx, ny)
+    spec = np.real(oracle.psf_spectrum(p))
+    sigma = 0.05
+    n = nx * ny
+    U = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros((1, nx, ny)); e.reshape(-1)[k] = 1.0
+        U[:, k] = oracle.u_apply(spec, sigma, e).reshape(-1)
+    assert np.abs(U - U.T).max() < 1e-12                     # symmetric by construction
+    assert np.linalg.eigvalsh(U).min() > 0
+    b = np.random.default_rng(19).normal(size=(1, nx, ny))
+    delta, res = oracle.cg(spec, sigma, b, iters=200, tol=1e-13)
+    ref = np.linalg.solve(U, b.reshape(-1)).reshape(1, nx, ny)
+    assert np.abs(delta - ref).max() < 1e-9 * np.abs(ref).max()
+    assert res[0] < 1e-12
+
+
+def test_symmetrised_psf_operator_is_symmetric_part():
+    """U uses Re(spectrum): the convolution with the PSF symmetrised about its
+    centre, i.e. (M + M^T)/2 for M the PSF-convolution matrix."""
+    nx = ny = 6
+    rng = np.random.default_rng(20)
+    p = rng.normal(size=(1, 12, 12))
+    n = nx * ny
+    M = np.zeros((n, n)); S = np.zeros((n, n))
+    spec = np.real(oracle.psf_spectrum(p))
+    for k in range(n):
+        e = np.zeros((1, nx, ny)); e.reshape(-1)[k] = 1.0
+        M[:, k] = oracle.psf_conv_direct(p, e).reshape(-1)
+        S[:, k] = oracle.u_apply(spec, 0.0, e).reshape(-1)
+    assert np.abs(S - 0.5 * (M + M.T)).max() < 1e-12
+
+
+# ------------------------------------------------------------------ wavelets (Eq. 9's Psi)
+def test_daubechies_filter_conditions():
+    for N in range(1, 7):
+        h = oracle.daubechies(N)
+        assert h.shape == (2 * N,)
+        assert h.sum() == pytest.approx(math.sqrt(2.0), abs=1e-13)
+        for m in range(N):
+            s = float(np.dot(h[: 2 * N - 2 * m], h[2 * m:]))
+            assert s == pytest.approx(1.0 if m == 0 else 0.0, abs=1e-12)
+        k = np.arange(2 * N)
+        for pw in range(N):
+            assert abs(float(np.sum((-1.0) ** k * k ** pw * h))) < 1e-9 * max(1, (2 * N) ** pw)
+    s3 = math.sqrt(3.0)
+    db2 = np.array([1 + s3, 3 + s3, 3 - s3, 1 - s3]) / (4 * math.sqrt(2.0))
+    assert np.abs(oracle.daubechies(2) - db2).max() < 1e-14
+
+
+def test_dwt_orthonormal_and_haar_closed_form():
+    rng = np.random.default_rng(21)
+    img = rng.normal(size=(16, 8))
+    for N in (1, 3, 6):
+        h = oracle.daubechies(N)
+        c = oracle.dwt2(img, h, 3)
+        assert np.linalg.norm(c) == pytest.approx(np.linalg.norm(img), rel=1e-13)
+        assert np.abs(oracle.idwt2(c, h, 3) - img).max() < 1e-12
+    c = oracle.dwt2(np.full((4, 4), 3.0), oracle.daubechies(1), 1)
+    ref = np.zeros((4, 4)); ref[:2, :2] = 6.0
+    assert np.abs(c - ref).max() < 1e-14
+
+
+def test_psi_tight_frame():
+    rng = np.random.default_rng(22)
+    x = rng.normal(size=(2, 16, 16))
+    bases = oracle.basis_list(0b1111111)
+    c = oracle.psi_adjoint(x, bases, 2)
+    assert np.abs(oracle.psi(c, bases, 2) - x).max() < 1e-12           # Psi Psi^dagger = Id
+    assert np.linalg.norm(c) == pytest.approx(np.linalg.norm(x), rel=1e-12)
+
+
+# ------------------------------------------------------------------ prox (Eq. 7)
+def test_prox_closed_form_sigma_metric_dirac():
+    """PSF = 0 so U = sigma Id, Psi = Dirac: Eq. 7 has the closed form
+    x_g = max(xbar_g, 0) * max(0, 1 - gamma lam / (sigma ||max(xbar_g, 0)||_2))."""
+    rng = np.random.default_rng(23)
+    nb, nx, ny = 3, 8, 8
+    xbar = rng.normal(size=(nb, nx, ny))
+    spec0 = np.zeros((nb, 16, 16))
+    p = oracle.Params(gamma=0.7, sigma=2.0, lam=0.9, pd_iters=3000, basis_mask=1)
+    x, v = oracle.prox(xbar, np.zeros((1, nb, nx, ny)), spec0, p)
+    z = np.maximum(xbar, 0)
+    nrm = np.sqrt((z ** 2).sum(axis=0, keepdims=True))
+    ref = z * np.maximum(0.0, 1.0 - p.gamma * p.lam / (p.sigma * np.maximum(nrm, 1e-300)))
+    assert np.abs(x - ref).max() < 1e-8
+
+
+def test_prox_lambda0_kkt():
+    nx = ny = 8
+    pn = _test_psf(nx, ny)
+    spec = np.real(oracle.psf_spectrum(pn))
+    rng = np.random.default_rng(24)
+    xbar = rng.normal(size=(1, nx, ny)) * 0.1
+    p = oracle.Params(gamma=1.0, sigma=0.05, lam=0.0, pd_iters=4000)
+    x, _ = oracle.prox(xbar, np.zeros((1, 1, nx, ny)), spec, p)
+    g = oracle.u_apply(spec, p.sigma, x - xbar)
+    assert x.min() >= 0
+    assert g.min() > -1e-7
+    assert np.abs(x * g).max() < 1e-7
+
+
+# ------------------------------------------------------------------ step (Eqs. 6-7)
+def test_step_fixed_point_at_truth():
+    """Noiseless data, lam = 0: the true non-negative image makes the exact residual
+    vanish (Eq. 3), so CG returns 0 and the prox of a feasible point with lam = 0 is
+    the point itself: x_true is a fixed point of one step."""
+    obs = synth.tiny_observation(nx=16, ny=16)
+    rng = np.random.default_rng(25)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    a = (obs.uvw, obs.freq, obs.band_of_chan)
+    xt = synth.sparse_random_image(rng, 1, 16, 16, 0.2)
+    V = oracle.degrid(*a, xt, obs.dl, obs.dm)
+    d, ws = oracle.dirty(*a, V, w, 16, 16, obs.dl, obs.dm, 1)
+    p, _ = oracle.psf(*a, w, 16, 16, obs.dl, obs.dm, 1)
+    prm = oracle.Params(gamma=1.0, sigma=1e-2, lam=0.0, cg_iters=20, pd_iters=50)
+    x1, v1, st = oracle.step(*a, w, d, p, ws, xt, np.zeros((1, 1, 16, 16)), obs.dl, obs.dm, prm)
+    assert np.abs(x1 - xt).max() < 1e-9
+    assert st[1] < 1e-9
+
+
+def test_step_decreases_objective():
+    obs = synth.tiny_observation(nx=16, ny=16)
+    rng = np.random.default_rng(26)
+    w = np.ones((obs.nrow, obs.nchan))
+    a = (obs.uvw, obs.freq, obs.band_of_chan)
+    xt = synth.point_source_image(rng, 1, 16, 16, 5)
+    V = oracle.degrid(*a, xt, obs.dl, obs.dm) + synth.complex_noise(rng, (obs.nrow, obs.nchan))
+    d, ws = oracle.dirty(*a, V, w, 16, 16, obs.dl, obs.dm, 1)
+    p, _ = oracle.psf(*a, w, 16, 16, obs.dl, obs.dm, 1)
+    prm = oracle.Params(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=30, pd_iters=100)
+    x = np.zeros((1, 16, 16)); v = np.zeros((1, 1, 16, 16))
+    objs = []
+    for _ in range(4):
+        x, v, st = oracle.step(*a, w, d, p, ws, x, v, obs.dl, obs.dm, prm)
+        objs.append(st[0])
+    assert x.min() >= 0
+    assert objs[-1] < objs[0]

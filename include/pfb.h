@@ -1,0 +1,185 @@
+/*
+ * libpfb: GB300 (sm_103a) implementation of the pfb-clean hot path
+ * (Bester, Repetti, Perkins, Smirnov & Kenyon, "A practical preconditioner for
+ * wide-field continuum imaging of radio interferometric data").
+ *
+ * The library evaluates the wide-field measurement operator R of Section 2
+ * (Eq. 1), its weighted adjoint R^dagger Sigma^-1 (Eq. 3), the dirty image,
+ * the PSF, the exact Hessian-vector product R^dagger Sigma^-1 R x (Eq. 3), the
+ * PSF convolution I^psf * x (Eq. 4) and one preconditioned forward-backward
+ * step (Eqs. 6-8 with the regulariser of Eq. 9).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Array arguments are DEVICE pointers to contiguous row-major memory owned by
+ *    the caller (for example torch tensors on the context's device), unless an
+ *    argument is marked "host".  The library never frees caller memory.
+ *  - uvw     [nrow][3]  float64, metres (rows as in a Measurement Set).
+ *  - freq    [nchan]    float64, Hz.
+ *  - band_of_chan [nchan] int32 in [0, nband): imaging band of each channel
+ *    (Section 2: n_b bands with n_b << n_nu channels).
+ *  - vis     [nrow][nchan] complex, interleaved (re, im): complex64 for PFB_F32,
+ *    complex128 for PFB_F64.
+ *  - wgt     [nrow][nchan] real >= 0 (float32 for PFB_F32, float64 for PFB_F64),
+ *    the diagonal of Sigma^-1; NULL means all ones.
+ *  - image   [nband][nx][ny] real (float32 / float64).  Pixel (i, j) sits at
+ *    l = (i - nx/2) dl, m = (j - ny/2) dm; n = sqrt(1 - l^2 - m^2).  The first
+ *    image axis pairs with u, the second with v.
+ *  - R x [d, nu] = sum_{i,j} x[b(nu),i,j] / n_ij exp(-2 pi i (u l_i + v m_j + w (n_ij - 1)))
+ *    with (u, v, w) = uvw_d f_nu / c.  R^dagger is the transpose under the real
+ *    inner products Re sum conj(a) b (visibilities) and sum x z (images).
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream).  Outputs are valid once the stream has completed
+ *    the work, except where an entry point writes a host output: those return
+ *    after synchronising the stream.
+ *  - The first call for a new (geometry, precision, uvw/freq/band pointers,
+ *    nrow, nchan) builds a plan (a device sort of the visibilities into uv tiles
+ *    and w-planes, pixel correction tables): it reads freq and band_of_chan back
+ *    to the host and synchronises the stream once.  The plan is cached in the
+ *    context and reused while those pointers and sizes stay the same.  If the
+ *    CONTENTS of uvw, freq or band_of_chan change under the same pointers, call
+ *    pfb_plan_reset() first.
+ *  - Return value: PFB_OK, or a negative PFB_ERR_* code; on error the outputs
+ *    are unspecified and pfb_last_error() describes the failure.
+ *  - A context is not thread-safe: use one context per host thread.
+ *  - Accuracy: epsilon is the requested relative L2 error of R x and R^dagger y
+ *    against the exact FP64 direct sum.  PFB_F32 keeps uvw x frequency -> grid
+ *    coordinates and the w-plane phases in FP64 and everything else in FP32; it
+ *    accepts epsilon >= 1e-6.  PFB_F64 computes in FP64 and accepts
+ *    epsilon >= 1e-13.
+ */
+#ifndef PFB_H
+#define PFB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pfb_ctx pfb_ctx;
+
+typedef enum { PFB_F32 = 0, PFB_F64 = 1 } pfb_prec;
+
+enum {
+    PFB_OK = 0,
+    PFB_ERR_ARG = -1,             /* invalid argument (null pointer, size, geometry, band id) */
+    PFB_ERR_OOM = -2,             /* device memory (or the context's HBM budget) exhausted */
+    PFB_ERR_CUDA = -3,            /* a CUDA runtime or cuFFT call failed */
+    PFB_ERR_EPS = -4,             /* epsilon outside what the precision can reach */
+    PFB_ERR_TIMEOUT = -5,         /* a bounded wait expired */
+    PFB_ERR_NOT_IMPLEMENTED = -6
+};
+
+/* pfb_geom.flags (test switches; production calls pass 0) */
+#define PFB_NO_DIVIDE_BY_N 1u     /* drop the 1/n factor of Eq. 1 */
+#define PFB_NO_WTERM 2u           /* drop the w (n - 1) term (coplanar 2-D NUFFT) */
+
+typedef struct {
+    int32_t nx, ny;      /* image pixels per band (even); the PSF is 2nx x 2ny */
+    double dl, dm;       /* pixel size, radians */
+    double fov_l, fov_m; /* field of view in radians: 0 = derive, else must equal nx*dl, ny*dm */
+    double epsilon;      /* requested relative L2 accuracy of R and R^dagger */
+    int32_t nband;       /* n_b imaging bands */
+    uint32_t flags;      /* PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM */
+} pfb_geom;
+
+/* Parameters of one pfb-clean step (Eqs. 6-9). */
+typedef struct {
+    double gamma;        /* step size (Eq. 6); the preconditioning allows gamma close to 1 */
+    double sigma;        /* sigma > 0 of U = I^psf* + sigma Id (Eq. 8), in PSF-peak units */
+    double lambda;       /* weight of the l2,1 term of Eq. 9 */
+    double cg_tol;       /* CG stops when ||r|| <= cg_tol ||IR|| (0: run cg_iters) */
+    double pd_tol;       /* reserved: the primal-dual solver runs pd_iters iterations */
+    int32_t cg_iters;    /* conjugate-gradient iterations for U delta = IR */
+    int32_t pd_iters;    /* Condat-Vu primal-dual iterations for Eq. 7 */
+    int32_t nlevel;      /* wavelet decomposition levels (wavelet bases) */
+    uint32_t basis_mask; /* bit 0 Dirac; bits 1..6 Daubechies db1..db6 (Eq. 9's dictionary) */
+    double unorm;        /* ||U|| for the primal step; <= 0: max |PSF spectrum| + sigma */
+} pfb_params;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the scratch
+ * (w-plane stacks, sort tables); 0 means 85% of the device memory free at creation.
+ * Returns PFB_OK and *ctx, or an error (then *ctx is NULL). */
+int pfb_create(pfb_ctx **ctx, int device, size_t hbm_budget_bytes);
+
+/* Free every device buffer the context owns.  Waits for the context's work. */
+void pfb_destroy(pfb_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none).  The pointer stays
+ * valid until the next call on the context. */
+const char *pfb_last_error(const pfb_ctx *ctx);
+
+/* Drop cached plans and PSF spectra (call after changing uvw/freq/band contents
+ * or PSF contents in place). */
+int pfb_plan_reset(pfb_ctx *ctx);
+
+/* R, degridding (Section 2, Eq. 1): image [nband][nx][ny] -> vis_out [nrow][nchan].
+ * w-stacking with an exponential-of-semicircle kernel; accuracy epsilon. */
+int pfb_degrid(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, int64_t nrow, int32_t nchan,
+               const double *uvw, const double *freq, const int32_t *band_of_chan,
+               const void *image, void *vis_out, void *stream);
+
+/* R^dagger Sigma^-1, gridding (Eq. 3): image_out = R^dagger (wgt . vis).
+ * image_out [nband][nx][ny] is overwritten. */
+int pfb_grid(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, int64_t nrow, int32_t nchan,
+             const double *uvw, const double *freq, const int32_t *band_of_chan,
+             const void *vis, const void *wgt, void *image_out, void *stream);
+
+/* Dirty image I^d = R^dagger Sigma^-1 V (Eq. 3) into image_out, and if wsum_out
+ * (host, [nband]) is not NULL the per-band weight sums (then the call returns
+ * after synchronising the stream). */
+int pfb_dirty(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, int64_t nrow, int32_t nchan,
+              const double *uvw, const double *freq, const int32_t *band_of_chan,
+              const void *vis, const void *wgt, void *image_out, double *wsum_out, void *stream);
+
+/* PSF I^psf (Eqs. 4 and 8): R'^dagger (wgt . 1) where R' is the operator on a
+ * 2nx x 2ny grid with the same pixel size; psf_out [nband][2nx][2ny], centre
+ * pixel (nx, ny), unnormalised (its centre value is the band's weight sum).
+ * wsum_out as in pfb_dirty. */
+int pfb_psf(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, int64_t nrow, int32_t nchan,
+            const double *uvw, const double *freq, const int32_t *band_of_chan,
+            const void *wgt, void *psf_out, double *wsum_out, void *stream);
+
+/* Exact Hessian-vector product (Eq. 3): y_out = R^dagger Sigma^-1 R x, both [nband][nx][ny]. */
+int pfb_hessian(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, int64_t nrow, int32_t nchan,
+                const double *uvw, const double *freq, const int32_t *band_of_chan,
+                const void *wgt, const void *x, void *y_out, void *stream);
+
+/* PSF convolution (Eq. 4): y_out[b,i,j] = sum_{i',j'} psf[b, i-i'+nx, j-j'+ny] x[b,i',j']
+ * (linear convolution, psf [nband][2nx][2ny] as written by pfb_psf).  Uses the
+ * geometry's nx, ny, nband only.  The PSF spectrum is cached per psf pointer. */
+int pfb_psf_conv(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const void *psf,
+                 const void *x, void *y_out, void *stream);
+
+/* One preconditioned forward-backward step (Eqs. 6-7):
+ *   wbar = mean_b wsum[b]; I^d, I^psf and the Hessian are divided by wbar;
+ *   IR = I^d - H x_k (one exact Hessian application, Eq. 3);
+ *   delta = CG solve of U delta = IR per band, U = I^psf_sym * + sigma Id (Eq. 8),
+ *           I^psf_sym the PSF symmetrised about its centre (the symmetric part of
+ *           the PSF convolution; identical to it when w = 0);
+ *   x_{k+1/2} = x_k + gamma delta (Eq. 6);
+ *   x_{k+1} = prox^U_{gamma r}(x_{k+1/2}) by Condat-Vu primal-dual iterations with
+ *             r(x) = lambda ||Psi^dagger x||_{2,1} + iota_+(x) (Eqs. 7 and 9).
+ * dirty [nband][nx][ny] and psf [nband][2nx][2ny] as written by pfb_dirty / pfb_psf;
+ * wsum (host, [nband]) the weight sums they returned; x_inout [nband][nx][ny];
+ * dual_inout [nbasis][nband][nx][ny] (nbasis = bits set in basis_mask), zero on
+ * the first step.  n_hessian_out (host, may be NULL) receives 1; stats_out (host,
+ * [3], may be NULL) receives [objective at x_k without the data constant,
+ * ||x_{k+1} - x_k|| / ||x_{k+1}||, largest CG relative residual]; when either is
+ * given the call returns after synchronising the stream. */
+int pfb_step(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_params *params,
+             int64_t nrow, int32_t nchan, const double *uvw, const double *freq,
+             const int32_t *band_of_chan, const void *wgt, const void *dirty, const void *psf,
+             const double *wsum, void *x_inout, void *dual_inout, int64_t *n_hessian_out,
+             double *stats_out, void *stream);
+
+/* Library version string. */
+const char *pfb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFB_H */

@@ -1,0 +1,336 @@
+// C ABI of libpfb: argument checking, the context (device buffers, plans,
+// cuFFT handles, PSF spectra) and the entry points declared in include/pfb.h.
+#include "ctx.cuh"
+
+#include <algorithm>
+
+struct pfb_ctx {
+    pfb::Ctx impl;
+};
+
+namespace pfb {
+
+Ctx::~Ctx() {
+    cudaSetDevice(device);
+    cudaDeviceSynchronize();
+    for (auto &pp : plans) free_plan(*pp);
+    plans.clear();
+    for (auto &s : spectra) cudaFree(s.spec);
+    spectra.clear();
+    for (auto &kv : bufs) cudaFree(kv.second.ptr);
+    bufs.clear();
+    for (auto &kv : ffts) cufftDestroy(kv.second);
+    ffts.clear();
+}
+
+void *Ctx::dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (used + bytes > budget)
+        throw Error(PFB_ERR_OOM, "HBM budget exceeded: need " + std::to_string(bytes) + " more bytes, " +
+                                     std::to_string(available()) + " left of " + std::to_string(budget));
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(e == cudaErrorMemoryAllocation ? PFB_ERR_OOM : PFB_ERR_CUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    used += bytes;
+    return p;
+}
+
+void Ctx::dfree(void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    used -= std::min(used, bytes == 0 ? (size_t)16 : bytes);
+}
+
+void *Ctx::scratch(const std::string &name, size_t bytes) {
+    DevBuf &b = bufs[name];
+    if (b.bytes >= bytes && b.ptr) return b.ptr;
+    if (b.ptr) {
+        dfree(b.ptr, b.bytes);
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    b.ptr = dalloc(bytes);
+    b.bytes = bytes == 0 ? 16 : bytes;
+    return b.ptr;
+}
+
+size_t Ctx::scratch_bytes(const std::string &name) const {
+    auto it = bufs.find(name);
+    return it == bufs.end() ? 0 : it->second.bytes;
+}
+
+void Ctx::free_plan(Plan &p) {
+    auto fr = [&](void *q, size_t n) {
+        if (q) dfree(q, n);
+    };
+    fr(p.d_scale, p.nchan * sizeof(double));
+    fr(p.d_band, p.nchan * sizeof(int));
+    fr(p.d_bg, p.nband * sizeof(BandGeom));
+    fr(p.d_items, (size_t)std::max<int64_t>(p.nitems, 1) * sizeof(uint32_t));
+    fr(p.d_off, (size_t)(p.nkeys + 1) * sizeof(int64_t));
+    fr(p.d_tp, (size_t)p.nx * p.ny * sizeof(double));
+    fr(p.d_corr, (size_t)p.nx * p.ny * (p.prec == PFB_F64 ? 8 : 4));
+    if (p.d_work) fr(p.d_work, (size_t)p.work_begin.back() * sizeof(WorkItem));
+    if (p.d_heavy) fr(p.d_heavy, (size_t)p.heavy_begin.back() * sizeof(int));
+    p.d_scale = nullptr; p.d_band = nullptr; p.d_bg = nullptr; p.d_items = nullptr; p.d_off = nullptr;
+    p.d_tp = nullptr; p.d_corr = nullptr; p.d_work = nullptr; p.d_heavy = nullptr;
+}
+
+void Ctx::reset() {
+    cudaDeviceSynchronize();
+    for (auto &pp : plans) free_plan(*pp);
+    plans.clear();
+    for (auto &s : spectra) dfree(s.spec, s.bytes);
+    spectra.clear();
+}
+
+cufftHandle Ctx::fft(int n0, int n1, int batch, cufftType type) {
+    FftKey k{n0, n1, batch, (int)type};
+    auto it = ffts.find(k);
+    cufftHandle h;
+    size_t ws = 0;
+    if (it == ffts.end()) {
+        PFB_CUFFT(cufftCreate(&h));
+        PFB_CUFFT(cufftSetAutoAllocation(h, 0));
+        int n[2] = {n0, n1};
+        cufftResult r = cufftMakePlanMany(h, 2, n, nullptr, 1, 0, nullptr, 1, 0, type, batch, &ws);
+        if (r != CUFFT_SUCCESS) {
+            cufftDestroy(h);
+            throw Error(PFB_ERR_CUDA, "cufftMakePlanMany failed: " + std::to_string((int)r));
+        }
+        ffts[k] = h;
+    } else {
+        h = it->second;
+        PFB_CUFFT(cufftGetSize(h, &ws));
+    }
+    // every handle uses the shared work area; grow it if this plan needs more
+    void *work = scratch("fftwork", std::max<size_t>(ws, 256));
+    PFB_CUFFT(cufftSetWorkArea(h, work));
+    return h;
+}
+
+}  // namespace pfb
+
+using namespace pfb;
+
+namespace {
+
+template <typename F>
+int guarded(pfb_ctx *ctx, F &&f) {
+    if (!ctx) return PFB_ERR_ARG;
+    ctx->impl.err.clear();
+    try {
+        PFB_CUDA(cudaSetDevice(ctx->impl.device));
+        f(ctx->impl);
+        return PFB_OK;
+    } catch (const Error &e) {
+        ctx->impl.err = e.what();
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        ctx->impl.err = "host allocation failed";
+        return PFB_ERR_OOM;
+    } catch (const std::exception &e) {
+        ctx->impl.err = e.what();
+        return PFB_ERR_CUDA;
+    }
+}
+
+void check_geom(const pfb_geom *g, pfb_prec prec) {
+    PFB_REQUIRE(g != nullptr, "geom is NULL");
+    PFB_REQUIRE(prec == PFB_F32 || prec == PFB_F64, "prec must be PFB_F32 or PFB_F64");
+    PFB_REQUIRE(g->nx >= 2 && g->ny >= 2 && g->nx % 2 == 0 && g->ny % 2 == 0, "nx, ny must be even and >= 2");
+    PFB_REQUIRE(g->nx <= 65536 && g->ny <= 65536, "nx, ny must be <= 65536");
+    PFB_REQUIRE(g->nband >= 1 && g->nband <= 32, "nband must be in [1, 32]");
+    PFB_REQUIRE(std::isfinite(g->dl) && std::isfinite(g->dm) && g->dl > 0 && g->dm > 0, "dl, dm must be > 0");
+    PFB_REQUIRE((g->flags & ~(PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM)) == 0, "unknown flag bits");
+    if (g->fov_l != 0)
+        PFB_REQUIRE(std::fabs(g->fov_l - g->nx * g->dl) <= 1e-9 * std::fabs(g->fov_l), "fov_l != nx * dl");
+    if (g->fov_m != 0)
+        PFB_REQUIRE(std::fabs(g->fov_m - g->ny * g->dm) <= 1e-9 * std::fabs(g->fov_m), "fov_m != ny * dm");
+    if (!(g->epsilon > 0 && g->epsilon < 1)) throw Error(PFB_ERR_EPS, "epsilon must be in (0, 1)");
+    if (prec == PFB_F32 && g->epsilon < 1e-6)
+        throw Error(PFB_ERR_EPS, "epsilon below 1e-6 is not reachable in PFB_F32; use PFB_F64");
+    if (prec == PFB_F64 && g->epsilon < 1e-13) throw Error(PFB_ERR_EPS, "epsilon below 1e-13 is not reachable");
+}
+
+void check_data(int64_t nrow, int32_t nchan, const double *uvw, const double *freq, const int32_t *band) {
+    PFB_REQUIRE(nrow >= 1 && nchan >= 1, "nrow and nchan must be >= 1");
+    PFB_REQUIRE(uvw && freq && band, "uvw, freq and band_of_chan must not be NULL");
+}
+
+cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+const char *pfb_version(void) { return "pfb-gb300 0.1 (sm_103a)"; }
+
+int pfb_create(pfb_ctx **out, int device, size_t budget) {
+    if (!out) return PFB_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return PFB_ERR_ARG;
+    }
+    pfb_ctx *c = new (std::nothrow) pfb_ctx;
+    if (!c) return PFB_ERR_OOM;
+    c->impl.device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return PFB_ERR_CUDA;
+    }
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    cudaDeviceGetAttribute(&c->impl.num_sms, cudaDevAttrMultiProcessorCount, device);
+    c->impl.budget = budget ? budget : (size_t)(0.85 * (double)fr);
+    *out = c;
+    return PFB_OK;
+}
+
+void pfb_destroy(pfb_ctx *ctx) { delete ctx; }
+
+const char *pfb_last_error(const pfb_ctx *ctx) { return ctx ? ctx->impl.err.c_str() : "null context"; }
+
+int pfb_plan_reset(pfb_ctx *ctx) {
+    return guarded(ctx, [&](Ctx &c) { c.reset(); });
+}
+
+int pfb_degrid(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
+               const double *freq, const int32_t *band, const void *image, void *vis_out, void *stream) {
+    return guarded(ctx, [&](Ctx &c) {
+        check_geom(g, prec);
+        check_data(nrow, nchan, uvw, freq, band);
+        PFB_REQUIRE(image && vis_out, "image and vis_out must not be NULL");
+        Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, S(stream));
+        if (prec == PFB_F64) op_degrid<double>(c, p, (const double *)image, (double2 *)vis_out, S(stream));
+        else op_degrid<float>(c, p, (const float *)image, (float2 *)vis_out, S(stream));
+    });
+}
+
+int pfb_grid(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
+             const double *freq, const int32_t *band, const void *vis, const void *wgt, void *image_out,
+             void *stream) {
+    return guarded(ctx, [&](Ctx &c) {
+        check_geom(g, prec);
+        check_data(nrow, nchan, uvw, freq, band);
+        PFB_REQUIRE(vis && image_out, "vis and image_out must not be NULL");
+        Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, S(stream));
+        if (prec == PFB_F64)
+            op_grid<double>(c, p, (const double2 *)vis, (const double *)wgt, false, (double *)image_out, S(stream));
+        else
+            op_grid<float>(c, p, (const float2 *)vis, (const float *)wgt, false, (float *)image_out, S(stream));
+    });
+}
+
+static void wsum_to_host(Ctx &c, const Plan &p, pfb_prec prec, const void *wgt, double *wsum_out, cudaStream_t st) {
+    double *d = (double *)c.scratch("wsum", 32 * sizeof(double));
+    if (prec == PFB_F64) op_wsum<double>(c, p, (const double *)wgt, d, st);
+    else op_wsum<float>(c, p, (const float *)wgt, d, st);
+    PFB_CUDA(cudaMemcpyAsync(wsum_out, d, p.nband * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PFB_CUDA(cudaStreamSynchronize(st));
+}
+
+int pfb_dirty(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
+              const double *freq, const int32_t *band, const void *vis, const void *wgt, void *image_out,
+              double *wsum_out, void *stream) {
+    return guarded(ctx, [&](Ctx &c) {
+        check_geom(g, prec);
+        check_data(nrow, nchan, uvw, freq, band);
+        PFB_REQUIRE(vis && image_out, "vis and image_out must not be NULL");
+        Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, S(stream));
+        if (prec == PFB_F64)
+            op_grid<double>(c, p, (const double2 *)vis, (const double *)wgt, false, (double *)image_out, S(stream));
+        else
+            op_grid<float>(c, p, (const float2 *)vis, (const float *)wgt, false, (float *)image_out, S(stream));
+        if (wsum_out) wsum_to_host(c, p, prec, wgt, wsum_out, S(stream));
+    });
+}
+
+int pfb_psf(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
+            const double *freq, const int32_t *band, const void *wgt, void *psf_out, double *wsum_out,
+            void *stream) {
+    return guarded(ctx, [&](Ctx &c) {
+        check_geom(g, prec);
+        check_data(nrow, nchan, uvw, freq, band);
+        PFB_REQUIRE(psf_out, "psf_out must not be NULL");
+        PFB_REQUIRE(2 * g->nx <= 65536 && 2 * g->ny <= 65536, "PSF grid too large");
+        Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, true, S(stream));
+        if (prec == PFB_F64)
+            op_grid<double>(c, p, nullptr, (const double *)wgt, true, (double *)psf_out, S(stream));
+        else
+            op_grid<float>(c, p, nullptr, (const float *)wgt, true, (float *)psf_out, S(stream));
+        if (wsum_out) wsum_to_host(c, p, prec, wgt, wsum_out, S(stream));
+    });
+}
+
+int pfb_hessian(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
+                const double *freq, const int32_t *band, const void *wgt, const void *x, void *y_out,
+                void *stream) {
+    return guarded(ctx, [&](Ctx &c) {
+        check_geom(g, prec);
+        check_data(nrow, nchan, uvw, freq, band);
+        PFB_REQUIRE(x && y_out, "x and y_out must not be NULL");
+        Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, S(stream));
+        const size_t cxs = prec == PFB_F64 ? 16 : 8;
+        void *vis = c.scratch("hess_vis", (size_t)nrow * nchan * cxs);
+        if (prec == PFB_F64) {
+            op_degrid<double>(c, p, (const double *)x, (double2 *)vis, S(stream));
+            op_grid<double>(c, p, (const double2 *)vis, (const double *)wgt, false, (double *)y_out, S(stream));
+        } else {
+            op_degrid<float>(c, p, (const float *)x, (float2 *)vis, S(stream));
+            op_grid<float>(c, p, (const float2 *)vis, (const float *)wgt, false, (float *)y_out, S(stream));
+        }
+    });
+}
+
+int pfb_psf_conv(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const void *psf, const void *x, void *y_out,
+                 void *stream) {
+    return guarded(ctx, [&](Ctx &c) {
+        PFB_REQUIRE(g != nullptr, "geom is NULL");
+        PFB_REQUIRE(prec == PFB_F32 || prec == PFB_F64, "prec must be PFB_F32 or PFB_F64");
+        PFB_REQUIRE(g->nx >= 2 && g->ny >= 2 && g->nx % 2 == 0 && g->ny % 2 == 0, "nx, ny must be even");
+        PFB_REQUIRE(g->nband >= 1 && g->nband <= 32, "nband must be in [1, 32]");
+        PFB_REQUIRE(psf && x && y_out, "psf, x and y_out must not be NULL");
+        if (prec == PFB_F64)
+            op_psf_conv<double>(c, g->nx, g->ny, g->nband, (const double *)psf, (const double *)x, (double *)y_out,
+                                S(stream));
+        else
+            op_psf_conv<float>(c, g->nx, g->ny, g->nband, (const float *)psf, (const float *)x, (float *)y_out,
+                               S(stream));
+    });
+}
+
+int pfb_step(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const pfb_params *prm, int64_t nrow, int32_t nchan,
+             const double *uvw, const double *freq, const int32_t *band, const void *wgt, const void *dirty,
+             const void *psf, const double *wsum, void *x_inout, void *dual_inout, int64_t *n_hessian_out,
+             double *stats_out, void *stream) {
+    return guarded(ctx, [&](Ctx &c) {
+        check_geom(g, prec);
+        check_data(nrow, nchan, uvw, freq, band);
+        PFB_REQUIRE(prm, "params is NULL");
+        PFB_REQUIRE(dirty && psf && wsum && x_inout && dual_inout, "dirty, psf, wsum, x and dual must not be NULL");
+        PFB_REQUIRE(prm->gamma > 0 && prm->sigma > 0 && prm->lambda >= 0, "need gamma > 0, sigma > 0, lambda >= 0");
+        PFB_REQUIRE(prm->cg_iters >= 0 && prm->pd_iters >= 0, "iteration counts must be >= 0");
+        if (prm->basis_mask != 1u)
+            throw Error(PFB_ERR_NOT_IMPLEMENTED, "only the Dirac basis (basis_mask = 1) is implemented in pfb_step");
+        Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, S(stream));
+        if (prec == PFB_F64)
+            op_step<double>(c, p, *prm, (const double *)wgt, (const double *)dirty, (const double *)psf, wsum,
+                            (double *)x_inout, (double *)dual_inout, stats_out, S(stream));
+        else
+            op_step<float>(c, p, *prm, (const float *)wgt, (const float *)dirty, (const float *)psf, wsum,
+                           (float *)x_inout, (float *)dual_inout, stats_out, S(stream));
+        if (n_hessian_out) {
+            *n_hessian_out = 1;
+            if (!stats_out) PFB_CUDA(cudaStreamSynchronize(S(stream)));
+        }
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// Host-side context and plan structures of libpfb (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace pfb {
+
+// One gridding work item: a uv tile of one band, either the tile's whole item
+// list (plain stores of the tile's cells) or one chunk of a heavy tile's list
+// (reduction into zeroed cells).
+struct WorkItem {
+    int tile;
+    int atomic_mode;
+    long long begin, end;
+};
+
+struct Plan {
+    // ---- key
+    int nx = 0, ny = 0, nband = 0;
+    double dl = 0, dm = 0;
+    uint32_t flags = 0;
+    int prec = 0;
+    int W = 0;
+    int64_t nrow = 0;
+    int nchan = 0;
+    const void *uvw = nullptr, *freq = nullptr, *band = nullptr;
+    uint64_t last_use = 0;
+
+    // ---- geometry
+    int Nu = 0, Nv = 0, Ww = 1, ntu = 0, ntv = 0, q = 1, nkq = 1, Pmax = 1;
+    double beta = 0, dw = 0, tc = 0, Thalf = 0;
+    bool wstack = false;
+    std::vector<double> w0, wlo, whi;
+    std::vector<int> P;
+    std::vector<double> scale;      // f / c per channel
+    std::vector<int> band_h;
+    std::vector<int64_t> band_items_begin, band_items_end;
+    std::vector<int64_t> work_begin; // per band offset into d_work (size nband + 1)
+    std::vector<int64_t> heavy_begin; // per band offset into d_heavy (size nband + 1)
+
+    // ---- device
+    double *d_scale = nullptr;
+    int *d_band = nullptr;
+    BandGeom *d_bg = nullptr;
+    uint32_t *d_items = nullptr;
+    int64_t nitems = 0;
+    int64_t *d_off = nullptr;
+    int64_t nkeys = 0;
+    double *d_tp = nullptr;   // n - 1 - tc per pixel
+    void *d_corr = nullptr;   // 1 / (n psi_u psi_v psi_w) per pixel, working precision
+    WorkItem *d_work = nullptr;
+    int *d_heavy = nullptr;
+    size_t bytes = 0;
+
+    BandGeom geom(int b) const {
+        BandGeom g;
+        g.Nu = Nu; g.Nv = Nv; g.W = W; g.Ww = Ww; g.ntu = ntu; g.ntv = ntv;
+        g.nkq = nkq; g.q = q; g.P = P[b]; g.band = b; g.nchan = nchan;
+        g.u2cell = dl * Nu; g.v2cell = dm * Nv;
+        g.inv_dw = wstack ? 1.0 / dw : 0.0;
+        g.w0 = w0[b];
+        g.tc = tc; g.beta = beta; g.inv_halfw = 2.0 / W;
+        return g;
+    }
+    int64_t key(int b, int tile, int kq) const { return ((int64_t)b * ntu * ntv + tile) * nkq + kq; }
+};
+
+struct PsfSpec {
+    const void *psf = nullptr;
+    int nx = 0, ny = 0, nband = 0, prec = 0;
+    void *spec = nullptr;   // complex [nband][2nx][ny+1]
+    size_t bytes = 0;
+};
+
+struct FftKey {
+    int n0, n1, batch, type;
+    bool operator<(const FftKey &o) const {
+        if (n0 != o.n0) return n0 < o.n0;
+        if (n1 != o.n1) return n1 < o.n1;
+        if (batch != o.batch) return batch < o.batch;
+        return type < o.type;
+    }
+};
+
+struct Ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    std::string err;
+    uint64_t clock = 0;
+    std::vector<std::unique_ptr<Plan>> plans;
+    std::map<std::string, DevBuf> bufs;
+    std::map<FftKey, cufftHandle> ffts;
+    std::vector<PsfSpec> spectra;
+
+    ~Ctx();
+    void *dalloc(size_t bytes);            // counted against the budget
+    void dfree(void *p, size_t bytes);
+    void *scratch(const std::string &name, size_t bytes);  // grow-only named buffer
+    size_t scratch_bytes(const std::string &name) const;
+    size_t available() const { return budget > used ? budget - used : 0; }
+    void free_plan(Plan &p);
+    void reset();
+    cufftHandle fft(int n0, int n1, int batch, cufftType type);
+};
+
+// plan.cu
+Plan &get_plan(Ctx &ctx, const pfb_geom &g, int prec, int64_t nrow, int nchan, const double *uvw,
+               const double *freq, const int32_t *band, bool psf_grid, cudaStream_t st);
+int kernel_support(double eps);
+
+// wstack.cu
+template <typename T>
+void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st);
+template <typename T>
+void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool unit_vis, T *image,
+             cudaStream_t st);
+template <typename T>
+void op_wsum(Ctx &ctx, const Plan &p, const T *wgt, double *d_wsum, cudaStream_t st);
+
+// image.cu
+template <typename T>
+void op_psf_conv(Ctx &ctx, int nx, int ny, int nband, const T *psf, const T *x, T *y, cudaStream_t st);
+template <typename T>
+void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const T *dirty,
+             const T *psf, const double *wsum_h, T *x, T *dual, double *stats_h, cudaStream_t st);
+
+}  // namespace pfb

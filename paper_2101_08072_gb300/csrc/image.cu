@@ -1,0 +1,460 @@
+// Image-side operators of pfb-clean: the PSF convolution I^psf * x (Eq. 4), the
+// preconditioner U = I^psf_sym * + sigma Id (Eq. 8), conjugate gradient for
+// U delta = IR (Eq. 6), the Condat-Vu primal-dual solver for the backward step
+// (Eq. 7) with r(x) = lambda ||Psi^dagger x||_{2,1} + iota_+(x) (Eq. 9), and the
+// composed step.  All scalars of the iterations (CG alpha/beta, step sizes)
+// stay on the device: a step launches a fixed sequence of kernels and reads
+// results back only when the caller asks for host statistics.
+#include "ctx.cuh"
+
+#include <algorithm>
+
+namespace pfb {
+
+template <typename T> struct RFft;
+template <> struct RFft<float> {
+    static constexpr cufftType r2c = CUFFT_R2C, c2r = CUFFT_C2R;
+    static cufftResult fwd(cufftHandle h, float *in, float2 *out) {
+        return cufftExecR2C(h, (cufftReal *)in, (cufftComplex *)out);
+    }
+    static cufftResult inv(cufftHandle h, float2 *in, float *out) {
+        return cufftExecC2R(h, (cufftComplex *)in, (cufftReal *)out);
+    }
+};
+template <> struct RFft<double> {
+    static constexpr cufftType r2c = CUFFT_D2Z, c2r = CUFFT_Z2D;
+    static cufftResult fwd(cufftHandle h, double *in, double2 *out) {
+        return cufftExecD2Z(h, (cufftDoubleReal *)in, (cufftDoubleComplex *)out);
+    }
+    static cufftResult inv(cufftHandle h, double2 *in, double *out) {
+        return cufftExecZ2D(h, (cufftDoubleComplex *)in, (cufftDoubleReal *)out);
+    }
+};
+
+// ------------------------------------------------------------------ small kernels
+// psf centre (nx, ny) moved to index (0, 0): s[i][j] = psf[(i + nx) mod 2nx][(j + ny) mod 2ny]
+template <typename T>
+__global__ void k_ifftshift(int nx, int ny, int nband, const T *__restrict__ psf, T *__restrict__ out) {
+    const int64_t NX = 2 * nx, NY = 2 * ny;
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nband * NX * NY) return;
+    const int64_t b = e / (NX * NY), r = e - b * NX * NY;
+    const int64_t i = r / NY, j = r - i * NY;
+    int64_t si = i + nx, sj = j + ny;
+    si -= si >= NX ? NX : 0;
+    sj -= sj >= NY ? NY : 0;
+    out[e] = psf[b * NX * NY + si * NY + sj];
+}
+
+// zero-padded copy of (a - b) (b may be null) into [nband][2nx][2ny]
+template <typename T>
+__global__ void k_pad(int nx, int ny, int nband, const T *__restrict__ a, const T *__restrict__ b,
+                      T *__restrict__ out) {
+    const int64_t NX = 2 * nx, NY = 2 * ny;
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nband * NX * NY) return;
+    const int64_t bb = e / (NX * NY), r = e - bb * NX * NY;
+    const int64_t i = r / NY, j = r - i * NY;
+    T v = 0;
+    if (i < nx && j < ny) {
+        const int64_t s = (bb * nx + i) * ny + j;
+        v = b ? a[s] - b[s] : a[s];
+    }
+    out[e] = v;
+}
+
+// X *= S * scale (complex S), or X *= Re(S) * scale (symmetric part)
+template <typename T>
+__global__ void k_spec_mul(int64_t n, const cx_t<T> *__restrict__ S, T scale, int sym, cx_t<T> *__restrict__ X) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const cx_t<T> s = S[e];
+    cx_t<T> x = X[e];
+    if (sym) {
+        x.x *= s.x * scale;
+        x.y *= s.x * scale;
+    } else {
+        const T r = (x.x * s.x - x.y * s.y) * scale;
+        const T i = (x.x * s.y + x.y * s.x) * scale;
+        x.x = r;
+        x.y = i;
+    }
+    X[e] = x;
+}
+
+template <typename T>
+__global__ void k_crop(int nx, int ny, int nband, const T *__restrict__ big, T *__restrict__ y) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nband * nx * ny) return;
+    const int64_t b = e / ((int64_t)nx * ny), r = e - b * nx * ny;
+    const int64_t i = r / ny, j = r - i * ny;
+    y[e] = big[(b * 2 * nx + i) * 2 * ny + j];
+}
+
+// max |Re S| over the spectrum (bits of a non-negative double)
+template <typename T>
+__global__ void k_absmax_re(int64_t n, const cx_t<T> *__restrict__ S, unsigned long long *out) {
+    double m = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs((double)S[e].x));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// block reduction of a double into *dst (atomic)
+__device__ __forceinline__ void block_sum_atomic(double v, double *dst) {
+    __shared__ double ws[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) atomicAdd(dst, v);
+    }
+    __syncthreads();
+}
+
+// Scalar slots of one step (device doubles)
+enum {
+    S_XHX = 0,      // x_k . H x_k
+    S_XD,           // x_k . I^d
+    S_UNORM,        // ||U|| (bits while reducing, then value)
+    S_DX2,          // ||x_{k+1} - x_k||^2
+    S_X2,           // ||x_{k+1}||^2
+    S_L21,          // ||Psi^dagger x_k||_{2,1}
+    S_COUNT
+};
+// per-band arrays follow: BB[nb] (||IR||^2), then RR[(iters+1)][nb], PAP[iters][nb]
+
+// IR = (I^d - H x) * inv_wbar; objective pieces (per band blocks, blockIdx.y = band)
+template <typename T>
+__global__ void k_residual(int64_t npix, const T *__restrict__ dirty, const T *__restrict__ hx,
+                           const T *__restrict__ x, double inv_wbar, T *__restrict__ ir, double *__restrict__ sc,
+                           double *__restrict__ bb) {
+    const int b = blockIdx.y;
+    double xhx = 0, xd = 0, rr = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = b * npix + p;
+        const double d = (double)dirty[e] * inv_wbar, h = (double)hx[e] * inv_wbar, xv = (double)x[e];
+        const T r = (T)(d - h);
+        ir[e] = r;
+        xhx += xv * h;
+        xd += xv * d;
+        rr += (double)r * (double)r;
+    }
+    block_sum_atomic(xhx, &sc[S_XHX]);
+    block_sum_atomic(xd, &sc[S_XD]);
+    block_sum_atomic(rr, &bb[b]);
+}
+
+// CG start: delta = 0, r = p = IR, RR[0] = BB
+template <typename T>
+__global__ void k_cg_init(int64_t n, const T *__restrict__ ir, T *__restrict__ delta, T *__restrict__ r,
+                          T *__restrict__ p) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const T v = ir[e];
+    delta[e] = 0;
+    r[e] = v;
+    p[e] = v;
+}
+
+__device__ __forceinline__ bool cg_active(double rr, double bb, double tol2) { return rr > 0.0 && rr > tol2 * bb; }
+
+// Ap = crop(conv) + sigma p, pap[b] += p . Ap
+template <typename T>
+__global__ void k_cg_ap(int nx, int ny, const T *__restrict__ big, const T *__restrict__ p, T sigma,
+                        T *__restrict__ ap, double *__restrict__ pap) {
+    const int b = blockIdx.y;
+    const int64_t npix = (int64_t)nx * ny;
+    double acc = 0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npix; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / ny, j = q - i * ny;
+        const int64_t e = b * npix + q;
+        const T v = big[((int64_t)b * 2 * nx + i) * 2 * ny + j] + sigma * p[e];
+        ap[e] = v;
+        acc += (double)p[e] * (double)v;
+    }
+    block_sum_atomic(acc, &pap[b]);
+}
+
+// delta += alpha p; r -= alpha Ap; rr_next[b] += r . r
+template <typename T>
+__global__ void k_cg_update(int64_t npix, const T *__restrict__ p, const T *__restrict__ ap,
+                            const double *__restrict__ rr, const double *__restrict__ pap,
+                            const double *__restrict__ bb, double tol2, T *__restrict__ delta, T *__restrict__ r,
+                            double *__restrict__ rr_next) {
+    const int b = blockIdx.y;
+    const bool act = cg_active(rr[b], bb[b], tol2) && pap[b] > 0.0;
+    const T alpha = act ? (T)(rr[b] / pap[b]) : (T)0;
+    double acc = 0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npix; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = b * npix + q;
+        delta[e] += alpha * p[e];
+        const T rv = r[e] - alpha * ap[e];
+        r[e] = rv;
+        acc += (double)rv * (double)rv;
+    }
+    block_sum_atomic(acc, &rr_next[b]);
+}
+
+// p = r + beta p, beta = rr_next / rr (0 once converged), written padded for the next U p
+template <typename T>
+__global__ void k_cg_dir(int nx, int ny, const T *__restrict__ r, const double *__restrict__ rr,
+                         const double *__restrict__ rr_next, const double *__restrict__ bb, double tol2,
+                         T *__restrict__ p, T *__restrict__ padded) {
+    const int b = blockIdx.y;
+    const int64_t NX = 2 * nx, NY = 2 * ny;
+    const bool act = cg_active(rr[b], bb[b], tol2);
+    const T beta = act ? (T)(rr_next[b] / rr[b]) : (T)0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < NX * NY; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / NY, j = q - i * NY;
+        T v = 0;
+        if (i < nx && j < ny) {
+            const int64_t e = ((int64_t)b * nx + i) * ny + j;
+            v = r[e] + beta * p[e];
+            p[e] = v;
+        }
+        padded[(int64_t)b * NX * NY + q] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_axpy_clamp(int64_t n, const T *__restrict__ x, const T *__restrict__ d, T gamma,
+                             T *__restrict__ xbar, T *__restrict__ xpd) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const T v = x[e] + gamma * d[e];
+    xbar[e] = v;
+    xpd[e] = v > 0 ? v : 0;
+}
+
+// One Condat-Vu iteration with Psi = Dirac (one thread per pixel, all bands):
+//   x~ = max(0, x - tau (grad + Psi v)),  grad = (conv + sigma (x - xbar)) / gamma
+//   v~ = v + Psi^dagger (2 x~ - x);  v = v~ min(1, lam / ||v~||_bands);  x = x~
+template <typename T>
+__global__ void k_pd_dirac(int nx, int ny, int nband, const T *__restrict__ big, const T *__restrict__ xbar,
+                           T sigma, T gamma, T lam, const double *__restrict__ sc, double inv_wbar,
+                           double unorm_fixed, T *__restrict__ x, T *__restrict__ v) {
+    const int64_t npix = (int64_t)nx * ny;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= npix) return;
+    // ||U|| = max |Re S| / wbar + sigma unless given (sc[S_UNORM] holds max |Re S|)
+    const double unorm = unorm_fixed > 0 ? unorm_fixed : sc[S_UNORM] * inv_wbar + (double)sigma;
+    const T tau = (T)(0.98 / (0.5 * unorm / (double)gamma + 1.0));
+    const int64_t i = q / ny, j = q - i * ny;
+    T xt[32], vt[32];
+    T nrm2 = 0;
+    for (int b = 0; b < nband; ++b) {
+        const int64_t e = b * npix + q;
+        const T xv = x[e];
+        const T grad = (big[((int64_t)b * 2 * nx + i) * 2 * ny + j] + sigma * (xv - xbar[e])) / gamma;
+        T xn = xv - tau * (grad + v[e]);
+        xn = xn > 0 ? xn : 0;
+        xt[b] = xn;
+        const T vn = v[e] + (2 * xn - xv);
+        vt[b] = vn;
+        nrm2 += vn * vn;
+    }
+    const T nrm = sqrt(nrm2);
+    const T s = nrm > lam ? lam / nrm : (T)1;
+    for (int b = 0; b < nband; ++b) {
+        const int64_t e = b * npix + q;
+        x[e] = xt[b];
+        v[e] = vt[b] * s;
+    }
+}
+
+// final statistics: ||x1 - x0||^2, ||x1||^2, sum_p ||x0[:, p]||_2 ; copy x1 to the output
+template <typename T>
+__global__ void k_finish(int64_t npix, int nband, const T *__restrict__ x1, T *__restrict__ x0_out,
+                         double *__restrict__ sc) {
+    double dx2 = 0, x2 = 0, l21 = 0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npix; q += (int64_t)gridDim.x * blockDim.x) {
+        double g2 = 0;
+        for (int b = 0; b < nband; ++b) {
+            const int64_t e = b * npix + q;
+            const double a = (double)x0_out[e], c = (double)x1[e];
+            dx2 += (c - a) * (c - a);
+            x2 += c * c;
+            g2 += a * a;
+            x0_out[e] = x1[e];
+        }
+        l21 += sqrt(g2);
+    }
+    block_sum_atomic(dx2, &sc[S_DX2]);
+    block_sum_atomic(x2, &sc[S_X2]);
+    block_sum_atomic(l21, &sc[S_L21]);
+}
+
+// ------------------------------------------------------------------ spectrum cache
+template <typename T>
+static cx_t<T> *psf_spectrum(Ctx &ctx, int nx, int ny, int nband, const T *psf, cudaStream_t st) {
+    const int prec = sizeof(T) == 8 ? PFB_F64 : PFB_F32;
+    for (auto &s : ctx.spectra)
+        if (s.psf == psf && s.nx == nx && s.ny == ny && s.nband == nband && s.prec == prec)
+            return (cx_t<T> *)s.spec;
+    const int64_t NX = 2 * nx, NY = 2 * ny, NH = NY / 2 + 1;
+    PsfSpec s;
+    s.psf = psf; s.nx = nx; s.ny = ny; s.nband = nband; s.prec = prec;
+    s.bytes = (size_t)nband * NX * NH * sizeof(cx_t<T>);
+    s.spec = ctx.dalloc(s.bytes);
+    T *shifted = (T *)ctx.scratch("img_pad", (size_t)nband * NX * NY * sizeof(T));
+    const int64_t n = nband * NX * NY;
+    k_ifftshift<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nx, ny, nband, psf, shifted);
+    check_launch("ifftshift");
+    cufftHandle h = ctx.fft((int)NX, (int)NY, nband, RFft<T>::r2c);
+    PFB_CUFFT(cufftSetStream(h, st));
+    PFB_CUFFT(RFft<T>::fwd(h, shifted, (cx_t<T> *)s.spec));
+    if (ctx.spectra.size() >= 4) {
+        ctx.dfree(ctx.spectra.front().spec, ctx.spectra.front().bytes);
+        ctx.spectra.erase(ctx.spectra.begin());
+    }
+    ctx.spectra.push_back(s);
+    return (cx_t<T> *)s.spec;
+}
+
+// padded real [nband][2nx][2ny] -> (conv with S) -> padded real, in place
+template <typename T>
+static void conv_padded(Ctx &ctx, int nx, int ny, int nband, T *padded, const cx_t<T> *S, T scale, bool sym,
+                        cudaStream_t st) {
+    const int64_t NX = 2 * nx, NY = 2 * ny, NH = NY / 2 + 1;
+    cx_t<T> *X = (cx_t<T> *)ctx.scratch("img_spec", (size_t)nband * NX * NH * sizeof(cx_t<T>));
+    cufftHandle hf = ctx.fft((int)NX, (int)NY, nband, RFft<T>::r2c);
+    PFB_CUFFT(cufftSetStream(hf, st));
+    PFB_CUFFT(RFft<T>::fwd(hf, padded, X));
+    const int64_t ns = nband * NX * NH;
+    k_spec_mul<T><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(ns, S, scale, sym ? 1 : 0, X);
+    check_launch("spec_mul");
+    cufftHandle hi = ctx.fft((int)NX, (int)NY, nband, RFft<T>::c2r);
+    PFB_CUFFT(cufftSetStream(hi, st));
+    PFB_CUFFT(RFft<T>::inv(hi, X, padded));
+}
+
+template <typename T>
+void op_psf_conv(Ctx &ctx, int nx, int ny, int nband, const T *psf, const T *x, T *y, cudaStream_t st) {
+    const int64_t NX = 2 * nx, NY = 2 * ny;
+    cx_t<T> *S = psf_spectrum<T>(ctx, nx, ny, nband, psf, st);
+    T *padded = (T *)ctx.scratch("img_pad", (size_t)nband * NX * NY * sizeof(T));
+    const int64_t nb = nband * NX * NY;
+    k_pad<T><<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(nx, ny, nband, x, (const T *)nullptr, padded);
+    check_launch("pad");
+    conv_padded<T>(ctx, nx, ny, nband, padded, S, (T)(1.0 / (double)(NX * NY)), false, st);
+    const int64_t n = (int64_t)nband * nx * ny;
+    k_crop<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nx, ny, nband, padded, y);
+    check_launch("crop");
+}
+
+static unsigned rblocks(int64_t n, int cap) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, cap)); }
+
+template <typename T>
+void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const T *dirty, const T *psf,
+             const double *wsum_h, T *x, T *dual, double *stats_h, cudaStream_t st) {
+    const int nx = p.nx, ny = p.ny, nb = p.nband;
+    const int64_t npix = (int64_t)nx * ny, n = npix * nb;
+    const int64_t NX = 2 * nx, NY = 2 * ny, nbig = nb * NX * NY;
+    double wbar = 0;
+    for (int b = 0; b < nb; ++b) wbar += wsum_h[b];
+    wbar /= nb;
+    PFB_REQUIRE(wbar > 0, "weight sums must be positive");
+    const double inv_wbar = 1.0 / wbar;
+    const int iters = std::max(0, prm.cg_iters);
+    const double tol2 = prm.cg_tol > 0 ? prm.cg_tol * prm.cg_tol : 0.0;
+
+    // scratch
+    const size_t img = (size_t)n * sizeof(T);
+    T *hx = (T *)ctx.scratch("st_hx", img);
+    T *ir = (T *)ctx.scratch("st_ir", img);
+    T *delta = (T *)ctx.scratch("st_delta", img);
+    T *r = (T *)ctx.scratch("st_r", img);
+    T *pp = (T *)ctx.scratch("st_p", img);
+    T *ap = (T *)ctx.scratch("st_ap", img);
+    T *xbar = (T *)ctx.scratch("st_xbar", img);
+    T *xk1 = (T *)ctx.scratch("st_x1", img);
+    const size_t nsc = S_COUNT + nb + (size_t)(iters + 1) * nb + (size_t)iters * nb;
+    double *sc = (double *)ctx.scratch("st_scal", nsc * sizeof(double));
+    double *bb = sc + S_COUNT, *RR = bb + nb, *PAP = RR + (size_t)(iters + 1) * nb;
+    PFB_CUDA(cudaMemsetAsync(sc, 0, nsc * sizeof(double), st));
+
+    // 1. one exact Hessian application: H x_k = R^dagger W R x_k (Eq. 3)
+    {
+        cx_t<T> *vis = (cx_t<T> *)ctx.scratch("st_vis", (size_t)p.nrow * p.nchan * sizeof(cx_t<T>));
+        op_degrid<T>(ctx, p, x, vis, st);
+        op_grid<T>(ctx, p, vis, wgt, false, hx, st);
+    }
+    // 2. IR = (I^d - H x_k) / wbar
+    {
+        dim3 gr(rblocks(npix, 2 * ctx.num_sms), nb);
+        k_residual<T><<<gr, 256, 0, st>>>(npix, dirty, hx, x, inv_wbar, ir, sc, bb);
+        check_launch("residual");
+    }
+    // 3. CG for U delta = IR (per band)
+    cx_t<T> *S = psf_spectrum<T>(ctx, nx, ny, nb, psf, st);
+    T *padded = (T *)ctx.scratch("img_pad", (size_t)nbig * sizeof(T));
+    const T conv_scale = (T)(inv_wbar / (double)(NX * NY));
+    const T sigma = (T)prm.sigma;
+    k_cg_init<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ir, delta, r, pp);
+    check_launch("cg_init");
+    PFB_CUDA(cudaMemcpyAsync(RR, bb, nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    k_pad<T><<<(unsigned)((nbig + 255) / 256), 256, 0, st>>>(nx, ny, nb, pp, (const T *)nullptr, padded);
+    check_launch("cg_pad");
+    for (int it = 0; it < iters; ++it) {
+        double *rr = RR + (size_t)it * nb, *rrn = RR + (size_t)(it + 1) * nb, *pap = PAP + (size_t)it * nb;
+        conv_padded<T>(ctx, nx, ny, nb, padded, S, conv_scale, true, st);
+        dim3 g1(rblocks(npix, 2 * ctx.num_sms), nb);
+        k_cg_ap<T><<<g1, 256, 0, st>>>(nx, ny, padded, pp, sigma, ap, pap);
+        check_launch("cg_ap");
+        k_cg_update<T><<<g1, 256, 0, st>>>(npix, pp, ap, rr, pap, bb, tol2, delta, r, rrn);
+        check_launch("cg_update");
+        dim3 gp(rblocks(NX * NY, 4 * ctx.num_sms), nb);
+        k_cg_dir<T><<<gp, 256, 0, st>>>(nx, ny, r, rr, rrn, bb, tol2, pp, padded);
+        check_launch("cg_dir");
+    }
+    // 4. x_{k+1/2} = x_k + gamma delta; primal start max(x_{k+1/2}, 0)
+    k_axpy_clamp<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, delta, (T)prm.gamma, xbar, xk1);
+    check_launch("axpy");
+    // 5. prox (Eq. 7) by Condat-Vu
+    if (prm.unorm <= 0) {
+        const int64_t ns = nb * NX * (NY / 2 + 1);
+        k_absmax_re<T><<<rblocks(ns, 4 * ctx.num_sms), 256, 0, st>>>(ns, S, (unsigned long long *)&sc[S_UNORM]);
+        check_launch("absmax");
+    }
+    const double unorm_fixed = prm.unorm > 0 ? prm.unorm : -1.0;
+    for (int it = 0; it < prm.pd_iters; ++it) {
+        k_pad<T><<<(unsigned)((nbig + 255) / 256), 256, 0, st>>>(nx, ny, nb, xk1, xbar, padded);
+        check_launch("pd_pad");
+        conv_padded<T>(ctx, nx, ny, nb, padded, S, conv_scale, true, st);
+        k_pd_dirac<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
+            nx, ny, nb, padded, xbar, sigma, (T)prm.gamma, (T)prm.lambda, sc, inv_wbar, unorm_fixed, xk1, dual);
+        check_launch("pd_dirac");
+    }
+    // 6. statistics and output
+    k_finish<T><<<rblocks(npix, 2 * ctx.num_sms), 256, 0, st>>>(npix, nb, xk1, x, sc);
+    check_launch("finish");
+    if (stats_h) {
+        std::vector<double> h(nsc);
+        PFB_CUDA(cudaMemcpyAsync(h.data(), sc, nsc * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PFB_CUDA(cudaStreamSynchronize(st));
+        const double fx = 0.5 * h[S_XHX] - h[S_XD];
+        stats_h[0] = fx + prm.lambda * h[S_L21];
+        stats_h[1] = h[S_X2] > 0 ? std::sqrt(h[S_DX2] / h[S_X2]) : 0.0;
+        double cgr = 0;
+        for (int b = 0; b < nb; ++b) {
+            const double rrl = h[S_COUNT + nb + (size_t)iters * nb + b];
+            const double bbv = h[S_COUNT + b];
+            cgr = std::max(cgr, bbv > 0 ? std::sqrt(rrl / bbv) : 0.0);
+        }
+        stats_h[2] = cgr;
+    }
+}
+
+template void op_psf_conv<float>(Ctx &, int, int, int, const float *, const float *, float *, cudaStream_t);
+template void op_psf_conv<double>(Ctx &, int, int, int, const double *, const double *, double *, cudaStream_t);
+template void op_step<float>(Ctx &, const Plan &, const pfb_params &, const float *, const float *, const float *,
+                             const double *, float *, float *, double *, cudaStream_t);
+template void op_step<double>(Ctx &, const Plan &, const pfb_params &, const double *, const double *,
+                              const double *, const double *, double *, double *, double *, cudaStream_t);
+
+}  // namespace pfb

@@ -1,0 +1,446 @@
+// R (degridding) and R^dagger Sigma^-1 (gridding) by w-stacking (Section 2,
+// Eqs. 1 and 3).  See plan.cu for the factorisation that these kernels apply:
+//
+//   R x       = exp(-2 pi i w t_c) sum_k phi_w sum_{g} phi_u phi_v FFT2[E_k x][g]
+//   R^dagger y = Re corr . sum_k exp(+2 pi i w_k t) IFFT2[S_k y]   (cropped)
+//
+// with E_k x = x corr exp(-2 pi i w_k t) zero padded to N_u x N_v, corr =
+// 1/(n psihat_u psihat_v psihat_w), S_k the adjoint of the kernel gather on
+// plane k, and rows with w < 0 mapped to (-u,-v,-w) with V -> conj V (exact for
+// a real image).  Planes are processed in blocks that fit the HBM budget; with
+// GB300's memory a whole band's stack is usually one block.
+#include "ctx.cuh"
+
+#include <algorithm>
+
+namespace pfb {
+
+// ------------------------------------------------------------------ pre-pass (R)
+// Writes x corr exp(-2 pi i w_k t) for planes [k_lo, k_hi) at the pixel's grid
+// position (i - nx/2 mod N_u, j - ny/2 mod N_v); the rest of each plane was zeroed.
+template <typename T>
+__global__ void k_prepass(int nx, int ny, const T *__restrict__ x, const T *__restrict__ corr,
+                          const double *__restrict__ tp, BandGeom g, int k_lo, int k_hi, double dw,
+                          cx_t<T> *__restrict__ planes) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= (int64_t)nx * ny) return;
+    const int i = (int)(p / ny), j = (int)(p - (int64_t)i * ny);
+    const T c = x[p] * corr[p];
+    int gu = i - nx / 2, gv = j - ny / 2;
+    gu += gu < 0 ? g.Nu : 0;
+    gv += gv < 0 ? g.Nv : 0;
+    const int64_t pos = (int64_t)gu * g.Nv + gv;
+    const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
+    const double t = tp[p];
+    for (int k = k_lo; k < k_hi; ++k) {
+        T cs = 1, sn = 0;
+        if (g.Ww > 1) cis_turns<T>((g.w0 + k * dw) * t, &cs, &sn);
+        cx_t<T> v;
+        v.x = c * cs;
+        v.y = -c * sn;
+        planes[(int64_t)(k - k_lo) * plane_sz + pos] = v;
+    }
+}
+
+// ------------------------------------------------------------------ gather (R)
+// One thread per home item of band g.band: interpolate the W_w planes x W x W taps
+// of the visibility, apply exp(-2 pi i w t_c) and the Hermitian flip.  Items whose
+// first plane lies below k_lo add to the partial sum of an earlier block.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ items, int64_t n_items,
+                                                const double *__restrict__ uvw, const double *__restrict__ scale,
+                                                BandGeom g, int k_lo, int k_hi,
+                                                const cx_t<T> *__restrict__ planes, cx_t<T> *__restrict__ vis) {
+    const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n_items;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t code = items[it];
+        if (code >> 30) continue;   // spill copy of a visibility homed elsewhere
+        const int64_t v = code;
+        const int64_t row = v / g.nchan;
+        const int ch = (int)(v - row * g.nchan);
+        const VisCoord c = vis_coord(uvw, row, scale[ch], g);
+        if (c.k0 >= k_hi || c.k0 + g.Ww <= k_lo) continue;
+        T ku[MAX_W], kv[MAX_W], kw[MAX_W];
+        es_taps<T>(c.ou, g.W, g, ku);
+        es_taps<T>(c.ov, g.W, g, kv);
+        if (g.Ww > 1) es_taps<T>(c.ow, g.Ww, g, kw);
+        else kw[0] = 1;
+        T ar = 0, ai = 0;
+        for (int cw = 0; cw < g.Ww; ++cw) {
+            const int k = c.k0 + cw;
+            if (k < k_lo || k >= k_hi) continue;
+            const cx_t<T> *pl = planes + (int64_t)(k - k_lo) * plane_sz;
+            T pr = 0, pi = 0;
+            for (int a = 0; a < g.W; ++a) {
+                int gu = c.gu0 + a;
+                gu -= gu >= g.Nu ? g.Nu : 0;
+                const cx_t<T> *prow = pl + (int64_t)gu * g.Nv;
+                T rr = 0, ri = 0;
+                if (c.gv0 + g.W <= g.Nv) {
+                    for (int b = 0; b < g.W; ++b) {
+                        const cx_t<T> gv = prow[c.gv0 + b];
+                        rr += kv[b] * gv.x;
+                        ri += kv[b] * gv.y;
+                    }
+                } else {
+                    for (int b = 0; b < g.W; ++b) {
+                        int gvi = c.gv0 + b;
+                        gvi -= gvi >= g.Nv ? g.Nv : 0;
+                        const cx_t<T> gv = prow[gvi];
+                        rr += kv[b] * gv.x;
+                        ri += kv[b] * gv.y;
+                    }
+                }
+                pr += ku[a] * rr;
+                pi += ku[a] * ri;
+            }
+            ar += kw[cw] * pr;
+            ai += kw[cw] * pi;
+        }
+        // exp(-2 pi i w t_c)
+        T cs = 1, sn = 0;
+        if (g.tc != 0.0) cis_turns<T>(c.wl * g.tc, &cs, &sn);
+        T vr = ar * cs + ai * sn;
+        T vi = ai * cs - ar * sn;
+        if (c.flip) vi = -vi;
+        cx_t<T> out;
+        if (c.k0 < k_lo) {
+            out = vis[v];
+            out.x += vr;
+            out.y += vi;
+        } else {
+            out.x = vr;
+            out.y = vi;
+        }
+        vis[v] = out;
+    }
+}
+
+// ------------------------------------------------------------------ gridding (R^dagger)
+template <typename T>
+__device__ __forceinline__ void smem_add(cx_t<T> *cell, T re, T im) {
+    atomicAdd(&cell->x, re);
+    atomicAdd(&cell->y, im);
+}
+
+template <typename T>
+__device__ __forceinline__ void global_add(cx_t<T> *cell, cx_t<T> v);
+template <>
+__device__ __forceinline__ void global_add<float>(float2 *cell, float2 v) {
+    atomicAdd(cell, v);   // vector reduction (sm_90+)
+}
+template <>
+__device__ __forceinline__ void global_add<double>(double2 *cell, double2 v) {
+    atomicAdd(&cell->x, v.x);
+    atomicAdd(&cell->y, v.y);
+}
+
+// One CTA per work item (a tile of TILE x TILE cells of band g.band, or a chunk
+// of a heavy tile's items).  The CTA owns its tile's cells: it scatters every item
+// listed for the tile (home items and spill copies of neighbours' items) into a
+// ring of W_w + q - 1 shared-memory planes, sweeping the w buckets in order; after
+// bucket kq the planes [kq q, kq q + q) are complete and are flushed to HBM with
+// coalesced stores (plain mode) or vector reductions (heavy-tile chunks).
+template <typename T>
+__global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__ work,
+                                                    const uint32_t *__restrict__ items,
+                                                    const int64_t *__restrict__ off,
+                                                    const double *__restrict__ uvw,
+                                                    const double *__restrict__ scale,
+                                                    const cx_t<T> *__restrict__ vis, const T *__restrict__ wgt,
+                                                    int unit_vis, BandGeom g, int k_lo, int k_hi,
+                                                    cx_t<T> *__restrict__ planes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx_t<T> *ring = reinterpret_cast<cx_t<T> *>(smem_raw);
+    const int R = g.Ww + g.q - 1;
+    const int cells = TILE * TILE;
+    const WorkItem wi = work[blockIdx.x];
+    const int tu = wi.tile / g.ntv, tv = wi.tile - tu * g.ntv;
+    const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
+    for (int e = threadIdx.x; e < R * cells; e += blockDim.x) ring[e] = cx_t<T>{0, 0};
+
+    const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
+    int kq_first, kq_last;
+    if (!wi.atomic_mode) {
+        kq_first = max(0, (k_lo - g.Ww + 1) / g.q);
+        kq_last = (k_hi - 1) / g.q;
+    } else {
+        if (wi.end <= wi.begin) return;
+        // buckets holding the first and last item of the chunk
+        int lo = 0, hi = g.nkq - 1;
+        while (lo < hi) {   // last bucket whose start <= begin
+            int mid = (lo + hi + 1) >> 1;
+            if (off[kbase + mid] <= wi.begin) lo = mid; else hi = mid - 1;
+        }
+        kq_first = lo;
+        lo = kq_first; hi = g.nkq - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (off[kbase + mid] <= wi.end - 1) lo = mid; else hi = mid - 1;
+        }
+        kq_last = lo + (g.Ww - 1 + g.q - 1) / g.q;   // trailing planes of the last bucket
+        kq_first = max(kq_first, max(0, (k_lo - g.Ww + 1) / g.q));
+        kq_last = min(kq_last, (k_hi - 1) / g.q);
+    }
+    __syncthreads();
+    for (int kq = kq_first; kq <= kq_last; ++kq) {
+        int64_t s = kq < g.nkq ? off[kbase + kq] : wi.end;
+        int64_t e = kq < g.nkq ? off[kbase + kq + 1] : wi.end;
+        s = max(s, (int64_t)wi.begin);
+        e = min(e, (int64_t)wi.end);
+        for (int64_t it = s + threadIdx.x; it < e; it += blockDim.x) {
+            const uint32_t code = items[it];
+            const int64_t v = code & VIS_MASK;
+            const int du = (code >> 30) & 1, dv = code >> 31;
+            const int64_t row = v / g.nchan;
+            const int ch = (int)(v - row * g.nchan);
+            const VisCoord c = vis_coord(uvw, row, scale[ch], g);
+            if (c.k0 >= k_hi || c.k0 + g.Ww <= k_lo) continue;
+            T yr, yi;
+            if (unit_vis) { yr = 1; yi = 0; }
+            else { const cx_t<T> y = vis[v]; yr = y.x; yi = y.y; }
+            if (wgt) { const T w = wgt[v]; yr *= w; yi *= w; }
+            if (c.flip) yi = -yi;
+            // multiply by exp(+2 pi i w t_c) (adjoint of the degridding phase)
+            if (g.tc != 0.0) {
+                T cs, sn;
+                cis_turns<T>(c.wl * g.tc, &cs, &sn);
+                const T r0 = yr * cs - yi * sn;
+                yi = yr * sn + yi * cs;
+                yr = r0;
+            }
+            T ku[MAX_W], kv[MAX_W], kw[MAX_W];
+            es_taps<T>(c.ou, g.W, g, ku);
+            es_taps<T>(c.ov, g.W, g, kv);
+            if (g.Ww > 1) es_taps<T>(c.ow, g.Ww, g, kw);
+            else kw[0] = 1;
+            const int lu = c.gu0 - (c.gu0 / TILE) * TILE - du * TILE;
+            const int lv = c.gv0 - (c.gv0 / TILE) * TILE - dv * TILE;
+            const int a0 = max(0, -lu), a1 = min(g.W, TILE - lu);
+            const int b0 = max(0, -lv), b1 = min(g.W, TILE - lv);
+            for (int cw = 0; cw < g.Ww; ++cw) {
+                const int k = c.k0 + cw;
+                if (k < k_lo || k >= k_hi) continue;
+                cx_t<T> *slot = ring + (k % R) * cells;
+                const T fr = kw[cw] * yr, fi = kw[cw] * yi;
+                for (int a = a0; a < a1; ++a) {
+                    const T gr = ku[a] * fr, gi = ku[a] * fi;
+                    cx_t<T> *srow = slot + (lu + a) * TILE + lv;
+                    for (int b = b0; b < b1; ++b) smem_add<T>(srow + b, kv[b] * gr, kv[b] * gi);
+                }
+            }
+        }
+        __syncthreads();
+        // planes [kq q, kq q + q) are complete
+        const int p0 = max(kq * g.q, k_lo), p1 = min(kq * g.q + g.q, k_hi);
+        for (int k = p0; k < p1; ++k) {
+            cx_t<T> *slot = ring + (k % R) * cells;
+            cx_t<T> *dst = planes + (int64_t)(k - k_lo) * plane_sz + (int64_t)(tu * TILE) * g.Nv + tv * TILE;
+            for (int e2 = threadIdx.x; e2 < cells; e2 += blockDim.x) {
+                const int r = e2 / TILE, cc = e2 - r * TILE;
+                const cx_t<T> val = slot[e2];
+                if (wi.atomic_mode) {
+                    if (val.x != 0 || val.y != 0) global_add<T>(dst + (int64_t)r * g.Nv + cc, val);
+                } else {
+                    dst[(int64_t)r * g.Nv + cc] = val;
+                }
+                slot[e2] = cx_t<T>{0, 0};
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Zero the cells of heavy tiles (filled by reductions) in planes [0, nplanes).
+template <typename T>
+__global__ void k_zero_tiles(const int *__restrict__ tiles, int ntiles, int ntv, int Nv, int64_t plane_sz,
+                             int nplanes, cx_t<T> *__restrict__ planes) {
+    const int t = tiles[blockIdx.x % ntiles];
+    const int k = blockIdx.x / ntiles;
+    if (k >= nplanes) return;
+    const int tu = t / ntv, tv = t - tu * ntv;
+    cx_t<T> *dst = planes + (int64_t)k * plane_sz + (int64_t)(tu * TILE) * Nv + tv * TILE;
+    for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+        const int r = e / TILE, c = e - r * TILE;
+        dst[(int64_t)r * Nv + c] = cx_t<T>{0, 0};
+    }
+}
+
+// ------------------------------------------------------------------ post-pass (R^dagger)
+// image[p] (+)= corr[p] Re sum_{k in block} exp(+2 pi i w_k t_p) H_k[pos(p)].
+template <typename T>
+__global__ void k_postpass(int nx, int ny, const T *__restrict__ corr, const double *__restrict__ tp, BandGeom g,
+                           int k_lo, int k_hi, double dw, const cx_t<T> *__restrict__ planes, int accumulate,
+                           T *__restrict__ image) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= (int64_t)nx * ny) return;
+    const int i = (int)(p / ny), j = (int)(p - (int64_t)i * ny);
+    int gu = i - nx / 2, gv = j - ny / 2;
+    gu += gu < 0 ? g.Nu : 0;
+    gv += gv < 0 ? g.Nv : 0;
+    const int64_t pos = (int64_t)gu * g.Nv + gv;
+    const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
+    const double t = tp[p];
+    T acc = 0;
+    for (int k = k_lo; k < k_hi; ++k) {
+        const cx_t<T> h = planes[(int64_t)(k - k_lo) * plane_sz + pos];
+        if (g.Ww > 1) {
+            T cs, sn;
+            cis_turns<T>((g.w0 + k * dw) * t, &cs, &sn);
+            acc += h.x * cs - h.y * sn;
+        } else {
+            acc += h.x;
+        }
+    }
+    acc *= corr[p];
+    image[p] = accumulate ? image[p] + acc : acc;
+}
+
+// ------------------------------------------------------------------ weight sums
+template <typename T>
+__global__ void k_wsum(const T *__restrict__ wgt, int64_t nrow, int nchan, const int *__restrict__ band,
+                       double *__restrict__ out) {
+    // one thread per (row, chan); block-level reduction per band via shared atomics
+    extern __shared__ double sacc[];
+    const int nb = blockDim.y;   // number of bands (<= 32), passed through blockDim.y == 1 trick avoided
+    (void)nb;
+    for (int b = threadIdx.x; b < 32; b += blockDim.x) sacc[b] = 0.0;
+    __syncthreads();
+    const int64_t n = nrow * nchan;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % nchan);
+        atomicAdd(&sacc[band[ch]], wgt ? (double)wgt[i] : 1.0);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 32; b += blockDim.x)
+        if (sacc[b] != 0.0) atomicAdd(&out[b], sacc[b]);
+}
+
+// ------------------------------------------------------------------ cuFFT helpers
+template <typename T> struct FftT;
+template <> struct FftT<float> {
+    static constexpr cufftType c2c = CUFFT_C2C;
+    static cufftResult exec(cufftHandle h, float2 *d, int dir) {
+        return cufftExecC2C(h, (cufftComplex *)d, (cufftComplex *)d, dir);
+    }
+};
+template <> struct FftT<double> {
+    static constexpr cufftType c2c = CUFFT_Z2Z;
+    static cufftResult exec(cufftHandle h, double2 *d, int dir) {
+        return cufftExecZ2Z(h, (cufftDoubleComplex *)d, (cufftDoubleComplex *)d, dir);
+    }
+};
+
+template <typename T>
+static void fft_planes(Ctx &ctx, cx_t<T> *data, int nplanes, int Nu, int Nv, int dir, cudaStream_t st) {
+    const int maxb = 8;
+    const int64_t plane_sz = (int64_t)Nu * Nv;
+    for (int k = 0; k < nplanes; k += maxb) {
+        const int b = std::min(maxb, nplanes - k);
+        cufftHandle h = ctx.fft(Nu, Nv, b, FftT<T>::c2c);
+        PFB_CUFFT(cufftSetStream(h, st));
+        PFB_CUFFT(FftT<T>::exec(h, data + k * plane_sz, dir));
+    }
+}
+
+static int plane_block(Ctx &ctx, const Plan &p, size_t cxs, size_t reserve) {
+    const size_t plane_bytes = (size_t)p.Nu * p.Nv * cxs;
+    const size_t have = ctx.scratch_bytes("planes");
+    const size_t avail = ctx.available() + have;
+    size_t room = avail > reserve ? avail - reserve : 0;
+    int blk = (int)std::min<size_t>((size_t)p.Pmax, room / plane_bytes);
+    if (blk < 1) throw Error(PFB_ERR_OOM, "HBM budget too small for one w-plane of " +
+                                              std::to_string(p.Nu) + "x" + std::to_string(p.Nv));
+    return blk;
+}
+
+static unsigned grid_blocks(int64_t n, int threads, int cap) {
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+// ------------------------------------------------------------------ operators
+template <typename T>
+void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st) {
+    const size_t cxs = sizeof(cx_t<T>);
+    // room for cuFFT work areas is taken from the same budget
+    const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
+    cx_t<T> *planes = (cx_t<T> *)ctx.scratch("planes", (size_t)blk * p.Nu * p.Nv * cxs);
+    const int64_t npix = (int64_t)p.nx * p.ny;
+    for (int b = 0; b < p.nband; ++b) {
+        const BandGeom g = p.geom(b);
+        const int64_t i0 = p.band_items_begin[b], i1 = p.band_items_end[b];
+        for (int k_lo = 0; k_lo < g.P; k_lo += blk) {
+            const int k_hi = std::min(g.P, k_lo + blk);
+            const int nk = k_hi - k_lo;
+            PFB_CUDA(cudaMemsetAsync(planes, 0, (size_t)nk * p.Nu * p.Nv * cxs, st));
+            k_prepass<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
+                p.nx, p.ny, image + b * npix, (const T *)p.d_corr, p.d_tp, g, k_lo, k_hi, p.dw, planes);
+            check_launch("prepass");
+            fft_planes<T>(ctx, planes, nk, p.Nu, p.Nv, CUFFT_FORWARD, st);
+            if (i1 > i0) {
+                k_gather<T><<<grid_blocks(i1 - i0, 256, 64 * ctx.num_sms), 256, 0, st>>>(
+                    p.d_items + i0, i1 - i0, (const double *)p.uvw, p.d_scale, g, k_lo, k_hi, planes, vis);
+                check_launch("gather");
+            }
+        }
+    }
+}
+
+template <typename T>
+void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool unit_vis, T *image,
+             cudaStream_t st) {
+    const size_t cxs = sizeof(cx_t<T>);
+    const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
+    cx_t<T> *planes = (cx_t<T> *)ctx.scratch("planes", (size_t)blk * p.Nu * p.Nv * cxs);
+    const int64_t npix = (int64_t)p.nx * p.ny;
+    const int R = p.Ww + p.q - 1;
+    const size_t smem = (size_t)R * TILE * TILE * cxs;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(T) == 8]) {
+        PFB_CUDA(cudaFuncSetAttribute(k_grid_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set[sizeof(T) == 8] = true;
+    }
+    for (int b = 0; b < p.nband; ++b) {
+        const BandGeom g = p.geom(b);
+        const int64_t w0 = p.work_begin[b], w1 = p.work_begin[b + 1];
+        const int64_t h0 = p.heavy_begin[b], h1 = p.heavy_begin[b + 1];
+        for (int k_lo = 0; k_lo < g.P; k_lo += blk) {
+            const int k_hi = std::min(g.P, k_lo + blk);
+            const int nk = k_hi - k_lo;
+            if (h1 > h0) {
+                k_zero_tiles<T><<<(unsigned)((h1 - h0) * nk), 256, 0, st>>>(
+                    p.d_heavy + h0, (int)(h1 - h0), p.ntv, p.Nv, (int64_t)p.Nu * p.Nv, nk, planes);
+                check_launch("zero_tiles");
+            }
+            k_grid_tiles<T><<<(unsigned)(w1 - w0), 256, smem, st>>>(p.d_work + w0, p.d_items, p.d_off,
+                                                                     (const double *)p.uvw, p.d_scale, vis, wgt,
+                                                                     unit_vis ? 1 : 0, g, k_lo, k_hi, planes);
+            check_launch("grid_tiles");
+            fft_planes<T>(ctx, planes, nk, p.Nu, p.Nv, CUFFT_INVERSE, st);
+            k_postpass<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
+                p.nx, p.ny, (const T *)p.d_corr, p.d_tp, g, k_lo, k_hi, p.dw, planes, k_lo > 0 ? 1 : 0,
+                image + b * npix);
+            check_launch("postpass");
+        }
+    }
+}
+
+template <typename T>
+void op_wsum(Ctx &ctx, const Plan &p, const T *wgt, double *d_wsum, cudaStream_t st) {
+    PFB_CUDA(cudaMemsetAsync(d_wsum, 0, 32 * sizeof(double), st));
+    const int64_t n = p.nrow * p.nchan;
+    k_wsum<T><<<grid_blocks(n, 256, 8 * ctx.num_sms), 256, 32 * sizeof(double), st>>>(wgt, p.nrow, p.nchan,
+                                                                                       p.d_band, d_wsum);
+    check_launch("wsum");
+}
+
+template void op_degrid<float>(Ctx &, const Plan &, const float *, float2 *, cudaStream_t);
+template void op_degrid<double>(Ctx &, const Plan &, const double *, double2 *, cudaStream_t);
+template void op_grid<float>(Ctx &, const Plan &, const float2 *, const float *, bool, float *, cudaStream_t);
+template void op_grid<double>(Ctx &, const Plan &, const double2 *, const double *, bool, double *, cudaStream_t);
+template void op_wsum<float>(Ctx &, const Plan &, const float *, double *, cudaStream_t);
+template void op_wsum<double>(Ctx &, const Plan &, const double *, double *, cudaStream_t);
+
+}  // namespace pfb

@@ -1,0 +1,264 @@
+"""Python binding of libpfb: the entry points of include/pfb.h, same names, on
+torch tensors.  Argument marshalling only (shapes, dtypes, device pointers,
+the current CUDA stream); every step of the computation runs in libpfb's
+kernels.  Tensors must be contiguous and on the context's device.
+
+Precision follows the dtype: float32 images / complex64 visibilities select
+PFB_F32 (FP64 coordinates and phases inside), float64 / complex128 select PFB_F64.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import threading
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PFB_F32, PFB_F64, PfbError
+
+
+@dataclasses.dataclass
+class Geometry:
+    """Image geometry and accuracy (pfb_geom)."""
+    nx: int
+    ny: int
+    dl: float
+    dm: float
+    nband: int = 1
+    epsilon: float = 1e-5
+    flags: int = 0
+
+    def c(self) -> _lib.pfb_geom:
+        return _lib.pfb_geom(self.nx, self.ny, self.dl, self.dm, 0.0, 0.0, self.epsilon, self.nband, self.flags)
+
+
+@dataclasses.dataclass
+class StepParams:
+    """Parameters of one pfb-clean step (pfb_params)."""
+    gamma: float = 1.0
+    sigma: float = 1e-3
+    lam: float = 1e-4
+    cg_tol: float = 0.0
+    pd_tol: float = 0.0
+    cg_iters: int = 50
+    pd_iters: int = 100
+    nlevel: int = 3
+    basis_mask: int = 1
+    unorm: float = 0.0
+
+    def c(self) -> _lib.pfb_params:
+        return _lib.pfb_params(self.gamma, self.sigma, self.lam, self.cg_tol, self.pd_tol, self.cg_iters,
+                               self.pd_iters, self.nlevel, self.basis_mask, self.unorm)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _prec_real(dtype) -> int:
+    if dtype == torch.float32:
+        return PFB_F32
+    if dtype == torch.float64:
+        return PFB_F64
+    raise TypeError(f"image dtype must be float32 or float64, got {dtype}")
+
+
+def _prec_cx(dtype) -> int:
+    if dtype == torch.complex64:
+        return PFB_F32
+    if dtype == torch.complex128:
+        return PFB_F64
+    raise TypeError(f"visibility dtype must be complex64 or complex128, got {dtype}")
+
+
+_RDT = {PFB_F32: torch.float32, PFB_F64: torch.float64}
+_CDT = {PFB_F32: torch.complex64, PFB_F64: torch.complex128}
+
+
+class Context:
+    """A libpfb context on one CUDA device (plans, scratch, cuFFT handles)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", device)
+        h = ctypes.c_void_p()
+        rc = self.lib.pfb_create(ctypes.byref(h), device, hbm_budget_bytes)
+        if rc != 0:
+            raise PfbError(rc, f"pfb_create(device={device}) failed")
+        self.h = h
+        # Inputs of the plans cached by libpfb, most recent last.  libpfb keys its
+        # plans on device pointers; holding the tensors keeps torch's caching
+        # allocator from handing the same addresses to different data while a plan
+        # that points at them may still be cached (libpfb keeps at most 4 plans).
+        self._keep: list[tuple] = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pfb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, rc: int):
+        if rc != 0:
+            raise PfbError(rc, self.lib.pfb_last_error(self.h).decode())
+
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _data(self, uvw, freq, band_of_chan):
+        for name, t, dt in (("uvw", uvw, torch.float64), ("freq", freq, torch.float64),
+                            ("band_of_chan", band_of_chan, torch.int32)):
+            if t.dtype != dt or not t.is_contiguous() or t.device != self.device:
+                raise TypeError(f"{name} must be a contiguous {dt} tensor on {self.device}")
+        if uvw.ndim != 2 or uvw.shape[1] != 3:
+            raise ValueError("uvw must be [nrow, 3]")
+        key = (uvw.data_ptr(), freq.data_ptr(), band_of_chan.data_ptr())
+        self._keep = [k for k in self._keep if k[0] != key] + [(key, uvw, freq, band_of_chan)]
+        del self._keep[:-16]
+        return uvw.shape[0], freq.shape[0]
+
+    def _t(self, t, name, dtype, shape):
+        if t.dtype != dtype or not t.is_contiguous() or t.device != self.device or tuple(t.shape) != tuple(shape):
+            raise TypeError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)} on {self.device}")
+        return t
+
+    # ------------------------------------------------------------------ entry points
+    def pfb_degrid(self, geom: Geometry, uvw, freq, band_of_chan, image, out=None):
+        """R x (Eq. 1): image [nband, nx, ny] -> visibilities [nrow, nchan]."""
+        nrow, nchan = self._data(uvw, freq, band_of_chan)
+        prec = _prec_real(image.dtype)
+        self._t(image, "image", _RDT[prec], (geom.nband, geom.nx, geom.ny))
+        if out is None:
+            out = torch.empty((nrow, nchan), dtype=_CDT[prec], device=self.device)
+        self._t(out, "vis_out", _CDT[prec], (nrow, nchan))
+        g = geom.c()
+        self._check(self.lib.pfb_degrid(self.h, ctypes.byref(g), prec, nrow, nchan, _ptr(uvw), _ptr(freq),
+                                        _ptr(band_of_chan), _ptr(image), _ptr(out), self._stream()))
+        return out
+
+    def pfb_grid(self, geom: Geometry, uvw, freq, band_of_chan, vis, wgt=None, out=None):
+        """R^dagger Sigma^-1 y (Eq. 3): visibilities -> image [nband, nx, ny]."""
+        nrow, nchan = self._data(uvw, freq, band_of_chan)
+        prec = _prec_cx(vis.dtype)
+        self._t(vis, "vis", _CDT[prec], (nrow, nchan))
+        if wgt is not None:
+            self._t(wgt, "wgt", _RDT[prec], (nrow, nchan))
+        if out is None:
+            out = torch.empty((geom.nband, geom.nx, geom.ny), dtype=_RDT[prec], device=self.device)
+        self._t(out, "image_out", _RDT[prec], (geom.nband, geom.nx, geom.ny))
+        g = geom.c()
+        self._check(self.lib.pfb_grid(self.h, ctypes.byref(g), prec, nrow, nchan, _ptr(uvw), _ptr(freq),
+                                      _ptr(band_of_chan), _ptr(vis), _ptr(wgt), _ptr(out), self._stream()))
+        return out
+
+    def pfb_dirty(self, geom: Geometry, uvw, freq, band_of_chan, vis, wgt=None, out=None):
+        """I^d = R^dagger Sigma^-1 V and the per-band weight sums (numpy, host)."""
+        nrow, nchan = self._data(uvw, freq, band_of_chan)
+        prec = _prec_cx(vis.dtype)
+        self._t(vis, "vis", _CDT[prec], (nrow, nchan))
+        if wgt is not None:
+            self._t(wgt, "wgt", _RDT[prec], (nrow, nchan))
+        if out is None:
+            out = torch.empty((geom.nband, geom.nx, geom.ny), dtype=_RDT[prec], device=self.device)
+        self._t(out, "image_out", _RDT[prec], (geom.nband, geom.nx, geom.ny))
+        ws = (ctypes.c_double * geom.nband)()
+        g = geom.c()
+        self._check(self.lib.pfb_dirty(self.h, ctypes.byref(g), prec, nrow, nchan, _ptr(uvw), _ptr(freq),
+                                       _ptr(band_of_chan), _ptr(vis), _ptr(wgt), _ptr(out), ws, self._stream()))
+        return out, np.array(ws[:], dtype=np.float64)
+
+    def pfb_psf(self, geom: Geometry, uvw, freq, band_of_chan, wgt=None, dtype=torch.float32, out=None):
+        """I^psf on the 2nx x 2ny grid (centre (nx, ny)) and the per-band weight sums."""
+        nrow, nchan = self._data(uvw, freq, band_of_chan)
+        prec = _prec_real(wgt.dtype if wgt is not None else dtype)
+        if wgt is not None:
+            self._t(wgt, "wgt", _RDT[prec], (nrow, nchan))
+        shape = (geom.nband, 2 * geom.nx, 2 * geom.ny)
+        if out is None:
+            out = torch.empty(shape, dtype=_RDT[prec], device=self.device)
+        self._t(out, "psf_out", _RDT[prec], shape)
+        ws = (ctypes.c_double * geom.nband)()
+        g = geom.c()
+        self._check(self.lib.pfb_psf(self.h, ctypes.byref(g), prec, nrow, nchan, _ptr(uvw), _ptr(freq),
+                                     _ptr(band_of_chan), _ptr(wgt), _ptr(out), ws, self._stream()))
+        return out, np.array(ws[:], dtype=np.float64)
+
+    def pfb_hessian(self, geom: Geometry, uvw, freq, band_of_chan, x, wgt=None, out=None):
+        """R^dagger Sigma^-1 R x (Eq. 3)."""
+        nrow, nchan = self._data(uvw, freq, band_of_chan)
+        prec = _prec_real(x.dtype)
+        self._t(x, "x", _RDT[prec], (geom.nband, geom.nx, geom.ny))
+        if wgt is not None:
+            self._t(wgt, "wgt", _RDT[prec], (nrow, nchan))
+        if out is None:
+            out = torch.empty_like(x)
+        self._t(out, "y_out", _RDT[prec], (geom.nband, geom.nx, geom.ny))
+        g = geom.c()
+        self._check(self.lib.pfb_hessian(self.h, ctypes.byref(g), prec, nrow, nchan, _ptr(uvw), _ptr(freq),
+                                         _ptr(band_of_chan), _ptr(wgt), _ptr(x), _ptr(out), self._stream()))
+        return out
+
+    def pfb_psf_conv(self, geom: Geometry, psf, x, out=None):
+        """I^psf * x (Eq. 4), linear convolution."""
+        prec = _prec_real(x.dtype)
+        self._t(x, "x", _RDT[prec], (geom.nband, geom.nx, geom.ny))
+        self._t(psf, "psf", _RDT[prec], (geom.nband, 2 * geom.nx, 2 * geom.ny))
+        if out is None:
+            out = torch.empty_like(x)
+        self._t(out, "y_out", _RDT[prec], (geom.nband, geom.nx, geom.ny))
+        g = geom.c()
+        self._check(self.lib.pfb_psf_conv(self.h, ctypes.byref(g), prec, _ptr(psf), _ptr(x), _ptr(out),
+                                          self._stream()))
+        return out
+
+    def pfb_step(self, geom: Geometry, params: StepParams, uvw, freq, band_of_chan, wgt, dirty, psf, wsum,
+                 x, dual, stats: bool = True):
+        """One preconditioned forward-backward step (Eqs. 6-7); x and dual are updated in place.
+        Returns (n_hessian, stats) with stats = [objective, relative update, CG residual]."""
+        nrow, nchan = self._data(uvw, freq, band_of_chan)
+        prec = _prec_real(x.dtype)
+        nb = bin(params.basis_mask).count("1")
+        self._t(x, "x", _RDT[prec], (geom.nband, geom.nx, geom.ny))
+        self._t(dirty, "dirty", _RDT[prec], (geom.nband, geom.nx, geom.ny))
+        self._t(psf, "psf", _RDT[prec], (geom.nband, 2 * geom.nx, 2 * geom.ny))
+        self._t(dual, "dual", _RDT[prec], (nb, geom.nband, geom.nx, geom.ny))
+        if wgt is not None:
+            self._t(wgt, "wgt", _RDT[prec], (nrow, nchan))
+        ws = (ctypes.c_double * geom.nband)(*[float(v) for v in wsum])
+        nh = ctypes.c_int64(0)
+        st = (ctypes.c_double * 3)()
+        g, p = geom.c(), params.c()
+        self._check(self.lib.pfb_step(self.h, ctypes.byref(g), prec, ctypes.byref(p), nrow, nchan, _ptr(uvw),
+                                      _ptr(freq), _ptr(band_of_chan), _ptr(wgt), _ptr(dirty), _ptr(psf), ws,
+                                      _ptr(x), _ptr(dual), ctypes.byref(nh), st if stats else None,
+                                      self._stream()))
+        return int(nh.value), np.array(st[:]) if stats else None
+
+    def pfb_plan_reset(self):
+        """Drop cached plans (after changing uvw/freq/band_of_chan in place)."""
+        self._check(self.lib.pfb_plan_reset(self.h))
+        self._keep.clear()
+
+
+_default: dict[int, Context] = {}
+_lock = threading.Lock()
+
+
+def default_context(device: int | None = None) -> Context:
+    d = torch.cuda.current_device() if device is None else device
+    with _lock:
+        if d not in _default:
+            _default[d] = Context(d)
+        return _default[d]
+
+
+def version() -> str:
+    return _lib.load().pfb_version().decode()

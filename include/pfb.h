@@ -46,7 +46,7 @@
  *    against the exact FP64 direct sum.  PFB_F32 keeps uvw x frequency -> grid
  *    coordinates and the w-plane phases in FP64 and everything else in FP32; it
  *    accepts epsilon >= 1e-6.  PFB_F64 computes in FP64 and accepts
- *    epsilon >= 1e-13.
+ *    epsilon >= 1e-12.
  */
 #ifndef PFB_H
 #define PFB_H
@@ -174,6 +174,23 @@ int pfb_step(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_params
              const int32_t *band_of_chan, const void *wgt, const void *dirty, const void *psf,
              const double *wsum, void *x_inout, void *dual_inout, int64_t *n_hessian_out,
              double *stats_out, void *stream);
+
+/* Per-kernel device timing (tracing; not part of the paper's method).
+ * pfb_timing(ctx, 1) clears the totals and starts recording CUDA events around
+ * every kernel group the library enqueues (on the caller's stream, so timings
+ * reflect that stream's order); pfb_timing(ctx, 0) stops recording. */
+int pfb_timing(pfb_ctx *ctx, int enable);
+
+/* Totals since timing was enabled for one kernel group name ("grid_tiles",
+ * "gather", "fft_fwd", ...), or "*" for all groups together (then *launches is
+ * the number of this library's own kernel launches, cuFFT excluded).  bytes (may
+ * be NULL) receives the algorithmic HBM traffic of those launches: the bytes the
+ * operation must read and write at minimum, computed from the sizes.  Waits for
+ * the recorded events. */
+int pfb_timing_read(pfb_ctx *ctx, const char *kernel, int64_t *launches, double *total_ms, double *bytes);
+
+/* Comma-separated names of the groups recorded so far, written into buf (len bytes). */
+int pfb_timing_names(pfb_ctx *ctx, char *buf, size_t len);
 
 /* Library version string. */
 const char *pfb_version(void);

@@ -19,7 +19,8 @@ ERRORS = {
 
 # every function the header declares (the CPU test checks the library exports them)
 EXPORTS = ["pfb_create", "pfb_destroy", "pfb_last_error", "pfb_plan_reset", "pfb_degrid", "pfb_grid",
-           "pfb_dirty", "pfb_psf", "pfb_hessian", "pfb_psf_conv", "pfb_step", "pfb_version"]
+           "pfb_dirty", "pfb_psf", "pfb_hessian", "pfb_psf_conv", "pfb_step", "pfb_version",
+           "pfb_timing", "pfb_timing_read", "pfb_timing_names"]
 
 
 class pfb_geom(ctypes.Structure):
@@ -72,6 +73,9 @@ def load(path: str = LIB_PATH):
     lib.pfb_psf_conv.argtypes = [P, G, ctypes.c_int, P, P, P, P]
     lib.pfb_step.argtypes = [P, G, ctypes.c_int, ctypes.POINTER(pfb_params), *data, P, P, P,
                              ctypes.POINTER(D), P, P, ctypes.POINTER(I64), ctypes.POINTER(D), P]
+    lib.pfb_timing.argtypes = [P, ctypes.c_int]
+    lib.pfb_timing_read.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.pfb_timing_names.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     for f in EXPORTS:
         if f not in ("pfb_destroy", "pfb_last_error", "pfb_version", "pfb_create"):
             getattr(lib, f).restype = ctypes.c_int

@@ -113,6 +113,46 @@ cufftHandle Ctx::fft(int n0, int n1, int batch, cufftType type) {
     return h;
 }
 
+cudaEvent_t Timing::get() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    PFB_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+void Timing::resolve() {
+    for (auto &r : pending) {
+        cudaEventSynchronize(r.b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        Total &t = totals[r.name];
+        t.launches += 1;
+        t.ms += ms;
+        t.bytes += r.bytes;
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    pending.clear();
+}
+
+void Timing::clear() {
+    resolve();
+    totals.clear();
+    own_launches = 0;
+}
+
+Timing::~Timing() {
+    for (auto &r : pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+}
+
 }  // namespace pfb
 
 using namespace pfb;
@@ -154,7 +194,7 @@ void check_geom(const pfb_geom *g, pfb_prec prec) {
     if (!(g->epsilon > 0 && g->epsilon < 1)) throw Error(PFB_ERR_EPS, "epsilon must be in (0, 1)");
     if (prec == PFB_F32 && g->epsilon < 1e-6)
         throw Error(PFB_ERR_EPS, "epsilon below 1e-6 is not reachable in PFB_F32; use PFB_F64");
-    if (prec == PFB_F64 && g->epsilon < 1e-13) throw Error(PFB_ERR_EPS, "epsilon below 1e-13 is not reachable");
+    if (prec == PFB_F64 && g->epsilon < 1e-12) throw Error(PFB_ERR_EPS, "epsilon below 1e-12 is not reachable");
 }
 
 void check_data(int64_t nrow, int32_t nchan, const double *uvw, const double *freq, const int32_t *band) {
@@ -169,6 +209,45 @@ cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 extern "C" {
 
 const char *pfb_version(void) { return "pfb-gb300 0.1 (sm_103a)"; }
+
+int pfb_timing(pfb_ctx *ctx, int enable) {
+    return guarded(ctx, [&](Ctx &c) {
+        c.timing.clear();
+        c.timing.on = enable != 0;
+    });
+}
+
+int pfb_timing_read(pfb_ctx *ctx, const char *kernel, int64_t *launches, double *total_ms, double *bytes) {
+    return guarded(ctx, [&](Ctx &c) {
+        PFB_REQUIRE(kernel && launches && total_ms, "kernel, launches and total_ms must not be NULL");
+        c.timing.resolve();
+        if (std::string(kernel) == "*") {
+            *launches = c.timing.own_launches;
+            double ms = 0, by = 0;
+            for (auto &kv : c.timing.totals) {
+                ms += kv.second.ms;
+                by += kv.second.bytes;
+            }
+            *total_ms = ms;
+            if (bytes) *bytes = by;
+            return;
+        }
+        auto it = c.timing.totals.find(kernel);
+        *launches = it == c.timing.totals.end() ? 0 : it->second.launches;
+        *total_ms = it == c.timing.totals.end() ? 0.0 : it->second.ms;
+        if (bytes) *bytes = it == c.timing.totals.end() ? 0.0 : it->second.bytes;
+    });
+}
+
+int pfb_timing_names(pfb_ctx *ctx, char *buf, size_t len) {
+    return guarded(ctx, [&](Ctx &c) {
+        PFB_REQUIRE(buf && len > 0, "buf must hold at least one byte");
+        c.timing.resolve();
+        std::string s;
+        for (auto &kv : c.timing.totals) s += (s.empty() ? "" : ",") + kv.first;
+        std::snprintf(buf, len, "%s", s.c_str());
+    });
+}
 
 int pfb_create(pfb_ctx **out, int device, size_t budget) {
     if (!out) return PFB_ERR_ARG;

@@ -82,6 +82,29 @@ struct FftKey {
     }
 };
 
+// Per-kernel device timing: CUDA events recorded around each launch on the
+// launch stream while enabled, resolved when read.
+struct Timing {
+    bool on = false;
+    struct Rec {
+        std::string name;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    struct Total {
+        int64_t launches = 0;
+        double ms = 0, bytes = 0;
+    };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> pending;
+    std::map<std::string, Total> totals;
+    int64_t own_launches = 0;   // kernels of this library launched while enabled
+    cudaEvent_t get();
+    void resolve();
+    void clear();
+    ~Timing();
+};
+
 struct Ctx {
     int device = 0;
     int num_sms = 0;
@@ -93,6 +116,7 @@ struct Ctx {
     std::map<std::string, DevBuf> bufs;
     std::map<FftKey, cufftHandle> ffts;
     std::vector<PsfSpec> spectra;
+    Timing timing;
 
     ~Ctx();
     void *dalloc(size_t bytes);            // counted against the budget
@@ -103,6 +127,30 @@ struct Ctx {
     void free_plan(Plan &p);
     void reset();
     cufftHandle fft(int n0, int n1, int batch, cufftType type);
+};
+
+// Scoped timer: records events around the enclosed launches when timing is on.
+// `bytes` is the algorithmic traffic of the enclosed work; `launches` the number
+// of this library's kernels it launches (cuFFT calls pass 0).
+struct KTimer {
+    Ctx &c;
+    const char *name;
+    cudaStream_t st;
+    double bytes;
+    cudaEvent_t a = nullptr;
+    KTimer(Ctx &c_, const char *n, cudaStream_t s, double b, int launches = 1) : c(c_), name(n), st(s), bytes(b) {
+        if (!c.timing.on) return;
+        c.timing.own_launches += launches;
+        a = c.timing.get();
+        cudaEventRecord(a, st);
+    }
+    ~KTimer() {
+        if (!a) return;
+        cudaEvent_t b = c.timing.get();
+        cudaEventRecord(b, st);
+        c.timing.pending.push_back({name, a, b, bytes});
+        if (c.timing.pending.size() > 8192) c.timing.resolve();
+    }
 };
 
 // plan.cu

@@ -22,16 +22,6 @@
 
 namespace pfb {
 
-// ------------------------------------------------------------------ kernel parameters
-// Support W from the requested accuracy at oversampling 2 (calibrated against
-// the FP64 direct sum): relative error ~ 10^-(W-1).
-int kernel_support(double eps) {
-    int W = (int)std::ceil(std::log10(1.0 / eps)) + 1;
-    return std::min(MAX_W, std::max(4, W));
-}
-
-static double es_beta(int W) { return 2.4 * W; }
-
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
 static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
     x.resize(n);
@@ -62,9 +52,9 @@ struct EsTransform {
     int W;
     double beta;
     std::vector<double> th, wt;
-    EsTransform(int W_, double beta_) : W(W_), beta(beta_) {
+    EsTransform(int W_, double beta_, int nodes = 200) : W(W_), beta(beta_) {
         std::vector<double> x, w;
-        gauss_legendre(160, x, w);
+        gauss_legendre(nodes, x, w);
         th.resize(x.size());
         wt.resize(x.size());
         for (size_t i = 0; i < x.size(); ++i) {
@@ -79,6 +69,50 @@ struct EsTransform {
         return s;
     }
 };
+
+// ------------------------------------------------------------------ kernel parameters
+// With oversampling 2 the correction psihat(xi)^-1 is applied for |xi| <= 1/4
+// (uv: |p / N| <= nx / (2 N); w: |dw t| <= 1/4 by the choice of dw), and the
+// Poisson-summation aliases psihat(xi + m), m != 0, are the approximation error.
+// For each support W the shape parameter beta is chosen to minimise the
+// worst-case aliasing ratio  max_{|xi| <= 1/4} sum_{m = +-1, +-2} |psihat(xi + m)| / psihat(xi),
+// and W is the smallest support whose ratio is <= epsilon.
+struct KernelChoice {
+    int W;
+    double beta, err;
+};
+
+static const std::vector<KernelChoice> &kernel_table() {
+    static const std::vector<KernelChoice> tab = [] {
+        std::vector<KernelChoice> t;
+        for (int W = 4; W <= MAX_W; ++W) {
+            KernelChoice best{W, 2.3 * W, 1e300};
+            for (int k = 0; k <= 8; ++k) {
+                const double beta = (2.0 + 0.05 * k) * W;
+                EsTransform es(W, beta);
+                double worst = 0;
+                for (int i = 0; i <= 25; ++i) {
+                    const double xi = 0.25 * i / 25.0;
+                    double a = 0;
+                    for (int m : {-2, -1, 1, 2}) a += std::fabs(es(xi + m));
+                    worst = std::max(worst, a / es(xi));
+                }
+                if (worst < best.err) best = {W, beta, worst};
+            }
+            t.push_back(best);
+        }
+        return t;
+    }();
+    return tab;
+}
+
+int kernel_support(double eps) {
+    for (const auto &k : kernel_table())
+        if (k.err <= eps) return k.W;
+    return MAX_W;
+}
+
+static double es_beta(int W) { return kernel_table()[W - 4].beta; }
 
 // Smallest n >= lo that is a multiple of TILE and has no prime factor above 7.
 static int good_size(int lo) {
@@ -353,7 +387,7 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     p.nkq = (p.Pmax + p.q - 1) / p.q;
     p.nkeys = (int64_t)p.nband * ntiles * p.nkq;
     const size_t cxs = p.prec == PFB_F64 ? 16 : 8;
-    PFB_REQUIRE((size_t)(p.Ww + p.q - 1) * TILE * TILE * cxs <= 200 * 1024,
+    PFB_REQUIRE((size_t)(p.Ww + p.q - 1) * TILE * TILE * cxs <= 227 * 1024,
                 "w-plane ring of the gridding kernel exceeds shared memory (reduce epsilon demands or image size)");
 
     // ---- device copies of per-channel data and band geometry
@@ -507,6 +541,7 @@ Plan &get_plan(Ctx &ctx, const pfb_geom &g, int prec, int64_t nrow, int nchan, c
     p.Nu = good_size(std::max(2 * nx, 2 * MAX_W));
     p.Nv = good_size(std::max(2 * ny, 2 * MAX_W));
     try {
+        KTimer t(ctx, "plan", st, 0.0, 0);
         build_plan(ctx, p, uvw, st);
     } catch (...) {
         ctx.free_plan(p);

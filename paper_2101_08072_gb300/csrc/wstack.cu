@@ -361,6 +361,13 @@ static unsigned grid_blocks(int64_t n, int threads, int cap) {
 }
 
 // ------------------------------------------------------------------ operators
+// visibilities of band b (rows x channels mapped to b)
+static int64_t band_nvis(const Plan &p, int b) {
+    int64_t nc = 0;
+    for (int c = 0; c < p.nchan; ++c) nc += p.band_h[c] == b;
+    return nc * p.nrow;
+}
+
 template <typename T>
 void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st) {
     const size_t cxs = sizeof(cx_t<T>);
@@ -368,18 +375,30 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
     const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
     cx_t<T> *planes = (cx_t<T> *)ctx.scratch("planes", (size_t)blk * p.Nu * p.Nv * cxs);
     const int64_t npix = (int64_t)p.nx * p.ny;
+    const double plane_bytes = (double)p.Nu * p.Nv * cxs;
     for (int b = 0; b < p.nband; ++b) {
         const BandGeom g = p.geom(b);
         const int64_t i0 = p.band_items_begin[b], i1 = p.band_items_end[b];
+        const double nvb = (double)band_nvis(p, b);
         for (int k_lo = 0; k_lo < g.P; k_lo += blk) {
             const int k_hi = std::min(g.P, k_lo + blk);
             const int nk = k_hi - k_lo;
-            PFB_CUDA(cudaMemsetAsync(planes, 0, (size_t)nk * p.Nu * p.Nv * cxs, st));
-            k_prepass<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
-                p.nx, p.ny, image + b * npix, (const T *)p.d_corr, p.d_tp, g, k_lo, k_hi, p.dw, planes);
-            check_launch("prepass");
-            fft_planes<T>(ctx, planes, nk, p.Nu, p.Nv, CUFFT_FORWARD, st);
+            {
+                KTimer t(ctx, "memset_planes", st, nk * plane_bytes, 0);
+                PFB_CUDA(cudaMemsetAsync(planes, 0, (size_t)nk * p.Nu * p.Nv * cxs, st));
+            }
+            {
+                KTimer t(ctx, "prepass", st, npix * (2.0 * sizeof(T) + 8.0 + nk * (double)cxs));
+                k_prepass<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
+                    p.nx, p.ny, image + b * npix, (const T *)p.d_corr, p.d_tp, g, k_lo, k_hi, p.dw, planes);
+                check_launch("prepass");
+            }
+            {
+                KTimer t(ctx, "fft_fwd", st, 2.0 * nk * plane_bytes, 0);
+                fft_planes<T>(ctx, planes, nk, p.Nu, p.Nv, CUFFT_FORWARD, st);
+            }
             if (i1 > i0) {
+                KTimer t(ctx, "gather", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
                 k_gather<T><<<grid_blocks(i1 - i0, 256, 64 * ctx.num_sms), 256, 0, st>>>(
                     p.d_items + i0, i1 - i0, (const double *)p.uvw, p.d_scale, g, k_lo, k_hi, planes, vis);
                 check_launch("gather");
@@ -397,32 +416,43 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
     const int64_t npix = (int64_t)p.nx * p.ny;
     const int R = p.Ww + p.q - 1;
     const size_t smem = (size_t)R * TILE * TILE * cxs;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == 8]) {
-        PFB_CUDA(cudaFuncSetAttribute(k_grid_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr_set[sizeof(T) == 8] = true;
-    }
+    PFB_CUDA(cudaFuncSetAttribute(k_grid_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const double plane_bytes = (double)p.Nu * p.Nv * cxs;
     for (int b = 0; b < p.nband; ++b) {
         const BandGeom g = p.geom(b);
         const int64_t w0 = p.work_begin[b], w1 = p.work_begin[b + 1];
         const int64_t h0 = p.heavy_begin[b], h1 = p.heavy_begin[b + 1];
+        const double nvb = (double)band_nvis(p, b);
+        const double nit = (double)(p.band_items_end[b] - p.band_items_begin[b]);
         for (int k_lo = 0; k_lo < g.P; k_lo += blk) {
             const int k_hi = std::min(g.P, k_lo + blk);
             const int nk = k_hi - k_lo;
             if (h1 > h0) {
+                KTimer t(ctx, "zero_tiles", st, (double)(h1 - h0) * nk * TILE * TILE * cxs);
                 k_zero_tiles<T><<<(unsigned)((h1 - h0) * nk), 256, 0, st>>>(
                     p.d_heavy + h0, (int)(h1 - h0), p.ntv, p.Nv, (int64_t)p.Nu * p.Nv, nk, planes);
                 check_launch("zero_tiles");
             }
-            k_grid_tiles<T><<<(unsigned)(w1 - w0), 256, smem, st>>>(p.d_work + w0, p.d_items, p.d_off,
-                                                                     (const double *)p.uvw, p.d_scale, vis, wgt,
-                                                                     unit_vis ? 1 : 0, g, k_lo, k_hi, planes);
-            check_launch("grid_tiles");
-            fft_planes<T>(ctx, planes, nk, p.Nu, p.Nv, CUFFT_INVERSE, st);
-            k_postpass<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
-                p.nx, p.ny, (const T *)p.d_corr, p.d_tp, g, k_lo, k_hi, p.dw, planes, k_lo > 0 ? 1 : 0,
-                image + b * npix);
-            check_launch("postpass");
+            {
+                const double vb = unit_vis ? 0.0 : (double)cxs;
+                const double wb = wgt ? (double)sizeof(T) : 0.0;
+                KTimer t(ctx, "grid_tiles", st, 4.0 * nit + nvb * (vb + wb) + nk * plane_bytes);
+                k_grid_tiles<T><<<(unsigned)(w1 - w0), 256, smem, st>>>(p.d_work + w0, p.d_items, p.d_off,
+                                                                         (const double *)p.uvw, p.d_scale, vis, wgt,
+                                                                         unit_vis ? 1 : 0, g, k_lo, k_hi, planes);
+                check_launch("grid_tiles");
+            }
+            {
+                KTimer t(ctx, "fft_inv", st, 2.0 * nk * plane_bytes, 0);
+                fft_planes<T>(ctx, planes, nk, p.Nu, p.Nv, CUFFT_INVERSE, st);
+            }
+            {
+                KTimer t(ctx, "postpass", st, npix * (nk * (double)cxs + 2.0 * sizeof(T) + 8.0));
+                k_postpass<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
+                    p.nx, p.ny, (const T *)p.d_corr, p.d_tp, g, k_lo, k_hi, p.dw, planes, k_lo > 0 ? 1 : 0,
+                    image + b * npix);
+                check_launch("postpass");
+            }
         }
     }
 }

@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Throughput of the exact Hessian-vector product R^dagger Sigma^-1 R x on the
+MeerKAT-like wide-field continuum workload (64 antennas / 2016 baselines x 450
+integrations = 907,200 rows, 256 channels over 0.856-1.712 GHz in 4 imaging
+bands, 4096^2 pixels of 1.5 arcsec, FP32 data with FP64 coordinates/phases,
+epsilon = 3e-5), in million visibilities per second.
+
+One step = one pfb_hessian call (R, weights, R^dagger over all 4 bands).
+Inputs are synthetic and seeded, resident in HBM before the timed region; every
+step touches tens of GB of w-plane stacks, far more than the 129 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) each rank runs an independent replica of the workload
+(the path shards only with an image all-reduce that this build does not use);
+value is the sum over ranks, timed as the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mvis/s for R^dagger Sigma^-1 R x (FP32, eps<=3e-5 vs FP64)"
+UNIT = "Mvis/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--eps", type=float, default=3e-5)
+    ap.add_argument("--ntime", type=int, default=450, help="integrations (907,200 rows at 450)")
+    ap.add_argument("--npix", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2101_08072_gb300 import synth
+    obs = synth.meerkat_like_observation(ntime=args.ntime, nx=args.npix, ny=args.npix)
+    rng = np.random.default_rng(2)
+    bf = synth.band_centre_freqs(obs.freq, obs.band_of_chan, obs.nband)
+    x = synth.point_source_image(rng, obs.nband, obs.nx, obs.ny, 1000, flux="pareto", fmin=1e-3, fmax=1.0,
+                                 spectral=True, band_freqs=bf)
+    return obs, x
+
+
+def config(args, obs):
+    return {"workload": f"MeerKAT-like wide-field Hessian: {obs.nrow} rows x {obs.nchan} channels, "
+                        f"{obs.nband} bands, {obs.nx}x{obs.ny} image at 1.5 arcsec, eps {args.eps:g}",
+            "rows": obs.nrow, "channels": obs.nchan, "bands": obs.nband, "image": [obs.nx, obs.ny],
+            "visibilities": obs.nvis, "epsilon": args.eps, "precision": args.prec,
+            "l2": "inputs larger than L2 (w-plane stacks of several GB per band)",
+            "sources": 1000}
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(obs, x, wgt_rows, rows, pix):
+    """Time the FP64 oracle on a bounded sample of the Hessian: R x on `rows`
+    (all channels, all sources) and R^dagger of the weighted result at `pix`.
+    Returns (Mvis/s extrapolated to a full-image Hessian, seconds, threads)."""
+    import oracle
+    sub_uvw = obs.uvw[rows]
+    t0 = time.perf_counter()
+    v = oracle.degrid(sub_uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm)
+    t1 = time.perf_counter()
+    oracle.grid(sub_uvw, obs.freq, obs.band_of_chan, v, wgt_rows, obs.nx, obs.ny, obs.dl, obs.dm, obs.nband,
+                pix=pix)
+    t2 = time.perf_counter()
+    nvis = len(rows) * obs.nchan
+    npix_total = obs.nband * obs.nx * obs.ny
+    # R^dagger at one pixel of band b reads only band b's channels: scale by pixels per band
+    sec_per_vis = (t1 - t0) / nvis + (t2 - t1) / nvis * (npix_total / len(pix))
+    return 1e-6 / sec_per_vis, t2 - t0, oracle.num_threads()
+
+
+def cpu_baseline(obs, x, wgt_np_fn, n_rows=8192, n_pix=2048, seed=5):
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(obs.nrow, n_rows, replace=False))
+    pix = np.sort(rng.choice(obs.nband * obs.nx * obs.ny, n_pix, replace=False))
+    value, secs, threads = oracle_sample(obs, x, wgt_np_fn(rows), rows, pix)
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"FP64 direct sum: R x on {n_rows} random rows x {obs.nchan} channels (1000 sources), "
+                      f"R^dagger at {n_pix} random pixels; cost extrapolated linearly to the full "
+                      f"{obs.nband}x{obs.nx}^2 Hessian ({secs:.1f} s of CPU work)"}
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    obs, x = workload(args)
+    wrng = np.random.default_rng(9)
+
+    def wgt(rows):
+        return wrng.uniform(0.5, 1.5, (len(rows), obs.nchan))
+
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = cpu_baseline(obs, x, wgt, n_rows=256, n_pix=128, seed=100 + i)
+        if i >= args.warmup:
+            vals.append(info["value"])
+    value = statistics.median(vals)
+    ms = obs.nvis / (value * 1e6) * 1e3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
+            "config": config(args, obs),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2101_08072_gb300 import Context, Geometry, _lib
+
+    obs, x_np = workload(args)
+    rdt = torch.float32 if args.prec == "f32" else torch.float64
+    uvw = torch.from_numpy(obs.uvw).to(dev)
+    freq = torch.from_numpy(obs.freq).to(dev)
+    band = torch.from_numpy(obs.band_of_chan.astype(np.int32)).to(dev)
+    x = torch.from_numpy(x_np).to(dev, rdt)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(9)
+    wgt = torch.empty((obs.nrow, obs.nchan), dtype=rdt, device=dev).uniform_(0.5, 1.5, generator=gen)
+    y = torch.empty_like(x)
+    g = Geometry(nx=obs.nx, ny=obs.ny, dl=obs.dl, dm=obs.dm, nband=obs.nband, epsilon=args.eps)
+    ctx = Context(local)
+    lib = _lib.load()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ctx.pfb_hessian(g, uvw, freq, band, x, wgt, out=y)
+
+    t_plan = time.perf_counter()
+    step()
+    torch.cuda.synchronize(dev)
+    t_plan = time.perf_counter() - t_plan
+    for _ in range(max(0, args.warmup - 1)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    lib.pfb_timing(ctx.h, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-kernel totals recorded by the library on the same stream
+    import ctypes
+    names = ctypes.create_string_buffer(4096)
+    lib.pfb_timing_names(ctx.h, names, 4096)
+    kern = {}
+    for nm in [n for n in names.value.decode().split(",") if n]:
+        L, T, B = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        lib.pfb_timing_read(ctx.h, nm.encode(), ctypes.byref(L), ctypes.byref(T), ctypes.byref(B))
+        kern[nm] = {"launches": L.value, "ms": T.value, "bytes": B.value}
+    L, T, B = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    lib.pfb_timing_read(ctx.h, b"*", ctypes.byref(L), ctypes.byref(T), ctypes.byref(B))
+    own_launches = L.value
+    lib.pfb_timing(ctx.h, 0)
+
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * obs.nvis / (ms * 1e-3) / 1e6
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_uvw = uvw.cpu().pin_memory()
+        h_freq = freq.cpu().pin_memory()
+        h_band = band.cpu().pin_memory()
+        h_wgt = wgt.cpu().pin_memory()
+        h_x = x.cpu().pin_memory()
+        h_y = torch.empty(y.shape, dtype=rdt, pin_memory=True)
+        bi = sum(t.numel() * t.element_size() for t in (h_uvw, h_freq, h_band, h_wgt, h_x))
+        bo = h_y.numel() * h_y.element_size()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.e2e_steps):
+            uvw.copy_(h_uvw, non_blocking=True)
+            freq.copy_(h_freq, non_blocking=True)
+            band.copy_(h_band, non_blocking=True)
+            wgt.copy_(h_wgt, non_blocking=True)
+            x.copy_(h_x, non_blocking=True)
+            step()
+            h_y.copy_(y, non_blocking=True)
+        f1.record(stream)
+        barrier()
+        ems = f0.elapsed_time(f1) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * obs.nvis / (ems * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo}
+
+    # ---- roofline of the dominant kernel group
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    dom = max(kern.items(), key=lambda kv: kv[1]["ms"]) if kern else None
+    roof = None
+    if dom:
+        nm, d = dom
+        per_launch_ms = d["ms"] / max(d["launches"], 1)
+        per_launch_bytes = d["bytes"] / max(d["launches"], 1)
+        ach = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": nm, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_source": peak_src, "traffic": None,
+                "share_of_step": d["ms"] / (ms * args.steps) if ms > 0 else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        wnp = wgt.cpu().numpy().astype(np.float64)
+        cpu = cpu_baseline(obs, x_np, lambda rows: wnp[rows])
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded)",
+                "config": config(args, obs), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": own_launches, "clocks": clk,
+                "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                                "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                            for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms"])},
+                "plan_s": t_plan}
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -68,6 +68,8 @@ void Ctx::free_plan(Plan &p) {
         if (q) dfree(q, n);
     };
     fr(p.d_scale, p.nchan * sizeof(double));
+    fr(p.d_rowdf, (size_t)p.nrow * 3 * sizeof(float2));
+    fr(p.d_chandf, p.nchan * sizeof(ChanDF));
     fr(p.d_band, p.nchan * sizeof(int));
     fr(p.d_bg, p.nband * sizeof(BandGeom));
     fr(p.d_items, (size_t)std::max<int64_t>(p.nitems, 1) * sizeof(uint32_t));
@@ -76,7 +78,7 @@ void Ctx::free_plan(Plan &p) {
     fr(p.d_corr, (size_t)p.nx * p.ny * (p.prec == PFB_F64 ? 8 : 4));
     if (p.d_work) fr(p.d_work, (size_t)p.work_begin.back() * sizeof(WorkItem));
     if (p.d_heavy) fr(p.d_heavy, (size_t)p.heavy_begin.back() * sizeof(int));
-    p.d_scale = nullptr; p.d_band = nullptr; p.d_bg = nullptr; p.d_items = nullptr; p.d_off = nullptr;
+    p.d_scale = nullptr; p.d_rowdf = nullptr; p.d_chandf = nullptr; p.d_band = nullptr; p.d_bg = nullptr; p.d_items = nullptr; p.d_off = nullptr;
     p.d_tp = nullptr; p.d_corr = nullptr; p.d_work = nullptr; p.d_heavy = nullptr;
 }
 

@@ -97,22 +97,36 @@ struct BandGeom {
     double tc;              // centre of (n - 1) over the image; removed per visibility
     double beta;
     double inv_halfw;       // 2 / W
+    // FP32 path: first-tap offsets O = W/2 (uv) and W/2 + w0/dw (w), split into
+    // an integer and a fraction so that the cell arithmetic stays exact
+    int uv_oi, w_oi;
+    float uv_of, w_of, hw;
 };
 
-// Grid coordinates of one visibility (FP64 arithmetic; fractional offsets of
-// the first tap stay in FP64 until the kernel converts them).
+// Per-row / per-channel factors of the FP32 path, each FP64 value stored as an
+// unevaluated sum hi + lo of two floats (double-float, Dekker 1971).
+struct ChanDF {
+    float su_hi, su_lo;   // f/c * dl * Nu  (metres -> u cells)
+    float sv_hi, sv_lo;   // f/c * dm * Nv
+    float sw_hi, sw_lo;   // f/c / dw       (metres -> w-plane coordinate)
+    float sp_hi, sp_lo;   // f/c * t_c      (metres -> turns of exp(-2 pi i w t_c))
+};
+
+// Grid coordinates of one visibility.
+template <typename T>
 struct VisCoord {
     int gu0, gv0;   // first tap cell, wrapped into [0, Nu) / [0, Nv)
     int k0;         // first w-plane
-    double ou, ov;  // first-tap offset from the visibility: gu0 - x_u, in (-W/2, -W/2 + 1]
-    double ow;      // first-plane offset k0 - z_w
-    double wl;      // w in wavelengths after the Hermitian flip
+    T ou, ov;       // first-tap offset from the visibility: gu0 - x_u, in (-W/2, -W/2 + 1]
+    T ow;           // first-plane offset k0 - z_w
+    T ph;           // w t_c in turns, reduced to [-1/2, 1/2]
     bool flip;      // the row was mapped (u,v,w) -> (-u,-v,-w) and V -> conj V
 };
 
-__device__ __forceinline__ VisCoord vis_coord(const double *__restrict__ uvw, int64_t row, double s,
-                                              const BandGeom &g) {
-    VisCoord c;
+// ---- FP64 path
+__device__ __forceinline__ VisCoord<double> vis_coord64(const double *__restrict__ uvw, int64_t row, double s,
+                                                        const BandGeom &g) {
+    VisCoord<double> c;
     double u = uvw[3 * row + 0] * s, v = uvw[3 * row + 1] * s, w = uvw[3 * row + 2] * s;
     c.flip = w < 0.0;
     if (c.flip) { u = -u; v = -v; w = -w; }
@@ -130,7 +144,8 @@ __device__ __forceinline__ VisCoord vis_coord(const double *__restrict__ uvw, in
     if (gv >= g.Nv) gv -= g.Nv;
     c.gu0 = gu;
     c.gv0 = gv;
-    c.wl = w;
+    double ph = w * g.tc;
+    c.ph = ph - rint(ph);
     if (g.Ww > 1) {
         double zw = (w - g.w0) * g.inv_dw;
         double fk = ceil(zw - hw);
@@ -145,10 +160,79 @@ __device__ __forceinline__ VisCoord vis_coord(const double *__restrict__ uvw, in
     return c;
 }
 
+// ---- FP32 path: double-float products, no FP64 instructions.
+// a * s with a = a_hi + a_lo, s = s_hi + s_lo: p + e (TwoProduct by FMA; the
+// a_lo * s_lo term is below the precision kept).
+__device__ __forceinline__ void df_mul(float a_hi, float a_lo, float s_hi, float s_lo, float &p, float &e) {
+    p = a_hi * s_hi;
+    e = fmaf(a_hi, s_hi, -p) + fmaf(a_hi, s_lo, a_lo * s_hi);
+}
+
+// First tap g0 = ceil(x - O) and offset g0 - x for x = p + e, O = oi + of.
+__device__ __forceinline__ void df_tap(float p, float e, int oi, float of, float hw, int &g0, float &off) {
+    const float r = floorf(p);
+    const float gf = ((p - r) + e) - of;    // p - r is exact
+    const float c = ceilf(gf);
+    g0 = (int)r - oi + (int)c;
+    off = (c - gf) - hw;
+}
+
+__device__ __forceinline__ VisCoord<float> vis_coord32(const float2 *__restrict__ rowdf, int64_t row,
+                                                       const ChanDF &cs, const BandGeom &g) {
+    VisCoord<float> c;
+    float2 u = rowdf[3 * row + 0], v = rowdf[3 * row + 1], w = rowdf[3 * row + 2];
+    c.flip = w.x < 0.0f || (w.x == 0.0f && w.y < 0.0f);
+    if (c.flip) {
+        u.x = -u.x; u.y = -u.y; v.x = -v.x; v.y = -v.y; w.x = -w.x; w.y = -w.y;
+    }
+    float p, e;
+    int g0;
+    df_mul(u.x, u.y, cs.su_hi, cs.su_lo, p, e);
+    df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ou);
+    g0 %= g.Nu;
+    c.gu0 = g0 < 0 ? g0 + g.Nu : g0;
+    df_mul(v.x, v.y, cs.sv_hi, cs.sv_lo, p, e);
+    df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ov);
+    g0 %= g.Nv;
+    c.gv0 = g0 < 0 ? g0 + g.Nv : g0;
+    df_mul(w.x, w.y, cs.sp_hi, cs.sp_lo, p, e);
+    c.ph = (p - rintf(p)) + e;
+    if (g.Ww > 1) {
+        df_mul(w.x, w.y, cs.sw_hi, cs.sw_lo, p, e);
+        df_tap(p, e, g.w_oi, g.w_of, g.hw, g0, c.ow);
+        c.k0 = g0 < 0 ? 0 : (g0 > g.P - g.Ww ? g.P - g.Ww : g0);
+    } else {
+        c.k0 = 0;
+        c.ow = 0.0f;
+    }
+    return c;
+}
+
+// Per-visibility inputs of the coordinate computation, for either path.
+struct CoordSrc {
+    const double *uvw;      // FP64 path
+    const double *scale;    // f / c per channel (FP64 path)
+    const float2 *rowdf;    // FP32 path: uvw as double-float
+    const ChanDF *chandf;   // FP32 path
+};
+
+template <typename T>
+__device__ __forceinline__ VisCoord<T> vis_coord(const CoordSrc &s, int64_t row, int ch, const BandGeom &g);
+template <>
+__device__ __forceinline__ VisCoord<double> vis_coord<double>(const CoordSrc &s, int64_t row, int ch,
+                                                              const BandGeom &g) {
+    return vis_coord64(s.uvw, row, s.scale[ch], g);
+}
+template <>
+__device__ __forceinline__ VisCoord<float> vis_coord<float>(const CoordSrc &s, int64_t row, int ch,
+                                                            const BandGeom &g) {
+    return vis_coord32(s.rowdf, row, s.chandf[ch], g);
+}
+
 // ES weights of the W taps starting at offset o (o, o+1, ..., o+W-1).
 template <typename T>
-__device__ __forceinline__ void es_taps(double o, int W, const BandGeom &g, T *out) {
-    T o0 = (T)o;
+__device__ __forceinline__ void es_taps(T o, int W, const BandGeom &g, T *out) {
+    T o0 = o;
     T ihw = (T)g.inv_halfw, b = (T)g.beta;
 #pragma unroll
     for (int t = 0; t < MAX_W; ++t)

@@ -40,6 +40,8 @@ struct Plan {
 
     // ---- device
     double *d_scale = nullptr;
+    float2 *d_rowdf = nullptr;   // uvw as double-float (FP32 path)
+    ChanDF *d_chandf = nullptr;  // per-channel double-float scales (FP32 path)
     int *d_band = nullptr;
     BandGeom *d_bg = nullptr;
     uint32_t *d_items = nullptr;
@@ -60,8 +62,16 @@ struct Plan {
         g.inv_dw = wstack ? 1.0 / dw : 0.0;
         g.w0 = w0[b];
         g.tc = tc; g.beta = beta; g.inv_halfw = 2.0 / W;
+        const double hw = 0.5 * W;
+        g.hw = (float)hw;
+        g.uv_oi = (int)std::floor(hw);
+        g.uv_of = (float)(hw - std::floor(hw));
+        const double O = wstack ? hw + w0[b] / dw : hw;
+        g.w_oi = (int)std::floor(O);
+        g.w_of = (float)(O - std::floor(O));
         return g;
     }
+    CoordSrc coords() const { return CoordSrc{(const double *)uvw, d_scale, d_rowdf, d_chandf}; }
     int64_t key(int b, int tile, int kq) const { return ((int64_t)b * ntu * ntv + tile) * nkq + kq; }
 };
 

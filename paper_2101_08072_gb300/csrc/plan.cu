@@ -154,9 +154,8 @@ __global__ void k_w_range(const double *__restrict__ uvw, int64_t nrow, unsigned
 // visibility: its home tile (the tile of its first tap) and each neighbouring
 // tile its W x W footprint spills into.  Lanes with equal keys are aggregated so
 // that one atomic serves the whole group.
-template <bool SCATTER>
-__global__ void k_bucket(const double *__restrict__ uvw, const double *__restrict__ scale,
-                         const int *__restrict__ band, int64_t nvis, int nchan,
+template <typename T, bool SCATTER>
+__global__ void k_bucket(CoordSrc src, const int *__restrict__ band, int64_t nvis, int nchan,
                          const BandGeom *__restrict__ bgs, int *__restrict__ counts,
                          const int64_t *__restrict__ off, uint32_t *__restrict__ items) {
     const int lane = threadIdx.x & 31;
@@ -169,7 +168,7 @@ __global__ void k_bucket(const double *__restrict__ uvw, const double *__restric
             const int64_t row = vis / nchan;
             const int ch = (int)(vis - row * nchan);
             const BandGeom g = bgs[band[ch]];
-            const VisCoord c = vis_coord(uvw, row, scale[ch], g);
+            const VisCoord<T> c = vis_coord<T>(src, row, ch, g);
             const int tu = c.gu0 / TILE, tv = c.gv0 / TILE;
             const bool su = c.gu0 - tu * TILE + g.W - 1 >= TILE;
             const bool sv = c.gv0 - tv * TILE + g.W - 1 >= TILE;
@@ -280,6 +279,20 @@ static void exclusive_scan(Ctx &ctx, const In *in, int64_t n, int64_t *out, cuda
     }
     k_scan_apply<In><<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, boff, out);
     check_launch("scan_apply");
+}
+
+// uvw (FP64) -> double-float pairs (hi, lo) for the FP32 path
+__global__ void k_split_uvw(const double *__restrict__ uvw, int64_t n, float2 *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = uvw[i];
+    const float hi = (float)v;
+    out[i] = make_float2(hi, (float)(v - (double)hi));
+}
+
+static void split_df(double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
 }
 
 __global__ void k_tile_begin(const int64_t *__restrict__ off, int64_t ntb, int nkq, int64_t *__restrict__ out) {
@@ -394,12 +407,28 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     p.d_scale = (double *)ctx.dalloc(p.nchan * sizeof(double));
     p.d_band = (int *)ctx.dalloc(p.nchan * sizeof(int));
     p.d_bg = (BandGeom *)ctx.dalloc(p.nband * sizeof(BandGeom));
-    p.bytes += p.nchan * (sizeof(double) + sizeof(int)) + p.nband * sizeof(BandGeom);
+    p.d_chandf = (ChanDF *)ctx.dalloc(p.nchan * sizeof(ChanDF));
+    p.bytes += p.nchan * (sizeof(double) + sizeof(int) + sizeof(ChanDF)) + p.nband * sizeof(BandGeom);
     std::vector<BandGeom> bgs(p.nband);
     for (int b = 0; b < p.nband; ++b) bgs[b] = p.geom(b);
+    std::vector<ChanDF> cdf(p.nchan);
+    for (int c = 0; c < p.nchan; ++c) {
+        split_df(p.scale[c] * p.dl * p.Nu, cdf[c].su_hi, cdf[c].su_lo);
+        split_df(p.scale[c] * p.dm * p.Nv, cdf[c].sv_hi, cdf[c].sv_lo);
+        split_df(p.wstack ? p.scale[c] / p.dw : 0.0, cdf[c].sw_hi, cdf[c].sw_lo);
+        split_df(p.scale[c] * p.tc, cdf[c].sp_hi, cdf[c].sp_lo);
+    }
     PFB_CUDA(cudaMemcpyAsync(p.d_scale, p.scale.data(), p.nchan * sizeof(double), cudaMemcpyHostToDevice, st));
     PFB_CUDA(cudaMemcpyAsync(p.d_band, p.band_h.data(), p.nchan * sizeof(int), cudaMemcpyHostToDevice, st));
     PFB_CUDA(cudaMemcpyAsync(p.d_bg, bgs.data(), p.nband * sizeof(BandGeom), cudaMemcpyHostToDevice, st));
+    PFB_CUDA(cudaMemcpyAsync(p.d_chandf, cdf.data(), p.nchan * sizeof(ChanDF), cudaMemcpyHostToDevice, st));
+    if (p.prec == PFB_F32) {
+        p.d_rowdf = (float2 *)ctx.dalloc((size_t)p.nrow * 3 * sizeof(float2));
+        p.bytes += (size_t)p.nrow * 3 * sizeof(float2);
+        const int64_t n3 = p.nrow * 3;
+        k_split_uvw<<<(unsigned)((n3 + 255) / 256), 256, 0, st>>>(uvw, n3, p.d_rowdf);
+        check_launch("split_uvw");
+    }
 
     // ---- counting sort of gridding items by key
     const int64_t nvis = p.nrow * (int64_t)p.nchan;
@@ -408,8 +437,12 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     p.d_off = (int64_t *)ctx.dalloc((size_t)(p.nkeys + 1) * sizeof(int64_t));
     p.bytes += (size_t)(p.nkeys + 1) * sizeof(int64_t);
     const int bblocks = (int)std::max<int64_t>(1, std::min<int64_t>((nvis + 255) / 256, 32 * ctx.num_sms));
-    k_bucket<false><<<bblocks, 256, 0, st>>>(uvw, p.d_scale, p.d_band, nvis, p.nchan, p.d_bg, counts,
-                                             nullptr, nullptr);
+    if (p.prec == PFB_F64)
+        k_bucket<double, false><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, counts,
+                                                         nullptr, nullptr);
+    else
+        k_bucket<float, false><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, counts,
+                                                        nullptr, nullptr);
     check_launch("bucket_count");
     exclusive_scan<int>(ctx, counts, p.nkeys, p.d_off, st);
     PFB_CUDA(cudaMemcpyAsync(&p.nitems, p.d_off + p.nkeys, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -417,8 +450,12 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     p.d_items = (uint32_t *)ctx.dalloc((size_t)std::max<int64_t>(p.nitems, 1) * sizeof(uint32_t));
     p.bytes += (size_t)std::max<int64_t>(p.nitems, 1) * sizeof(uint32_t);
     PFB_CUDA(cudaMemsetAsync(counts, 0, (size_t)p.nkeys * sizeof(int), st));
-    k_bucket<true><<<bblocks, 256, 0, st>>>(uvw, p.d_scale, p.d_band, nvis, p.nchan, p.d_bg, counts, p.d_off,
-                                            p.d_items);
+    if (p.prec == PFB_F64)
+        k_bucket<double, true><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, counts,
+                                                        p.d_off, p.d_items);
+    else
+        k_bucket<float, true><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, counts,
+                                                       p.d_off, p.d_items);
     check_launch("bucket_scatter");
 
     // ---- per-tile item ranges -> host -> work list

@@ -48,8 +48,7 @@ __global__ void k_prepass(int nx, int ny, const T *__restrict__ x, const T *__re
 // first plane lies below k_lo add to the partial sum of an earlier block.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ items, int64_t n_items,
-                                                const double *__restrict__ uvw, const double *__restrict__ scale,
-                                                BandGeom g, int k_lo, int k_hi,
+                                                CoordSrc src, BandGeom g, int k_lo, int k_hi,
                                                 const cx_t<T> *__restrict__ planes, cx_t<T> *__restrict__ vis) {
     const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < n_items;
@@ -59,7 +58,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ ite
         const int64_t v = code;
         const int64_t row = v / g.nchan;
         const int ch = (int)(v - row * g.nchan);
-        const VisCoord c = vis_coord(uvw, row, scale[ch], g);
+        const VisCoord<T> c = vis_coord<T>(src, row, ch, g);
         if (c.k0 >= k_hi || c.k0 + g.Ww <= k_lo) continue;
         T ku[MAX_W], kv[MAX_W], kw[MAX_W];
         es_taps<T>(c.ou, g.W, g, ku);
@@ -100,7 +99,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ ite
         }
         // exp(-2 pi i w t_c)
         T cs = 1, sn = 0;
-        if (g.tc != 0.0) cis_turns<T>(c.wl * g.tc, &cs, &sn);
+        if (g.tc != 0.0) sincos_turns(c.ph, &sn, &cs);
         T vr = ar * cs + ai * sn;
         T vi = ai * cs - ar * sn;
         if (c.flip) vi = -vi;
@@ -145,9 +144,7 @@ __device__ __forceinline__ void global_add<double>(double2 *cell, double2 v) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__ work,
                                                     const uint32_t *__restrict__ items,
-                                                    const int64_t *__restrict__ off,
-                                                    const double *__restrict__ uvw,
-                                                    const double *__restrict__ scale,
+                                                    const int64_t *__restrict__ off, CoordSrc src,
                                                     const cx_t<T> *__restrict__ vis, const T *__restrict__ wgt,
                                                     int unit_vis, BandGeom g, int k_lo, int k_hi,
                                                     cx_t<T> *__restrict__ planes) {
@@ -189,13 +186,19 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
         int64_t e = kq < g.nkq ? off[kbase + kq + 1] : wi.end;
         s = max(s, (int64_t)wi.begin);
         e = min(e, (int64_t)wi.end);
-        for (int64_t it = s + threadIdx.x; it < e; it += blockDim.x) {
+        // each thread takes a contiguous run of the bucket's items, so that the 32
+        // lanes of a warp work on items far apart (different rows): consecutive
+        // items are consecutive channels of one row and hit the same cells
+        const int64_t n = e - s;
+        const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+        const int64_t i_beg = s + per * threadIdx.x, i_end = min(e, i_beg + per);
+        for (int64_t it = i_beg; it < i_end; ++it) {
             const uint32_t code = items[it];
             const int64_t v = code & VIS_MASK;
             const int du = (code >> 30) & 1, dv = code >> 31;
             const int64_t row = v / g.nchan;
             const int ch = (int)(v - row * g.nchan);
-            const VisCoord c = vis_coord(uvw, row, scale[ch], g);
+            const VisCoord<T> c = vis_coord<T>(src, row, ch, g);
             if (c.k0 >= k_hi || c.k0 + g.Ww <= k_lo) continue;
             T yr, yi;
             if (unit_vis) { yr = 1; yi = 0; }
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
             // multiply by exp(+2 pi i w t_c) (adjoint of the degridding phase)
             if (g.tc != 0.0) {
                 T cs, sn;
-                cis_turns<T>(c.wl * g.tc, &cs, &sn);
+                sincos_turns(c.ph, &sn, &cs);
                 const T r0 = yr * cs - yi * sn;
                 yi = yr * sn + yi * cs;
                 yr = r0;
@@ -400,7 +403,7 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
             if (i1 > i0) {
                 KTimer t(ctx, "gather", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
                 k_gather<T><<<grid_blocks(i1 - i0, 256, 64 * ctx.num_sms), 256, 0, st>>>(
-                    p.d_items + i0, i1 - i0, (const double *)p.uvw, p.d_scale, g, k_lo, k_hi, planes, vis);
+                    p.d_items + i0, i1 - i0, p.coords(), g, k_lo, k_hi, planes, vis);
                 check_launch("gather");
             }
         }
@@ -438,7 +441,7 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                 const double wb = wgt ? (double)sizeof(T) : 0.0;
                 KTimer t(ctx, "grid_tiles", st, 4.0 * nit + nvb * (vb + wb) + nk * plane_bytes);
                 k_grid_tiles<T><<<(unsigned)(w1 - w0), 256, smem, st>>>(p.d_work + w0, p.d_items, p.d_off,
-                                                                         (const double *)p.uvw, p.d_scale, vis, wgt,
+                                                                         p.coords(), vis, wgt,
                                                                          unit_vis ? 1 : 0, g, k_lo, k_hi, planes);
                 check_launch("grid_tiles");
             }

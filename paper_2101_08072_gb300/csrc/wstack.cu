@@ -255,6 +255,348 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
     }
 }
 
+// ------------------------------------------------------------------ FP32 gridding by residue classes
+// Same work decomposition and plane ring as k_grid_tiles, but the scatter is
+// organised so that threads do not contend: the items of a bucket are staged in
+// chunks of CH records (first-tap cell, ES taps, weighted value times the w taps),
+// and each group of W^2 threads sweeps a contiguous run of records.  Thread (a, b)
+// of a group owns the footprint cell whose local indices are congruent to
+// (a, b) mod W (exactly one per visibility), accumulates its W_w plane
+// contributions in registers while consecutive visibilities (neighbouring
+// channels of one row) keep it on the same cell, and adds them to the shared
+// ring only when its cell changes.  Cells of different threads of a group never
+// coincide; only different groups can meet, so the ring adds stay atomic but
+// rarely collide.
+constexpr int RES_CH = 256;
+
+struct ResSmem {
+    // byte offsets of the record arrays after the ring
+    int cell, gmod, k0, ku, kv, wy, total;
+};
+
+__host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
+    ResSmem L;
+    int o = R * TILE * TILE * (int)sizeof(float2);
+    L.cell = o; o += RES_CH * (int)sizeof(short2);
+    L.gmod = o; o += RES_CH * (int)sizeof(char2);
+    o = (o + 15) & ~15;
+    L.k0 = o; o += RES_CH * (int)sizeof(int);
+    L.ku = o; o += RES_CH * W * (int)sizeof(float);
+    L.kv = o; o += RES_CH * W * (int)sizeof(float);
+    o = (o + 15) & ~15;
+    L.wy = o; o += RES_CH * Ww * (int)sizeof(float2);
+    L.total = o;
+    return L;
+}
+
+template <int W, int Ww>
+__global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ work,
+                                                  const uint32_t *__restrict__ items,
+                                                  const int64_t *__restrict__ off, CoordSrc src,
+                                                  const float2 *__restrict__ vis, const float *__restrict__ wgt,
+                                                  int unit_vis, BandGeom g, int k_lo, int k_hi,
+                                                  float2 *__restrict__ planes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int R = Ww + g.q - 1;
+    const ResSmem L = res_layout(R, W, Ww);
+    float2 *ring = reinterpret_cast<float2 *>(smem_raw);
+    short2 *rcell = reinterpret_cast<short2 *>(smem_raw + L.cell);
+    char2 *rgmod = reinterpret_cast<char2 *>(smem_raw + L.gmod);
+    int *rk0 = reinterpret_cast<int *>(smem_raw + L.k0);
+    float *rku = reinterpret_cast<float *>(smem_raw + L.ku);
+    float *rkv = reinterpret_cast<float *>(smem_raw + L.kv);
+    float2 *rwy = reinterpret_cast<float2 *>(smem_raw + L.wy);
+    const int cells = TILE * TILE;
+    const WorkItem wi = work[blockIdx.x];
+    const int tu = wi.tile / g.ntv, tv = wi.tile - tu * g.ntv;
+    const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
+    for (int e = threadIdx.x; e < R * cells; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
+
+    // group geometry
+    const int G = W * W;
+    const int ngroups = blockDim.x / G;
+    const int grp = threadIdx.x / G, lid = threadIdx.x - grp * G;
+    const int ta = lid / W, tb = lid - ta * W;
+    const bool in_group = grp < ngroups;
+
+    const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
+    int kq_first, kq_last;
+    if (!wi.atomic_mode) {
+        kq_first = max(0, (k_lo - Ww + 1) / g.q);
+        kq_last = (k_hi - 1) / g.q;
+    } else {
+        if (wi.end <= wi.begin) return;
+        int lo = 0, hi = g.nkq - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (off[kbase + mid] <= wi.begin) lo = mid; else hi = mid - 1;
+        }
+        kq_first = lo;
+        lo = kq_first; hi = g.nkq - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (off[kbase + mid] <= wi.end - 1) lo = mid; else hi = mid - 1;
+        }
+        kq_last = lo + (Ww - 1 + g.q - 1) / g.q;
+        kq_first = max(kq_first, max(0, (k_lo - Ww + 1) / g.q));
+        kq_last = min(kq_last, (k_hi - 1) / g.q);
+    }
+    __syncthreads();
+
+    float2 acc[Ww];
+    int cu = -1000, cv = -1000, ck = -1000;
+    auto flush = [&]() {
+        if (cu >= 0 && cu < TILE && cv >= 0 && cv < TILE) {
+#pragma unroll
+            for (int c = 0; c < Ww; ++c) {
+                const int k = ck + c;
+                if (k >= k_lo && k < k_hi && (acc[c].x != 0.f || acc[c].y != 0.f)) {
+                    float2 *cell = ring + (k % R) * cells + cu * TILE + cv;
+                    atomicAdd(&cell->x, acc[c].x);
+                    atomicAdd(&cell->y, acc[c].y);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
+        cu = cv = ck = -1000;
+    };
+#pragma unroll
+    for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
+
+    for (int kq = kq_first; kq <= kq_last; ++kq) {
+        int64_t s = kq < g.nkq ? off[kbase + kq] : wi.end;
+        int64_t e = kq < g.nkq ? off[kbase + kq + 1] : wi.end;
+        s = max(s, (int64_t)wi.begin);
+        e = min(e, (int64_t)wi.end);
+        for (int64_t c0 = s; c0 < e; c0 += RES_CH) {
+            const int cnt = (int)min((int64_t)RES_CH, e - c0);
+            // ---- stage records
+            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+                const uint32_t code = items[c0 + t];
+                const int64_t v = code & VIS_MASK;
+                const int du = (code >> 30) & 1, dv = code >> 31;
+                const int64_t row = v / g.nchan;
+                const int ch = (int)(v - row * g.nchan);
+                const VisCoord<float> c = vis_coord<float>(src, row, ch, g);
+                if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
+                    rcell[t] = make_short2(-30000, -30000);
+                    continue;
+                }
+                float yr, yi;
+                if (unit_vis) { yr = 1.f; yi = 0.f; }
+                else { const float2 y = vis[v]; yr = y.x; yi = y.y; }
+                if (wgt) { const float w = wgt[v]; yr *= w; yi *= w; }
+                if (c.flip) yi = -yi;
+                if (g.tc != 0.0) {
+                    float cs, sn;
+                    sincos_turns(c.ph, &sn, &cs);
+                    const float r0 = yr * cs - yi * sn;
+                    yi = yr * sn + yi * cs;
+                    yr = r0;
+                }
+                const int lu = c.gu0 - (c.gu0 / TILE) * TILE - du * TILE;
+                const int lv = c.gv0 - (c.gv0 / TILE) * TILE - dv * TILE;
+                rcell[t] = make_short2((short)lu, (short)lv);
+                int mu = lu % W, mv = lv % W;
+                mu += mu < 0 ? W : 0;
+                mv += mv < 0 ? W : 0;
+                rgmod[t] = make_char2((char)mu, (char)mv);
+                rk0[t] = c.k0;
+                const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    rku[t * W + i] = es_kernel(c.ou + (float)i, ihw, bt);
+                    rkv[t * W + i] = es_kernel(c.ov + (float)i, ihw, bt);
+                }
+                if (Ww > 1) {
+#pragma unroll
+                    for (int i = 0; i < Ww; ++i) {
+                        const float kw = es_kernel(c.ow + (float)i, ihw, bt);
+                        rwy[t * Ww + i] = make_float2(kw * yr, kw * yi);
+                    }
+                } else {
+                    rwy[t] = make_float2(yr, yi);
+                }
+            }
+            __syncthreads();
+            // ---- scatter by residue classes
+            if (in_group) {
+                const int per = (cnt + ngroups - 1) / ngroups;
+                const int r0 = grp * per, r1 = min(cnt, r0 + per);
+                for (int r = r0; r < r1; ++r) {
+                    const short2 gc = rcell[r];
+                    if (gc.x == -30000) continue;
+                    const char2 gm = rgmod[r];
+                    int ap = ta - gm.x, bp = tb - gm.y;
+                    ap += ap < 0 ? W : 0;
+                    bp += bp < 0 ? W : 0;
+                    const int nu = gc.x + ap, nv = gc.y + bp, nk = rk0[r];
+                    if (nu != cu || nv != cv || nk != ck) {
+                        flush();
+                        cu = nu; cv = nv; ck = nk;
+                    }
+                    const float wuv = rku[r * W + ap] * rkv[r * W + bp];
+                    const float2 *wy = rwy + r * Ww;
+#pragma unroll
+                    for (int c = 0; c < Ww; ++c) {
+                        const float2 q = wy[c];
+                        acc[c].x = fmaf(wuv, q.x, acc[c].x);
+                        acc[c].y = fmaf(wuv, q.y, acc[c].y);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (in_group) flush();
+        __syncthreads();
+        // planes [kq q, kq q + q) are complete
+        const int p0 = max(kq * g.q, k_lo), p1 = min(kq * g.q + g.q, k_hi);
+        for (int k = p0; k < p1; ++k) {
+            float2 *slot = ring + (k % R) * cells;
+            float2 *dst = planes + (int64_t)(k - k_lo) * plane_sz + (int64_t)(tu * TILE) * g.Nv + tv * TILE;
+            for (int e2 = threadIdx.x; e2 < cells; e2 += blockDim.x) {
+                const int r = e2 / TILE, cc = e2 - r * TILE;
+                const float2 val = slot[e2];
+                if (wi.atomic_mode) {
+                    if (val.x != 0.f || val.y != 0.f) atomicAdd(dst + (int64_t)r * g.Nv + cc, val);
+                } else {
+                    dst[(int64_t)r * g.Nv + cc] = val;
+                }
+                slot[e2] = make_float2(0.f, 0.f);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ FP32 degridding from staged tiles
+// One CTA per work item (home items of a tile, or a chunk of a heavy tile).  The
+// tile's footprint region of (TILE + W - 1)^2 cells is staged in shared memory for
+// the planes the current w bucket needs (a ring of W_w + q - 1 planes, refilled as
+// the buckets advance), with coalesced 8-byte loads; then one thread per home item
+// interpolates from shared memory.
+template <int W, int Ww>
+__global__ void __launch_bounds__(256) k_degrid_tiles(const WorkItem *__restrict__ work,
+                                                      const uint32_t *__restrict__ items,
+                                                      const int64_t *__restrict__ off, CoordSrc src, BandGeom g,
+                                                      int k_lo, int k_hi, const float2 *__restrict__ planes,
+                                                      float2 *__restrict__ vis) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *reg = reinterpret_cast<float2 *>(smem_raw);
+    __shared__ int slot_plane[MAX_W + 32];
+    const int R = Ww + g.q - 1;
+    const int E = TILE + W - 1;          // region edge
+    const int ES = E | 1;                // odd row stride: fewer bank conflicts
+    const int reg_sz = E * ES;
+    const WorkItem wi = work[blockIdx.x];
+    if (wi.end <= wi.begin) return;
+    const int tu = wi.tile / g.ntv, tv = wi.tile - tu * g.ntv;
+    const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
+    const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) slot_plane[i] = -1;
+    int lo = 0, hi = g.nkq - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[kbase + mid] <= wi.begin) lo = mid; else hi = mid - 1;
+    }
+    const int kq_first = lo;
+    lo = kq_first; hi = g.nkq - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[kbase + mid] <= wi.end - 1) lo = mid; else hi = mid - 1;
+    }
+    const int kq_last = lo;
+    __syncthreads();
+    for (int kq = kq_first; kq <= kq_last; ++kq) {
+        const int64_t s = max(off[kbase + kq], (int64_t)wi.begin), e = min(off[kbase + kq + 1], (int64_t)wi.end);
+        if (e <= s) continue;
+        // planes this bucket needs, clipped to the block
+        const int pa = max(kq * g.q, k_lo), pb = min(kq * g.q + g.q + Ww - 1, k_hi);
+        if (pa >= pb) continue;
+        // load missing planes into their ring slots
+        bool loaded = false;
+        for (int k = pa; k < pb; ++k) {
+            const int sl = k % R;
+            if (slot_plane[sl] == k) continue;
+            loaded = true;
+            float2 *dst = reg + sl * reg_sz;
+            const float2 *srcp = planes + (int64_t)(k - k_lo) * plane_sz;
+            for (int i = threadIdx.x; i < E * E; i += blockDim.x) {
+                const int r = i / E, c = i - r * E;
+                int gu = tu * TILE + r, gv = tv * TILE + c;
+                gu -= gu >= g.Nu ? g.Nu : 0;
+                gv -= gv >= g.Nv ? g.Nv : 0;
+                dst[r * ES + c] = srcp[(int64_t)gu * g.Nv + gv];
+            }
+        }
+        __syncthreads();
+        if (loaded && threadIdx.x == 0)
+            for (int k = pa; k < pb; ++k) slot_plane[k % R] = k;
+        for (int64_t it = s + threadIdx.x; it < e; it += blockDim.x) {
+            const uint32_t code = items[it];
+            if (code >> 30) continue;
+            const int64_t v = code;
+            const int64_t row = v / g.nchan;
+            const int ch = (int)(v - row * g.nchan);
+            const VisCoord<float> c = vis_coord<float>(src, row, ch, g);
+            if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) continue;
+            const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
+            float ku[W], kv[W], kw[Ww];
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                ku[i] = es_kernel(c.ou + (float)i, ihw, bt);
+                kv[i] = es_kernel(c.ov + (float)i, ihw, bt);
+            }
+            if (Ww > 1) {
+#pragma unroll
+                for (int i = 0; i < Ww; ++i) kw[i] = es_kernel(c.ow + (float)i, ihw, bt);
+            } else {
+                kw[0] = 1.f;
+            }
+            const int lu = c.gu0 - tu * TILE, lv = c.gv0 - tv * TILE;
+            float ar = 0.f, ai = 0.f;
+#pragma unroll
+            for (int cw = 0; cw < Ww; ++cw) {
+                const int k = c.k0 + cw;
+                if (k < k_lo || k >= k_hi) continue;
+                const float2 *pl = reg + (k % R) * reg_sz + lu * ES + lv;
+                float pr = 0.f, pi = 0.f;
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const float2 *prow = pl + a * ES;
+                    float rr = 0.f, ri = 0.f;
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        const float2 q = prow[b];
+                        rr = fmaf(kv[b], q.x, rr);
+                        ri = fmaf(kv[b], q.y, ri);
+                    }
+                    pr = fmaf(ku[a], rr, pr);
+                    pi = fmaf(ku[a], ri, pi);
+                }
+                ar = fmaf(kw[cw], pr, ar);
+                ai = fmaf(kw[cw], pi, ai);
+            }
+            float cs = 1.f, sn = 0.f;
+            if (g.tc != 0.0) sincos_turns(c.ph, &sn, &cs);
+            const float vr = ar * cs + ai * sn;
+            float vi = ai * cs - ar * sn;
+            if (c.flip) vi = -vi;
+            float2 out;
+            if (c.k0 < k_lo) {
+                out = vis[v];
+                out.x += vr;
+                out.y += vi;
+            } else {
+                out = make_float2(vr, vi);
+            }
+            vis[v] = out;
+        }
+        __syncthreads();
+    }
+}
+
 // Zero the cells of heavy tiles (filled by reductions) in planes [0, nplanes).
 template <typename T>
 __global__ void k_zero_tiles(const int *__restrict__ tiles, int ntiles, int ntv, int Nv, int64_t plane_sz,
@@ -363,6 +705,45 @@ static unsigned grid_blocks(int64_t n, int threads, int cap) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
+// ------------------------------------------------------------------ FP32 kernel dispatch on W
+static bool fast_path_f32(const Plan &p) { return p.prec == PFB_F32 && p.W >= 4 && p.W <= 8; }
+static bool degrid_tiles_fit(const Plan &p) {
+    const int R = p.Ww + p.q - 1, E = TILE + p.W - 1, ES = E | 1;
+    return fast_path_f32(p) && (size_t)R * E * ES * sizeof(float2) <= 227 * 1024;
+}
+static bool grid_res_fit(const Plan &p) {
+    return fast_path_f32(p) && (size_t)res_layout(p.Ww + p.q - 1, p.W, p.Ww).total <= 227 * 1024;
+}
+
+template <int W, int Ww>
+static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkItem *work, const Plan &p,
+                              const float2 *vis, const float *wgt, int unit, const BandGeom &g, int k_lo, int k_hi,
+                              float2 *planes) {
+    const size_t smem = (size_t)res_layout(R, W, Ww).total;
+    PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_grid_res<W, Ww><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo, k_hi,
+                                               planes);
+}
+
+template <int W, int Ww>
+static void launch_degrid_t(unsigned nblk, int R, cudaStream_t st, const WorkItem *work, const Plan &p,
+                            const BandGeom &g, int k_lo, int k_hi, const float2 *planes, float2 *vis) {
+    const int E = TILE + W - 1, ES = E | 1;
+    const size_t smem = (size_t)R * E * ES * sizeof(float2);
+    PFB_CUDA(cudaFuncSetAttribute(k_degrid_tiles<W, Ww>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_degrid_tiles<W, Ww><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), g, k_lo, k_hi, planes, vis);
+}
+
+#define PFB_W_SWITCH(W, WS, CALL)                                                     \
+    switch (W) {                                                                    \
+        case 4: if (WS) CALL(4, 4); else CALL(4, 1); break;                          \
+        case 5: if (WS) CALL(5, 5); else CALL(5, 1); break;                          \
+        case 6: if (WS) CALL(6, 6); else CALL(6, 1); break;                          \
+        case 7: if (WS) CALL(7, 7); else CALL(7, 1); break;                          \
+        case 8: if (WS) CALL(8, 8); else CALL(8, 1); break;                          \
+        default: throw Error(PFB_ERR_ARG, "no FP32 kernel for this support");        \
+    }
+
 // ------------------------------------------------------------------ operators
 // visibilities of band b (rows x channels mapped to b)
 static int64_t band_nvis(const Plan &p, int b) {
@@ -400,7 +781,17 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
                 KTimer t(ctx, "fft_fwd", st, 2.0 * nk * plane_bytes, 0);
                 fft_planes<T>(ctx, planes, nk, p.Nu, p.Nv, CUFFT_FORWARD, st);
             }
-            if (i1 > i0) {
+            if (i1 > i0 && sizeof(T) == 4 && degrid_tiles_fit(p)) {
+                KTimer t(ctx, "degrid_tiles", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
+                const int64_t w0 = p.work_begin[b], w1 = p.work_begin[b + 1];
+                const int R = p.Ww + p.q - 1;
+#define PFB_DEGRID_CALL(WV, WWV)                                                                          \
+    launch_degrid_t<WV, WWV>((unsigned)(w1 - w0), R, st, p.d_work + w0, p, g, k_lo, k_hi, (const float2 *)planes, \
+                             (float2 *)vis)
+                PFB_W_SWITCH(p.W, p.wstack, PFB_DEGRID_CALL)
+#undef PFB_DEGRID_CALL
+                check_launch("degrid_tiles");
+            } else if (i1 > i0) {
                 KTimer t(ctx, "gather", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
                 k_gather<T><<<grid_blocks(i1 - i0, 256, 64 * ctx.num_sms), 256, 0, st>>>(
                     p.d_items + i0, i1 - i0, p.coords(), g, k_lo, k_hi, planes, vis);
@@ -440,9 +831,18 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                 const double vb = unit_vis ? 0.0 : (double)cxs;
                 const double wb = wgt ? (double)sizeof(T) : 0.0;
                 KTimer t(ctx, "grid_tiles", st, 4.0 * nit + nvb * (vb + wb) + nk * plane_bytes);
-                k_grid_tiles<T><<<(unsigned)(w1 - w0), 256, smem, st>>>(p.d_work + w0, p.d_items, p.d_off,
-                                                                         p.coords(), vis, wgt,
-                                                                         unit_vis ? 1 : 0, g, k_lo, k_hi, planes);
+                if (sizeof(T) == 4 && grid_res_fit(p)) {
+                    const int R = p.Ww + p.q - 1;
+#define PFB_GRID_CALL(WV, WWV)                                                                            \
+    launch_grid_res_t<WV, WWV>((unsigned)(w1 - w0), R, st, p.d_work + w0, p, (const float2 *)vis,          \
+                               (const float *)wgt, unit_vis ? 1 : 0, g, k_lo, k_hi, (float2 *)planes)
+                    PFB_W_SWITCH(p.W, p.wstack, PFB_GRID_CALL)
+#undef PFB_GRID_CALL
+                } else {
+                    k_grid_tiles<T><<<(unsigned)(w1 - w0), 256, smem, st>>>(p.d_work + w0, p.d_items, p.d_off,
+                                                                             p.coords(), vis, wgt,
+                                                                             unit_vis ? 1 : 0, g, k_lo, k_hi, planes);
+                }
                 check_launch("grid_tiles");
             }
             {

@@ -101,7 +101,17 @@ struct BandGeom {
     // an integer and a fraction so that the cell arithmetic stays exact
     int uv_oi, w_oi;
     float uv_of, w_of, hw;
+    float inv_Nu, inv_Nv;
 };
+
+// x mod n in [0, n) for |x| < 2^24, by a float reciprocal and one correction
+__device__ __forceinline__ int wrap_mod(int x, int n, float inv_n) {
+    int q = (int)floorf((float)x * inv_n);
+    int r = x - q * n;
+    r += r < 0 ? n : 0;
+    r -= r >= n ? n : 0;
+    return r;
+}
 
 // Per-row / per-channel factors of the FP32 path, each FP64 value stored as an
 // unevaluated sum hi + lo of two floats (double-float, Dekker 1971).
@@ -189,12 +199,10 @@ __device__ __forceinline__ VisCoord<float> vis_coord32(const float2 *__restrict_
     int g0;
     df_mul(u.x, u.y, cs.su_hi, cs.su_lo, p, e);
     df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ou);
-    g0 %= g.Nu;
-    c.gu0 = g0 < 0 ? g0 + g.Nu : g0;
+    c.gu0 = wrap_mod(g0, g.Nu, g.inv_Nu);
     df_mul(v.x, v.y, cs.sv_hi, cs.sv_lo, p, e);
     df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ov);
-    g0 %= g.Nv;
-    c.gv0 = g0 < 0 ? g0 + g.Nv : g0;
+    c.gv0 = wrap_mod(g0, g.Nv, g.inv_Nv);
     df_mul(w.x, w.y, cs.sp_hi, cs.sp_lo, p, e);
     c.ph = (p - rintf(p)) + e;
     if (g.Ww > 1) {

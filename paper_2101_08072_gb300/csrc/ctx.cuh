@@ -69,6 +69,8 @@ struct Plan {
         const double O = wstack ? hw + w0[b] / dw : hw;
         g.w_oi = (int)std::floor(O);
         g.w_of = (float)(O - std::floor(O));
+        g.inv_Nu = 1.0f / (float)Nu;
+        g.inv_Nv = 1.0f / (float)Nv;
         return g;
     }
     CoordSrc coords() const { return CoordSrc{(const double *)uvw, d_scale, d_rowdf, d_chandf}; }

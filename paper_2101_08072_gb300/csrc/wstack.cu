@@ -269,6 +269,12 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 // rarely collide.
 constexpr int RES_CH = 256;
 
+__host__ __device__ inline int ring_pow2(int n) {
+    int r = 1;
+    while (r < n) r <<= 1;
+    return r;
+}
+
 struct ResSmem {
     // byte offsets of the record arrays after the ring
     int cell, gmod, k0, ku, kv, wy, total;
@@ -297,7 +303,7 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
                                                   int unit_vis, BandGeom g, int k_lo, int k_hi,
                                                   float2 *__restrict__ planes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int R = Ww + g.q - 1;
+    const int R = ring_pow2(Ww + g.q - 1);   // slot of plane k: k & (R - 1)
     const ResSmem L = res_layout(R, W, Ww);
     float2 *ring = reinterpret_cast<float2 *>(smem_raw);
     short2 *rcell = reinterpret_cast<short2 *>(smem_raw + L.cell);
@@ -351,7 +357,7 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
             for (int c = 0; c < Ww; ++c) {
                 const int k = ck + c;
                 if (k >= k_lo && k < k_hi && (acc[c].x != 0.f || acc[c].y != 0.f)) {
-                    float2 *cell = ring + (k % R) * cells + cu * TILE + cv;
+                    float2 *cell = ring + (k & (R - 1)) * cells + cu * TILE + cv;
                     atomicAdd(&cell->x, acc[c].x);
                     atomicAdd(&cell->y, acc[c].y);
                 }
@@ -374,10 +380,10 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
             // ---- stage records
             for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
                 const uint32_t code = items[c0 + t];
-                const int64_t v = code & VIS_MASK;
+                const uint32_t v = code & VIS_MASK;
                 const int du = (code >> 30) & 1, dv = code >> 31;
-                const int64_t row = v / g.nchan;
-                const int ch = (int)(v - row * g.nchan);
+                const uint32_t row = v / (uint32_t)g.nchan;
+                const int ch = (int)(v - row * (uint32_t)g.nchan);
                 const VisCoord<float> c = vis_coord<float>(src, row, ch, g);
                 if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
                     rcell[t] = make_short2(-30000, -30000);
@@ -453,7 +459,7 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
         // planes [kq q, kq q + q) are complete
         const int p0 = max(kq * g.q, k_lo), p1 = min(kq * g.q + g.q, k_hi);
         for (int k = p0; k < p1; ++k) {
-            float2 *slot = ring + (k % R) * cells;
+            float2 *slot = ring + (k & (R - 1)) * cells;
             float2 *dst = planes + (int64_t)(k - k_lo) * plane_sz + (int64_t)(tu * TILE) * g.Nv + tv * TILE;
             for (int e2 = threadIdx.x; e2 < cells; e2 += blockDim.x) {
                 const int r = e2 / TILE, cc = e2 - r * TILE;
@@ -484,8 +490,8 @@ __global__ void __launch_bounds__(256) k_degrid_tiles(const WorkItem *__restrict
                                                       float2 *__restrict__ vis) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *reg = reinterpret_cast<float2 *>(smem_raw);
-    __shared__ int slot_plane[MAX_W + 32];
-    const int R = Ww + g.q - 1;
+    __shared__ int slot_plane[64];
+    const int R = ring_pow2(Ww + g.q - 1);   // slot of plane k: k & (R - 1)
     const int E = TILE + W - 1;          // region edge
     const int ES = E | 1;                // odd row stride: fewer bank conflicts
     const int reg_sz = E * ES;
@@ -517,7 +523,7 @@ __global__ void __launch_bounds__(256) k_degrid_tiles(const WorkItem *__restrict
         // load missing planes into their ring slots
         bool loaded = false;
         for (int k = pa; k < pb; ++k) {
-            const int sl = k % R;
+            const int sl = k & (R - 1);
             if (slot_plane[sl] == k) continue;
             loaded = true;
             float2 *dst = reg + sl * reg_sz;
@@ -532,13 +538,13 @@ __global__ void __launch_bounds__(256) k_degrid_tiles(const WorkItem *__restrict
         }
         __syncthreads();
         if (loaded && threadIdx.x == 0)
-            for (int k = pa; k < pb; ++k) slot_plane[k % R] = k;
+            for (int k = pa; k < pb; ++k) slot_plane[k & (R - 1)] = k;
         for (int64_t it = s + threadIdx.x; it < e; it += blockDim.x) {
             const uint32_t code = items[it];
             if (code >> 30) continue;
-            const int64_t v = code;
-            const int64_t row = v / g.nchan;
-            const int ch = (int)(v - row * g.nchan);
+            const uint32_t v = code;
+            const uint32_t row = v / (uint32_t)g.nchan;
+            const int ch = (int)(v - row * (uint32_t)g.nchan);
             const VisCoord<float> c = vis_coord<float>(src, row, ch, g);
             if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) continue;
             const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
@@ -560,7 +566,7 @@ __global__ void __launch_bounds__(256) k_degrid_tiles(const WorkItem *__restrict
             for (int cw = 0; cw < Ww; ++cw) {
                 const int k = c.k0 + cw;
                 if (k < k_lo || k >= k_hi) continue;
-                const float2 *pl = reg + (k % R) * reg_sz + lu * ES + lv;
+                const float2 *pl = reg + (k & (R - 1)) * reg_sz + lu * ES + lv;
                 float pr = 0.f, pi = 0.f;
 #pragma unroll
                 for (int a = 0; a < W; ++a) {
@@ -708,11 +714,11 @@ static unsigned grid_blocks(int64_t n, int threads, int cap) {
 // ------------------------------------------------------------------ FP32 kernel dispatch on W
 static bool fast_path_f32(const Plan &p) { return p.prec == PFB_F32 && p.W >= 4 && p.W <= 8; }
 static bool degrid_tiles_fit(const Plan &p) {
-    const int R = p.Ww + p.q - 1, E = TILE + p.W - 1, ES = E | 1;
+    const int R = ring_pow2(p.Ww + p.q - 1), E = TILE + p.W - 1, ES = E | 1;
     return fast_path_f32(p) && (size_t)R * E * ES * sizeof(float2) <= 227 * 1024;
 }
 static bool grid_res_fit(const Plan &p) {
-    return fast_path_f32(p) && (size_t)res_layout(p.Ww + p.q - 1, p.W, p.Ww).total <= 227 * 1024;
+    return fast_path_f32(p) && (size_t)res_layout(ring_pow2(p.Ww + p.q - 1), p.W, p.Ww).total <= 227 * 1024;
 }
 
 template <int W, int Ww>
@@ -784,7 +790,7 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
             if (i1 > i0 && sizeof(T) == 4 && degrid_tiles_fit(p)) {
                 KTimer t(ctx, "degrid_tiles", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
                 const int64_t w0 = p.work_begin[b], w1 = p.work_begin[b + 1];
-                const int R = p.Ww + p.q - 1;
+                const int R = ring_pow2(p.Ww + p.q - 1);
 #define PFB_DEGRID_CALL(WV, WWV)                                                                          \
     launch_degrid_t<WV, WWV>((unsigned)(w1 - w0), R, st, p.d_work + w0, p, g, k_lo, k_hi, (const float2 *)planes, \
                              (float2 *)vis)
@@ -832,7 +838,7 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                 const double wb = wgt ? (double)sizeof(T) : 0.0;
                 KTimer t(ctx, "grid_tiles", st, 4.0 * nit + nvb * (vb + wb) + nk * plane_bytes);
                 if (sizeof(T) == 4 && grid_res_fit(p)) {
-                    const int R = p.Ww + p.q - 1;
+                    const int R = ring_pow2(p.Ww + p.q - 1);
 #define PFB_GRID_CALL(WV, WWV)                                                                            \
     launch_grid_res_t<WV, WWV>((unsigned)(w1 - w0), R, st, p.d_work + w0, p, (const float2 *)vis,          \
                                (const float *)wgt, unit_vis ? 1 : 0, g, k_lo, k_hi, (float2 *)planes)

@@ -316,42 +316,43 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
     const WorkItem wi = work[blockIdx.x];
     const int tu = wi.tile / g.ntv, tv = wi.tile - tu * g.ntv;
     const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
+    float2 *tile0 = planes + (int64_t)(tu * TILE) * g.Nv + tv * TILE;
+
+    if (wi.end <= wi.begin) {
+        // no items: the tile's cells of every plane of the block are zero
+        if (!wi.atomic_mode) {
+            const int nk = k_hi - k_lo;
+            for (int e = threadIdx.x; e < nk * cells / 2; e += blockDim.x) {
+                const int k = e / (cells / 2), c2 = e - k * (cells / 2);
+                const int r = c2 / (TILE / 2), cc = (c2 - r * (TILE / 2)) * 2;
+                *reinterpret_cast<float4 *>(tile0 + (int64_t)k * plane_sz + (int64_t)r * g.Nv + cc) =
+                    make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        return;
+    }
     for (int e = threadIdx.x; e < R * cells; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
 
-    // group geometry
+    // group geometry: thread (ta, tb) of a group owns the cells congruent to (ta, tb) mod W
     const int G = W * W;
     const int ngroups = blockDim.x / G;
     const int grp = threadIdx.x / G, lid = threadIdx.x - grp * G;
     const int ta = lid / W, tb = lid - ta * W;
     const bool in_group = grp < ngroups;
-
     const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
-    int kq_first, kq_last;
-    if (!wi.atomic_mode) {
-        kq_first = max(0, (k_lo - Ww + 1) / g.q);
-        kq_last = (k_hi - 1) / g.q;
-    } else {
-        if (wi.end <= wi.begin) return;
+    // bucket (w quantum) of an item position, by binary search in the tile's offsets
+    auto bucket_of = [&](int64_t pos) {
         int lo = 0, hi = g.nkq - 1;
         while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (off[kbase + mid] <= wi.begin) lo = mid; else hi = mid - 1;
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[kbase + mid] <= pos) lo = mid; else hi = mid - 1;
         }
-        kq_first = lo;
-        lo = kq_first; hi = g.nkq - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (off[kbase + mid] <= wi.end - 1) lo = mid; else hi = mid - 1;
-        }
-        kq_last = lo + (Ww - 1 + g.q - 1) / g.q;
-        kq_first = max(kq_first, max(0, (k_lo - Ww + 1) / g.q));
-        kq_last = min(kq_last, (k_hi - 1) / g.q);
-    }
-    __syncthreads();
+        return lo;
+    };
 
     float2 acc[Ww];
     int cu = -1000, cv = -1000, ck = -1000;
-    auto flush = [&]() {
+    auto flush_acc = [&]() {
         if (cu >= 0 && cu < TILE && cv >= 0 && cv < TILE) {
 #pragma unroll
             for (int c = 0; c < Ww; ++c) {
@@ -369,98 +370,13 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
     };
 #pragma unroll
     for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
-
-    for (int kq = kq_first; kq <= kq_last; ++kq) {
-        int64_t s = kq < g.nkq ? off[kbase + kq] : wi.end;
-        int64_t e = kq < g.nkq ? off[kbase + kq + 1] : wi.end;
-        s = max(s, (int64_t)wi.begin);
-        e = min(e, (int64_t)wi.end);
-        for (int64_t c0 = s; c0 < e; c0 += RES_CH) {
-            const int cnt = (int)min((int64_t)RES_CH, e - c0);
-            // ---- stage records
-            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-                const uint32_t code = items[c0 + t];
-                const uint32_t v = code & VIS_MASK;
-                const int du = (code >> 30) & 1, dv = code >> 31;
-                const uint32_t row = v / (uint32_t)g.nchan;
-                const int ch = (int)(v - row * (uint32_t)g.nchan);
-                const VisCoord<float> c = vis_coord<float>(src, row, ch, g);
-                if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
-                    rcell[t] = make_short2(-30000, -30000);
-                    continue;
-                }
-                float yr, yi;
-                if (unit_vis) { yr = 1.f; yi = 0.f; }
-                else { const float2 y = vis[v]; yr = y.x; yi = y.y; }
-                if (wgt) { const float w = wgt[v]; yr *= w; yi *= w; }
-                if (c.flip) yi = -yi;
-                if (g.tc != 0.0) {
-                    float cs, sn;
-                    sincos_turns(c.ph, &sn, &cs);
-                    const float r0 = yr * cs - yi * sn;
-                    yi = yr * sn + yi * cs;
-                    yr = r0;
-                }
-                const int lu = c.gu0 - (c.gu0 / TILE) * TILE - du * TILE;
-                const int lv = c.gv0 - (c.gv0 / TILE) * TILE - dv * TILE;
-                rcell[t] = make_short2((short)lu, (short)lv);
-                int mu = lu % W, mv = lv % W;
-                mu += mu < 0 ? W : 0;
-                mv += mv < 0 ? W : 0;
-                rgmod[t] = make_char2((char)mu, (char)mv);
-                rk0[t] = c.k0;
-                const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
-#pragma unroll
-                for (int i = 0; i < W; ++i) {
-                    rku[t * W + i] = es_kernel(c.ou + (float)i, ihw, bt);
-                    rkv[t * W + i] = es_kernel(c.ov + (float)i, ihw, bt);
-                }
-                if (Ww > 1) {
-#pragma unroll
-                    for (int i = 0; i < Ww; ++i) {
-                        const float kw = es_kernel(c.ow + (float)i, ihw, bt);
-                        rwy[t * Ww + i] = make_float2(kw * yr, kw * yi);
-                    }
-                } else {
-                    rwy[t] = make_float2(yr, yi);
-                }
-            }
-            __syncthreads();
-            // ---- scatter by residue classes
-            if (in_group) {
-                const int per = (cnt + ngroups - 1) / ngroups;
-                const int r0 = grp * per, r1 = min(cnt, r0 + per);
-                for (int r = r0; r < r1; ++r) {
-                    const short2 gc = rcell[r];
-                    if (gc.x == -30000) continue;
-                    const char2 gm = rgmod[r];
-                    int ap = ta - gm.x, bp = tb - gm.y;
-                    ap += ap < 0 ? W : 0;
-                    bp += bp < 0 ? W : 0;
-                    const int nu = gc.x + ap, nv = gc.y + bp, nk = rk0[r];
-                    if (nu != cu || nv != cv || nk != ck) {
-                        flush();
-                        cu = nu; cv = nv; ck = nk;
-                    }
-                    const float wuv = rku[r * W + ap] * rkv[r * W + bp];
-                    const float2 *wy = rwy + r * Ww;
-#pragma unroll
-                    for (int c = 0; c < Ww; ++c) {
-                        const float2 q = wy[c];
-                        acc[c].x = fmaf(wuv, q.x, acc[c].x);
-                        acc[c].y = fmaf(wuv, q.y, acc[c].y);
-                    }
-                }
-            }
-            __syncthreads();
-        }
-        if (in_group) flush();
-        __syncthreads();
-        // planes [kq q, kq q + q) are complete
-        const int p0 = max(kq * g.q, k_lo), p1 = min(kq * g.q + g.q, k_hi);
-        for (int k = p0; k < p1; ++k) {
+    // write planes [next, upto) from the ring to HBM and clear their slots (CTA-wide)
+    int next = k_lo;
+    auto flush_planes = [&](int upto) {
+        upto = min(upto, k_hi);
+        for (int k = next; k < upto; ++k) {
             float2 *slot = ring + (k & (R - 1)) * cells;
-            float2 *dst = planes + (int64_t)(k - k_lo) * plane_sz + (int64_t)(tu * TILE) * g.Nv + tv * TILE;
+            float2 *dst = tile0 + (int64_t)(k - k_lo) * plane_sz;
             for (int e2 = threadIdx.x; e2 < cells; e2 += blockDim.x) {
                 const int r = e2 / TILE, cc = e2 - r * TILE;
                 const float2 val = slot[e2];
@@ -472,8 +388,101 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
                 slot[e2] = make_float2(0.f, 0.f);
             }
         }
+        if (upto > next) next = upto;
+    };
+    __syncthreads();
+
+    const int span = R - Ww + 1;   // w buckets of width q whose planes fit the ring together
+    int64_t c0 = wi.begin;
+    int kq = bucket_of(c0);
+    while (c0 < wi.end) {
+        // chunk: at most RES_CH items whose w buckets span fewer than `span` quanta
+        const int kq_end = min(kq + max(1, span / g.q), g.nkq);
+        const int64_t lim = min((int64_t)wi.end, off[kbase + kq_end]);
+        const int64_t c1 = min(lim, c0 + RES_CH);
+        const int cnt = (int)(c1 - c0);
+        // planes below this chunk's first plane are complete
+        flush_planes(max(kq * g.q, k_lo));
+        // ---- stage records
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const uint32_t code = items[c0 + t];
+            const uint32_t v = code & VIS_MASK;
+            const int du = (code >> 30) & 1, dv = code >> 31;
+            const uint32_t row = v / (uint32_t)g.nchan;
+            const int ch = (int)(v - row * (uint32_t)g.nchan);
+            const VisCoord<float> c = vis_coord<float>(src, row, ch, g);
+            if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
+                rcell[t] = make_short2(-30000, -30000);
+                continue;
+            }
+            float yr, yi;
+            if (unit_vis) { yr = 1.f; yi = 0.f; }
+            else { const float2 y = vis[v]; yr = y.x; yi = y.y; }
+            if (wgt) { const float w = wgt[v]; yr *= w; yi *= w; }
+            if (c.flip) yi = -yi;
+            if (g.tc != 0.0) {
+                float cs, sn;
+                sincos_turns(c.ph, &sn, &cs);
+                const float r0 = yr * cs - yi * sn;
+                yi = yr * sn + yi * cs;
+                yr = r0;
+            }
+            const int lu = (c.gu0 & (TILE - 1)) - du * TILE;
+            const int lv = (c.gv0 & (TILE - 1)) - dv * TILE;
+            rcell[t] = make_short2((short)lu, (short)lv);
+            int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
+            rgmod[t] = make_char2((char)mu, (char)mv);
+            rk0[t] = c.k0;
+            const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                rku[t * W + i] = es_kernel(c.ou + (float)i, ihw, bt);
+                rkv[t * W + i] = es_kernel(c.ov + (float)i, ihw, bt);
+            }
+            if (Ww > 1) {
+#pragma unroll
+                for (int i = 0; i < Ww; ++i) {
+                    const float kw = es_kernel(c.ow + (float)i, ihw, bt);
+                    rwy[t * Ww + i] = make_float2(kw * yr, kw * yi);
+                }
+            } else {
+                rwy[t] = make_float2(yr, yi);
+            }
+        }
         __syncthreads();
+        // ---- scatter by residue classes
+        if (in_group) {
+            const int per = (cnt + ngroups - 1) / ngroups;
+            const int r0 = grp * per, r1 = min(cnt, r0 + per);
+            for (int r = r0; r < r1; ++r) {
+                const short2 gc = rcell[r];
+                if (gc.x == -30000) continue;
+                const char2 gm = rgmod[r];
+                int ap = ta - gm.x, bp = tb - gm.y;
+                ap += ap < 0 ? W : 0;
+                bp += bp < 0 ? W : 0;
+                const int nu = gc.x + ap, nv = gc.y + bp, nk = rk0[r];
+                if (nu != cu || nv != cv || nk != ck) {
+                    flush_acc();
+                    cu = nu; cv = nv; ck = nk;
+                }
+                const float wuv = rku[r * W + ap] * rkv[r * W + bp];
+                const float2 *wy = rwy + r * Ww;
+#pragma unroll
+                for (int c = 0; c < Ww; ++c) {
+                    const float2 q = wy[c];
+                    acc[c].x = fmaf(wuv, q.x, acc[c].x);
+                    acc[c].y = fmaf(wuv, q.y, acc[c].y);
+                }
+            }
+            flush_acc();
+        }
+        __syncthreads();
+        c0 = c1;
+        if (c0 < wi.end && c0 >= off[kbase + kq + 1]) kq = bucket_of(c0);
     }
+    // remaining planes: all of the block for an owned tile, the touched ones for a chunk
+    flush_planes(wi.atomic_mode ? min(k_hi, next + R) : k_hi);
 }
 
 // ------------------------------------------------------------------ FP32 degridding from staged tiles

@@ -256,18 +256,17 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 }
 
 // ------------------------------------------------------------------ FP32 gridding by residue classes
-// Same work decomposition and plane ring as k_grid_tiles, but the scatter is
-// organised so that threads do not contend: the items of a bucket are staged in
-// chunks of CH records (first-tap cell, ES taps, weighted value times the w taps),
-// and each group of W^2 threads sweeps a contiguous run of records.  Thread (a, b)
-// of a group owns the footprint cell whose local indices are congruent to
-// (a, b) mod W (exactly one per visibility), accumulates its W_w plane
-// contributions in registers while consecutive visibilities (neighbouring
-// channels of one row) keep it on the same cell, and adds them to the shared
-// ring only when its cell changes.  Cells of different threads of a group never
-// coincide; only different groups can meet, so the ring adds stay atomic but
-// rarely collide.
+// Same work decomposition as k_grid_tiles (a CTA owns a tile's cells), with a
+// scatter that needs no atomics: the CTA has W * W * W_w threads and thread
+// (a, b, c) owns the ring cells whose local indices are congruent to (a, b) mod W
+// in the planes congruent to c mod W_w.  A visibility's W x W x W_w footprint holds
+// exactly one cell of each class, so every thread adds one tap per visibility with
+// a plain shared-memory read-modify-write and no two threads ever touch the same
+// cell.  Items are staged in chunks of RES_CH records (first-tap cell, residues,
+// ES taps, weighted value times the w taps); chunks run across w buckets with a
+// sliding window of ring planes, which are written to HBM once complete.
 constexpr int RES_CH = 256;
+constexpr int RSTRIDE = TILE + 6;   // padded ring row: spreads a footprint over the banks
 
 __host__ __device__ inline int ring_pow2(int n) {
     int r = 1;
@@ -276,17 +275,13 @@ __host__ __device__ inline int ring_pow2(int n) {
 }
 
 struct ResSmem {
-    // byte offsets of the record arrays after the ring
-    int cell, gmod, k0, ku, kv, wy, total;
+    int head, ku, kv, wy, total;
 };
 
 __host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
     ResSmem L;
-    int o = R * TILE * TILE * (int)sizeof(float2);
-    L.cell = o; o += RES_CH * (int)sizeof(short2);
-    L.gmod = o; o += RES_CH * (int)sizeof(char2);
-    o = (o + 15) & ~15;
-    L.k0 = o; o += RES_CH * (int)sizeof(int);
+    int o = R * TILE * RSTRIDE * (int)sizeof(float2);
+    L.head = o; o += RES_CH * (int)sizeof(int4);
     L.ku = o; o += RES_CH * W * (int)sizeof(float);
     L.kv = o; o += RES_CH * W * (int)sizeof(float);
     o = (o + 15) & ~15;
@@ -296,19 +291,16 @@ __host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
 }
 
 template <int W, int Ww>
-__global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ work,
-                                                  const uint32_t *__restrict__ items,
-                                                  const int64_t *__restrict__ off, CoordSrc src,
-                                                  const float2 *__restrict__ vis, const float *__restrict__ wgt,
-                                                  int unit_vis, BandGeom g, int k_lo, int k_hi,
-                                                  float2 *__restrict__ planes) {
+__global__ void __launch_bounds__(W * W * Ww < 64 ? 64 : W * W * Ww)
+k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items, const int64_t *__restrict__ off,
+           CoordSrc src, const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, BandGeom g,
+           int k_lo, int k_hi, float2 *__restrict__ planes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int R = ring_pow2(Ww + g.q - 1);   // slot of plane k: k & (R - 1)
     const ResSmem L = res_layout(R, W, Ww);
+    constexpr int SLOT = TILE * RSTRIDE;
     float2 *ring = reinterpret_cast<float2 *>(smem_raw);
-    short2 *rcell = reinterpret_cast<short2 *>(smem_raw + L.cell);
-    char2 *rgmod = reinterpret_cast<char2 *>(smem_raw + L.gmod);
-    int *rk0 = reinterpret_cast<int *>(smem_raw + L.k0);
+    int4 *rhead = reinterpret_cast<int4 *>(smem_raw + L.head);
     float *rku = reinterpret_cast<float *>(smem_raw + L.ku);
     float *rkv = reinterpret_cast<float *>(smem_raw + L.kv);
     float2 *rwy = reinterpret_cast<float2 *>(smem_raw + L.wy);
@@ -331,16 +323,13 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
         }
         return;
     }
-    for (int e = threadIdx.x; e < R * cells; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
+    for (int e = threadIdx.x; e < R * SLOT; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
 
-    // group geometry: thread (ta, tb) of a group owns the cells congruent to (ta, tb) mod W
-    const int G = W * W;
-    const int ngroups = blockDim.x / G;
-    const int grp = threadIdx.x / G, lid = threadIdx.x - grp * G;
-    const int ta = lid / W, tb = lid - ta * W;
-    const bool in_group = grp < ngroups;
+    // residue class of this thread
+    const int tc = threadIdx.x / (W * W), rem = threadIdx.x - tc * (W * W);
+    const int ta = rem / W, tb = rem - ta * W;
+    const bool owner = threadIdx.x < W * W * Ww;
     const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
-    // bucket (w quantum) of an item position, by binary search in the tile's offsets
     auto bucket_of = [&](int64_t pos) {
         int lo = 0, hi = g.nkq - 1;
         while (lo < hi) {
@@ -349,60 +338,37 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
         }
         return lo;
     };
-
-    float2 acc[Ww];
-    int cu = -1000, cv = -1000, ck = -1000;
-    auto flush_acc = [&]() {
-        if (cu >= 0 && cu < TILE && cv >= 0 && cv < TILE) {
-#pragma unroll
-            for (int c = 0; c < Ww; ++c) {
-                const int k = ck + c;
-                if (k >= k_lo && k < k_hi && (acc[c].x != 0.f || acc[c].y != 0.f)) {
-                    float2 *cell = ring + (k & (R - 1)) * cells + cu * TILE + cv;
-                    atomicAdd(&cell->x, acc[c].x);
-                    atomicAdd(&cell->y, acc[c].y);
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
-        cu = cv = ck = -1000;
-    };
-#pragma unroll
-    for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
     // write planes [next, upto) from the ring to HBM and clear their slots (CTA-wide)
     int next = k_lo;
     auto flush_planes = [&](int upto) {
         upto = min(upto, k_hi);
         for (int k = next; k < upto; ++k) {
-            float2 *slot = ring + (k & (R - 1)) * cells;
+            float2 *slot = ring + (k & (R - 1)) * SLOT;
             float2 *dst = tile0 + (int64_t)(k - k_lo) * plane_sz;
             for (int e2 = threadIdx.x; e2 < cells; e2 += blockDim.x) {
                 const int r = e2 / TILE, cc = e2 - r * TILE;
-                const float2 val = slot[e2];
+                const float2 val = slot[r * RSTRIDE + cc];
                 if (wi.atomic_mode) {
                     if (val.x != 0.f || val.y != 0.f) atomicAdd(dst + (int64_t)r * g.Nv + cc, val);
                 } else {
                     dst[(int64_t)r * g.Nv + cc] = val;
                 }
-                slot[e2] = make_float2(0.f, 0.f);
+                slot[r * RSTRIDE + cc] = make_float2(0.f, 0.f);
             }
         }
         if (upto > next) next = upto;
     };
     __syncthreads();
 
-    const int span = R - Ww + 1;   // w buckets of width q whose planes fit the ring together
+    const int span = R - Ww + 1;   // planes of first taps that fit the ring together
     int64_t c0 = wi.begin;
     int kq = bucket_of(c0);
     while (c0 < wi.end) {
-        // chunk: at most RES_CH items whose w buckets span fewer than `span` quanta
         const int kq_end = min(kq + max(1, span / g.q), g.nkq);
         const int64_t lim = min((int64_t)wi.end, off[kbase + kq_end]);
         const int64_t c1 = min(lim, c0 + RES_CH);
         const int cnt = (int)(c1 - c0);
-        // planes below this chunk's first plane are complete
-        flush_planes(max(kq * g.q, k_lo));
+        flush_planes(max(kq * g.q, k_lo));   // planes below the chunk's first plane are complete
         // ---- stage records
         for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
             const uint32_t code = items[c0 + t];
@@ -412,7 +378,7 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
             const int ch = (int)(v - row * (uint32_t)g.nchan);
             const VisCoord<float> c = vis_coord<float>(src, row, ch, g);
             if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
-                rcell[t] = make_short2(-30000, -30000);
+                rhead[t] = make_int4(-30000, 0, 0, 0);
                 continue;
             }
             float yr, yi;
@@ -429,10 +395,8 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
             }
             const int lu = (c.gu0 & (TILE - 1)) - du * TILE;
             const int lv = (c.gv0 & (TILE - 1)) - dv * TILE;
-            rcell[t] = make_short2((short)lu, (short)lv);
-            int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
-            rgmod[t] = make_char2((char)mu, (char)mv);
-            rk0[t] = c.k0;
+            const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W, mk = c.k0 % Ww;
+            rhead[t] = make_int4(lu, lv, mu | (mv << 8) | (mk << 16), c.k0);
             const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
 #pragma unroll
             for (int i = 0; i < W; ++i) {
@@ -450,32 +414,26 @@ __global__ void __launch_bounds__(256) k_grid_res(const WorkItem *__restrict__ w
             }
         }
         __syncthreads();
-        // ---- scatter by residue classes
-        if (in_group) {
-            const int per = (cnt + ngroups - 1) / ngroups;
-            const int r0 = grp * per, r1 = min(cnt, r0 + per);
-            for (int r = r0; r < r1; ++r) {
-                const short2 gc = rcell[r];
-                if (gc.x == -30000) continue;
-                const char2 gm = rgmod[r];
-                int ap = ta - gm.x, bp = tb - gm.y;
+        // ---- scatter: one cell per thread per visibility, no atomics
+        if (owner) {
+            for (int r = 0; r < cnt; ++r) {
+                const int4 h = rhead[r];
+                if (h.x == -30000) continue;
+                int ap = ta - (h.z & 0xff), bp = tb - ((h.z >> 8) & 0xff), cp = tc - (h.z >> 16);
                 ap += ap < 0 ? W : 0;
                 bp += bp < 0 ? W : 0;
-                const int nu = gc.x + ap, nv = gc.y + bp, nk = rk0[r];
-                if (nu != cu || nv != cv || nk != ck) {
-                    flush_acc();
-                    cu = nu; cv = nv; ck = nk;
-                }
+                cp += cp < 0 ? Ww : 0;
+                const int cu = h.x + ap, cv = h.y + bp, k = h.w + cp;
+                if ((unsigned)cu >= (unsigned)TILE || (unsigned)cv >= (unsigned)TILE || k < k_lo || k >= k_hi)
+                    continue;
                 const float wuv = rku[r * W + ap] * rkv[r * W + bp];
-                const float2 *wy = rwy + r * Ww;
-#pragma unroll
-                for (int c = 0; c < Ww; ++c) {
-                    const float2 q = wy[c];
-                    acc[c].x = fmaf(wuv, q.x, acc[c].x);
-                    acc[c].y = fmaf(wuv, q.y, acc[c].y);
-                }
+                const float2 q = rwy[r * Ww + cp];
+                float2 *cell = ring + (k & (R - 1)) * SLOT + cu * RSTRIDE + cv;
+                float2 a = *cell;
+                a.x = fmaf(wuv, q.x, a.x);
+                a.y = fmaf(wuv, q.y, a.y);
+                *cell = a;
             }
-            flush_acc();
         }
         __syncthreads();
         c0 = c1;
@@ -736,8 +694,9 @@ static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkI
                               float2 *planes) {
     const size_t smem = (size_t)res_layout(R, W, Ww).total;
     PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_grid_res<W, Ww><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo, k_hi,
-                                               planes);
+    const int threads = std::max(64, W * W * Ww);
+    k_grid_res<W, Ww><<<nblk, threads, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
+                                                   k_hi, planes);
 }
 
 template <int W, int Ww>

@@ -58,6 +58,13 @@ void *Ctx::scratch(const std::string &name, size_t bytes) {
     return b.ptr;
 }
 
+void Ctx::release(const std::string &name) {
+    auto it = bufs.find(name);
+    if (it == bufs.end()) return;
+    dfree(it->second.ptr, it->second.bytes);
+    bufs.erase(it);
+}
+
 size_t Ctx::scratch_bytes(const std::string &name) const {
     auto it = bufs.find(name);
     return it == bufs.end() ? 0 : it->second.bytes;

@@ -135,6 +135,7 @@ struct Ctx {
     void dfree(void *p, size_t bytes);
     void *scratch(const std::string &name, size_t bytes);  // grow-only named buffer
     size_t scratch_bytes(const std::string &name) const;
+    void release(const std::string &name);     // free a named scratch buffer
     size_t available() const { return budget > used ? budget - used : 0; }
     void free_plan(Plan &p);
     void reset();

@@ -281,6 +281,75 @@ static void exclusive_scan(Ctx &ctx, const In *in, int64_t n, int64_t *out, cuda
     check_launch("scan_apply");
 }
 
+// Second-level sort of every (tile, w bucket) item list by the local first-tap
+// cell (lu, lv) in [-TILE, TILE)^2 (spill copies have negative local indices).
+// Items that start on the same cell then sit next to each other, so the gridding
+// kernel's per-thread accumulators rarely change cell.  One CTA per (band, tile):
+// a shared-memory histogram and scan per bucket, a scatter into tmp and a copy back.
+constexpr int FINE_BINS = 4 * TILE * TILE;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fine_sort(CoordSrc src, const int64_t *__restrict__ off, int ntiles,
+                                                   int nkq, const BandGeom *__restrict__ bgs, int nchan,
+                                                   uint32_t *__restrict__ items, uint32_t *__restrict__ tmp) {
+    __shared__ int hist[FINE_BINS];
+    const int bt = blockIdx.x;                 // band * ntiles + tile
+    const int band = bt / ntiles;
+    const BandGeom g = bgs[band];
+    auto key_of = [&](uint32_t code) {
+        const uint32_t v = code & VIS_MASK;
+        const int du = (code >> 30) & 1, dv = code >> 31;
+        const uint32_t row = v / (uint32_t)nchan;
+        const int ch = (int)(v - row * (uint32_t)nchan);
+        const VisCoord<T> c = vis_coord<T>(src, row, ch, g);
+        const int lu = (c.gu0 & (TILE - 1)) - du * TILE + TILE;
+        const int lv = (c.gv0 & (TILE - 1)) - dv * TILE + TILE;
+        return lu * 2 * TILE + lv;
+    };
+    for (int kq = 0; kq < nkq; ++kq) {
+        const int64_t s = off[(int64_t)bt * nkq + kq], e = off[(int64_t)bt * nkq + kq + 1];
+        if (e - s < 2) continue;
+        for (int i = threadIdx.x; i < FINE_BINS; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) atomicAdd(&hist[key_of(items[i])], 1);
+        __syncthreads();
+        // exclusive scan of hist (FINE_BINS / 256 per thread, then across threads)
+        {
+            constexpr int PER = FINE_BINS / 256;
+            __shared__ int part[256];
+            int loc[PER], sum = 0;
+            for (int j = 0; j < PER; ++j) {
+                loc[j] = hist[threadIdx.x * PER + j];
+                sum += loc[j];
+            }
+            part[threadIdx.x] = sum;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int run = 0;
+                for (int t = 0; t < 256; ++t) {
+                    const int x = part[t];
+                    part[t] = run;
+                    run += x;
+                }
+            }
+            __syncthreads();
+            int run = part[threadIdx.x];
+            for (int j = 0; j < PER; ++j) {
+                hist[threadIdx.x * PER + j] = run;
+                run += loc[j];
+            }
+        }
+        __syncthreads();
+        for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
+            const uint32_t code = items[i];
+            tmp[s + atomicAdd(&hist[key_of(code)], 1)] = code;
+        }
+        __syncthreads();
+        for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) items[i] = tmp[i];
+        __syncthreads();
+    }
+}
+
 // uvw (FP64) -> double-float pairs (hi, lo) for the FP32 path
 __global__ void k_split_uvw(const double *__restrict__ uvw, int64_t n, float2 *__restrict__ out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -458,6 +527,14 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
                                                        p.d_off, p.d_items);
     check_launch("bucket_scatter");
 
+    // ---- order each bucket by first-tap cell (FP32 path: feeds the register accumulators)
+    if (p.prec == PFB_F32 && p.nitems > 0) {
+        uint32_t *tmp = (uint32_t *)ctx.scratch("sort_tmp", (size_t)p.nitems * sizeof(uint32_t));
+        k_fine_sort<float><<<(unsigned)(p.nband * ntiles), 256, 0, st>>>(p.coords(), p.d_off, (int)ntiles, p.nkq,
+                                                                         p.d_bg, p.nchan, p.d_items, tmp);
+        check_launch("fine_sort");
+    }
+
     // ---- per-tile item ranges -> host -> work list
     const int64_t ntb = (int64_t)p.nband * ntiles;
     int64_t *d_tb = (int64_t *)ctx.scratch("tilebegin", (size_t)(ntb + 1) * sizeof(int64_t));
@@ -535,6 +612,8 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     check_launch("pixel_tables");
     // the host vectors above die with this scope: wait for the copies
     PFB_CUDA(cudaStreamSynchronize(st));
+    ctx.release("sort_tmp");
+    ctx.release("counts");
 }
 
 Plan &get_plan(Ctx &ctx, const pfb_geom &g, int prec, int64_t nrow, int nchan, const double *uvw,

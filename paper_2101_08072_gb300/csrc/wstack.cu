@@ -256,15 +256,16 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 }
 
 // ------------------------------------------------------------------ FP32 gridding by residue classes
-// Same work decomposition as k_grid_tiles (a CTA owns a tile's cells), with a
-// scatter that needs no atomics: the CTA has W * W * W_w threads and thread
-// (a, b, c) owns the ring cells whose local indices are congruent to (a, b) mod W
-// in the planes congruent to c mod W_w.  A visibility's W x W x W_w footprint holds
-// exactly one cell of each class, so every thread adds one tap per visibility with
-// a plain shared-memory read-modify-write and no two threads ever touch the same
-// cell.  Items are staged in chunks of RES_CH records (first-tap cell, residues,
-// ES taps, weighted value times the w taps); chunks run across w buckets with a
-// sliding window of ring planes, which are written to HBM once complete.
+// Same work decomposition as k_grid_tiles (a CTA owns a tile's cells).  Items are
+// staged in chunks of RES_CH records (first-tap cell, residues, ES taps, weighted
+// value times the w taps); chunks run across w buckets with a sliding window of
+// ring planes, which are written to HBM once complete.  The scatter uses groups of
+// W * W threads: thread (a, b) of a group owns the footprint cell whose local
+// indices are congruent to (a, b) mod W (exactly one per visibility), keeps the
+// W_w plane sums of that cell in registers, and adds them to the ring only when its
+// cell changes.  The plan sorts every bucket by first-tap cell, so in the dense
+// tiles a thread stays on one cell for long runs of visibilities; distinct groups
+// can meet on a cell, so the (rare) ring adds are atomic.
 constexpr int RES_CH = 256;
 constexpr int RSTRIDE = TILE + 6;   // padded ring row: spreads a footprint over the banks
 
@@ -291,7 +292,7 @@ __host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
 }
 
 template <int W, int Ww>
-__global__ void __launch_bounds__(W * W * Ww < 64 ? 64 : W * W * Ww)
+__global__ void __launch_bounds__(256)
 k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items, const int64_t *__restrict__ off,
            CoordSrc src, const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, BandGeom g,
            int k_lo, int k_hi, float2 *__restrict__ planes) {
@@ -325,10 +326,12 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     }
     for (int e = threadIdx.x; e < R * SLOT; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
 
-    // residue class of this thread
-    const int tc = threadIdx.x / (W * W), rem = threadIdx.x - tc * (W * W);
-    const int ta = rem / W, tb = rem - ta * W;
-    const bool owner = threadIdx.x < W * W * Ww;
+    // group geometry
+    constexpr int G = W * W;
+    const int ngroups = blockDim.x / G;
+    const int grp = threadIdx.x / G, lid = threadIdx.x - grp * G;
+    const int ta = lid / W, tb = lid - ta * W;
+    const bool in_group = grp < ngroups;
     const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
     auto bucket_of = [&](int64_t pos) {
         int lo = 0, hi = g.nkq - 1;
@@ -338,6 +341,26 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         }
         return lo;
     };
+    float2 acc[Ww];
+    int cu = -1000, cv = -1000, ck = -1000;
+    auto flush_acc = [&]() {
+        if ((unsigned)cu < (unsigned)TILE && (unsigned)cv < (unsigned)TILE) {
+#pragma unroll
+            for (int c = 0; c < Ww; ++c) {
+                const int k = ck + c;
+                if (k >= k_lo && k < k_hi) {
+                    float2 *cell = ring + (k & (R - 1)) * SLOT + cu * RSTRIDE + cv;
+                    atomicAdd(&cell->x, acc[c].x);
+                    atomicAdd(&cell->y, acc[c].y);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
+        cu = cv = ck = -1000;
+    };
+#pragma unroll
+    for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
     // write planes [next, upto) from the ring to HBM and clear their slots (CTA-wide)
     int next = k_lo;
     auto flush_planes = [&](int upto) {
@@ -414,26 +437,31 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             }
         }
         __syncthreads();
-        // ---- scatter: one cell per thread per visibility, no atomics
-        if (owner) {
-            for (int r = 0; r < cnt; ++r) {
+        // ---- scatter by residue classes with register accumulation
+        if (in_group) {
+            const int per = (cnt + ngroups - 1) / ngroups;
+            const int r0 = grp * per, r1 = min(cnt, r0 + per);
+            for (int r = r0; r < r1; ++r) {
                 const int4 h = rhead[r];
                 if (h.x == -30000) continue;
-                int ap = ta - (h.z & 0xff), bp = tb - ((h.z >> 8) & 0xff), cp = tc - (h.z >> 16);
+                int ap = ta - (h.z & 0xff), bp = tb - ((h.z >> 8) & 0xff);
                 ap += ap < 0 ? W : 0;
                 bp += bp < 0 ? W : 0;
-                cp += cp < 0 ? Ww : 0;
-                const int cu = h.x + ap, cv = h.y + bp, k = h.w + cp;
-                if ((unsigned)cu >= (unsigned)TILE || (unsigned)cv >= (unsigned)TILE || k < k_lo || k >= k_hi)
-                    continue;
+                const int nu = h.x + ap, nv = h.y + bp;
+                if (nu != cu || nv != cv || h.w != ck) {
+                    flush_acc();
+                    cu = nu; cv = nv; ck = h.w;
+                }
                 const float wuv = rku[r * W + ap] * rkv[r * W + bp];
-                const float2 q = rwy[r * Ww + cp];
-                float2 *cell = ring + (k & (R - 1)) * SLOT + cu * RSTRIDE + cv;
-                float2 a = *cell;
-                a.x = fmaf(wuv, q.x, a.x);
-                a.y = fmaf(wuv, q.y, a.y);
-                *cell = a;
+                const float2 *wy = rwy + r * Ww;
+#pragma unroll
+                for (int c = 0; c < Ww; ++c) {
+                    const float2 q = wy[c];
+                    acc[c].x = fmaf(wuv, q.x, acc[c].x);
+                    acc[c].y = fmaf(wuv, q.y, acc[c].y);
+                }
             }
+            flush_acc();
         }
         __syncthreads();
         c0 = c1;
@@ -694,8 +722,7 @@ static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkI
                               float2 *planes) {
     const size_t smem = (size_t)res_layout(R, W, Ww).total;
     PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int threads = std::max(64, W * W * Ww);
-    k_grid_res<W, Ww><<<nblk, threads, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
+    k_grid_res<W, Ww><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
                                                    k_hi, planes);
 }
 

@@ -258,15 +258,18 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 // ------------------------------------------------------------------ FP32 gridding by residue classes
 // Same work decomposition as k_grid_tiles (a CTA owns a tile's cells).  Items are
 // staged in chunks of RES_CH records (first-tap cell, residues, ES taps, weighted
-// value times the w taps); chunks run across w buckets with a sliding window of
-// ring planes, which are written to HBM once complete.  The scatter uses groups of
-// W * W threads: thread (a, b) of a group owns the footprint cell whose local
-// indices are congruent to (a, b) mod W (exactly one per visibility), keeps the
-// W_w plane sums of that cell in registers, and adds them to the ring only when its
-// cell changes.  The plan sorts every bucket by first-tap cell, so in the dense
-// tiles a thread stays on one cell for long runs of visibilities; distinct groups
-// can meet on a cell, so the (rare) ring adds are atomic.
-constexpr int RES_CH = 256;
+// value times the w taps); chunks run across w planes with a sliding window of
+// W_w ring planes (one plane per bucket), which are written to HBM once complete.
+// The scatter uses groups of W * W threads: thread (a, b) of a group owns the
+// footprint cell whose local indices are congruent to (a, b) mod W (exactly one per
+// visibility), keeps the W_w plane sums of that cell in registers, and adds them to
+// the ring only when its cell changes.  The plan sorts every bucket by first-tap
+// cell, so in the dense tiles a thread stays on one cell for long runs of
+// visibilities; distinct groups can meet on a cell, so the (rare) ring adds are
+// atomic.  The raw inputs of the next chunk (item codes, uvw, visibility, weight)
+// are loaded into registers before the current chunk's scatter, hiding their
+// latency behind it.
+constexpr int RES_CH = 128;
 constexpr int RSTRIDE = TILE + 6;   // padded ring row: spreads a footprint over the banks
 
 __host__ __device__ inline int ring_pow2(int n) {
@@ -291,15 +294,23 @@ __host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
     return L;
 }
 
+// raw inputs of one record, held in registers between prefetch and staging
+struct RawRec {
+    uint32_t code;
+    float2 u, v, w;   // uvw of the row as double-float
+    float2 y;
+    float wt;
+};
+
 template <int W, int Ww>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items, const int64_t *__restrict__ off,
            CoordSrc src, const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, BandGeom g,
            int k_lo, int k_hi, float2 *__restrict__ planes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int R = ring_pow2(Ww + g.q - 1);   // slot of plane k: k & (R - 1)
-    const ResSmem L = res_layout(R, W, Ww);
+    constexpr int R = Ww;                  // ring planes (one w bucket per plane)
     constexpr int SLOT = TILE * RSTRIDE;
+    const ResSmem L = res_layout(R, W, Ww);
     float2 *ring = reinterpret_cast<float2 *>(smem_raw);
     int4 *rhead = reinterpret_cast<int4 *>(smem_raw + L.head);
     float *rku = reinterpret_cast<float *>(smem_raw + L.ku);
@@ -341,6 +352,13 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         }
         return lo;
     };
+    // chunk after [c0, c1) starting in bucket kq: at most RES_CH items of one bucket
+    auto next_chunk = [&](int64_t c0, int &kq, int64_t &c1) {
+        if (c0 >= wi.end) { c1 = c0; return; }
+        if (c0 >= off[kbase + kq + 1]) kq = bucket_of(c0);
+        c1 = min(min((int64_t)wi.end, off[kbase + kq + 1]), c0 + RES_CH);
+    };
+
     float2 acc[Ww];
     int cu = -1000, cv = -1000, ck = -1000;
     auto flush_acc = [&]() {
@@ -349,7 +367,7 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             for (int c = 0; c < Ww; ++c) {
                 const int k = ck + c;
                 if (k >= k_lo && k < k_hi) {
-                    float2 *cell = ring + (k & (R - 1)) * SLOT + cu * RSTRIDE + cv;
+                    float2 *cell = ring + (k % R) * SLOT + cu * RSTRIDE + cv;
                     atomicAdd(&cell->x, acc[c].x);
                     atomicAdd(&cell->y, acc[c].y);
                 }
@@ -366,7 +384,7 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     auto flush_planes = [&](int upto) {
         upto = min(upto, k_hi);
         for (int k = next; k < upto; ++k) {
-            float2 *slot = ring + (k & (R - 1)) * SLOT;
+            float2 *slot = ring + (k % R) * SLOT;
             float2 *dst = tile0 + (int64_t)(k - k_lo) * plane_sz;
             for (int e2 = threadIdx.x; e2 < cells; e2 += blockDim.x) {
                 const int r = e2 / TILE, cc = e2 - r * TILE;
@@ -381,91 +399,149 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         }
         if (upto > next) next = upto;
     };
-    __syncthreads();
-
-    const int span = R - Ww + 1;   // planes of first taps that fit the ring together
-    int64_t c0 = wi.begin;
-    int kq = bucket_of(c0);
-    while (c0 < wi.end) {
-        const int kq_end = min(kq + max(1, span / g.q), g.nkq);
-        const int64_t lim = min((int64_t)wi.end, off[kbase + kq_end]);
-        const int64_t c1 = min(lim, c0 + RES_CH);
-        const int cnt = (int)(c1 - c0);
-        flush_planes(max(kq * g.q, k_lo));   // planes below the chunk's first plane are complete
-        // ---- stage records
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const uint32_t code = items[c0 + t];
-            const uint32_t v = code & VIS_MASK;
-            const int du = (code >> 30) & 1, dv = code >> 31;
-            const uint32_t row = v / (uint32_t)g.nchan;
-            const int ch = (int)(v - row * (uint32_t)g.nchan);
-            const VisCoord<float> c = vis_coord<float>(src, row, ch, g);
-            if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
-                rhead[t] = make_int4(-30000, 0, 0, 0);
-                continue;
+    // loads of one record's raw inputs (second level: after its item code arrived)
+    auto load_raw = [&](RawRec &q) {
+        const uint32_t v = q.code & VIS_MASK;
+        const uint32_t row = v / (uint32_t)g.nchan;
+        q.u = src.rowdf[3 * row + 0];
+        q.v = src.rowdf[3 * row + 1];
+        q.w = src.rowdf[3 * row + 2];
+        q.y = unit_vis ? make_float2(1.f, 0.f) : vis[v];
+        q.wt = wgt ? wgt[v] : 1.f;
+    };
+    // records from raw inputs
+    auto stage = [&](const RawRec &q, int t) {
+        const uint32_t v = q.code & VIS_MASK;
+        const int du = (q.code >> 30) & 1, dv = q.code >> 31;
+        const uint32_t row = v / (uint32_t)g.nchan;
+        const int ch = (int)(v - row * (uint32_t)g.nchan);
+        const ChanDF cs = src.chandf[ch];
+        VisCoord<float> c;
+        {
+            float2 u = q.u, vv = q.v, w = q.w;
+            c.flip = w.x < 0.0f || (w.x == 0.0f && w.y < 0.0f);
+            if (c.flip) {
+                u.x = -u.x; u.y = -u.y; vv.x = -vv.x; vv.y = -vv.y; w.x = -w.x; w.y = -w.y;
             }
-            float yr, yi;
-            if (unit_vis) { yr = 1.f; yi = 0.f; }
-            else { const float2 y = vis[v]; yr = y.x; yi = y.y; }
-            if (wgt) { const float w = wgt[v]; yr *= w; yi *= w; }
-            if (c.flip) yi = -yi;
-            if (g.tc != 0.0) {
-                float cs, sn;
-                sincos_turns(c.ph, &sn, &cs);
-                const float r0 = yr * cs - yi * sn;
-                yi = yr * sn + yi * cs;
-                yr = r0;
-            }
-            const int lu = (c.gu0 & (TILE - 1)) - du * TILE;
-            const int lv = (c.gv0 & (TILE - 1)) - dv * TILE;
-            const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W, mk = c.k0 % Ww;
-            rhead[t] = make_int4(lu, lv, mu | (mv << 8) | (mk << 16), c.k0);
-            const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                rku[t * W + i] = es_kernel(c.ou + (float)i, ihw, bt);
-                rkv[t * W + i] = es_kernel(c.ov + (float)i, ihw, bt);
-            }
+            float p, e;
+            int g0;
+            df_mul(u.x, u.y, cs.su_hi, cs.su_lo, p, e);
+            df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ou);
+            c.gu0 = wrap_mod(g0, g.Nu, g.inv_Nu);
+            df_mul(vv.x, vv.y, cs.sv_hi, cs.sv_lo, p, e);
+            df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ov);
+            c.gv0 = wrap_mod(g0, g.Nv, g.inv_Nv);
+            df_mul(w.x, w.y, cs.sp_hi, cs.sp_lo, p, e);
+            c.ph = (p - rintf(p)) + e;
             if (Ww > 1) {
-#pragma unroll
-                for (int i = 0; i < Ww; ++i) {
-                    const float kw = es_kernel(c.ow + (float)i, ihw, bt);
-                    rwy[t * Ww + i] = make_float2(kw * yr, kw * yi);
-                }
+                df_mul(w.x, w.y, cs.sw_hi, cs.sw_lo, p, e);
+                df_tap(p, e, g.w_oi, g.w_of, g.hw, g0, c.ow);
+                c.k0 = g0 < 0 ? 0 : (g0 > g.P - Ww ? g.P - Ww : g0);
             } else {
-                rwy[t] = make_float2(yr, yi);
+                c.k0 = 0;
+                c.ow = 0.0f;
             }
         }
+        if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
+            rhead[t] = make_int4(-30000, 0, 0, 0);
+            return;
+        }
+        float yr = q.y.x * q.wt, yi = q.y.y * q.wt;
+        if (c.flip) yi = -yi;
+        if (g.tc != 0.0) {
+            float cs2, sn;
+            sincos_turns(c.ph, &sn, &cs2);
+            const float r0 = yr * cs2 - yi * sn;
+            yi = yr * sn + yi * cs2;
+            yr = r0;
+        }
+        const int lu = (c.gu0 & (TILE - 1)) - du * TILE;
+        const int lv = (c.gv0 & (TILE - 1)) - dv * TILE;
+        const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
+        rhead[t] = make_int4(lu, lv, mu | (mv << 8), c.k0);
+        const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            rku[t * W + i] = es_kernel(c.ou + (float)i, ihw, bt);
+            rkv[t * W + i] = es_kernel(c.ov + (float)i, ihw, bt);
+        }
+        if (Ww > 1) {
+#pragma unroll
+            for (int i = 0; i < Ww; ++i) {
+                const float kw = es_kernel(c.ow + (float)i, ihw, bt);
+                rwy[t * Ww + i] = make_float2(kw * yr, kw * yi);
+            }
+        } else {
+            rwy[t] = make_float2(yr, yi);
+        }
+    };
+    auto scatter_one = [&](const int4 h, int r) {
+        int ap = ta - (h.z & 0xff), bp = tb - (h.z >> 8);
+        ap += ap < 0 ? W : 0;
+        bp += bp < 0 ? W : 0;
+        const int nu = h.x + ap, nv = h.y + bp;
+        if (nu != cu || nv != cv || h.w != ck) {
+            flush_acc();
+            cu = nu; cv = nv; ck = h.w;
+        }
+        const float wuv = rku[r * W + ap] * rkv[r * W + bp];
+        const float2 *wy = rwy + r * Ww;
+#pragma unroll
+        for (int c = 0; c < Ww; ++c) {
+            const float2 q = wy[c];
+            acc[c].x = fmaf(wuv, q.x, acc[c].x);
+            acc[c].y = fmaf(wuv, q.y, acc[c].y);
+        }
+    };
+    __syncthreads();
+
+    // ---- prologue: stage chunk 0, prefetch the codes of chunk 1
+    int kq = bucket_of(wi.begin);
+    int64_t c0 = wi.begin, c1;
+    next_chunk(c0, kq, c1);
+    RawRec raw;
+    raw.code = threadIdx.x < c1 - c0 ? items[c0 + threadIdx.x] : 0u;
+    if (threadIdx.x < c1 - c0) load_raw(raw);
+    if (threadIdx.x < c1 - c0) stage(raw, threadIdx.x);
+    int kq_n = kq;
+    int64_t n0 = c1, n1;
+    next_chunk(n0, kq_n, n1);
+    RawRec nxt;
+    nxt.code = threadIdx.x < n1 - n0 ? items[n0 + threadIdx.x] : 0u;
+    __syncthreads();
+    while (c0 < wi.end) {
+        const int cnt = (int)(c1 - c0);
+        // raw inputs of the next chunk: issued now, consumed after this chunk's scatter
+        if (threadIdx.x < n1 - n0) load_raw(nxt);
+        // planes below this chunk's first plane are complete
+        flush_planes(max(kq * g.q, k_lo));
         __syncthreads();
         // ---- scatter by residue classes with register accumulation
         if (in_group) {
             const int per = (cnt + ngroups - 1) / ngroups;
             const int r0 = grp * per, r1 = min(cnt, r0 + per);
-            for (int r = r0; r < r1; ++r) {
-                const int4 h = rhead[r];
-                if (h.x == -30000) continue;
-                int ap = ta - (h.z & 0xff), bp = tb - ((h.z >> 8) & 0xff);
-                ap += ap < 0 ? W : 0;
-                bp += bp < 0 ? W : 0;
-                const int nu = h.x + ap, nv = h.y + bp;
-                if (nu != cu || nv != cv || h.w != ck) {
-                    flush_acc();
-                    cu = nu; cv = nv; ck = h.w;
-                }
-                const float wuv = rku[r * W + ap] * rkv[r * W + bp];
-                const float2 *wy = rwy + r * Ww;
-#pragma unroll
-                for (int c = 0; c < Ww; ++c) {
-                    const float2 q = wy[c];
-                    acc[c].x = fmaf(wuv, q.x, acc[c].x);
-                    acc[c].y = fmaf(wuv, q.y, acc[c].y);
-                }
+            int r = r0;
+            for (; r + 1 < r1; r += 2) {
+                const int4 h0 = rhead[r], h1 = rhead[r + 1];
+                if (h0.x != -30000) scatter_one(h0, r);
+                if (h1.x != -30000) scatter_one(h1, r + 1);
+            }
+            if (r < r1) {
+                const int4 h0 = rhead[r];
+                if (h0.x != -30000) scatter_one(h0, r);
             }
             flush_acc();
         }
         __syncthreads();
-        c0 = c1;
-        if (c0 < wi.end && c0 >= off[kbase + kq + 1]) kq = bucket_of(c0);
+        // ---- advance: stage the next chunk, prefetch the codes of the one after
+        c0 = n0; c1 = n1; kq = kq_n;
+        if (c0 < wi.end) {
+            if (threadIdx.x < c1 - c0) stage(nxt, threadIdx.x);
+            n0 = c1;
+            next_chunk(n0, kq_n, n1);
+            nxt.code = threadIdx.x < n1 - n0 ? items[n0 + threadIdx.x] : 0u;
+        }
+        __syncthreads();
     }
     // remaining planes: all of the block for an owned tile, the touched ones for a chunk
     flush_planes(wi.atomic_mode ? min(k_hi, next + R) : k_hi);
@@ -478,15 +554,15 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
 // the buckets advance), with coalesced 8-byte loads; then one thread per home item
 // interpolates from shared memory.
 template <int W, int Ww>
-__global__ void __launch_bounds__(256) k_degrid_tiles(const WorkItem *__restrict__ work,
+__global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restrict__ work,
                                                       const uint32_t *__restrict__ items,
                                                       const int64_t *__restrict__ off, CoordSrc src, BandGeom g,
                                                       int k_lo, int k_hi, const float2 *__restrict__ planes,
                                                       float2 *__restrict__ vis) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *reg = reinterpret_cast<float2 *>(smem_raw);
-    __shared__ int slot_plane[64];
-    const int R = ring_pow2(Ww + g.q - 1);   // slot of plane k: k & (R - 1)
+    __shared__ int slot_plane[MAX_W];
+    constexpr int R = Ww;                  // ring planes (one w bucket per plane)
     const int E = TILE + W - 1;          // region edge
     const int ES = E | 1;                // odd row stride: fewer bank conflicts
     const int reg_sz = E * ES;
@@ -518,7 +594,7 @@ __global__ void __launch_bounds__(256) k_degrid_tiles(const WorkItem *__restrict
         // load missing planes into their ring slots
         bool loaded = false;
         for (int k = pa; k < pb; ++k) {
-            const int sl = k & (R - 1);
+            const int sl = k % R;
             if (slot_plane[sl] == k) continue;
             loaded = true;
             float2 *dst = reg + sl * reg_sz;
@@ -533,7 +609,7 @@ __global__ void __launch_bounds__(256) k_degrid_tiles(const WorkItem *__restrict
         }
         __syncthreads();
         if (loaded && threadIdx.x == 0)
-            for (int k = pa; k < pb; ++k) slot_plane[k & (R - 1)] = k;
+            for (int k = pa; k < pb; ++k) slot_plane[k % R] = k;
         for (int64_t it = s + threadIdx.x; it < e; it += blockDim.x) {
             const uint32_t code = items[it];
             if (code >> 30) continue;
@@ -561,7 +637,7 @@ __global__ void __launch_bounds__(256) k_degrid_tiles(const WorkItem *__restrict
             for (int cw = 0; cw < Ww; ++cw) {
                 const int k = c.k0 + cw;
                 if (k < k_lo || k >= k_hi) continue;
-                const float2 *pl = reg + (k & (R - 1)) * reg_sz + lu * ES + lv;
+                const float2 *pl = reg + (k % R) * reg_sz + lu * ES + lv;
                 float pr = 0.f, pi = 0.f;
 #pragma unroll
                 for (int a = 0; a < W; ++a) {
@@ -707,13 +783,13 @@ static unsigned grid_blocks(int64_t n, int threads, int cap) {
 }
 
 // ------------------------------------------------------------------ FP32 kernel dispatch on W
-static bool fast_path_f32(const Plan &p) { return p.prec == PFB_F32 && p.W >= 4 && p.W <= 8; }
+static bool fast_path_f32(const Plan &p) { return p.prec == PFB_F32 && p.W >= 4 && p.W <= 8 && p.q == 1; }
 static bool degrid_tiles_fit(const Plan &p) {
-    const int R = ring_pow2(p.Ww + p.q - 1), E = TILE + p.W - 1, ES = E | 1;
+    const int R = p.Ww, E = TILE + p.W - 1, ES = E | 1;
     return fast_path_f32(p) && (size_t)R * E * ES * sizeof(float2) <= 227 * 1024;
 }
 static bool grid_res_fit(const Plan &p) {
-    return fast_path_f32(p) && (size_t)res_layout(ring_pow2(p.Ww + p.q - 1), p.W, p.Ww).total <= 227 * 1024;
+    return fast_path_f32(p) && (size_t)res_layout(p.Ww, p.W, p.Ww).total <= 227 * 1024;
 }
 
 template <int W, int Ww>
@@ -785,7 +861,7 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
             if (i1 > i0 && sizeof(T) == 4 && degrid_tiles_fit(p)) {
                 KTimer t(ctx, "degrid_tiles", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
                 const int64_t w0 = p.work_begin[b], w1 = p.work_begin[b + 1];
-                const int R = ring_pow2(p.Ww + p.q - 1);
+                const int R = p.Ww;
 #define PFB_DEGRID_CALL(WV, WWV)                                                                          \
     launch_degrid_t<WV, WWV>((unsigned)(w1 - w0), R, st, p.d_work + w0, p, g, k_lo, k_hi, (const float2 *)planes, \
                              (float2 *)vis)
@@ -833,7 +909,7 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                 const double wb = wgt ? (double)sizeof(T) : 0.0;
                 KTimer t(ctx, "grid_tiles", st, 4.0 * nit + nvb * (vb + wb) + nk * plane_bytes);
                 if (sizeof(T) == 4 && grid_res_fit(p)) {
-                    const int R = ring_pow2(p.Ww + p.q - 1);
+                    const int R = p.Ww;
 #define PFB_GRID_CALL(WV, WWV)                                                                            \
     launch_grid_res_t<WV, WWV>((unsigned)(w1 - w0), R, st, p.d_work + w0, p, (const float2 *)vis,          \
                                (const float *)wgt, unit_vis ? 1 : 0, g, k_lo, k_hi, (float2 *)planes)

@@ -108,7 +108,8 @@ int pfb_create(pfb_ctx **ctx, int device, size_t hbm_budget_bytes);
 void pfb_destroy(pfb_ctx *ctx);
 
 /* Message of the last failure on this context ("" if none).  The pointer stays
- * valid until the next call on the context. */
+ * valid until the next call on the context.  With ctx == NULL: the last failure
+ * of a context-free call (pfb_wsum_static) on the calling thread. */
 const char *pfb_last_error(const pfb_ctx *ctx);
 
 /* Drop cached plans and PSF spectra (call after changing uvw/freq/band contents
@@ -191,6 +192,29 @@ int pfb_timing_read(pfb_ctx *ctx, const char *kernel, int64_t *launches, double 
 
 /* Comma-separated names of the groups recorded so far, written into buf (len bytes). */
 int pfb_timing_names(pfb_ctx *ctx, char *buf, size_t len);
+
+/* Per-band weight sums with no device allocation (the paper has no counterpart:
+ * this is a deployment variant of the weight-sum reduction behind pfb_dirty's and
+ * pfb_psf's wsum_out).  For callers that may not call cudaMalloc at this point,
+ * such as an engine that owns the whole HBM pool, or a stream where an allocation
+ * could synchronise the device.
+ *   wsum_out[b] = sum over rows and the channels c of band b of wgt[row][c]
+ *   (1 per visibility when wgt is NULL).
+ * device: CUDA device to run on; band_of_chan [nchan] int32 (device), ids outside
+ * [0, nband) are skipped; wgt [nrow][nchan] float32 (PFB_F32) / float64 (PFB_F64)
+ * (device) or NULL; wsum_out [nband] float64, DEVICE memory owned by the caller,
+ * valid once `stream` has completed the work.
+ * The accumulators are a fixed device array of 32 doubles inside the library
+ * (every GPU that loads the library holds it until the process exits): nband > 32
+ * returns PFB_ERR_ARG.  The call clears them on `stream` before use.  All calls on
+ * a device share that array, so calls whose work overlaps on the GPU (different
+ * streams, or host threads without ordering) race: order them on one stream.  The
+ * first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Errors: PFB_ERR_ARG
+ * for bad sizes or pointers, PFB_ERR_CUDA for a failed launch; pfb_last_error(NULL)
+ * gives the message. */
+int pfb_wsum_static(int device, pfb_prec prec, int64_t nrow, int32_t nchan, int32_t nband,
+                    const int32_t *band_of_chan, const void *wgt, double *wsum_out, void *stream);
 
 /* Library version string. */
 const char *pfb_version(void);

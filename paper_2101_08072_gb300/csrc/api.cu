@@ -283,7 +283,7 @@ int pfb_create(pfb_ctx **out, int device, size_t budget) {
 
 void pfb_destroy(pfb_ctx *ctx) { delete ctx; }
 
-const char *pfb_last_error(const pfb_ctx *ctx) { return ctx ? ctx->impl.err.c_str() : "null context"; }
+const char *pfb_last_error(const pfb_ctx *ctx) { return ctx ? ctx->impl.err.c_str() : pfb::g_free_error.c_str(); }
 
 int pfb_plan_reset(pfb_ctx *ctx) {
     return guarded(ctx, [&](Ctx &c) { c.reset(); });

@@ -166,6 +166,9 @@ struct KTimer {
     }
 };
 
+// noalloc.cu: message of the last failure of a context-free call on this thread
+extern thread_local std::string g_free_error;
+
 // plan.cu
 Plan &get_plan(Ctx &ctx, const pfb_geom &g, int prec, int64_t nrow, int nchan, const double *uvw,
                const double *freq, const int32_t *band, bool psf_grid, cudaStream_t st);

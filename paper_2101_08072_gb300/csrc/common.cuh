@@ -76,6 +76,13 @@ __device__ __forceinline__ float es_kernel(float z, float inv_halfw, float beta)
     float t = 1.0f - x * x;
     return t > 0.0f ? __expf(beta * (sqrtf(t) - 1.0f)) : 0.0f;
 }
+// Same kernel with sqrt(t) as t * rsqrt(t) (hardware approximation, relative error
+// about 1e-7, i.e. about beta * 1e-7 in phi: far below the FP32 path's epsilon).
+__device__ __forceinline__ float es_kernel_fast(float z, float inv_halfw, float beta) {
+    float x = z * inv_halfw;
+    float t = 1.0f - x * x;
+    return t > 0.0f ? __expf(beta * (t * rsqrtf(t) - 1.0f)) : 0.0f;
+}
 __device__ __forceinline__ double es_kernel(double z, double inv_halfw, double beta) {
     double x = z * inv_halfw;
     double t = 1.0 - x * x;

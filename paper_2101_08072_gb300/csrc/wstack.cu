@@ -282,14 +282,18 @@ struct ResSmem {
     int head, ku, kv, wy, total;
 };
 
+// record row strides: odd (in words) so that consecutive records hit different banks
+__host__ __device__ constexpr int res_ks(int W) { return W | 1; }
+__host__ __device__ constexpr int res_ws(int Ww) { return Ww + ((Ww & 1) ? 0 : 1); }
+
 __host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
     ResSmem L;
     int o = R * TILE * RSTRIDE * (int)sizeof(float2);
     L.head = o; o += RES_CH * (int)sizeof(int4);
-    L.ku = o; o += RES_CH * W * (int)sizeof(float);
-    L.kv = o; o += RES_CH * W * (int)sizeof(float);
+    L.ku = o; o += RES_CH * res_ks(W) * (int)sizeof(float);
+    L.kv = o; o += RES_CH * res_ks(W) * (int)sizeof(float);
     o = (o + 15) & ~15;
-    L.wy = o; o += RES_CH * Ww * (int)sizeof(float2);
+    L.wy = o; o += RES_CH * res_ws(Ww) * (int)sizeof(float2);
     L.total = o;
     return L;
 }
@@ -310,6 +314,7 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int R = Ww;                  // ring planes (one w bucket per plane)
     constexpr int SLOT = TILE * RSTRIDE;
+    constexpr int KS = res_ks(W), WS = res_ws(Ww);
     const ResSmem L = res_layout(R, W, Ww);
     float2 *ring = reinterpret_cast<float2 *>(smem_raw);
     int4 *rhead = reinterpret_cast<int4 *>(smem_raw + L.head);
@@ -337,11 +342,14 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     }
     for (int e = threadIdx.x; e < R * SLOT; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
 
-    // group geometry
-    constexpr int G = W * W;
+    // group geometry: thread (ta, tb) of a group owns the cell classes (ta, tb) and
+    // (ta, tb + NBH) mod W (the second only when tb + NBH < W)
+    constexpr int NBH = (W + 1) / 2;
+    constexpr int G = W * NBH;
     const int ngroups = blockDim.x / G;
     const int grp = threadIdx.x / G, lid = threadIdx.x - grp * G;
-    const int ta = lid / W, tb = lid - ta * W;
+    const int ta = lid / NBH, tb = lid - ta * NBH;
+    const bool two = tb + NBH < W;
     const bool in_group = grp < ngroups;
     const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
     auto bucket_of = [&](int64_t pos) {
@@ -359,26 +367,40 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         c1 = min(min((int64_t)wi.end, off[kbase + kq + 1]), c0 + RES_CH);
     };
 
-    float2 acc[Ww];
-    int cu = -1000, cv = -1000, ck = -1000;
+    float2 acc0[Ww], acc1[Ww];
+    int cu = -1000, cv = -1000, ck = -1000;   // current cells (cu, cv) and (cu, cv1), planes ck..ck+Ww-1
+    int cv1 = -1000;
     auto flush_acc = [&]() {
-        if ((unsigned)cu < (unsigned)TILE && (unsigned)cv < (unsigned)TILE) {
+        if ((unsigned)cu < (unsigned)TILE) {
+            const bool ok0 = (unsigned)cv < (unsigned)TILE, ok1 = two && (unsigned)cv1 < (unsigned)TILE;
 #pragma unroll
             for (int c = 0; c < Ww; ++c) {
                 const int k = ck + c;
                 if (k >= k_lo && k < k_hi) {
-                    float2 *cell = ring + (k % R) * SLOT + cu * RSTRIDE + cv;
-                    atomicAdd(&cell->x, acc[c].x);
-                    atomicAdd(&cell->y, acc[c].y);
+                    float2 *rowp = ring + (k % R) * SLOT + cu * RSTRIDE;
+                    if (ok0) {
+                        atomicAdd(&rowp[cv].x, acc0[c].x);
+                        atomicAdd(&rowp[cv].y, acc0[c].y);
+                    }
+                    if (ok1) {
+                        atomicAdd(&rowp[cv1].x, acc1[c].x);
+                        atomicAdd(&rowp[cv1].y, acc1[c].y);
+                    }
                 }
             }
         }
 #pragma unroll
-        for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
-        cu = cv = ck = -1000;
+        for (int c = 0; c < Ww; ++c) {
+            acc0[c] = make_float2(0.f, 0.f);
+            acc1[c] = make_float2(0.f, 0.f);
+        }
+        cu = cv = cv1 = ck = -1000;
     };
 #pragma unroll
-    for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
+    for (int c = 0; c < Ww; ++c) {
+        acc0[c] = make_float2(0.f, 0.f);
+        acc1[c] = make_float2(0.f, 0.f);
+    }
     // write planes [next, upto) from the ring to HBM and clear their slots (CTA-wide)
     int next = k_lo;
     auto flush_planes = [&](int upto) {
@@ -462,35 +484,41 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
 #pragma unroll
         for (int i = 0; i < W; ++i) {
-            rku[t * W + i] = es_kernel(c.ou + (float)i, ihw, bt);
-            rkv[t * W + i] = es_kernel(c.ov + (float)i, ihw, bt);
+            rku[t * KS + i] = es_kernel_fast(c.ou + (float)i, ihw, bt);
+            rkv[t * KS + i] = es_kernel_fast(c.ov + (float)i, ihw, bt);
         }
         if (Ww > 1) {
 #pragma unroll
             for (int i = 0; i < Ww; ++i) {
-                const float kw = es_kernel(c.ow + (float)i, ihw, bt);
-                rwy[t * Ww + i] = make_float2(kw * yr, kw * yi);
+                const float kw = es_kernel_fast(c.ow + (float)i, ihw, bt);
+                rwy[t * WS + i] = make_float2(kw * yr, kw * yi);
             }
         } else {
-            rwy[t] = make_float2(yr, yi);
+            rwy[t * WS] = make_float2(yr, yi);
         }
     };
     auto scatter_one = [&](const int4 h, int r) {
-        int ap = ta - (h.z & 0xff), bp = tb - (h.z >> 8);
+        const int mv = h.z >> 8;
+        int ap = ta - (h.z & 0xff), bp = tb - mv, bp1 = tb + NBH - mv;
         ap += ap < 0 ? W : 0;
         bp += bp < 0 ? W : 0;
+        bp1 += bp1 < 0 ? W : 0;
+        bp1 -= bp1 >= W ? W : 0;
         const int nu = h.x + ap, nv = h.y + bp;
         if (nu != cu || nv != cv || h.w != ck) {
             flush_acc();
-            cu = nu; cv = nv; ck = h.w;
+            cu = nu; cv = nv; cv1 = h.y + bp1; ck = h.w;
         }
-        const float wuv = rku[r * W + ap] * rkv[r * W + bp];
-        const float2 *wy = rwy + r * Ww;
+        const float ku = rku[r * KS + ap];
+        const float w0 = ku * rkv[r * KS + bp], w1 = two ? ku * rkv[r * KS + bp1] : 0.f;
+        const float2 *wy = rwy + r * WS;
 #pragma unroll
         for (int c = 0; c < Ww; ++c) {
             const float2 q = wy[c];
-            acc[c].x = fmaf(wuv, q.x, acc[c].x);
-            acc[c].y = fmaf(wuv, q.y, acc[c].y);
+            acc0[c].x = fmaf(w0, q.x, acc0[c].x);
+            acc0[c].y = fmaf(w0, q.y, acc0[c].y);
+            acc1[c].x = fmaf(w1, q.x, acc1[c].x);
+            acc1[c].y = fmaf(w1, q.y, acc1[c].y);
         }
     };
     __syncthreads();
@@ -622,12 +650,12 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
             float ku[W], kv[W], kw[Ww];
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                ku[i] = es_kernel(c.ou + (float)i, ihw, bt);
-                kv[i] = es_kernel(c.ov + (float)i, ihw, bt);
+                ku[i] = es_kernel_fast(c.ou + (float)i, ihw, bt);
+                kv[i] = es_kernel_fast(c.ov + (float)i, ihw, bt);
             }
             if (Ww > 1) {
 #pragma unroll
-                for (int i = 0; i < Ww; ++i) kw[i] = es_kernel(c.ow + (float)i, ihw, bt);
+                for (int i = 0; i < Ww; ++i) kw[i] = es_kernel_fast(c.ow + (float)i, ihw, bt);
             } else {
                 kw[0] = 1.f;
             }

@@ -504,10 +504,10 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         bp += bp < 0 ? W : 0;
         bp1 += bp1 < 0 ? W : 0;
         bp1 -= bp1 >= W ? W : 0;
-        const int nu = h.x + ap, nv = h.y + bp;
-        if (nu != cu || nv != cv || h.w != ck) {
+        const int nu = h.x + ap, nv = h.y + bp, nv1 = h.y + bp1;
+        if (nu != cu || nv != cv || nv1 != cv1 || h.w != ck) {
             flush_acc();
-            cu = nu; cv = nv; cv1 = h.y + bp1; ck = h.w;
+            cu = nu; cv = nv; cv1 = nv1; ck = h.w;
         }
         const float ku = rku[r * KS + ap];
         const float w0 = ku * rkv[r * KS + bp], w1 = two ? ku * rkv[r * KS + bp1] : 0.f;

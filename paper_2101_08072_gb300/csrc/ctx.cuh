@@ -36,6 +36,7 @@ struct Plan {
     std::vector<int> band_h;
     std::vector<int64_t> band_items_begin, band_items_end;
     std::vector<int64_t> work_begin; // per band offset into d_work (size nband + 1)
+    std::vector<int64_t> work_heavy_end; // per band: end of the heavy-tile chunks (they come first)
     std::vector<int64_t> heavy_begin; // per band offset into d_heavy (size nband + 1)
 
     // ---- device

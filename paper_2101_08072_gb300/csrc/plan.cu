@@ -546,6 +546,7 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     std::vector<WorkItem> work;
     std::vector<int> heavy;
     p.work_begin.assign(p.nband + 1, 0);
+    p.work_heavy_end.assign(p.nband, 0);
     p.heavy_begin.assign(p.nband + 1, 0);
     p.band_items_begin.assign(p.nband, 0);
     p.band_items_end.assign(p.nband, 0);
@@ -563,6 +564,7 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
                 for (int64_t c = s; c < e; c += chunk) work.push_back({(int)t, 1, c, std::min(e, c + chunk)});
             }
         }
+        p.work_heavy_end[b] = (int64_t)work.size();
         for (int64_t t = 0; t < ntiles; ++t) {
             const int64_t s = tb[b * ntiles + t], e = tb[b * ntiles + t + 1];
             if (e - s <= chunk) work.push_back({(int)t, 0, s, e});

@@ -342,14 +342,11 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     }
     for (int e = threadIdx.x; e < R * SLOT; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
 
-    // group geometry: thread (ta, tb) of a group owns the cell classes (ta, tb) and
-    // (ta, tb + NBH) mod W (the second only when tb + NBH < W)
-    constexpr int NBH = (W + 1) / 2;
-    constexpr int G = W * NBH;
+    // group geometry: thread (ta, tb) of a group owns the cell class (ta, tb) mod W
+    constexpr int G = W * W;
     const int ngroups = blockDim.x / G;
     const int grp = threadIdx.x / G, lid = threadIdx.x - grp * G;
-    const int ta = lid / NBH, tb = lid - ta * NBH;
-    const bool two = tb + NBH < W;
+    const int ta = lid / W, tb = lid - ta * W;
     const bool in_group = grp < ngroups;
     const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
     auto bucket_of = [&](int64_t pos) {
@@ -367,40 +364,26 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         c1 = min(min((int64_t)wi.end, off[kbase + kq + 1]), c0 + RES_CH);
     };
 
-    float2 acc0[Ww], acc1[Ww];
-    int cu = -1000, cv = -1000, ck = -1000;   // current cells (cu, cv) and (cu, cv1), planes ck..ck+Ww-1
-    int cv1 = -1000;
+    float2 acc[Ww];
+    int cu = -1000, cv = -1000, ck = -1000;   // current cell (cu, cv), planes ck..ck+Ww-1
     auto flush_acc = [&]() {
-        if ((unsigned)cu < (unsigned)TILE) {
-            const bool ok0 = (unsigned)cv < (unsigned)TILE, ok1 = two && (unsigned)cv1 < (unsigned)TILE;
+        if ((unsigned)cu < (unsigned)TILE && (unsigned)cv < (unsigned)TILE) {
 #pragma unroll
             for (int c = 0; c < Ww; ++c) {
                 const int k = ck + c;
                 if (k >= k_lo && k < k_hi) {
-                    float2 *rowp = ring + (k % R) * SLOT + cu * RSTRIDE;
-                    if (ok0) {
-                        atomicAdd(&rowp[cv].x, acc0[c].x);
-                        atomicAdd(&rowp[cv].y, acc0[c].y);
-                    }
-                    if (ok1) {
-                        atomicAdd(&rowp[cv1].x, acc1[c].x);
-                        atomicAdd(&rowp[cv1].y, acc1[c].y);
-                    }
+                    float2 *cell = ring + (k % R) * SLOT + cu * RSTRIDE + cv;
+                    atomicAdd(&cell->x, acc[c].x);
+                    atomicAdd(&cell->y, acc[c].y);
                 }
             }
         }
 #pragma unroll
-        for (int c = 0; c < Ww; ++c) {
-            acc0[c] = make_float2(0.f, 0.f);
-            acc1[c] = make_float2(0.f, 0.f);
-        }
-        cu = cv = cv1 = ck = -1000;
+        for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
+        cu = cv = ck = -1000;
     };
 #pragma unroll
-    for (int c = 0; c < Ww; ++c) {
-        acc0[c] = make_float2(0.f, 0.f);
-        acc1[c] = make_float2(0.f, 0.f);
-    }
+    for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
     // write planes [next, upto) from the ring to HBM and clear their slots (CTA-wide)
     int next = k_lo;
     auto flush_planes = [&](int upto) {
@@ -498,27 +481,21 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         }
     };
     auto scatter_one = [&](const int4 h, int r) {
-        const int mv = h.z >> 8;
-        int ap = ta - (h.z & 0xff), bp = tb - mv, bp1 = tb + NBH - mv;
+        int ap = ta - (h.z & 0xff), bp = tb - (h.z >> 8);
         ap += ap < 0 ? W : 0;
         bp += bp < 0 ? W : 0;
-        bp1 += bp1 < 0 ? W : 0;
-        bp1 -= bp1 >= W ? W : 0;
-        const int nu = h.x + ap, nv = h.y + bp, nv1 = h.y + bp1;
-        if (nu != cu || nv != cv || nv1 != cv1 || h.w != ck) {
+        const int nu = h.x + ap, nv = h.y + bp;
+        if (nu != cu || nv != cv || h.w != ck) {
             flush_acc();
-            cu = nu; cv = nv; cv1 = nv1; ck = h.w;
+            cu = nu; cv = nv; ck = h.w;
         }
-        const float ku = rku[r * KS + ap];
-        const float w0 = ku * rkv[r * KS + bp], w1 = two ? ku * rkv[r * KS + bp1] : 0.f;
+        const float wuv = rku[r * KS + ap] * rkv[r * KS + bp];
         const float2 *wy = rwy + r * WS;
 #pragma unroll
         for (int c = 0; c < Ww; ++c) {
             const float2 q = wy[c];
-            acc0[c].x = fmaf(w0, q.x, acc0[c].x);
-            acc0[c].y = fmaf(w0, q.y, acc0[c].y);
-            acc1[c].x = fmaf(w1, q.x, acc1[c].x);
-            acc1[c].y = fmaf(w1, q.y, acc1[c].y);
+            acc[c].x = fmaf(wuv, q.x, acc[c].x);
+            acc[c].y = fmaf(wuv, q.y, acc[c].y);
         }
     };
     __syncthreads();
@@ -938,11 +915,18 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                 KTimer t(ctx, "grid_tiles", st, 4.0 * nit + nvb * (vb + wb) + nk * plane_bytes);
                 if (sizeof(T) == 4 && grid_res_fit(p)) {
                     const int R = p.Ww;
+                    // dense (chunked) tiles first, then the owned light tiles, as two timed launches
+                    const int64_t wh = p.work_heavy_end[b];
+                    for (int part = 0; part < 2; ++part) {
+                        const int64_t a0 = part == 0 ? w0 : wh, a1 = part == 0 ? wh : w1;
+                        if (a1 <= a0) continue;
+                        KTimer tp(ctx, part == 0 ? "grid_dense" : "grid_light", st, 0.0, 0);
 #define PFB_GRID_CALL(WV, WWV)                                                                            \
-    launch_grid_res_t<WV, WWV>((unsigned)(w1 - w0), R, st, p.d_work + w0, p, (const float2 *)vis,          \
+    launch_grid_res_t<WV, WWV>((unsigned)(a1 - a0), R, st, p.d_work + a0, p, (const float2 *)vis,          \
                                (const float *)wgt, unit_vis ? 1 : 0, g, k_lo, k_hi, (float2 *)planes)
-                    PFB_W_SWITCH(p.W, p.wstack, PFB_GRID_CALL)
+                        PFB_W_SWITCH(p.W, p.wstack, PFB_GRID_CALL)
 #undef PFB_GRID_CALL
+                    }
                 } else {
                     k_grid_tiles<T><<<(unsigned)(w1 - w0), 256, smem, st>>>(p.d_work + w0, p.d_items, p.d_off,
                                                                              p.coords(), vis, wgt,

@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--serve", action="store_true",
+                    help="serving workload instead: Poisson stream of mixed-size pfb-clean requests")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--fp64", action="store_true", help="also time the FP64 path (eps 1e-9) on the same workload")
     return ap.parse_args()
 
 
@@ -304,6 +308,27 @@ def run_ours(args):
                 "frac": ach / hbm, "peak_source": peak_src, "traffic": None,
                 "share_of_step": d["ms"] / (ms * args.steps) if ms > 0 else None}
 
+    # ---- the FP64 path on the same workload (eps 1e-9), for the FP32-vs-FP64 comparison
+    fp64 = None
+    if args.fp64:
+        x64 = x.double()
+        w64 = wgt.double()
+        y64 = torch.empty_like(x64)
+        g64 = Geometry(nx=obs.nx, ny=obs.ny, dl=obs.dl, dm=obs.dm, nband=obs.nband, epsilon=1e-9)
+        ctx.pfb_hessian(g64, uvw, freq, band, x64, w64, out=y64)
+        torch.cuda.synchronize(dev)
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n64 = max(1, min(args.steps, 2))
+        h0.record(stream)
+        for _ in range(n64):
+            ctx.pfb_hessian(g64, uvw, freq, band, x64, w64, out=y64)
+        h1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = h0.elapsed_time(h1) / n64
+        fp64 = {"value": obs.nvis / (ms64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms64, "epsilon": 1e-9,
+                "steps": n64}
+        del x64, w64, y64
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         wnp = wgt.cpu().numpy().astype(np.float64)
@@ -314,7 +339,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded)",
                 "config": config(args, obs), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": own_launches, "clocks": clk,
+                "gpu_launches": own_launches, "clocks": clk, "fp64_path": fp64,
                 "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                             for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms"])},
@@ -326,10 +351,82 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ serving workload
+def serve_requests(n, seed=3, max_pix=4096, max_rows=1_000_000):
+    """n requests, each an independent pfb-clean solve: image 512^2..4096^2, rows 1e4..1e6,
+    channels 8..128, bands 1..4 (log-uniform), half FP32 at eps 1e-5 and half FP64 at
+    eps 1e-9, 10 steps each.  Visibilities are noise-like (the solver's cost does not
+    depend on their values); geometry from the MeerKAT-like array."""
+    from paper_2101_08072_gb300 import StepParams, synth
+    from paper_2101_08072_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    base = synth.meerkat_like_observation(ntime=450)
+    out = []
+    for i in range(n):
+        npix = int(2 ** round(np.log2(synth.log_uniform_int(rng, 512, max_pix + 1))))
+        nrow = int(min(synth.log_uniform_int(rng, 1e4, max_rows), base.nrow))
+        nchan = int(synth.log_uniform_int(rng, 8, 129))
+        nband = int(min(nchan, synth.log_uniform_int(rng, 1, 5)))
+        prec = "f32" if i % 2 == 0 else "f64"
+        rows = np.sort(rng.choice(base.nrow, nrow, replace=False))
+        freq = np.linspace(0.856e9, 1.712e9, nchan)
+        cell = 1.5 * 4096 / npix * synth.ARCSEC
+        vis = (rng.normal(size=(nrow, nchan)) + 1j * rng.normal(size=(nrow, nchan))).astype(
+            np.complex64 if prec == "f32" else np.complex128)
+        wgt = rng.uniform(0.5, 1.5, (nrow, nchan)).astype(np.float32 if prec == "f32" else np.float64)
+        out.append(Request(uvw=base.uvw[rows], freq=freq, band_of_chan=synth.contiguous_bands(nchan, nband),
+                           vis=vis, wgt=wgt, nx=npix, ny=npix, dl=cell, dm=cell, nband=nband,
+                           epsilon=1e-5 if prec == "f32" else 1e-9, precision=prec, n_iter=10,
+                           params=StepParams(gamma=1.0, sigma=1e-3, lam=1e-4, cg_iters=20, pd_iters=20)))
+    return out
+
+
+def run_serve(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2101_08072_gb300.serve import Server
+    reqs = serve_requests(args.serve_requests)
+    # offered load: a Poisson stream at 0.8 of the sequential capacity measured on the first request
+    srv = Server(0, max_active=8)
+    t0 = time.perf_counter()
+    srv.submit(reqs[0]).result()
+    t_one = time.perf_counter() - t0
+    srv.close()
+    rate = 0.8 / max(t_one, 1e-3)
+    from paper_2101_08072_gb300 import synth
+    arrivals = synth.poisson_arrivals(np.random.default_rng(4), len(reqs), rate)
+    srv = Server(0, max_active=8)
+    t0 = time.perf_counter()
+    futs = []
+    for r, ta in zip(reqs, arrivals):
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.001)
+        futs.append(srv.submit(r))
+    errors = 0
+    for f in futs:
+        try:
+            f.result()
+        except Exception:
+            errors += 1
+    srv.close()
+    m = srv.metrics()
+    line = {"metric": "serving latency (pfb-clean requests, 10 steps each)", "value": m["p50_s"], "unit": "s",
+            "higher_is_better": False, "p50_s": m["p50_s"], "p99_s": m["p99_s"], "mvis_per_s": m["mvis_per_s"],
+            "completed": m["completed"], "errors": errors, "requests": len(reqs), "arrival_rate_per_s": rate,
+            "data": "synthetic (seeded)", "n_gpus": 1,
+            "config": {"workload": "Poisson stream of mixed-size requests: 512^2-4096^2, 1e4-1e6 rows, "
+                                   "8-128 channels, 1-4 bands, half FP32 eps 1e-5 / half FP64 eps 1e-9"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -168,8 +168,9 @@ int pfb_psf_conv(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const void *
  * dual_inout [nbasis][nband][nx][ny] (nbasis = bits set in basis_mask), zero on
  * the first step.  n_hessian_out (host, may be NULL) receives 1; stats_out (host,
  * [3], may be NULL) receives [objective at x_k without the data constant,
- * ||x_{k+1} - x_k|| / ||x_{k+1}||, largest CG relative residual]; when either is
- * given the call returns after synchronising the stream. */
+ * ||x_{k+1} - x_k|| / ||x_{k+1}||, largest CG relative residual]; when stats_out
+ * is given the call returns after synchronising the stream, otherwise it only
+ * enqueues work. */
 int pfb_step(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_params *params,
              int64_t nrow, int32_t nchan, const double *uvw, const double *freq,
              const int32_t *band_of_chan, const void *wgt, const void *dirty, const void *psf,

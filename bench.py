@@ -115,6 +115,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ multi-rank helpers
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (the slowest rank times the job)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank processes
+    units_per_rank (independent replicas), timed by the slowest rank."""
+    return world * units_per_rank / (ms_max * 1e-3) / 1e6
+
+
 # ------------------------------------------------------------------ CPU oracle sample
 def oracle_sample(obs, x, wgt_rows, rows, pix):
     """Time the FP64 oracle on a bounded sample of the Hessian: R x on `rows`
@@ -250,11 +268,8 @@ def run_ours(args):
     own_launches = L.value
     lib.pfb_timing(ctx.h, 0)
 
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * obs.nvis / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, world, dev)
+    value = job_throughput(obs.nvis, world, ms)
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -280,12 +295,8 @@ def run_ours(args):
             h_y.copy_(y, non_blocking=True)
         f1.record(stream)
         barrier()
-        ems = f0.elapsed_time(f1) / args.e2e_steps
-        if world > 1:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * obs.nvis / (ems * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": bi,
+        ems = max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, world, dev)
+        e2e = {"value": job_throughput(obs.nvis, world, ems), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo}
 
     # ---- roofline of the dominant kernel group

@@ -405,8 +405,12 @@ int pfb_step(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const pfb_params *p
         PFB_REQUIRE(dirty && psf && wsum && x_inout && dual_inout, "dirty, psf, wsum, x and dual must not be NULL");
         PFB_REQUIRE(prm->gamma > 0 && prm->sigma > 0 && prm->lambda >= 0, "need gamma > 0, sigma > 0, lambda >= 0");
         PFB_REQUIRE(prm->cg_iters >= 0 && prm->pd_iters >= 0, "iteration counts must be >= 0");
-        if (prm->basis_mask != 1u)
-            throw Error(PFB_ERR_NOT_IMPLEMENTED, "only the Dirac basis (basis_mask = 1) is implemented in pfb_step");
+        PFB_REQUIRE(prm->basis_mask >= 1u && prm->basis_mask < 128u, "basis_mask must select bits 0..6");
+        if (prm->basis_mask != 1u) {
+            PFB_REQUIRE(prm->nlevel >= 1 && prm->nlevel <= 12, "nlevel must be in [1, 12]");
+            PFB_REQUIRE(g->nx % (1 << prm->nlevel) == 0 && g->ny % (1 << prm->nlevel) == 0,
+                        "wavelet bases need nx, ny divisible by 2^nlevel (periodised transform)");
+        }
         Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, S(stream));
         if (prec == PFB_F64)
             op_step<double>(c, p, *prm, (const double *)wgt, (const double *)dirty, (const double *)psf, wsum,

@@ -8,6 +8,7 @@
 #include "ctx.cuh"
 
 #include <algorithm>
+#include <complex>
 
 namespace pfb {
 
@@ -127,6 +128,7 @@ enum {
     S_COUNT
 };
 // per-band arrays follow: BB[nb] (||IR||^2), then RR[(iters+1)][nb], PAP[iters][nb]
+#define S_UNORM_IDX S_UNORM
 
 // IR = (I^d - H x) * inv_wbar; objective pieces (per band blocks, blockIdx.y = band)
 template <typename T>
@@ -271,7 +273,7 @@ __global__ void k_pd_dirac(int nx, int ny, int nband, const T *__restrict__ big,
 template <typename T>
 __global__ void k_finish(int64_t npix, int nband, const T *__restrict__ x1, T *__restrict__ x0_out,
                          double *__restrict__ sc) {
-    double dx2 = 0, x2 = 0, l21 = 0;
+    double dx2 = 0, x2 = 0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npix; q += (int64_t)gridDim.x * blockDim.x) {
         double g2 = 0;
         for (int b = 0; b < nband; ++b) {
@@ -282,11 +284,254 @@ __global__ void k_finish(int64_t npix, int nband, const T *__restrict__ x1, T *_
             g2 += a * a;
             x0_out[e] = x1[e];
         }
-        l21 += sqrt(g2);
+        (void)g2;
     }
     block_sum_atomic(dx2, &sc[S_DX2]);
     block_sum_atomic(x2, &sc[S_X2]);
-    block_sum_atomic(l21, &sc[S_L21]);
+}
+
+// ------------------------------------------------------------------ Daubechies dictionary (Eq. 9's Psi)
+// Low-pass filter of db_N by spectral factorisation (Daubechies 1988): the roots
+// y_k of P(y) = sum_{k<N} C(N-1+k, k) y^k (Durand-Kerner iteration), each mapped to
+// the root inside the unit circle of z^2 - (2 - 4 y_k) z + 1; h holds the
+// coefficients of (z + 1)^N prod (z - z_k), highest power first, scaled to sum sqrt(2).
+static std::vector<double> daubechies_filter(int N) {
+    typedef std::complex<double> C;
+    if (N == 1) return {M_SQRT1_2, M_SQRT1_2};
+    const int deg = N - 1;
+    std::vector<double> c(N);   // increasing powers
+    for (int k = 0; k < N; ++k) {
+        double b = 1.0;   // C(N-1+k, k)
+        for (int j = 1; j <= k; ++j) b = b * (N - 1 + j) / j;
+        c[k] = b;
+    }
+    auto P = [&](C y) {
+        C r = 0;
+        for (int k = deg; k >= 0; --k) r = r * y + c[k];
+        return r;
+    };
+    std::vector<C> ys(deg);
+    for (int i = 0; i < deg; ++i) ys[i] = std::pow(C(0.4, 0.9), i);
+    for (int it = 0; it < 500; ++it) {
+        double move = 0;
+        for (int i = 0; i < deg; ++i) {
+            C den = c[deg];
+            for (int j = 0; j < deg; ++j)
+                if (j != i) den *= ys[i] - ys[j];
+            const C d = P(ys[i]) / den;
+            ys[i] -= d;
+            move = std::max(move, std::abs(d));
+        }
+        if (move < 1e-15) break;
+    }
+    std::vector<C> poly(1, C(1));   // increasing powers
+    auto mul = [&](C root) {       // poly *= (z - root)
+        std::vector<C> np(poly.size() + 1, C(0));
+        for (size_t k = 0; k < poly.size(); ++k) {
+            np[k + 1] += poly[k];
+            np[k] -= root * poly[k];
+        }
+        poly = np;
+    };
+    for (int k = 0; k < N; ++k) mul(C(-1));
+    for (int i = 0; i < deg; ++i) {
+        const C a = 1.0 - 2.0 * ys[i];
+        const C sq = std::sqrt(a * a - 1.0);
+        const C z1 = a + sq, z2 = a - sq;
+        mul(std::abs(z1) < 1.0 ? z1 : z2);
+    }
+    std::vector<double> h(poly.size());
+    double sum = 0;
+    for (size_t k = 0; k < poly.size(); ++k) {
+        h[k] = poly[poly.size() - 1 - k].real();   // highest power first
+        sum += h[k];
+    }
+    for (auto &v : h) v *= M_SQRT2 / sum;
+    return h;
+}
+
+constexpr int MAX_TAPS = 12;
+struct WavFilt {
+    int L;
+    double h[MAX_TAPS], g[MAX_TAPS];   // low-pass and high-pass g_k = (-1)^k h_{L-1-k}
+};
+
+static WavFilt wav_filter(int N) {
+    static std::map<int, WavFilt> cache;
+    auto it = cache.find(N);
+    if (it != cache.end()) return it->second;
+    std::vector<double> h = daubechies_filter(N);
+    WavFilt f;
+    f.L = (int)h.size();
+    for (int k = 0; k < f.L; ++k) {
+        f.h[k] = h[k];
+        f.g[k] = ((k & 1) ? -1.0 : 1.0) * h[f.L - 1 - k];
+    }
+    cache[N] = f;
+    return f;
+}
+
+// One level of the periodised DWT of the [n x m] block at the top-left of each
+// band image (row stride ny) along axis 0 (rows, i) or 1 (columns, j):
+//   a[k] = sum_t h[t] x[(2k + t) mod n_ax],  d[k] = sum_t g[t] x[(2k + t) mod n_ax]
+// with a stored in [0, n_ax/2) and d in [n_ax/2, n_ax) of that axis.
+template <typename T>
+__global__ void k_dwt_level(int nx, int ny, int nband, int n, int m, int axis, WavFilt f,
+                            const T *__restrict__ in, T *__restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)n * m;
+    if (e >= per * nband) return;
+    const int b = (int)(e / per);
+    const int r = (int)(e - (int64_t)b * per);
+    const int i = r / m, j = r - i * m;
+    const T *src = in + (int64_t)b * nx * ny;
+    const int N = axis == 0 ? n : m;
+    const int pos = axis == 0 ? i : j;
+    const int half = N / 2;
+    const bool hi = pos >= half;
+    const int k = hi ? pos - half : pos;
+    double acc = 0;
+    for (int t = 0; t < f.L; ++t) {
+        int q = 2 * k + t;
+        q %= N;
+        const double xv = axis == 0 ? (double)src[(int64_t)q * ny + j] : (double)src[(int64_t)i * ny + q];
+        acc += (hi ? f.g[t] : f.h[t]) * xv;
+    }
+    out[(int64_t)b * nx * ny + (int64_t)i * ny + j] = (T)acc;
+}
+
+// Transpose (= inverse) of k_dwt_level:
+//   x[p] = sum_{t = p mod 2} h[t] a[((p - t) mod N)/2] + g[t] d[((p - t) mod N)/2]
+template <typename T>
+__global__ void k_idwt_level(int nx, int ny, int nband, int n, int m, int axis, WavFilt f,
+                             const T *__restrict__ in, T *__restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)n * m;
+    if (e >= per * nband) return;
+    const int b = (int)(e / per);
+    const int r = (int)(e - (int64_t)b * per);
+    const int i = r / m, j = r - i * m;
+    const T *src = in + (int64_t)b * nx * ny;
+    const int N = axis == 0 ? n : m;
+    const int pos = axis == 0 ? i : j;
+    const int half = N / 2;
+    double acc = 0;
+    for (int t = 0; t < f.L; ++t) {
+        int q = pos - t;
+        q %= N;
+        q += q < 0 ? N : 0;
+        if (q & 1) continue;
+        const int k = q >> 1;
+        const double av = axis == 0 ? (double)src[(int64_t)k * ny + j] : (double)src[(int64_t)i * ny + k];
+        const double dv = axis == 0 ? (double)src[(int64_t)(k + half) * ny + j] : (double)src[(int64_t)i * ny + k + half];
+        acc += f.h[t] * av + f.g[t] * dv;
+    }
+    out[(int64_t)b * nx * ny + (int64_t)i * ny + j] = (T)acc;
+}
+
+// copy the [n x m] top-left block of each band image
+template <typename T>
+__global__ void k_copy_block(int nx, int ny, int nband, int n, int m, const T *__restrict__ in, T *__restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)n * m;
+    if (e >= per * nband) return;
+    const int b = (int)(e / per);
+    const int r = (int)(e - (int64_t)b * per);
+    const int i = r / m, j = r - i * m;
+    const int64_t o = (int64_t)b * nx * ny + (int64_t)i * ny + j;
+    out[o] = in[o];
+}
+
+// coef = multi-level 2-D DWT of img (Mallat layout); tmp is scratch of the same size
+template <typename T>
+static void dwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, const T *img, T *coef, T *tmp,
+                 cudaStream_t st) {
+    PFB_CUDA(cudaMemcpyAsync(coef, img, (size_t)nband * nx * ny * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    int n = nx, m = ny;
+    for (int lv = 0; lv < nlevel; ++lv) {
+        const int64_t cnt = (int64_t)n * m * nband;
+        const unsigned gb = (unsigned)((cnt + 255) / 256);
+        k_dwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 0, f, coef, tmp);
+        k_dwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 1, f, tmp, coef);
+        check_launch("dwt");
+        n /= 2;
+        m /= 2;
+    }
+}
+
+// img = inverse of dwt2 (coef is overwritten)
+template <typename T>
+static void idwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, T *coef, T *tmp, cudaStream_t st) {
+    int n = nx >> (nlevel - 1), m = ny >> (nlevel - 1);
+    for (int lv = 0; lv < nlevel; ++lv) {
+        const int64_t cnt = (int64_t)n * m * nband;
+        const unsigned gb = (unsigned)((cnt + 255) / 256);
+        k_idwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 1, f, coef, tmp);
+        k_idwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 0, f, tmp, coef);
+        check_launch("idwt");
+        n *= 2;
+        m *= 2;
+    }
+}
+
+// primal update for a general dictionary: x~ = max(0, x - tau (grad + psiv)),
+// u = 2 x~ - x (kept for the dual update), x = x~
+template <typename T>
+__global__ void k_pd_primal(int nx, int ny, int nband, const T *__restrict__ big, const T *__restrict__ xbar,
+                            const T *__restrict__ psiv, T sigma, T gamma, const double *__restrict__ sc,
+                            double inv_wbar, double unorm_fixed, T *__restrict__ x, T *__restrict__ u) {
+    const int64_t npix = (int64_t)nx * ny;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= npix * nband) return;
+    const double unorm = unorm_fixed > 0 ? unorm_fixed : sc[S_UNORM_IDX] * inv_wbar + (double)sigma;
+    const T tau = (T)(0.98 / (0.5 * unorm / (double)gamma + 1.0));
+    const int64_t b = e / npix, q = e - b * npix;
+    const int64_t i = q / ny, j = q - i * ny;
+    const T xv = x[e];
+    const T grad = (big[(b * 2 * nx + i) * 2 * ny + j] + sigma * (xv - xbar[e])) / gamma;
+    T xn = xv - tau * (grad + psiv[e]);
+    xn = xn > 0 ? xn : 0;
+    u[e] = 2 * xn - xv;
+    x[e] = xn;
+}
+
+// dual update of one basis: v~ = v + c * s (s = 1/sqrt(K)), projected onto the l2
+// ball of radius lam per group (the bands of one coefficient)
+template <typename T>
+__global__ void k_pd_dual(int64_t npix, int nband, const T *__restrict__ c, T s, T lam, T *__restrict__ v) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= npix) return;
+    T vt[32];
+    T n2 = 0;
+    for (int b = 0; b < nband; ++b) {
+        const T t = v[b * npix + q] + s * c[b * npix + q];
+        vt[b] = t;
+        n2 += t * t;
+    }
+    const T nrm = sqrt(n2);
+    const T f = nrm > lam ? lam / nrm : (T)1;
+    for (int b = 0; b < nband; ++b) v[b * npix + q] = vt[b] * f;
+}
+
+template <typename T>
+__global__ void k_axpy(int64_t n, T a, const T *__restrict__ x, T *__restrict__ y) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) y[e] += a * x[e];
+}
+
+// sum_q ||coef[:, q]||_2 over bands (for the l2,1 term of the objective)
+template <typename T>
+__global__ void k_l21(int64_t npix, int nband, const T *__restrict__ c, double scale, double *__restrict__ out) {
+    double acc = 0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npix; q += (int64_t)gridDim.x * blockDim.x) {
+        double g2 = 0;
+        for (int b = 0; b < nband; ++b) {
+            const double v = (double)c[b * npix + q];
+            g2 += v * v;
+        }
+        acc += sqrt(g2);
+    }
+    block_sum_atomic(acc * scale, out);
 }
 
 // ------------------------------------------------------------------ spectrum cache
@@ -390,6 +635,26 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
         k_residual<T><<<gr, 256, 0, st>>>(npix, dirty, hx, x, inv_wbar, ir, sc, bb);
         check_launch("residual");
     }
+    // objective's l2,1 term at x_k: ||Psi^dagger x_k||_{2,1} (Psi normalised by 1/sqrt(K))
+    std::vector<int> bases;
+    for (int k = 0; k < 7; ++k)
+        if (prm.basis_mask >> k & 1u) bases.push_back(k);
+    const int K = (int)bases.size();
+    const double inv_sqrt_k = 1.0 / std::sqrt((double)K);
+    T *wa = nullptr, *wb = nullptr;
+    if (prm.basis_mask != 1u) {
+        wa = (T *)ctx.scratch("st_wa", img);
+        wb = (T *)ctx.scratch("st_wb", img);
+    }
+    for (int k : bases) {
+        const T *coef = x;
+        if (k > 0) {
+            dwt2<T>(nx, ny, nb, prm.nlevel, wav_filter(k), x, wa, wb, st);
+            coef = wa;
+        }
+        k_l21<T><<<rblocks(npix, 2 * ctx.num_sms), 256, 0, st>>>(npix, nb, coef, inv_sqrt_k, &sc[S_L21]);
+        check_launch("l21");
+    }
     // 3. CG for U delta = IR (per band)
     cx_t<T> *S = psf_spectrum<T>(ctx, nx, ny, nb, psf, st);
     T *padded = (T *)ctx.scratch("img_pad", (size_t)nbig * sizeof(T));
@@ -422,13 +687,49 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
         check_launch("absmax");
     }
     const double unorm_fixed = prm.unorm > 0 ? prm.unorm : -1.0;
+    T *psiv = nullptr, *ubuf = nullptr;
+    if (prm.basis_mask != 1u) {
+        psiv = (T *)ctx.scratch("st_psiv", img);
+        ubuf = (T *)ctx.scratch("st_u", img);
+    }
+    const unsigned gn = (unsigned)((n + 255) / 256);
     for (int it = 0; it < prm.pd_iters; ++it) {
         k_pad<T><<<(unsigned)((nbig + 255) / 256), 256, 0, st>>>(nx, ny, nb, xk1, xbar, padded);
         check_launch("pd_pad");
         conv_padded<T>(ctx, nx, ny, nb, padded, S, conv_scale, true, st);
-        k_pd_dirac<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
-            nx, ny, nb, padded, xbar, sigma, (T)prm.gamma, (T)prm.lambda, sc, inv_wbar, unorm_fixed, xk1, dual);
-        check_launch("pd_dirac");
+        if (prm.basis_mask == 1u) {   // Dirac only: one fused kernel
+            k_pd_dirac<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
+                nx, ny, nb, padded, xbar, sigma, (T)prm.gamma, (T)prm.lambda, sc, inv_wbar, unorm_fixed, xk1, dual);
+            check_launch("pd_dirac");
+            continue;
+        }
+        // Psi v = sum_k Psi_k v_k / sqrt(K)
+        PFB_CUDA(cudaMemsetAsync(psiv, 0, img, st));
+        for (int t = 0; t < K; ++t) {
+            T *vk = dual + (size_t)t * n;
+            if (bases[t] == 0) {
+                k_axpy<T><<<gn, 256, 0, st>>>(n, (T)inv_sqrt_k, vk, psiv);
+            } else {
+                PFB_CUDA(cudaMemcpyAsync(wa, vk, img, cudaMemcpyDeviceToDevice, st));
+                idwt2<T>(nx, ny, nb, prm.nlevel, wav_filter(bases[t]), wa, wb, st);
+                k_axpy<T><<<gn, 256, 0, st>>>(n, (T)inv_sqrt_k, wa, psiv);
+            }
+            check_launch("psi");
+        }
+        k_pd_primal<T><<<gn, 256, 0, st>>>(nx, ny, nb, padded, xbar, psiv, sigma, (T)prm.gamma, sc, inv_wbar,
+                                           unorm_fixed, xk1, ubuf);
+        check_launch("pd_primal");
+        // v_k = proj(v_k + Psi_k^dagger (2 x~ - x) / sqrt(K))
+        for (int t = 0; t < K; ++t) {
+            const T *c = ubuf;
+            if (bases[t] != 0) {
+                dwt2<T>(nx, ny, nb, prm.nlevel, wav_filter(bases[t]), ubuf, wa, wb, st);
+                c = wa;
+            }
+            k_pd_dual<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(npix, nb, c, (T)inv_sqrt_k,
+                                                                        (T)prm.lambda, dual + (size_t)t * n);
+            check_launch("pd_dual");
+        }
     }
     // 6. statistics and output
     k_finish<T><<<rblocks(npix, 2 * ctx.num_sms), 256, 0, st>>>(npix, nb, xk1, x, sc);

@@ -165,9 +165,10 @@ def test_psf_conv(ctx, prec):
     assert rel_l2(y, ref) <= (1e-5 if prec == 32 else 1e-12)
 
 
-@pytest.mark.parametrize("prec", [32, 64])
-def test_step_fixed_iterations(ctx, prec):
-    """One pfb step against the oracle's step at identical iteration counts."""
+@pytest.mark.parametrize("prec,mask", [(32, 1), (64, 1), (32, 0b1111111), (64, 0b1111111)])
+def test_step_fixed_iterations(ctx, prec, mask):
+    """One pfb step against the oracle's step at identical iteration counts, with the
+    Dirac basis alone and with the full dictionary of Eq. 9 (Dirac + db1..db6)."""
     from paper_2101_08072_gb300 import StepParams
     obs = synth.tiny_observation(nx=32, ny=32, nband=2)
     rng = np.random.default_rng(107)
@@ -178,13 +179,15 @@ def test_step_fixed_iterations(ctx, prec):
     d, ws = oracle.dirty(*a, V, w, 32, 32, obs.dl, obs.dm, 2)
     p, _ = oracle.psf(*a, w, 32, 32, obs.dl, obs.dm, 2)
     x0 = 0.5 * xt
-    v0 = np.zeros((1, 2, 32, 32))
-    prm = oracle.Params(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=10, pd_iters=20)
+    nbasis = bin(mask).count("1")
+    v0 = np.zeros((nbasis, 2, 32, 32))
+    prm = oracle.Params(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=10, pd_iters=20, nlevel=2, basis_mask=mask)
     x1, v1, st = oracle.step(*a, w, d, p, ws, x0, v0, obs.dl, obs.dm, prm)
     eps = EPS32 if prec == 32 else EPS64
     g = geometry(obs, eps)
     xg, vg = real_t(x0, prec), real_t(v0, prec)
-    nh, stg = ctx.pfb_step(g, StepParams(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=10, pd_iters=20), *dev_obs(obs),
+    nh, stg = ctx.pfb_step(g, StepParams(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=10, pd_iters=20, nlevel=2,
+                                         basis_mask=mask), *dev_obs(obs),
                            real_t(w, prec), real_t(d, prec), real_t(p, prec), ws, xg, vg)
     tol = 1e-4 if prec == 32 else 1e-8
     assert nh == 1

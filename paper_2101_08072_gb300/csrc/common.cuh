@@ -61,6 +61,21 @@ template <typename T> using cx_t = typename Cx<T>::type;
 __device__ __forceinline__ void sincos_turns(float r, float *s, float *c) { sincospif(2.0f * r, s, c); }
 __device__ __forceinline__ void sincos_turns(double r, double *s, double *c) { sincospi(2.0 * r, s, c); }
 
+// Phase of w-plane k in turns, th0 + k * dth, for a pixel whose per-plane step
+// dth = dth_hi + dth_lo (double-float) and offset th0 were reduced in FP64 once.
+// FP32: the product k * dth_hi is split exactly (TwoProduct by FMA) and its integer
+// part dropped before the small terms are added, so the result stays accurate to
+// ~1e-9 turns for any plane count.
+__device__ __forceinline__ float plane_turns(int k, float th0, float dth_hi, float dth_lo) {
+    const float kf = (float)k;
+    const float p = kf * dth_hi;
+    const float e = fmaf(kf, dth_hi, -p);
+    return (p - rintf(p)) + (e + fmaf(kf, dth_lo, th0));
+}
+__device__ __forceinline__ double plane_turns(int k, double th0, double dth_hi, double dth_lo) {
+    return th0 + (double)k * (dth_hi + dth_lo);
+}
+
 // exp(i 2 pi phi) for a phase given in turns; the phase is range-reduced in FP64
 // first, then evaluated in the working precision T.
 template <typename T>

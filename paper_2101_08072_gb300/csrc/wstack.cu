@@ -32,9 +32,14 @@ __global__ void k_prepass(int nx, int ny, const T *__restrict__ x, const T *__re
     const int64_t pos = (int64_t)gu * g.Nv + gv;
     const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
     const double t = tp[p];
+    // phase of plane k in turns: (w0 + k dw) t = th0 + k dth, both reduced mod 1 in
+    // FP64 once per pixel; the per-plane sum is formed in the working precision
+    const double a0 = g.w0 * t, a1 = dw * t;
+    const double d1 = a1 - rint(a1);
+    const T th0 = (T)(a0 - rint(a0)), dth_hi = (T)d1, dth_lo = (T)(d1 - (double)dth_hi);
     for (int k = k_lo; k < k_hi; ++k) {
         T cs = 1, sn = 0;
-        if (g.Ww > 1) cis_turns<T>((g.w0 + k * dw) * t, &cs, &sn);
+        if (g.Ww > 1) sincos_turns(plane_turns(k, th0, dth_hi, dth_lo), &sn, &cs);
         cx_t<T> v;
         v.x = c * cs;
         v.y = -c * sn;
@@ -709,12 +714,15 @@ __global__ void k_postpass(int nx, int ny, const T *__restrict__ corr, const dou
     const int64_t pos = (int64_t)gu * g.Nv + gv;
     const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
     const double t = tp[p];
+    const double a0 = g.w0 * t, a1 = dw * t;
+    const double d1 = a1 - rint(a1);
+    const T th0 = (T)(a0 - rint(a0)), dth_hi = (T)d1, dth_lo = (T)(d1 - (double)dth_hi);
     T acc = 0;
     for (int k = k_lo; k < k_hi; ++k) {
         const cx_t<T> h = planes[(int64_t)(k - k_lo) * plane_sz + pos];
         if (g.Ww > 1) {
             T cs, sn;
-            cis_turns<T>((g.w0 + k * dw) * t, &cs, &sn);
+            sincos_turns(plane_turns(k, th0, dth_hi, dth_lo), &sn, &cs);
             acc += h.x * cs - h.y * sn;
         } else {
             acc += h.x;

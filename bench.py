@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving workload instead: Poisson stream of mixed-size pfb-clean requests")
     ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-max-pix", type=int, default=4096)
+    ap.add_argument("--serve-max-rows", type=int, default=1_000_000)
     ap.add_argument("--fp64", action="store_true", help="also time the FP64 path (eps 1e-9) on the same workload")
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-entry-point timings")
     return ap.parse_args()
 
 
@@ -113,6 +116,76 @@ class Clocks:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ measured traffic
+def source_digest() -> str:
+    """Digest of the CUDA sources (a profiled traffic figure is only valid for them)."""
+    import hashlib
+    d = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2101_08072_gb300", "csrc")
+    for f in sorted(os.listdir(src)):
+        d.update(open(os.path.join(src, f), "rb").read())
+    return d.hexdigest()[:16]
+
+
+def profiled_traffic(group: str):
+    """DRAM bytes (read + write) per launch of a kernel group, from profiles/traffic.json,
+    or None when absent or taken on different sources."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    e = t.get(group)
+    if not e or e.get("source_digest") != source_digest():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------ per-row timings
+def time_rows(ctx, lib, g, obs, uvw, freq, band, x, wgt, stream, dev, reps=2):
+    import torch
+    from paper_2101_08072_gb300 import StepParams
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    nvis = obs.nvis
+    vis = torch.empty((obs.nrow, obs.nchan), dtype=torch.complex64, device=dev)
+    out = {}
+    ms = timed(lambda: ctx.pfb_degrid(g, uvw, freq, band, x, out=vis))
+    out["R (pfb_degrid)"] = {"ms": ms, "Mvis/s": nvis / ms / 1e3}
+    img = torch.empty_like(x)
+    ms = timed(lambda: ctx.pfb_grid(g, uvw, freq, band, vis, wgt, out=img))
+    out["R^dagger Sigma^-1 (pfb_grid)"] = {"ms": ms, "Mvis/s": nvis / ms / 1e3}
+    ms = timed(lambda: ctx.pfb_dirty(g, uvw, freq, band, vis, wgt, out=img))
+    out["dirty (pfb_dirty)"] = {"ms": ms, "Mvis/s": nvis / ms / 1e3}
+    psf = torch.empty((obs.nband, 2 * obs.nx, 2 * obs.ny), dtype=x.dtype, device=dev)
+    ms = timed(lambda: ctx.pfb_psf(g, uvw, freq, band, wgt, out=psf))
+    out["PSF (pfb_psf, 2x field)"] = {"ms": ms, "Mvis/s": nvis / ms / 1e3}
+    ms = timed(lambda: ctx.pfb_psf_conv(g, psf, x, out=img))
+    # algorithmic bytes: read x, write y, read the cached half spectrum of the 2x grid
+    b = obs.nband * (obs.nx * obs.ny * 8 + (2 * obs.nx) * (obs.ny + 1) * 8)
+    out["PSF convolution (pfb_psf_conv)"] = {"ms": ms, "GB/s": b / ms / 1e6}
+    _, ws = ctx.pfb_dirty(g, uvw, freq, band, vis, wgt, out=img)
+    prm = StepParams(gamma=1.0, sigma=1e-3, lam=1e-4, cg_iters=10, pd_iters=10, basis_mask=1)
+    xs = torch.zeros_like(x)
+    dual = torch.zeros((1,) + tuple(x.shape), dtype=x.dtype, device=dev)
+    ms = timed(lambda: ctx.pfb_step(g, prm, uvw, freq, band, wgt, img, psf, ws, xs, dual, stats=False))
+    out["pfb_step (1 Hessian, 10 CG, 10 primal-dual, Dirac)"] = {"ms": ms, "Mvis/s": nvis / ms / 1e3}
+    prm7 = StepParams(gamma=1.0, sigma=1e-3, lam=1e-4, cg_iters=10, pd_iters=10, basis_mask=0b1111111, nlevel=3)
+    dual7 = torch.zeros((7,) + tuple(x.shape), dtype=x.dtype, device=dev)
+    ms = timed(lambda: ctx.pfb_step(g, prm7, uvw, freq, band, wgt, img, psf, ws, xs, dual7, stats=False))
+    out["pfb_step (10 CG, 10 primal-dual, Dirac + db1..db6)"] = {"ms": ms}
+    return out
 
 
 # ------------------------------------------------------------------ multi-rank helpers
@@ -299,7 +372,8 @@ def run_ours(args):
         e2e = {"value": job_throughput(obs.nvis, world, ems), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo}
 
-    # ---- roofline of the dominant kernel group
+    # ---- roofline of the dominant kernel group (traffic from the committed DRAM capture
+    # of that kernel, when its source has not changed since)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -316,7 +390,7 @@ def run_ours(args):
         per_launch_bytes = d["bytes"] / max(d["launches"], 1)
         ach = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
         roof = {"kernel": nm, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "peak_source": peak_src, "traffic": None,
+                "frac": ach / hbm, "peak_source": peak_src, "traffic": profiled_traffic(nm),
                 "share_of_step": d["ms"] / (ms * args.steps) if ms > 0 else None}
 
     # ---- the FP64 path on the same workload (eps 1e-9), for the FP32-vs-FP64 comparison
@@ -340,6 +414,11 @@ def run_ours(args):
                 "steps": n64}
         del x64, w64, y64
 
+    # ---- every entry point of the path on the same workload (one warm call, then timed calls)
+    rows = None
+    if not args.no_rows:
+        rows = time_rows(ctx, lib, g, obs, uvw, freq, band, x, wgt, stream, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         wnp = wgt.cpu().numpy().astype(np.float64)
@@ -350,7 +429,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded)",
                 "config": config(args, obs), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": own_launches, "clocks": clk, "fp64_path": fp64,
+                "gpu_launches": own_launches, "clocks": clk, "fp64_path": fp64, "rows": rows,
                 "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                             for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms"])},
@@ -397,7 +476,7 @@ def run_serve(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2101_08072_gb300.serve import Server
-    reqs = serve_requests(args.serve_requests)
+    reqs = serve_requests(args.serve_requests, max_pix=args.serve_max_pix, max_rows=args.serve_max_rows)
     # offered load: a Poisson stream at 0.8 of the sequential capacity measured on the first request
     srv = Server(0, max_active=8)
     t0 = time.perf_counter()
@@ -426,8 +505,9 @@ def run_serve(args):
             "higher_is_better": False, "p50_s": m["p50_s"], "p99_s": m["p99_s"], "mvis_per_s": m["mvis_per_s"],
             "completed": m["completed"], "errors": errors, "requests": len(reqs), "arrival_rate_per_s": rate,
             "data": "synthetic (seeded)", "n_gpus": 1,
-            "config": {"workload": "Poisson stream of mixed-size requests: 512^2-4096^2, 1e4-1e6 rows, "
-                                   "8-128 channels, 1-4 bands, half FP32 eps 1e-5 / half FP64 eps 1e-9"}}
+            "config": {"workload": f"Poisson stream of mixed-size requests: 512^2-{args.serve_max_pix}^2, "
+                                   f"1e4-{args.serve_max_rows:.0e} rows, 8-128 channels, 1-4 bands, "
+                                   "half FP32 eps 1e-5 / half FP64 eps 1e-9"}}
     print(json.dumps(line))
     return 0
 

@@ -463,7 +463,7 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     p.ntu = p.Nu / TILE;
     p.ntv = p.Nv / TILE;
     const int64_t ntiles = (int64_t)p.ntu * p.ntv;
-    const int64_t key_cap = int64_t(1) << 25;
+    const int64_t key_cap = int64_t(1) << 27;   // 1 GiB of bucket offsets at most
     p.q = 1;
     while ((int64_t)p.nband * ntiles * ((p.Pmax + p.q - 1) / p.q) > key_cap) ++p.q;
     p.nkq = (p.Pmax + p.q - 1) / p.q;

@@ -767,9 +767,23 @@ template <> struct FftT<double> {
     }
 };
 
+// cuFFT work area of a batched 2-D C2C plan, without creating it
+template <typename T>
+static size_t fft_work_estimate(int Nu, int Nv, int batch) {
+    int n[2] = {Nu, Nv};
+    size_t ws = 0;
+    if (cufftEstimateMany(2, n, nullptr, 1, 0, nullptr, 1, 0, FftT<T>::c2c, batch, &ws) != CUFFT_SUCCESS)
+        ws = (size_t)Nu * Nv * sizeof(cx_t<T>) * batch;
+    return ws;
+}
+
+// FFT of nplanes planes in batches of up to 8, smaller when the work area would not
+// fit the context's HBM budget
 template <typename T>
 static void fft_planes(Ctx &ctx, cx_t<T> *data, int nplanes, int Nu, int Nv, int dir, cudaStream_t st) {
-    const int maxb = 8;
+    int maxb = 8;
+    const size_t room = ctx.available() + ctx.scratch_bytes("fftwork");
+    while (maxb > 1 && fft_work_estimate<T>(Nu, Nv, std::min(maxb, nplanes)) > room) maxb /= 2;
     const int64_t plane_sz = (int64_t)Nu * Nv;
     for (int k = 0; k < nplanes; k += maxb) {
         const int b = std::min(maxb, nplanes - k);
@@ -779,7 +793,11 @@ static void fft_planes(Ctx &ctx, cx_t<T> *data, int nplanes, int Nu, int Nv, int
     }
 }
 
-static int plane_block(Ctx &ctx, const Plan &p, size_t cxs, size_t reserve) {
+static int plane_block(Ctx &ctx, const Plan &p, size_t cxs, size_t reserve_unused) {
+    // keep room for the cuFFT work area of a single-plane transform
+    (void)reserve_unused;
+    const size_t reserve = (cxs == 16 ? fft_work_estimate<double>(p.Nu, p.Nv, 1)
+                                      : fft_work_estimate<float>(p.Nu, p.Nv, 1)) + (64u << 20);
     const size_t plane_bytes = (size_t)p.Nu * p.Nv * cxs;
     const size_t have = ctx.scratch_bytes("planes");
     const size_t avail = ctx.available() + have;

@@ -79,7 +79,7 @@ def footprint_bytes(r: Request) -> int:
     images = img * rs * 10 + 4 * img * rs * 2 + 4 * img * cs                # x, dual, dirty, CG vectors, PSF, spectra
     tables = img * 16 + 4 * img * 16 + 2 * (1 << 25) * 12                  # pixel tables, bucket offsets
     grid = 4 * r.nx * r.ny * cs                                             # one oversampled plane
-    planes = 8 * grid + 4 * 8 * grid                                        # operator and PSF plane blocks
+    planes = 12 * grid + 4 * 12 * grid                                      # operator and PSF plane blocks + FFT work
     return int(1.15 * (data + images + tables + planes)) + (64 << 20)
 
 

@@ -623,6 +623,14 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
     double *bb = sc + S_COUNT, *RR = bb + nb, *PAP = RR + (size_t)(iters + 1) * nb;
     PFB_CUDA(cudaMemsetAsync(sc, 0, nsc * sizeof(double), st));
 
+    // image-side buffers and FFT plans first: the Hessian's w-plane stack then takes
+    // whatever the budget has left
+    cx_t<T> *S = psf_spectrum<T>(ctx, nx, ny, nb, psf, st);
+    T *padded = (T *)ctx.scratch("img_pad", (size_t)nbig * sizeof(T));
+    ctx.scratch("img_spec", (size_t)nb * NX * (NY / 2 + 1) * sizeof(cx_t<T>));
+    ctx.fft((int)NX, (int)NY, nb, RFft<T>::c2r);
+    if (prm.basis_mask != 1u)
+        for (const char *nm : {"st_wa", "st_wb", "st_psiv", "st_u"}) ctx.scratch(nm, img);
     // 1. one exact Hessian application: H x_k = R^dagger W R x_k (Eq. 3)
     {
         cx_t<T> *vis = (cx_t<T> *)ctx.scratch("st_vis", (size_t)p.nrow * p.nchan * sizeof(cx_t<T>));
@@ -656,8 +664,6 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
         check_launch("l21");
     }
     // 3. CG for U delta = IR (per band)
-    cx_t<T> *S = psf_spectrum<T>(ctx, nx, ny, nb, psf, st);
-    T *padded = (T *)ctx.scratch("img_pad", (size_t)nbig * sizeof(T));
     const T conv_scale = (T)(inv_wbar / (double)(NX * NY));
     const T sigma = (T)prm.sigma;
     k_cg_init<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ir, delta, r, pp);

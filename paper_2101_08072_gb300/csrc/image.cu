@@ -355,6 +355,18 @@ struct WavFilt {
     int L;
     double h[MAX_TAPS], g[MAX_TAPS];   // low-pass and high-pass g_k = (-1)^k h_{L-1-k}
 };
+// taps in the working precision (passed to the kernels by value)
+template <typename T>
+struct WavTaps {
+    int L;
+    T h[MAX_TAPS], g[MAX_TAPS];
+    explicit WavTaps(const WavFilt &f) : L(f.L) {
+        for (int k = 0; k < MAX_TAPS; ++k) {
+            h[k] = (T)(k < f.L ? f.h[k] : 0.0);
+            g[k] = (T)(k < f.L ? f.g[k] : 0.0);
+        }
+    }
+};
 
 static WavFilt wav_filter(int N) {
     static std::map<int, WavFilt> cache;
@@ -376,7 +388,7 @@ static WavFilt wav_filter(int N) {
 //   a[k] = sum_t h[t] x[(2k + t) mod n_ax],  d[k] = sum_t g[t] x[(2k + t) mod n_ax]
 // with a stored in [0, n_ax/2) and d in [n_ax/2, n_ax) of that axis.
 template <typename T>
-__global__ void k_dwt_level(int nx, int ny, int nband, int n, int m, int axis, WavFilt f,
+__global__ void k_dwt_level(int nx, int ny, int nband, int n, int m, int axis, WavTaps<T> f,
                             const T *__restrict__ in, T *__restrict__ out) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t per = (int64_t)n * m;
@@ -390,20 +402,20 @@ __global__ void k_dwt_level(int nx, int ny, int nband, int n, int m, int axis, W
     const int half = N / 2;
     const bool hi = pos >= half;
     const int k = hi ? pos - half : pos;
-    double acc = 0;
-    for (int t = 0; t < f.L; ++t) {
-        int q = 2 * k + t;
-        q %= N;
-        const double xv = axis == 0 ? (double)src[(int64_t)q * ny + j] : (double)src[(int64_t)i * ny + q];
+    T acc = 0;
+    int q = 2 * k;
+    for (int t = 0; t < f.L; ++t, ++q) {
+        q -= q >= N ? N : 0;
+        const T xv = axis == 0 ? src[(int64_t)q * ny + j] : src[(int64_t)i * ny + q];
         acc += (hi ? f.g[t] : f.h[t]) * xv;
     }
-    out[(int64_t)b * nx * ny + (int64_t)i * ny + j] = (T)acc;
+    out[(int64_t)b * nx * ny + (int64_t)i * ny + j] = acc;
 }
 
 // Transpose (= inverse) of k_dwt_level:
 //   x[p] = sum_{t = p mod 2} h[t] a[((p - t) mod N)/2] + g[t] d[((p - t) mod N)/2]
 template <typename T>
-__global__ void k_idwt_level(int nx, int ny, int nband, int n, int m, int axis, WavFilt f,
+__global__ void k_idwt_level(int nx, int ny, int nband, int n, int m, int axis, WavTaps<T> f,
                              const T *__restrict__ in, T *__restrict__ out) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t per = (int64_t)n * m;
@@ -415,18 +427,18 @@ __global__ void k_idwt_level(int nx, int ny, int nband, int n, int m, int axis, 
     const int N = axis == 0 ? n : m;
     const int pos = axis == 0 ? i : j;
     const int half = N / 2;
-    double acc = 0;
+    T acc = 0;
     for (int t = 0; t < f.L; ++t) {
         int q = pos - t;
         q %= N;
         q += q < 0 ? N : 0;
         if (q & 1) continue;
         const int k = q >> 1;
-        const double av = axis == 0 ? (double)src[(int64_t)k * ny + j] : (double)src[(int64_t)i * ny + k];
-        const double dv = axis == 0 ? (double)src[(int64_t)(k + half) * ny + j] : (double)src[(int64_t)i * ny + k + half];
+        const T av = axis == 0 ? src[(int64_t)k * ny + j] : src[(int64_t)i * ny + k];
+        const T dv = axis == 0 ? src[(int64_t)(k + half) * ny + j] : src[(int64_t)i * ny + k + half];
         acc += f.h[t] * av + f.g[t] * dv;
     }
-    out[(int64_t)b * nx * ny + (int64_t)i * ny + j] = (T)acc;
+    out[(int64_t)b * nx * ny + (int64_t)i * ny + j] = acc;
 }
 
 // copy the [n x m] top-left block of each band image
@@ -451,8 +463,8 @@ static void dwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, const 
     for (int lv = 0; lv < nlevel; ++lv) {
         const int64_t cnt = (int64_t)n * m * nband;
         const unsigned gb = (unsigned)((cnt + 255) / 256);
-        k_dwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 0, f, coef, tmp);
-        k_dwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 1, f, tmp, coef);
+        k_dwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 0, WavTaps<T>(f), coef, tmp);
+        k_dwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 1, WavTaps<T>(f), tmp, coef);
         check_launch("dwt");
         n /= 2;
         m /= 2;
@@ -466,8 +478,8 @@ static void idwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, T *co
     for (int lv = 0; lv < nlevel; ++lv) {
         const int64_t cnt = (int64_t)n * m * nband;
         const unsigned gb = (unsigned)((cnt + 255) / 256);
-        k_idwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 1, f, coef, tmp);
-        k_idwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 0, f, tmp, coef);
+        k_idwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 1, WavTaps<T>(f), coef, tmp);
+        k_idwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 0, WavTaps<T>(f), tmp, coef);
         check_launch("idwt");
         n *= 2;
         m *= 2;

@@ -303,6 +303,29 @@ __host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
     return L;
 }
 
+// ---- tensor-core scatter of runs of visibilities that share a footprint
+// For visibilities r with the same first-tap cell and first plane, the ring update is
+//   C[(a, b), (c, re/im)] += sum_r (ku_r[a] kv_r[b]) * wy_r[c]
+// an [W^2 x n] x [n x 2 W_w] product: mma.sync m16n8k8 with TF32 operands, each FP32
+// operand split as hi + lo (both TF32) and the products hi*hi + hi*lo + lo*hi
+// accumulated in FP32, which keeps FP32-level accuracy.
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
+    hi = tf32_bits(x);
+    lo = tf32_bits(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 // raw inputs of one record, held in registers between prefetch and staging
 struct RawRec {
     uint32_t code;
@@ -311,7 +334,7 @@ struct RawRec {
     float wt;
 };
 
-template <int W, int Ww>
+template <int W, int Ww, bool MMA>
 __global__ void __launch_bounds__(256, 3)
 k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items, const int64_t *__restrict__ off,
            CoordSrc src, const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, BandGeom g,
@@ -320,6 +343,7 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     constexpr int R = Ww;                  // ring planes (one w bucket per plane)
     constexpr int SLOT = TILE * RSTRIDE;
     constexpr int KS = res_ks(W), WS = res_ws(Ww);
+    constexpr int MT = (W * W + 15) / 16, NT = (2 * Ww + 7) / 8;   // MMA tiles (rows, columns)
     const ResSmem L = res_layout(R, W, Ww);
     float2 *ring = reinterpret_cast<float2 *>(smem_raw);
     int4 *rhead = reinterpret_cast<int4 *>(smem_raw + L.head);
@@ -526,8 +550,98 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         // planes below this chunk's first plane are complete
         flush_planes(max(kq * g.q, k_lo));
         __syncthreads();
-        // ---- scatter by residue classes with register accumulation
-        if (in_group) {
+        if (MMA) {
+            // ---- scatter runs on tensor cores: warp w takes a contiguous range of records
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            const int gid = lane >> 2, tig = lane & 3;
+            const int nwarps = blockDim.x >> 5;
+            const int per = (cnt + nwarps - 1) / nwarps;
+            const int r0 = warp * per, r1 = min(cnt, r0 + per);
+            int r = r0;
+            while (r < r1) {
+                const int4 key = rhead[r];
+                // the run: records r .. re-1 share the key (same footprint and planes)
+                int re = r + 1;
+                while (re < r1) {
+                    const int4 h = rhead[re];
+                    if (h.x != key.x || h.y != key.y || h.w != key.w) break;
+                    ++re;
+                }
+                if (key.x != -30000) {
+                    float d[MT][NT][4];
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) d[mt][nt][e] = 0.f;
+                    for (int g0 = r; g0 < re; g0 += 8) {
+                        const int ja = g0 + tig, jb = g0 + tig + 4;   // records of this thread's A/B columns
+                        const bool va = ja < re, vb = jb < re;
+                        // B fragments: B[k][n] = (re, im) of wy[k][n/2]
+                        uint32_t bh[NT][2], bl[NT][2];
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) {
+                            const int n = 8 * nt + gid;
+                            float x0 = 0.f, x1 = 0.f;
+                            if (n < 2 * Ww) {
+                                const int c = n >> 1;
+                                if (va) { const float2 q = rwy[ja * WS + c]; x0 = (n & 1) ? q.y : q.x; }
+                                if (vb) { const float2 q = rwy[jb * WS + c]; x1 = (n & 1) ? q.y : q.x; }
+                            }
+                            tf32_split(x0, bh[nt][0], bl[nt][0]);
+                            tf32_split(x1, bh[nt][1], bl[nt][1]);
+                        }
+#pragma unroll
+                        for (int mt = 0; mt < MT; ++mt) {
+                            const int ra = 16 * mt + gid, rb = ra + 8;   // rows (a, b) = (row / W, row % W)
+                            float v[4] = {0.f, 0.f, 0.f, 0.f};
+                            if (ra < W * W) {
+                                const int a = ra / W, b = ra - a * W;
+                                if (va) v[0] = rku[ja * KS + a] * rkv[ja * KS + b];
+                                if (vb) v[2] = rku[jb * KS + a] * rkv[jb * KS + b];
+                            }
+                            if (rb < W * W) {
+                                const int a = rb / W, b = rb - a * W;
+                                if (va) v[1] = rku[ja * KS + a] * rkv[ja * KS + b];
+                                if (vb) v[3] = rku[jb * KS + a] * rkv[jb * KS + b];
+                            }
+                            uint32_t ah[4], al[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) tf32_split(v[e], ah[e], al[e]);
+#pragma unroll
+                            for (int nt = 0; nt < NT; ++nt) {
+                                mma_tf32(d[mt][nt], ah, bh[nt]);
+                                mma_tf32(d[mt][nt], ah, bl[nt]);
+                                mma_tf32(d[mt][nt], al, bh[nt]);
+                            }
+                        }
+                    }
+                    // add the run's footprint to the ring (other warps may touch the same cells)
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int half = 0; half < 2; ++half) {
+                            const int row = 16 * mt + gid + 8 * half;
+                            if (row >= W * W) continue;
+                            const int a = row / W, b = row - a * W;
+                            const int cu2 = key.x + a, cv2 = key.y + b;
+                            if ((unsigned)cu2 >= (unsigned)TILE || (unsigned)cv2 >= (unsigned)TILE) continue;
+#pragma unroll
+                            for (int nt = 0; nt < NT; ++nt) {
+                                const int c = 4 * nt + tig;   // columns 2c, 2c + 1 of this thread
+                                const int k = key.w + c;
+                                if (c >= Ww || k < k_lo || k >= k_hi) continue;
+                                float2 *cell = ring + (k % R) * SLOT + cu2 * RSTRIDE + cv2;
+                                atomicAdd(&cell->x, d[mt][nt][2 * half + 0]);
+                                atomicAdd(&cell->y, d[mt][nt][2 * half + 1]);
+                            }
+                        }
+                }
+                r = re;
+            }
+        } else if (in_group) {
+            // ---- scatter by residue classes with register accumulation
             const int per = (cnt + ngroups - 1) / ngroups;
             const int r0 = grp * per, r1 = min(cnt, r0 + per);
             int r = r0;
@@ -828,8 +942,9 @@ static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkI
                               const float2 *vis, const float *wgt, int unit, const BandGeom &g, int k_lo, int k_hi,
                               float2 *planes) {
     const size_t smem = (size_t)res_layout(R, W, Ww).total;
-    PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_grid_res<W, Ww><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
+    constexpr bool MMA = true;
+    PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww, MMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_grid_res<W, Ww, MMA><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
                                                    k_hi, planes);
 }
 

@@ -910,8 +910,12 @@ static void fft_planes(Ctx &ctx, cx_t<T> *data, int nplanes, int Nu, int Nv, int
 static int plane_block(Ctx &ctx, const Plan &p, size_t cxs, size_t reserve_unused) {
     // keep room for the cuFFT work area of a single-plane transform
     (void)reserve_unused;
+    // leave room for the other buffers a call sequence needs after the stack exists:
+    // a visibility-sized scratch (Hessian) and a dozen image-sized buffers (step)
+    const size_t rs = cxs / 2;
+    const size_t others = (size_t)p.nrow * p.nchan * cxs + 16 * (size_t)p.nband * p.nx * p.ny * rs;
     const size_t reserve = (cxs == 16 ? fft_work_estimate<double>(p.Nu, p.Nv, 1)
-                                      : fft_work_estimate<float>(p.Nu, p.Nv, 1)) + (64u << 20);
+                                      : fft_work_estimate<float>(p.Nu, p.Nv, 1)) + others + (64u << 20);
     const size_t plane_bytes = (size_t)p.Nu * p.Nv * cxs;
     const size_t have = ctx.scratch_bytes("planes");
     const size_t avail = ctx.available() + have;

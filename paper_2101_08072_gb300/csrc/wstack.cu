@@ -897,7 +897,10 @@ template <typename T>
 static void fft_planes(Ctx &ctx, cx_t<T> *data, int nplanes, int Nu, int Nv, int dir, cudaStream_t st) {
     int maxb = 8;
     const size_t room = ctx.available() + ctx.scratch_bytes("fftwork");
-    while (maxb > 1 && fft_work_estimate<T>(Nu, Nv, std::min(maxb, nplanes)) > room) maxb /= 2;
+    const size_t plane_bytes = (size_t)Nu * Nv * sizeof(cx_t<T>);
+    // the (host-side) estimate only when memory is tight: a batch needs at most a few planes of work area
+    if (room < 4 * (size_t)maxb * plane_bytes)
+        while (maxb > 1 && fft_work_estimate<T>(Nu, Nv, std::min(maxb, nplanes)) > room) maxb /= 2;
     const int64_t plane_sz = (int64_t)Nu * Nv;
     for (int k = 0; k < nplanes; k += maxb) {
         const int b = std::min(maxb, nplanes - k);
@@ -946,7 +949,7 @@ static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkI
                               const float2 *vis, const float *wgt, int unit, const BandGeom &g, int k_lo, int k_hi,
                               float2 *planes) {
     const size_t smem = (size_t)res_layout(R, W, Ww).total;
-    constexpr bool MMA = true;
+    constexpr bool MMA = false;   // measured: the CUDA-core residue scatter is faster on this workload
     PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww, MMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_grid_res<W, Ww, MMA><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
                                                    k_hi, planes);

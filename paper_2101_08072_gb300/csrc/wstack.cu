@@ -542,6 +542,11 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     next_chunk(n0, kq_n, n1);
     RawRec nxt;
     nxt.code = threadIdx.x < n1 - n0 ? items[n0 + threadIdx.x] : 0u;
+    // chunk after next: its item codes travel one iteration ahead of its raw inputs
+    int kq_m = kq_n;
+    int64_t m0 = n1, m1;
+    next_chunk(m0, kq_m, m1);
+    uint32_t code2 = threadIdx.x < m1 - m0 ? items[m0 + threadIdx.x] : 0u;
     __syncthreads();
     while (c0 < wi.end) {
         const int cnt = (int)(c1 - c0);
@@ -657,13 +662,16 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             flush_acc();
         }
         __syncthreads();
-        // ---- advance: stage the next chunk, prefetch the codes of the one after
+        // ---- advance: stage the next chunk; codes move one chunk along, and the codes of
+        // the chunk after that are requested now (used one iteration later)
         c0 = n0; c1 = n1; kq = kq_n;
         if (c0 < wi.end) {
             if (threadIdx.x < c1 - c0) stage(nxt, threadIdx.x);
-            n0 = c1;
-            next_chunk(n0, kq_n, n1);
-            nxt.code = threadIdx.x < n1 - n0 ? items[n0 + threadIdx.x] : 0u;
+            n0 = m0; n1 = m1; kq_n = kq_m;
+            nxt.code = code2;
+            m0 = n1;
+            next_chunk(m0, kq_m, m1);
+            code2 = threadIdx.x < m1 - m0 ? items[m0 + threadIdx.x] : 0u;
         }
         __syncthreads();
     }

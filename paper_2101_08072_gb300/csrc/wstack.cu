@@ -262,68 +262,44 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 
 // ------------------------------------------------------------------ FP32 gridding by residue classes
 // Same work decomposition as k_grid_tiles (a CTA owns a tile's cells).  Items are
-// staged in chunks of RES_CH records (first-tap cell, residues, ES taps, weighted
-// value times the w taps); chunks run across w planes with a sliding window of
-// W_w ring planes (one plane per bucket), which are written to HBM once complete.
-// The scatter uses groups of W * W threads: thread (a, b) of a group owns the
-// footprint cell whose local indices are congruent to (a, b) mod W (exactly one per
-// visibility), keeps the W_w plane sums of that cell in registers, and adds them to
-// the ring only when its cell changes.  The plan sorts every bucket by first-tap
+// staged in chunks of RES_CH records; chunks run across w planes with a sliding
+// window of W_w ring planes (one plane per bucket), which are written to HBM once
+// complete.  The scatter uses groups of W * W threads: thread (a, b) of a group owns
+// the footprint cell whose local indices are congruent to (a, b) mod W (exactly one
+// per visibility), keeps the W_w plane sums of that cell in registers, and adds them
+// to the ring only when its cell changes.  The plan sorts every bucket by first-tap
 // cell, so in the dense tiles a thread stays on one cell for long runs of
 // visibilities; distinct groups can meet on a cell, so the (rare) ring adds are
-// atomic.  The raw inputs of the next chunk (item codes, uvw, visibility, weight)
-// are loaded into registers before the current chunk's scatter, hiding their
-// latency behind it.
+// atomic.
+//
+// Staging does the per-visibility index work once: for every residue class j it
+// stores the ES tap that lands on that class together with a packed cell key
+// (u cell, first plane in the u entry; v cell in the v entry), so a scatter step is
+// two 8-byte loads, an OR and a compare, one multiply and 2 W_w FMAs.  The raw
+// inputs of the next chunk (uvw, visibility, weight) are loaded into registers
+// before the current chunk's scatter, and the item codes of the chunk after that one
+// iteration earlier still, hiding both latencies behind the scatter.
 constexpr int RES_CH = 128;
 constexpr int RSTRIDE = TILE + 6;   // padded ring row: spreads a footprint over the banks
-
-__host__ __device__ inline int ring_pow2(int n) {
-    int r = 1;
-    while (r < n) r <<= 1;
-    return r;
-}
+// packed cell key: (u + 64) << 25 | (v + 64) << 18 | first plane (18 bits)
+constexpr int KEY_PLANE_BITS = 18;
+constexpr uint32_t KEY_NONE = 0xffffffffu;   // decodes to u = 63, outside every tile
 
 struct ResSmem {
-    int head, ku, kv, wy, total;
+    int ru, rv, wy, total;
 };
 
-// record row strides: odd (in words) so that consecutive records hit different banks
-__host__ __device__ constexpr int res_ks(int W) { return W | 1; }
-__host__ __device__ constexpr int res_ws(int Ww) { return Ww + ((Ww & 1) ? 0 : 1); }
+// w-tap row stride in float2: even, so a record's row starts on 16 bytes
+__host__ __device__ constexpr int res_ws(int Ww) { return (Ww + 1) & ~1; }
 
 __host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
     ResSmem L;
     int o = R * TILE * RSTRIDE * (int)sizeof(float2);
-    L.head = o; o += RES_CH * (int)sizeof(int4);
-    L.ku = o; o += RES_CH * res_ks(W) * (int)sizeof(float);
-    L.kv = o; o += RES_CH * res_ks(W) * (int)sizeof(float);
-    o = (o + 15) & ~15;
+    L.ru = o; o += RES_CH * W * (int)sizeof(float2);
+    L.rv = o; o += RES_CH * W * (int)sizeof(float2);
     L.wy = o; o += RES_CH * res_ws(Ww) * (int)sizeof(float2);
     L.total = o;
     return L;
-}
-
-// ---- tensor-core scatter of runs of visibilities that share a footprint
-// For visibilities r with the same first-tap cell and first plane, the ring update is
-//   C[(a, b), (c, re/im)] += sum_r (ku_r[a] kv_r[b]) * wy_r[c]
-// an [W^2 x n] x [n x 2 W_w] product: mma.sync m16n8k8 with TF32 operands, each FP32
-// operand split as hi + lo (both TF32) and the products hi*hi + hi*lo + lo*hi
-// accumulated in FP32, which keeps FP32-level accuracy.
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
-    hi = tf32_bits(x);
-    lo = tf32_bits(x - __uint_as_float(hi));
-}
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
 // raw inputs of one record, held in registers between prefetch and staging
@@ -334,7 +310,7 @@ struct RawRec {
     float wt;
 };
 
-template <int W, int Ww, bool MMA>
+template <int W, int Ww>
 __global__ void __launch_bounds__(256, 3)
 k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items, const int64_t *__restrict__ off,
            CoordSrc src, const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, BandGeom g,
@@ -342,13 +318,11 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int R = Ww;                  // ring planes (one w bucket per plane)
     constexpr int SLOT = TILE * RSTRIDE;
-    constexpr int KS = res_ks(W), WS = res_ws(Ww);
-    constexpr int MT = (W * W + 15) / 16, NT = (2 * Ww + 7) / 8;   // MMA tiles (rows, columns)
+    constexpr int WS = res_ws(Ww);
     const ResSmem L = res_layout(R, W, Ww);
     float2 *ring = reinterpret_cast<float2 *>(smem_raw);
-    int4 *rhead = reinterpret_cast<int4 *>(smem_raw + L.head);
-    float *rku = reinterpret_cast<float *>(smem_raw + L.ku);
-    float *rkv = reinterpret_cast<float *>(smem_raw + L.kv);
+    float2 *ru = reinterpret_cast<float2 *>(smem_raw + L.ru);
+    float2 *rv = reinterpret_cast<float2 *>(smem_raw + L.rv);
     float2 *rwy = reinterpret_cast<float2 *>(smem_raw + L.wy);
     const int cells = TILE * TILE;
     const WorkItem wi = work[blockIdx.x];
@@ -394,22 +368,25 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     };
 
     float2 acc[Ww];
-    int cu = -1000, cv = -1000, ck = -1000;   // current cell (cu, cv), planes ck..ck+Ww-1
+    uint32_t ckey = KEY_NONE;   // cell and first plane the accumulators belong to
     auto flush_acc = [&]() {
+        const int cu = (int)(ckey >> 25) - 64, cv = (int)((ckey >> KEY_PLANE_BITS) & 127u) - 64;
+        const int ck = (int)(ckey & ((1u << KEY_PLANE_BITS) - 1u));
         if ((unsigned)cu < (unsigned)TILE && (unsigned)cv < (unsigned)TILE) {
+            float2 *cell = ring + cu * RSTRIDE + cv;
 #pragma unroll
             for (int c = 0; c < Ww; ++c) {
                 const int k = ck + c;
                 if (k >= k_lo && k < k_hi) {
-                    float2 *cell = ring + (k % R) * SLOT + cu * RSTRIDE + cv;
-                    atomicAdd(&cell->x, acc[c].x);
-                    atomicAdd(&cell->y, acc[c].y);
+                    float2 *dst = cell + (k % R) * SLOT;
+                    atomicAdd(&dst->x, acc[c].x);
+                    atomicAdd(&dst->y, acc[c].y);
                 }
             }
         }
 #pragma unroll
         for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
-        cu = cv = ck = -1000;
+        ckey = KEY_NONE;
     };
 #pragma unroll
     for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
@@ -443,7 +420,7 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         q.y = unit_vis ? make_float2(1.f, 0.f) : vis[v];
         q.wt = wgt ? wgt[v] : 1.f;
     };
-    // records from raw inputs
+    // record t from raw inputs: per residue class the tap and the packed cell key
     auto stage = [&](const RawRec &q, int t) {
         const uint32_t v = q.code & VIS_MASK;
         const int du = (q.code >> 30) & 1, dv = q.code >> 31;
@@ -476,28 +453,33 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                 c.ow = 0.0f;
             }
         }
-        if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
-            rhead[t] = make_int4(-30000, 0, 0, 0);
-            return;
-        }
         float yr = q.y.x * q.wt, yi = q.y.y * q.wt;
-        if (c.flip) yi = -yi;
-        if (g.tc != 0.0) {
-            float cs2, sn;
-            sincos_turns(c.ph, &sn, &cs2);
-            const float r0 = yr * cs2 - yi * sn;
-            yi = yr * sn + yi * cs2;
-            yr = r0;
+        if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
+            yr = yi = 0.f;   // none of its planes is in this block: scattered with zero weight
+        } else {
+            if (c.flip) yi = -yi;
+            if (g.tc != 0.0) {
+                float cs2, sn;
+                sincos_turns(c.ph, &sn, &cs2);
+                const float r0 = yr * cs2 - yi * sn;
+                yi = yr * sn + yi * cs2;
+                yr = r0;
+            }
         }
         const int lu = (c.gu0 & (TILE - 1)) - du * TILE;
         const int lv = (c.gv0 & (TILE - 1)) - dv * TILE;
         const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
-        rhead[t] = make_int4(lu, lv, mu | (mv << 8), c.k0);
         const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
+        const uint32_t kbits = (uint32_t)c.k0;
 #pragma unroll
-        for (int i = 0; i < W; ++i) {
-            rku[t * KS + i] = es_kernel_fast(c.ou + (float)i, ihw, bt);
-            rkv[t * KS + i] = es_kernel_fast(c.ov + (float)i, ihw, bt);
+        for (int j = 0; j < W; ++j) {
+            int ap = j - mu, bp = j - mv;   // taps that land on residue class j
+            ap += ap < 0 ? W : 0;
+            bp += bp < 0 ? W : 0;
+            ru[t * W + j] = make_float2(es_kernel_fast(c.ou + (float)ap, ihw, bt),
+                                        __uint_as_float(((uint32_t)(lu + ap + 64) << 25) | kbits));
+            rv[t * W + j] = make_float2(es_kernel_fast(c.ov + (float)bp, ihw, bt),
+                                        __uint_as_float((uint32_t)(lv + bp + 64) << KEY_PLANE_BITS));
         }
         if (Ww > 1) {
 #pragma unroll
@@ -509,27 +491,9 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             rwy[t * WS] = make_float2(yr, yi);
         }
     };
-    auto scatter_one = [&](const int4 h, int r) {
-        int ap = ta - (h.z & 0xff), bp = tb - (h.z >> 8);
-        ap += ap < 0 ? W : 0;
-        bp += bp < 0 ? W : 0;
-        const int nu = h.x + ap, nv = h.y + bp;
-        if (nu != cu || nv != cv || h.w != ck) {
-            flush_acc();
-            cu = nu; cv = nv; ck = h.w;
-        }
-        const float wuv = rku[r * KS + ap] * rkv[r * KS + bp];
-        const float2 *wy = rwy + r * WS;
-#pragma unroll
-        for (int c = 0; c < Ww; ++c) {
-            const float2 q = wy[c];
-            acc[c].x = fmaf(wuv, q.x, acc[c].x);
-            acc[c].y = fmaf(wuv, q.y, acc[c].y);
-        }
-    };
     __syncthreads();
 
-    // ---- prologue: stage chunk 0, prefetch the codes of chunk 1
+    // ---- prologue: stage chunk 0, prefetch the raw inputs of chunk 1 and the codes of chunk 2
     int kq = bucket_of(wi.begin);
     int64_t c0 = wi.begin, c1;
     next_chunk(c0, kq, c1);
@@ -542,7 +506,6 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     next_chunk(n0, kq_n, n1);
     RawRec nxt;
     nxt.code = threadIdx.x < n1 - n0 ? items[n0 + threadIdx.x] : 0u;
-    // chunk after next: its item codes travel one iteration ahead of its raw inputs
     int kq_m = kq_n;
     int64_t m0 = n1, m1;
     next_chunk(m0, kq_m, m1);
@@ -555,111 +518,39 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         // planes below this chunk's first plane are complete
         flush_planes(max(kq * g.q, k_lo));
         __syncthreads();
-        if (MMA) {
-            // ---- scatter runs on tensor cores: warp w takes a contiguous range of records
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            const int gid = lane >> 2, tig = lane & 3;
-            const int nwarps = blockDim.x >> 5;
-            const int per = (cnt + nwarps - 1) / nwarps;
-            const int r0 = warp * per, r1 = min(cnt, r0 + per);
-            int r = r0;
-            while (r < r1) {
-                const int4 key = rhead[r];
-                // the run: records r .. re-1 share the key (same footprint and planes)
-                int re = r + 1;
-                while (re < r1) {
-                    const int4 h = rhead[re];
-                    if (h.x != key.x || h.y != key.y || h.w != key.w) break;
-                    ++re;
-                }
-                if (key.x != -30000) {
-                    float d[MT][NT][4];
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) d[mt][nt][e] = 0.f;
-                    for (int g0 = r; g0 < re; g0 += 8) {
-                        const int ja = g0 + tig, jb = g0 + tig + 4;   // records of this thread's A/B columns
-                        const bool va = ja < re, vb = jb < re;
-                        // B fragments: B[k][n] = (re, im) of wy[k][n/2]
-                        uint32_t bh[NT][2], bl[NT][2];
-#pragma unroll
-                        for (int nt = 0; nt < NT; ++nt) {
-                            const int n = 8 * nt + gid;
-                            float x0 = 0.f, x1 = 0.f;
-                            if (n < 2 * Ww) {
-                                const int c = n >> 1;
-                                if (va) { const float2 q = rwy[ja * WS + c]; x0 = (n & 1) ? q.y : q.x; }
-                                if (vb) { const float2 q = rwy[jb * WS + c]; x1 = (n & 1) ? q.y : q.x; }
-                            }
-                            tf32_split(x0, bh[nt][0], bl[nt][0]);
-                            tf32_split(x1, bh[nt][1], bl[nt][1]);
-                        }
-#pragma unroll
-                        for (int mt = 0; mt < MT; ++mt) {
-                            const int ra = 16 * mt + gid, rb = ra + 8;   // rows (a, b) = (row / W, row % W)
-                            float v[4] = {0.f, 0.f, 0.f, 0.f};
-                            if (ra < W * W) {
-                                const int a = ra / W, b = ra - a * W;
-                                if (va) v[0] = rku[ja * KS + a] * rkv[ja * KS + b];
-                                if (vb) v[2] = rku[jb * KS + a] * rkv[jb * KS + b];
-                            }
-                            if (rb < W * W) {
-                                const int a = rb / W, b = rb - a * W;
-                                if (va) v[1] = rku[ja * KS + a] * rkv[ja * KS + b];
-                                if (vb) v[3] = rku[jb * KS + a] * rkv[jb * KS + b];
-                            }
-                            uint32_t ah[4], al[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) tf32_split(v[e], ah[e], al[e]);
-#pragma unroll
-                            for (int nt = 0; nt < NT; ++nt) {
-                                mma_tf32(d[mt][nt], ah, bh[nt]);
-                                mma_tf32(d[mt][nt], ah, bl[nt]);
-                                mma_tf32(d[mt][nt], al, bh[nt]);
-                            }
-                        }
-                    }
-                    // add the run's footprint to the ring (other warps may touch the same cells)
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int half = 0; half < 2; ++half) {
-                            const int row = 16 * mt + gid + 8 * half;
-                            if (row >= W * W) continue;
-                            const int a = row / W, b = row - a * W;
-                            const int cu2 = key.x + a, cv2 = key.y + b;
-                            if ((unsigned)cu2 >= (unsigned)TILE || (unsigned)cv2 >= (unsigned)TILE) continue;
-#pragma unroll
-                            for (int nt = 0; nt < NT; ++nt) {
-                                const int c = 4 * nt + tig;   // columns 2c, 2c + 1 of this thread
-                                const int k = key.w + c;
-                                if (c >= Ww || k < k_lo || k >= k_hi) continue;
-                                float2 *cell = ring + (k % R) * SLOT + cu2 * RSTRIDE + cv2;
-                                atomicAdd(&cell->x, d[mt][nt][2 * half + 0]);
-                                atomicAdd(&cell->y, d[mt][nt][2 * half + 1]);
-                            }
-                        }
-                }
-                r = re;
-            }
-        } else if (in_group) {
-            // ---- scatter by residue classes with register accumulation
+        if (in_group) {
+            // ---- scatter: each group takes a contiguous range of the chunk's records
             const int per = (cnt + ngroups - 1) / ngroups;
             const int r0 = grp * per, r1 = min(cnt, r0 + per);
-            int r = r0;
-            for (; r + 1 < r1; r += 2) {
-                const int4 h0 = rhead[r], h1 = rhead[r + 1];
-                if (h0.x != -30000) scatter_one(h0, r);
-                if (h1.x != -30000) scatter_one(h1, r + 1);
+            const float2 *pu = ru + ta, *pv = rv + tb;
+            for (int r = r0; r < r1; ++r) {
+                const float2 a = pu[r * W], b = pv[r * W];
+                float4 q[Ww / 2 > 0 ? Ww / 2 : 1];
+                float2 qo;
+                const float4 *wy4 = reinterpret_cast<const float4 *>(rwy + r * WS);
+#pragma unroll
+                for (int c2 = 0; c2 < Ww / 2; ++c2) q[c2] = wy4[c2];
+                if (Ww & 1) qo = rwy[r * WS + Ww - 1];
+                const uint32_t key = __float_as_uint(a.y) | __float_as_uint(b.y);
+                if (key != ckey) {
+                    flush_acc();
+                    ckey = key;
+                }
+                const float wuv = a.x * b.x;
+#pragma unroll
+                for (int c2 = 0; c2 < Ww / 2; ++c2) {
+                    acc[2 * c2].x = fmaf(wuv, q[c2].x, acc[2 * c2].x);
+                    acc[2 * c2].y = fmaf(wuv, q[c2].y, acc[2 * c2].y);
+                    acc[2 * c2 + 1].x = fmaf(wuv, q[c2].z, acc[2 * c2 + 1].x);
+                    acc[2 * c2 + 1].y = fmaf(wuv, q[c2].w, acc[2 * c2 + 1].y);
+                }
+                if (Ww & 1) {
+                    acc[Ww - 1].x = fmaf(wuv, qo.x, acc[Ww - 1].x);
+                    acc[Ww - 1].y = fmaf(wuv, qo.y, acc[Ww - 1].y);
+                }
             }
-            if (r < r1) {
-                const int4 h0 = rhead[r];
-                if (h0.x != -30000) scatter_one(h0, r);
-            }
-            flush_acc();
+            // the sums stay in registers while the next chunk continues this bucket
+            if (n0 >= wi.end || kq_n != kq) flush_acc();
         }
         __syncthreads();
         // ---- advance: stage the next chunk; codes move one chunk along, and the codes of
@@ -943,7 +834,9 @@ static unsigned grid_blocks(int64_t n, int threads, int cap) {
 }
 
 // ------------------------------------------------------------------ FP32 kernel dispatch on W
-static bool fast_path_f32(const Plan &p) { return p.prec == PFB_F32 && p.W >= 4 && p.W <= 8 && p.q == 1; }
+static bool fast_path_f32(const Plan &p) {
+    return p.prec == PFB_F32 && p.W >= 4 && p.W <= 8 && p.q == 1 && p.Pmax < (1 << KEY_PLANE_BITS);
+}
 static bool degrid_tiles_fit(const Plan &p) {
     const int R = p.Ww, E = TILE + p.W - 1, ES = E | 1;
     return fast_path_f32(p) && (size_t)R * E * ES * sizeof(float2) <= 227 * 1024;
@@ -957,9 +850,8 @@ static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkI
                               const float2 *vis, const float *wgt, int unit, const BandGeom &g, int k_lo, int k_hi,
                               float2 *planes) {
     const size_t smem = (size_t)res_layout(R, W, Ww).total;
-    constexpr bool MMA = false;   // measured: the CUDA-core residue scatter is faster on this workload
-    PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww, MMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_grid_res<W, Ww, MMA><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
+    PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_grid_res<W, Ww><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
                                                    k_hi, planes);
 }
 

@@ -262,44 +262,78 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 
 // ------------------------------------------------------------------ FP32 gridding by residue classes
 // Same work decomposition as k_grid_tiles (a CTA owns a tile's cells).  Items are
-// staged in chunks of RES_CH records; chunks run across w planes with a sliding
-// window of W_w ring planes (one plane per bucket), which are written to HBM once
-// complete.  The scatter uses groups of W * W threads: thread (a, b) of a group owns
-// the footprint cell whose local indices are congruent to (a, b) mod W (exactly one
-// per visibility), keeps the W_w plane sums of that cell in registers, and adds them
-// to the ring only when its cell changes.  The plan sorts every bucket by first-tap
+// processed in chunks of at most res_ch(W) records of one w bucket; chunks run
+// across w planes with a sliding window of W_w ring planes (one plane per bucket) in
+// shared memory, which are written to HBM once complete.
+//
+// The CTA is warp-specialised.  Four producer warps stage chunk i+1 (coordinates,
+// ES taps, weighted and phase-rotated value) into one of two shared buffers while
+// eight consumer warps scatter chunk i from the other; named barriers hand each
+// buffer back and forth (FULL: producers -> consumers, EMPTY: consumers -> producers).
+// The producers keep their global loads two chunks ahead: item codes of chunk i+2 and
+// raw inputs (uvw, visibility, weight) of chunk i+1 are in flight while chunk i is
+// staged.
+//
+// The consumers form groups of W * W threads: thread (a, b) of a group owns the
+// footprint cell whose local indices are congruent to (a, b) mod W (exactly one per
+// visibility), keeps the W_w plane sums of that cell in registers, and adds them to
+// the ring only when its cell changes.  The plan sorts every bucket by first-tap
 // cell, so in the dense tiles a thread stays on one cell for long runs of
 // visibilities; distinct groups can meet on a cell, so the (rare) ring adds are
-// atomic.
-//
-// Staging does the per-visibility index work once: for every residue class j it
-// stores the ES tap that lands on that class together with a packed cell key
-// (u cell, first plane in the u entry; v cell in the v entry), so a scatter step is
-// two 8-byte loads, an OR and a compare, one multiply and 2 W_w FMAs.  The raw
-// inputs of the next chunk (uvw, visibility, weight) are loaded into registers
-// before the current chunk's scatter, and the item codes of the chunk after that one
-// iteration earlier still, hiding both latencies behind the scatter.
-constexpr int RES_CH = 128;
+// atomic.  Staging does the per-visibility index work once: for every residue class j
+// it stores the ES tap that lands on that class together with a packed cell key (u
+// cell and first plane in the u entry, v cell in the v entry), so a scatter step is
+// two 8-byte loads, an OR and a compare, one multiply and 2 W_w FMAs.
 constexpr int RSTRIDE = TILE + 6;   // padded ring row: spreads a footprint over the banks
+constexpr int GRID_NP = 128;        // producer threads (4 warps)
+constexpr int GRID_NC = 256;        // consumer threads (8 warps)
+constexpr int GRID_NT = GRID_NP + GRID_NC;
+// named barriers (0 is __syncthreads)
+constexpr int BAR_FULL = 1, BAR_EMPTY = 3, BAR_CONS = 5;
 // packed cell key: (u + 64) << 25 | (v + 64) << 18 | first plane (18 bits)
 constexpr int KEY_PLANE_BITS = 18;
 constexpr uint32_t KEY_NONE = 0xffffffffu;   // decodes to u = 63, outside every tile
 
-struct ResSmem {
-    int ru, rv, wy, total;
-};
-
+// records per chunk: two buffers and the ring fit twice in an SM's shared memory
+__host__ __device__ constexpr int res_ch(int W) { return W <= 7 ? 128 : 96; }
 // w-tap row stride in float2: even, so a record's row starts on 16 bytes
 __host__ __device__ constexpr int res_ws(int Ww) { return (Ww + 1) & ~1; }
 
+struct ResSmem {
+    int ru[2], rv[2], wy[2], meta, total;
+};
+
 __host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
     ResSmem L;
+    const int ch = res_ch(W);
     int o = R * TILE * RSTRIDE * (int)sizeof(float2);
-    L.ru = o; o += RES_CH * W * (int)sizeof(float2);
-    L.rv = o; o += RES_CH * W * (int)sizeof(float2);
-    L.wy = o; o += RES_CH * res_ws(Ww) * (int)sizeof(float2);
+    for (int s = 0; s < 2; ++s) {
+        L.ru[s] = o; o += ch * W * (int)sizeof(float2);
+        L.rv[s] = o; o += ch * W * (int)sizeof(float2);
+        L.wy[s] = o; o += ch * res_ws(Ww) * (int)sizeof(float2);
+    }
+    L.meta = o; o += 2 * (int)sizeof(int4);
     L.total = o;
     return L;
+}
+
+// barrier ids are immediates, so that only the barriers used are reserved
+template <int ID, int N>
+__device__ __forceinline__ void named_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(N) : "memory");
+}
+template <int ID, int N>
+__device__ __forceinline__ void named_arrive() {
+    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(N) : "memory");
+}
+// buffer sb of a FULL / EMPTY pair
+template <int ID>
+__device__ __forceinline__ void pair_sync(int sb) {
+    if (sb) named_sync<ID + 1, GRID_NT>(); else named_sync<ID, GRID_NT>();
+}
+template <int ID>
+__device__ __forceinline__ void pair_arrive(int sb) {
+    if (sb) named_arrive<ID + 1, GRID_NT>(); else named_arrive<ID, GRID_NT>();
 }
 
 // raw inputs of one record, held in registers between prefetch and staging
@@ -311,7 +345,7 @@ struct RawRec {
 };
 
 template <int W, int Ww>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(GRID_NT, 2)
 k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items, const int64_t *__restrict__ off,
            CoordSrc src, const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, BandGeom g,
            int k_lo, int k_hi, float2 *__restrict__ planes) {
@@ -319,11 +353,10 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     constexpr int R = Ww;                  // ring planes (one w bucket per plane)
     constexpr int SLOT = TILE * RSTRIDE;
     constexpr int WS = res_ws(Ww);
+    constexpr int CH = res_ch(W);
     const ResSmem L = res_layout(R, W, Ww);
     float2 *ring = reinterpret_cast<float2 *>(smem_raw);
-    float2 *ru = reinterpret_cast<float2 *>(smem_raw + L.ru);
-    float2 *rv = reinterpret_cast<float2 *>(smem_raw + L.rv);
-    float2 *rwy = reinterpret_cast<float2 *>(smem_raw + L.wy);
+    int4 *meta = reinterpret_cast<int4 *>(smem_raw + L.meta);
     const int cells = TILE * TILE;
     const WorkItem wi = work[blockIdx.x];
     const int tu = wi.tile / g.ntv, tv = wi.tile - tu * g.ntv;
@@ -345,59 +378,14 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     }
     for (int e = threadIdx.x; e < R * SLOT; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
 
-    // group geometry: thread (ta, tb) of a group owns the cell class (ta, tb) mod W
-    constexpr int G = W * W;
-    const int ngroups = blockDim.x / G;
-    const int grp = threadIdx.x / G, lid = threadIdx.x - grp * G;
-    const int ta = lid / W, tb = lid - ta * W;
-    const bool in_group = grp < ngroups;
-    const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
-    auto bucket_of = [&](int64_t pos) {
-        int lo = 0, hi = g.nkq - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (off[kbase + mid] <= pos) lo = mid; else hi = mid - 1;
-        }
-        return lo;
-    };
-    // chunk after [c0, c1) starting in bucket kq: at most RES_CH items of one bucket
-    auto next_chunk = [&](int64_t c0, int &kq, int64_t &c1) {
-        if (c0 >= wi.end) { c1 = c0; return; }
-        if (c0 >= off[kbase + kq + 1]) kq = bucket_of(c0);
-        c1 = min(min((int64_t)wi.end, off[kbase + kq + 1]), c0 + RES_CH);
-    };
-
-    float2 acc[Ww];
-    uint32_t ckey = KEY_NONE;   // cell and first plane the accumulators belong to
-    auto flush_acc = [&]() {
-        const int cu = (int)(ckey >> 25) - 64, cv = (int)((ckey >> KEY_PLANE_BITS) & 127u) - 64;
-        const int ck = (int)(ckey & ((1u << KEY_PLANE_BITS) - 1u));
-        if ((unsigned)cu < (unsigned)TILE && (unsigned)cv < (unsigned)TILE) {
-            float2 *cell = ring + cu * RSTRIDE + cv;
-#pragma unroll
-            for (int c = 0; c < Ww; ++c) {
-                const int k = ck + c;
-                if (k >= k_lo && k < k_hi) {
-                    float2 *dst = cell + (k % R) * SLOT;
-                    atomicAdd(&dst->x, acc[c].x);
-                    atomicAdd(&dst->y, acc[c].y);
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
-        ckey = KEY_NONE;
-    };
-#pragma unroll
-    for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
-    // write planes [next, upto) from the ring to HBM and clear their slots (CTA-wide)
+    // write planes [next, upto) from the ring to HBM and clear their slots
     int next = k_lo;
-    auto flush_planes = [&](int upto) {
+    auto flush_planes = [&](int upto, int tid, int nthr) {
         upto = min(upto, k_hi);
         for (int k = next; k < upto; ++k) {
             float2 *slot = ring + (k % R) * SLOT;
             float2 *dst = tile0 + (int64_t)(k - k_lo) * plane_sz;
-            for (int e2 = threadIdx.x; e2 < cells; e2 += blockDim.x) {
+            for (int e2 = tid; e2 < cells; e2 += nthr) {
                 const int r = e2 / TILE, cc = e2 - r * TILE;
                 const float2 val = slot[r * RSTRIDE + cc];
                 if (wi.atomic_mode) {
@@ -410,164 +398,233 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         }
         if (upto > next) next = upto;
     };
-    // loads of one record's raw inputs (second level: after its item code arrived)
-    auto load_raw = [&](RawRec &q) {
-        const uint32_t v = q.code & VIS_MASK;
-        const uint32_t row = v / (uint32_t)g.nchan;
-        q.u = src.rowdf[3 * row + 0];
-        q.v = src.rowdf[3 * row + 1];
-        q.w = src.rowdf[3 * row + 2];
-        q.y = unit_vis ? make_float2(1.f, 0.f) : vis[v];
-        q.wt = wgt ? wgt[v] : 1.f;
-    };
-    // record t from raw inputs: per residue class the tap and the packed cell key
-    auto stage = [&](const RawRec &q, int t) {
-        const uint32_t v = q.code & VIS_MASK;
-        const int du = (q.code >> 30) & 1, dv = q.code >> 31;
-        const uint32_t row = v / (uint32_t)g.nchan;
-        const int ch = (int)(v - row * (uint32_t)g.nchan);
-        const ChanDF cs = src.chandf[ch];
-        VisCoord<float> c;
-        {
-            float2 u = q.u, vv = q.v, w = q.w;
-            c.flip = w.x < 0.0f || (w.x == 0.0f && w.y < 0.0f);
-            if (c.flip) {
-                u.x = -u.x; u.y = -u.y; vv.x = -vv.x; vv.y = -vv.y; w.x = -w.x; w.y = -w.y;
-            }
-            float p, e;
-            int g0;
-            df_mul(u.x, u.y, cs.su_hi, cs.su_lo, p, e);
-            df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ou);
-            c.gu0 = wrap_mod(g0, g.Nu, g.inv_Nu);
-            df_mul(vv.x, vv.y, cs.sv_hi, cs.sv_lo, p, e);
-            df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ov);
-            c.gv0 = wrap_mod(g0, g.Nv, g.inv_Nv);
-            df_mul(w.x, w.y, cs.sp_hi, cs.sp_lo, p, e);
-            c.ph = (p - rintf(p)) + e;
-            if (Ww > 1) {
-                df_mul(w.x, w.y, cs.sw_hi, cs.sw_lo, p, e);
-                df_tap(p, e, g.w_oi, g.w_of, g.hw, g0, c.ow);
-                c.k0 = g0 < 0 ? 0 : (g0 > g.P - Ww ? g.P - Ww : g0);
-            } else {
-                c.k0 = 0;
-                c.ow = 0.0f;
-            }
-        }
-        float yr = q.y.x * q.wt, yi = q.y.y * q.wt;
-        if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
-            yr = yi = 0.f;   // none of its planes is in this block: scattered with zero weight
-        } else {
-            if (c.flip) yi = -yi;
-            if (g.tc != 0.0) {
-                float cs2, sn;
-                sincos_turns(c.ph, &sn, &cs2);
-                const float r0 = yr * cs2 - yi * sn;
-                yi = yr * sn + yi * cs2;
-                yr = r0;
-            }
-        }
-        const int lu = (c.gu0 & (TILE - 1)) - du * TILE;
-        const int lv = (c.gv0 & (TILE - 1)) - dv * TILE;
-        const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
-        const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
-        const uint32_t kbits = (uint32_t)c.k0;
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            int ap = j - mu, bp = j - mv;   // taps that land on residue class j
-            ap += ap < 0 ? W : 0;
-            bp += bp < 0 ? W : 0;
-            ru[t * W + j] = make_float2(es_kernel_fast(c.ou + (float)ap, ihw, bt),
-                                        __uint_as_float(((uint32_t)(lu + ap + 64) << 25) | kbits));
-            rv[t * W + j] = make_float2(es_kernel_fast(c.ov + (float)bp, ihw, bt),
-                                        __uint_as_float((uint32_t)(lv + bp + 64) << KEY_PLANE_BITS));
-        }
-        if (Ww > 1) {
-#pragma unroll
-            for (int i = 0; i < Ww; ++i) {
-                const float kw = es_kernel_fast(c.ow + (float)i, ihw, bt);
-                rwy[t * WS + i] = make_float2(kw * yr, kw * yi);
-            }
-        } else {
-            rwy[t * WS] = make_float2(yr, yi);
-        }
-    };
     __syncthreads();
 
-    // ---- prologue: stage chunk 0, prefetch the raw inputs of chunk 1 and the codes of chunk 2
-    int kq = bucket_of(wi.begin);
-    int64_t c0 = wi.begin, c1;
-    next_chunk(c0, kq, c1);
-    RawRec raw;
-    raw.code = threadIdx.x < c1 - c0 ? items[c0 + threadIdx.x] : 0u;
-    if (threadIdx.x < c1 - c0) load_raw(raw);
-    if (threadIdx.x < c1 - c0) stage(raw, threadIdx.x);
-    int kq_n = kq;
-    int64_t n0 = c1, n1;
-    next_chunk(n0, kq_n, n1);
-    RawRec nxt;
-    nxt.code = threadIdx.x < n1 - n0 ? items[n0 + threadIdx.x] : 0u;
-    int kq_m = kq_n;
-    int64_t m0 = n1, m1;
-    next_chunk(m0, kq_m, m1);
-    uint32_t code2 = threadIdx.x < m1 - m0 ? items[m0 + threadIdx.x] : 0u;
-    __syncthreads();
-    while (c0 < wi.end) {
-        const int cnt = (int)(c1 - c0);
-        // raw inputs of the next chunk: issued now, consumed after this chunk's scatter
-        if (threadIdx.x < n1 - n0) load_raw(nxt);
-        // planes below this chunk's first plane are complete
-        flush_planes(max(kq * g.q, k_lo));
-        __syncthreads();
-        if (in_group) {
-            // ---- scatter: each group takes a contiguous range of the chunk's records
-            const int per = (cnt + ngroups - 1) / ngroups;
-            const int r0 = grp * per, r1 = min(cnt, r0 + per);
-            const float2 *pu = ru + ta, *pv = rv + tb;
-            for (int r = r0; r < r1; ++r) {
-                const float2 a = pu[r * W], b = pv[r * W];
-                float4 q[Ww / 2 > 0 ? Ww / 2 : 1];
-                float2 qo;
-                const float4 *wy4 = reinterpret_cast<const float4 *>(rwy + r * WS);
-#pragma unroll
-                for (int c2 = 0; c2 < Ww / 2; ++c2) q[c2] = wy4[c2];
-                if (Ww & 1) qo = rwy[r * WS + Ww - 1];
-                const uint32_t key = __float_as_uint(a.y) | __float_as_uint(b.y);
-                if (key != ckey) {
-                    flush_acc();
-                    ckey = key;
+    if (threadIdx.x < GRID_NP) {
+        // ================================================================ producers
+        const int pt = threadIdx.x;
+        const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
+        auto bucket_of = [&](int64_t pos) {
+            int lo = 0, hi = g.nkq - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (off[kbase + mid] <= pos) lo = mid; else hi = mid - 1;
+            }
+            return lo;
+        };
+        // chunk after [c0, c1) starting in bucket kq: at most CH items of one bucket
+        auto next_chunk = [&](int64_t c0, int &kq, int64_t &c1) {
+            if (c0 >= wi.end) { c1 = c0; return; }
+            if (c0 >= off[kbase + kq + 1]) kq = bucket_of(c0);
+            c1 = min(min((int64_t)wi.end, off[kbase + kq + 1]), c0 + CH);
+        };
+        auto load_raw = [&](RawRec &q) {
+            const uint32_t v = q.code & VIS_MASK;
+            const uint32_t row = v / (uint32_t)g.nchan;
+            q.u = src.rowdf[3 * row + 0];
+            q.v = src.rowdf[3 * row + 1];
+            q.w = src.rowdf[3 * row + 2];
+            q.y = unit_vis ? make_float2(1.f, 0.f) : vis[v];
+            q.wt = wgt ? wgt[v] : 1.f;
+        };
+        // record t of buffer sb: per residue class the tap and the packed cell key
+        auto stage = [&](const RawRec &q, int t, int sb) {
+            float2 *ru = reinterpret_cast<float2 *>(smem_raw + L.ru[sb]);
+            float2 *rv = reinterpret_cast<float2 *>(smem_raw + L.rv[sb]);
+            float2 *rwy = reinterpret_cast<float2 *>(smem_raw + L.wy[sb]);
+            const uint32_t v = q.code & VIS_MASK;
+            const int du = (q.code >> 30) & 1, dv = q.code >> 31;
+            const uint32_t row = v / (uint32_t)g.nchan;
+            const int ch = (int)(v - row * (uint32_t)g.nchan);
+            const ChanDF cs = src.chandf[ch];
+            VisCoord<float> c;
+            {
+                float2 u = q.u, vv = q.v, w = q.w;
+                c.flip = w.x < 0.0f || (w.x == 0.0f && w.y < 0.0f);
+                if (c.flip) {
+                    u.x = -u.x; u.y = -u.y; vv.x = -vv.x; vv.y = -vv.y; w.x = -w.x; w.y = -w.y;
                 }
-                const float wuv = a.x * b.x;
-#pragma unroll
-                for (int c2 = 0; c2 < Ww / 2; ++c2) {
-                    acc[2 * c2].x = fmaf(wuv, q[c2].x, acc[2 * c2].x);
-                    acc[2 * c2].y = fmaf(wuv, q[c2].y, acc[2 * c2].y);
-                    acc[2 * c2 + 1].x = fmaf(wuv, q[c2].z, acc[2 * c2 + 1].x);
-                    acc[2 * c2 + 1].y = fmaf(wuv, q[c2].w, acc[2 * c2 + 1].y);
-                }
-                if (Ww & 1) {
-                    acc[Ww - 1].x = fmaf(wuv, qo.x, acc[Ww - 1].x);
-                    acc[Ww - 1].y = fmaf(wuv, qo.y, acc[Ww - 1].y);
+                float p, e;
+                int g0;
+                df_mul(u.x, u.y, cs.su_hi, cs.su_lo, p, e);
+                df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ou);
+                c.gu0 = wrap_mod(g0, g.Nu, g.inv_Nu);
+                df_mul(vv.x, vv.y, cs.sv_hi, cs.sv_lo, p, e);
+                df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ov);
+                c.gv0 = wrap_mod(g0, g.Nv, g.inv_Nv);
+                df_mul(w.x, w.y, cs.sp_hi, cs.sp_lo, p, e);
+                c.ph = (p - rintf(p)) + e;
+                if (Ww > 1) {
+                    df_mul(w.x, w.y, cs.sw_hi, cs.sw_lo, p, e);
+                    df_tap(p, e, g.w_oi, g.w_of, g.hw, g0, c.ow);
+                    c.k0 = g0 < 0 ? 0 : (g0 > g.P - Ww ? g.P - Ww : g0);
+                } else {
+                    c.k0 = 0;
+                    c.ow = 0.0f;
                 }
             }
-            // the sums stay in registers while the next chunk continues this bucket
-            if (n0 >= wi.end || kq_n != kq) flush_acc();
-        }
-        __syncthreads();
-        // ---- advance: stage the next chunk; codes move one chunk along, and the codes of
-        // the chunk after that are requested now (used one iteration later)
-        c0 = n0; c1 = n1; kq = kq_n;
-        if (c0 < wi.end) {
-            if (threadIdx.x < c1 - c0) stage(nxt, threadIdx.x);
+            float yr = q.y.x * q.wt, yi = q.y.y * q.wt;
+            if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
+                yr = yi = 0.f;   // none of its planes is in this block: scattered with zero weight
+            } else {
+                if (c.flip) yi = -yi;
+                if (g.tc != 0.0) {
+                    float cs2, sn;
+                    sincos_turns(c.ph, &sn, &cs2);
+                    const float r0 = yr * cs2 - yi * sn;
+                    yi = yr * sn + yi * cs2;
+                    yr = r0;
+                }
+            }
+            const int lu = (c.gu0 & (TILE - 1)) - du * TILE;
+            const int lv = (c.gv0 & (TILE - 1)) - dv * TILE;
+            const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
+            const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
+            const uint32_t kbits = (uint32_t)c.k0;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                int ap = j - mu, bp = j - mv;   // taps that land on residue class j
+                ap += ap < 0 ? W : 0;
+                bp += bp < 0 ? W : 0;
+                ru[t * W + j] = make_float2(es_kernel_fast(c.ou + (float)ap, ihw, bt),
+                                            __uint_as_float(((uint32_t)(lu + ap + 64) << 25) | kbits));
+                rv[t * W + j] = make_float2(es_kernel_fast(c.ov + (float)bp, ihw, bt),
+                                            __uint_as_float((uint32_t)(lv + bp + 64) << KEY_PLANE_BITS));
+            }
+            if (Ww > 1) {
+#pragma unroll
+                for (int i = 0; i < Ww; ++i) {
+                    const float kw = es_kernel_fast(c.ow + (float)i, ihw, bt);
+                    rwy[t * WS + i] = make_float2(kw * yr, kw * yi);
+                }
+            } else {
+                rwy[t * WS] = make_float2(yr, yi);
+            }
+        };
+
+        // chunk i = [c0, c1) in bucket kq; chunk i+1 = [n0, n1) in kq_n; chunk i+2 starts at n1
+        int kq = bucket_of(wi.begin);
+        int64_t c0 = wi.begin, c1;
+        next_chunk(c0, kq, c1);
+        RawRec raw;
+        raw.code = pt < c1 - c0 ? items[c0 + pt] : 0u;
+        if (pt < c1 - c0) load_raw(raw);
+        int kq_n = kq;
+        int64_t n0 = c1, n1;
+        next_chunk(n0, kq_n, n1);
+        RawRec nxt;
+        nxt.code = pt < n1 - n0 ? items[n0 + pt] : 0u;
+        int i = 0;
+        while (c0 < wi.end) {
+            const int sb = i & 1;
+            // raw inputs of chunk i+1 and item codes of chunk i+2: in flight during this stage
+            if (pt < n1 - n0) load_raw(nxt);
+            int kq_m = kq_n;
+            int64_t m0 = n1, m1;
+            next_chunk(m0, kq_m, m1);
+            const uint32_t code2 = pt < m1 - m0 ? items[m0 + pt] : 0u;
+            if (i >= 2) pair_sync<BAR_EMPTY>(sb);   // buffer sb released (chunk i-2)
+            if (pt < c1 - c0) stage(raw, pt, sb);
+            if (pt == 0) meta[sb] = make_int4((int)(c1 - c0), kq, n0 >= wi.end ? 1 : 0, kq_n);
+            __threadfence_block();
+            pair_arrive<BAR_FULL>(sb);
+            raw = nxt;
+            c0 = n0; c1 = n1; kq = kq_n;
             n0 = m0; n1 = m1; kq_n = kq_m;
             nxt.code = code2;
-            m0 = n1;
-            next_chunk(m0, kq_m, m1);
-            code2 = threadIdx.x < m1 - m0 ? items[m0 + threadIdx.x] : 0u;
+            ++i;
         }
-        __syncthreads();
+        // wait until the consumers have released the last buffers
+        for (int j = i >= 2 ? i - 2 : 0; j < i; ++j) pair_sync<BAR_EMPTY>(j & 1);
+    } else {
+        // ================================================================ consumers
+        const int ct = threadIdx.x - GRID_NP;
+        constexpr int G = W * W;
+        constexpr int NG = GRID_NC / G;
+        const int grp = ct / G, lid = ct - grp * G;
+        const int ta = lid / W, tb = lid - ta * W;
+        const bool in_group = grp < NG;
+        float2 acc[Ww];
+#pragma unroll
+        for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
+        uint32_t ckey = KEY_NONE;   // cell and first plane the accumulators belong to
+        auto flush_acc = [&]() {
+            const int cu = (int)(ckey >> 25) - 64, cv = (int)((ckey >> KEY_PLANE_BITS) & 127u) - 64;
+            const int ck = (int)(ckey & ((1u << KEY_PLANE_BITS) - 1u));
+            if ((unsigned)cu < (unsigned)TILE && (unsigned)cv < (unsigned)TILE) {
+                float2 *cell = ring + cu * RSTRIDE + cv;
+#pragma unroll
+                for (int c = 0; c < Ww; ++c) {
+                    const int k = ck + c;
+                    if (k >= k_lo && k < k_hi) {
+                        float2 *dst = cell + (k % R) * SLOT;
+                        atomicAdd(&dst->x, acc[c].x);
+                        atomicAdd(&dst->y, acc[c].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
+            ckey = KEY_NONE;
+        };
+        int prev_kq = -1;
+        for (int i = 0;; ++i) {
+            const int sb = i & 1;
+            pair_sync<BAR_FULL>(sb);
+            const int4 m = meta[sb];   // records, bucket, last chunk, bucket of the next chunk
+            if (m.y != prev_kq) {
+                // planes below this bucket's first plane are complete (the sums of the previous
+                // bucket were added to the ring at the end of its last chunk)
+                named_sync<BAR_CONS, GRID_NC>();
+                flush_planes(max(m.y * g.q, k_lo), ct, GRID_NC);
+                named_sync<BAR_CONS, GRID_NC>();
+                prev_kq = m.y;
+            }
+            if (in_group) {
+                const float2 *ru = reinterpret_cast<const float2 *>(smem_raw + L.ru[sb]);
+                const float2 *rv = reinterpret_cast<const float2 *>(smem_raw + L.rv[sb]);
+                const float2 *rwy = reinterpret_cast<const float2 *>(smem_raw + L.wy[sb]);
+                const int cnt = m.x;
+                const int per = (cnt + NG - 1) / NG;
+                const int r0 = grp * per, r1 = min(cnt, r0 + per);
+                const float2 *pu = ru + ta, *pv = rv + tb;
+                for (int r = r0; r < r1; ++r) {
+                    const float2 a = pu[r * W], b = pv[r * W];
+                    float4 q[Ww / 2 > 0 ? Ww / 2 : 1];
+                    float2 qo;
+                    const float4 *wy4 = reinterpret_cast<const float4 *>(rwy + r * WS);
+#pragma unroll
+                    for (int c2 = 0; c2 < Ww / 2; ++c2) q[c2] = wy4[c2];
+                    if (Ww & 1) qo = rwy[r * WS + Ww - 1];
+                    const uint32_t key = __float_as_uint(a.y) | __float_as_uint(b.y);
+                    if (key != ckey) {
+                        flush_acc();
+                        ckey = key;
+                    }
+                    const float wuv = a.x * b.x;
+#pragma unroll
+                    for (int c2 = 0; c2 < Ww / 2; ++c2) {
+                        acc[2 * c2].x = fmaf(wuv, q[c2].x, acc[2 * c2].x);
+                        acc[2 * c2].y = fmaf(wuv, q[c2].y, acc[2 * c2].y);
+                        acc[2 * c2 + 1].x = fmaf(wuv, q[c2].z, acc[2 * c2 + 1].x);
+                        acc[2 * c2 + 1].y = fmaf(wuv, q[c2].w, acc[2 * c2 + 1].y);
+                    }
+                    if (Ww & 1) {
+                        acc[Ww - 1].x = fmaf(wuv, qo.x, acc[Ww - 1].x);
+                        acc[Ww - 1].y = fmaf(wuv, qo.y, acc[Ww - 1].y);
+                    }
+                }
+                // the sums stay in registers while the next chunk continues this bucket
+                if (m.z || m.w != m.y) flush_acc();
+            }
+            __threadfence_block();
+            pair_arrive<BAR_EMPTY>(sb);
+            if (m.z) break;
+        }
+        // remaining planes: all of the block for an owned tile, the touched ones for a chunk
+        named_sync<BAR_CONS, GRID_NC>();
+        flush_planes(wi.atomic_mode ? min(k_hi, next + R) : k_hi, ct, GRID_NC);
     }
-    // remaining planes: all of the block for an owned tile, the touched ones for a chunk
-    flush_planes(wi.atomic_mode ? min(k_hi, next + R) : k_hi);
 }
 
 // ------------------------------------------------------------------ FP32 degridding from staged tiles
@@ -851,7 +908,7 @@ static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkI
                               float2 *planes) {
     const size_t smem = (size_t)res_layout(R, W, Ww).total;
     PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_grid_res<W, Ww><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
+    k_grid_res<W, Ww><<<nblk, GRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
                                                    k_hi, planes);
 }
 

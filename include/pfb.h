@@ -75,6 +75,12 @@ enum {
 /* pfb_geom.flags (test switches; production calls pass 0) */
 #define PFB_NO_DIVIDE_BY_N 1u     /* drop the 1/n factor of Eq. 1 */
 #define PFB_NO_WTERM 2u           /* drop the w (n - 1) term (coplanar 2-D NUFFT) */
+/* Memory/speed trade-off, no effect on the result beyond rounding: by default an
+   FP32 plan whose budget has room also keeps 24 bytes of precomputed geometry per
+   gridding item (first-tap cell, plane, flip, tap offsets, phase rotor), which the
+   gridding and degridding kernels stream instead of recomputing it from uvw.  With
+   this flag the plan never keeps them. */
+#define PFB_NO_ITEM_RECORDS 4u
 
 typedef struct {
     int32_t nx, ny;      /* image pixels per band (even); the PSF is 2nx x 2ny */
@@ -82,7 +88,7 @@ typedef struct {
     double fov_l, fov_m; /* field of view in radians: 0 = derive, else must equal nx*dl, ny*dm */
     double epsilon;      /* requested relative L2 accuracy of R and R^dagger */
     int32_t nband;       /* n_b imaging bands */
-    uint32_t flags;      /* PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM */
+    uint32_t flags;      /* PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM | PFB_NO_ITEM_RECORDS */
 } pfb_geom;
 
 /* Parameters of one pfb-clean step (Eqs. 6-9). */

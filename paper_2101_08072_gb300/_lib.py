@@ -11,6 +11,7 @@ PFB_F32 = 0
 PFB_F64 = 1
 PFB_NO_DIVIDE_BY_N = 1
 PFB_NO_WTERM = 2
+PFB_NO_ITEM_RECORDS = 4
 
 ERRORS = {
     0: "PFB_OK", -1: "PFB_ERR_ARG", -2: "PFB_ERR_OOM", -3: "PFB_ERR_CUDA", -4: "PFB_ERR_EPS",

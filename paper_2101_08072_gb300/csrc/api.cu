@@ -85,6 +85,10 @@ void Ctx::free_plan(Plan &p) {
     fr(p.d_corr, (size_t)p.nx * p.ny * (p.prec == PFB_F64 ? 8 : 4));
     if (p.d_work) fr(p.d_work, (size_t)p.work_begin.back() * sizeof(WorkItem));
     if (p.d_heavy) fr(p.d_heavy, (size_t)p.heavy_begin.back() * sizeof(int));
+    fr(p.d_rec, (size_t)p.nitems * sizeof(float4));
+    fr(p.d_rph, (size_t)p.nitems * sizeof(float2));
+    p.d_rec = nullptr;
+    p.d_rph = nullptr;
     p.d_scale = nullptr; p.d_rowdf = nullptr; p.d_chandf = nullptr; p.d_band = nullptr; p.d_bg = nullptr; p.d_items = nullptr; p.d_off = nullptr;
     p.d_tp = nullptr; p.d_corr = nullptr; p.d_work = nullptr; p.d_heavy = nullptr;
 }
@@ -195,7 +199,7 @@ void check_geom(const pfb_geom *g, pfb_prec prec) {
     PFB_REQUIRE(g->nx <= 65536 && g->ny <= 65536, "nx, ny must be <= 65536");
     PFB_REQUIRE(g->nband >= 1 && g->nband <= 32, "nband must be in [1, 32]");
     PFB_REQUIRE(std::isfinite(g->dl) && std::isfinite(g->dm) && g->dl > 0 && g->dm > 0, "dl, dm must be > 0");
-    PFB_REQUIRE((g->flags & ~(PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM)) == 0, "unknown flag bits");
+    PFB_REQUIRE((g->flags & ~(PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM | PFB_NO_ITEM_RECORDS)) == 0, "unknown flag bits");
     if (g->fov_l != 0)
         PFB_REQUIRE(std::fabs(g->fov_l - g->nx * g->dl) <= 1e-9 * std::fabs(g->fov_l), "fov_l != nx * dl");
     if (g->fov_m != 0)

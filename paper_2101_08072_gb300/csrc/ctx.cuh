@@ -53,6 +53,9 @@ struct Plan {
     void *d_corr = nullptr;   // 1 / (n psi_u psi_v psi_w) per pixel, working precision
     WorkItem *d_work = nullptr;
     int *d_heavy = nullptr;
+    // FP32 tile kernels: per-item geometry records in item order (optional)
+    float4 *d_rec = nullptr;
+    float2 *d_rph = nullptr;
     size_t bytes = 0;
 
     BandGeom geom(int b) const {
@@ -176,6 +179,7 @@ Plan &get_plan(Ctx &ctx, const pfb_geom &g, int prec, int64_t nrow, int nchan, c
 int kernel_support(double eps);
 
 // wstack.cu
+void build_item_records(Ctx &ctx, Plan &p, cudaStream_t st);
 template <typename T>
 void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st);
 template <typename T>

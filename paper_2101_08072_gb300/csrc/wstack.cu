@@ -339,15 +339,49 @@ __device__ __forceinline__ void pair_arrive(int sb) {
 // raw inputs of one record, held in registers between prefetch and staging
 struct RawRec {
     uint32_t code;
-    float2 u, v, w;   // uvw of the row as double-float
+    float2 u, v, w;   // uvw of the row as double-float (coordinates computed here)
+    float4 rec;       // precomputed item record (see k_item_records)
+    float2 ph;        // precomputed phase rotor
     float2 y;
     float wt;
 };
 
-template <int W, int Ww>
+// ---- precomputed item records
+// The geometry of an item (its first-tap cell relative to its tile, first plane,
+// Hermitian flip, fractional tap offsets and the rotor exp(2 pi i w t_c)) depends
+// only on uvw, the frequencies and the plan, so a plan that has the room keeps it
+// for every item, in item order: 16 + 8 bytes streamed per item instead of a
+// gathered uvw row and the double-float coordinate arithmetic on every call.
+//   rec = (ou, ov, ow, bits): bits = (lu + 32) | (lv + 32) << 6 | flip << 12 | k0 << 13
+//   rph = (cos, sin) of 2 pi w t_c
+__device__ __forceinline__ uint32_t rec_bits(int lu, int lv, bool flip, int k0) {
+    return (uint32_t)(lu + 32) | ((uint32_t)(lv + 32) << 6) | (flip ? 1u << 12 : 0u) | ((uint32_t)k0 << 13);
+}
+
+__global__ void k_item_records(const uint32_t *__restrict__ items, int64_t i0, int64_t n, CoordSrc src, BandGeom g,
+                               float4 *__restrict__ rec, float2 *__restrict__ rph) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + e;
+        const uint32_t code = items[i];
+        const uint32_t v = code & VIS_MASK;
+        const int du = (code >> 30) & 1, dv = code >> 31;
+        const uint32_t row = v / (uint32_t)g.nchan;
+        const int ch = (int)(v - row * (uint32_t)g.nchan);
+        const VisCoord<float> c = vis_coord32(src.rowdf, row, src.chandf[ch], g);
+        const int lu = (c.gu0 & (TILE - 1)) - du * TILE;
+        const int lv = (c.gv0 & (TILE - 1)) - dv * TILE;
+        rec[i] = make_float4(c.ou, c.ov, c.ow, __uint_as_float(rec_bits(lu, lv, c.flip, c.k0)));
+        float cs = 1.f, sn = 0.f;
+        if (g.tc != 0.0) sincos_turns(c.ph, &sn, &cs);
+        rph[i] = make_float2(cs, sn);
+    }
+}
+
+template <int W, int Ww, bool REC>
 __global__ void __launch_bounds__(GRID_NT, 2)
 k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items, const int64_t *__restrict__ off,
-           CoordSrc src, const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, BandGeom g,
+           CoordSrc src, const float4 *__restrict__ recs, const float2 *__restrict__ rph,
+           const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, BandGeom g,
            int k_lo, int k_hi, float2 *__restrict__ planes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int R = Ww;                  // ring planes (one w bucket per plane)
@@ -418,12 +452,17 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             if (c0 >= off[kbase + kq + 1]) kq = bucket_of(c0);
             c1 = min(min((int64_t)wi.end, off[kbase + kq + 1]), c0 + CH);
         };
-        auto load_raw = [&](RawRec &q) {
+        auto load_raw = [&](RawRec &q, int64_t idx) {
             const uint32_t v = q.code & VIS_MASK;
-            const uint32_t row = v / (uint32_t)g.nchan;
-            q.u = src.rowdf[3 * row + 0];
-            q.v = src.rowdf[3 * row + 1];
-            q.w = src.rowdf[3 * row + 2];
+            if constexpr (REC) {
+                q.rec = recs[idx];
+                q.ph = rph[idx];
+            } else {
+                const uint32_t row = v / (uint32_t)g.nchan;
+                q.u = src.rowdf[3 * row + 0];
+                q.v = src.rowdf[3 * row + 1];
+                q.w = src.rowdf[3 * row + 2];
+            }
             q.y = unit_vis ? make_float2(1.f, 0.f) : vis[v];
             q.wt = wgt ? wgt[v] : 1.f;
         };
@@ -432,13 +471,26 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             float2 *ru = reinterpret_cast<float2 *>(smem_raw + L.ru[sb]);
             float2 *rv = reinterpret_cast<float2 *>(smem_raw + L.rv[sb]);
             float2 *rwy = reinterpret_cast<float2 *>(smem_raw + L.wy[sb]);
-            const uint32_t v = q.code & VIS_MASK;
-            const int du = (q.code >> 30) & 1, dv = q.code >> 31;
-            const uint32_t row = v / (uint32_t)g.nchan;
-            const int ch = (int)(v - row * (uint32_t)g.nchan);
-            const ChanDF cs = src.chandf[ch];
             VisCoord<float> c;
-            {
+            int lu, lv;
+            float cs2 = 1.f, sn = 0.f;
+            if constexpr (REC) {
+                const uint32_t bits = __float_as_uint(q.rec.w);
+                c.ou = q.rec.x;
+                c.ov = q.rec.y;
+                c.ow = q.rec.z;
+                lu = (int)(bits & 63u) - 32;
+                lv = (int)((bits >> 6) & 63u) - 32;
+                c.flip = (bits >> 12) & 1u;
+                c.k0 = (int)(bits >> 13);
+                cs2 = q.ph.x;
+                sn = q.ph.y;
+            } else {
+                const uint32_t v = q.code & VIS_MASK;
+                const int du = (q.code >> 30) & 1, dv = q.code >> 31;
+                const uint32_t row = v / (uint32_t)g.nchan;
+                const int ch = (int)(v - row * (uint32_t)g.nchan);
+                const ChanDF cs = src.chandf[ch];
                 float2 u = q.u, vv = q.v, w = q.w;
                 c.flip = w.x < 0.0f || (w.x == 0.0f && w.y < 0.0f);
                 if (c.flip) {
@@ -462,22 +514,19 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                     c.k0 = 0;
                     c.ow = 0.0f;
                 }
+                lu = (c.gu0 & (TILE - 1)) - du * TILE;
+                lv = (c.gv0 & (TILE - 1)) - dv * TILE;
+                if (g.tc != 0.0) sincos_turns(c.ph, &sn, &cs2);
             }
             float yr = q.y.x * q.wt, yi = q.y.y * q.wt;
             if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
                 yr = yi = 0.f;   // none of its planes is in this block: scattered with zero weight
             } else {
                 if (c.flip) yi = -yi;
-                if (g.tc != 0.0) {
-                    float cs2, sn;
-                    sincos_turns(c.ph, &sn, &cs2);
-                    const float r0 = yr * cs2 - yi * sn;
-                    yi = yr * sn + yi * cs2;
-                    yr = r0;
-                }
+                const float r0 = yr * cs2 - yi * sn;
+                yi = yr * sn + yi * cs2;
+                yr = r0;
             }
-            const int lu = (c.gu0 & (TILE - 1)) - du * TILE;
-            const int lv = (c.gv0 & (TILE - 1)) - dv * TILE;
             const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
             const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
             const uint32_t kbits = (uint32_t)c.k0;
@@ -508,7 +557,7 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         next_chunk(c0, kq, c1);
         RawRec raw;
         raw.code = pt < c1 - c0 ? items[c0 + pt] : 0u;
-        if (pt < c1 - c0) load_raw(raw);
+        if (pt < c1 - c0) load_raw(raw, c0 + pt);
         int kq_n = kq;
         int64_t n0 = c1, n1;
         next_chunk(n0, kq_n, n1);
@@ -518,7 +567,7 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         while (c0 < wi.end) {
             const int sb = i & 1;
             // raw inputs of chunk i+1 and item codes of chunk i+2: in flight during this stage
-            if (pt < n1 - n0) load_raw(nxt);
+            if (pt < n1 - n0) load_raw(nxt, n0 + pt);
             int kq_m = kq_n;
             int64_t m0 = n1, m1;
             next_chunk(m0, kq_m, m1);
@@ -633,11 +682,12 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
 // the planes the current w bucket needs (a ring of W_w + q - 1 planes, refilled as
 // the buckets advance), with coalesced 8-byte loads; then one thread per home item
 // interpolates from shared memory.
-template <int W, int Ww>
+template <int W, int Ww, bool REC>
 __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restrict__ work,
                                                       const uint32_t *__restrict__ items,
-                                                      const int64_t *__restrict__ off, CoordSrc src, BandGeom g,
-                                                      int k_lo, int k_hi, const float2 *__restrict__ planes,
+                                                      const int64_t *__restrict__ off, CoordSrc src,
+                                                      const float4 *__restrict__ recs, const float2 *__restrict__ rph,
+                                                      BandGeom g, int k_lo, int k_hi, const float2 *__restrict__ planes,
                                                       float2 *__restrict__ vis) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *reg = reinterpret_cast<float2 *>(smem_raw);
@@ -694,9 +744,30 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
             const uint32_t code = items[it];
             if (code >> 30) continue;
             const uint32_t v = code;
-            const uint32_t row = v / (uint32_t)g.nchan;
-            const int ch = (int)(v - row * (uint32_t)g.nchan);
-            const VisCoord<float> c = vis_coord<float>(src, row, ch, g);
+            VisCoord<float> c;
+            int lu, lv;
+            float cs = 1.f, sn = 0.f;
+            if constexpr (REC) {
+                const float4 r4 = recs[it];
+                const uint32_t bits = __float_as_uint(r4.w);
+                c.ou = r4.x;
+                c.ov = r4.y;
+                c.ow = r4.z;
+                lu = (int)(bits & 63u) - 32;
+                lv = (int)((bits >> 6) & 63u) - 32;
+                c.flip = (bits >> 12) & 1u;
+                c.k0 = (int)(bits >> 13);
+                const float2 ph = rph[it];
+                cs = ph.x;
+                sn = ph.y;
+            } else {
+                const uint32_t row = v / (uint32_t)g.nchan;
+                const int ch = (int)(v - row * (uint32_t)g.nchan);
+                c = vis_coord<float>(src, row, ch, g);
+                lu = c.gu0 - tu * TILE;
+                lv = c.gv0 - tv * TILE;
+                if (g.tc != 0.0) sincos_turns(c.ph, &sn, &cs);
+            }
             if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) continue;
             const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
             float ku[W], kv[W], kw[Ww];
@@ -711,7 +782,6 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
             } else {
                 kw[0] = 1.f;
             }
-            const int lu = c.gu0 - tu * TILE, lv = c.gv0 - tv * TILE;
             float ar = 0.f, ai = 0.f;
 #pragma unroll
             for (int cw = 0; cw < Ww; ++cw) {
@@ -735,8 +805,6 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
                 ar = fmaf(kw[cw], pr, ar);
                 ai = fmaf(kw[cw], pi, ai);
             }
-            float cs = 1.f, sn = 0.f;
-            if (g.tc != 0.0) sincos_turns(c.ph, &sn, &cs);
             const float vr = ar * cs + ai * sn;
             float vi = ai * cs - ar * sn;
             if (c.flip) vi = -vi;
@@ -894,6 +962,27 @@ static unsigned grid_blocks(int64_t n, int threads, int cap) {
 static bool fast_path_f32(const Plan &p) {
     return p.prec == PFB_F32 && p.W >= 4 && p.W <= 8 && p.q == 1 && p.Pmax < (1 << KEY_PLANE_BITS);
 }
+// Item records for the FP32 tile kernels, when the budget leaves room for them next to
+// a plane block and a visibility-sized scratch; otherwise the kernels compute the
+// geometry on the fly.
+void build_item_records(Ctx &ctx, Plan &p, cudaStream_t st) {
+    if (!fast_path_f32(p) || p.nitems <= 0 || (p.flags & PFB_NO_ITEM_RECORDS)) return;
+    const size_t need = (size_t)p.nitems * (sizeof(float4) + sizeof(float2));
+    const size_t keep = 2 * (size_t)p.Ww * p.Nu * p.Nv * sizeof(float2) + (size_t)p.nrow * p.nchan * sizeof(float2) +
+                        16 * (size_t)p.nband * p.nx * p.ny * sizeof(float) + (256u << 20);
+    if (ctx.available() < need + keep) return;
+    p.d_rec = (float4 *)ctx.dalloc((size_t)p.nitems * sizeof(float4));
+    p.d_rph = (float2 *)ctx.dalloc((size_t)p.nitems * sizeof(float2));
+    p.bytes += need;
+    for (int b = 0; b < p.nband; ++b) {
+        const int64_t i0 = p.band_items_begin[b], n = p.band_items_end[b] - i0;
+        if (n <= 0) continue;
+        k_item_records<<<grid_blocks(n, 256, 32 * ctx.num_sms), 256, 0, st>>>(p.d_items, i0, n, p.coords(), p.geom(b),
+                                                                             p.d_rec, p.d_rph);
+        check_launch("item_records");
+    }
+}
+
 static bool degrid_tiles_fit(const Plan &p) {
     const int R = p.Ww, E = TILE + p.W - 1, ES = E | 1;
     return fast_path_f32(p) && (size_t)R * E * ES * sizeof(float2) <= 227 * 1024;
@@ -907,9 +996,17 @@ static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkI
                               const float2 *vis, const float *wgt, int unit, const BandGeom &g, int k_lo, int k_hi,
                               float2 *planes) {
     const size_t smem = (size_t)res_layout(R, W, Ww).total;
-    PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_grid_res<W, Ww><<<nblk, GRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), vis, wgt, unit, g, k_lo,
-                                                   k_hi, planes);
+    if (p.d_rec) {
+        PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        k_grid_res<W, Ww, true><<<nblk, GRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), p.d_rec,
+                                                             p.d_rph, vis, wgt, unit, g, k_lo, k_hi, planes);
+    } else {
+        PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        k_grid_res<W, Ww, false><<<nblk, GRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), nullptr,
+                                                              nullptr, vis, wgt, unit, g, k_lo, k_hi, planes);
+    }
 }
 
 template <int W, int Ww>
@@ -917,8 +1014,17 @@ static void launch_degrid_t(unsigned nblk, int R, cudaStream_t st, const WorkIte
                             const BandGeom &g, int k_lo, int k_hi, const float2 *planes, float2 *vis) {
     const int E = TILE + W - 1, ES = E | 1;
     const size_t smem = (size_t)R * E * ES * sizeof(float2);
-    PFB_CUDA(cudaFuncSetAttribute(k_degrid_tiles<W, Ww>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_degrid_tiles<W, Ww><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), g, k_lo, k_hi, planes, vis);
+    if (p.d_rec) {
+        PFB_CUDA(cudaFuncSetAttribute(k_degrid_tiles<W, Ww, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        k_degrid_tiles<W, Ww, true><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), p.d_rec, p.d_rph,
+                                                             g, k_lo, k_hi, planes, vis);
+    } else {
+        PFB_CUDA(cudaFuncSetAttribute(k_degrid_tiles<W, Ww, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        k_degrid_tiles<W, Ww, false><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), nullptr, nullptr,
+                                                              g, k_lo, k_hi, planes, vis);
+    }
 }
 
 #define PFB_W_SWITCH(W, WS, CALL)                                                     \

@@ -67,6 +67,32 @@ def test_wide_multiband(ctx, prec, eps, tol):
         assert rel_l2(img[b], ref[b]) <= tol, b
 
 
+def test_item_records_off_matches(ctx):
+    """PFB_NO_ITEM_RECORDS (geometry recomputed from uvw in the kernels) gives the
+    oracle's result and agrees with the default plan that streams stored item records."""
+    from paper_2101_08072_gb300._lib import PFB_NO_ITEM_RECORDS
+    obs = wide_observation()
+    rng = np.random.default_rng(103)
+    x = synth.point_source_image(rng, obs.nband, obs.nx, obs.ny, 12)
+    y = synth.random_vis(rng, (obs.nrow, obs.nchan))
+    w = synth.uniform_weights(rng, (obs.nrow, obs.nchan))
+    g_on = geometry(obs, EPS32)
+    g_off = geometry(obs, EPS32, flags=PFB_NO_ITEM_RECORDS)
+    d = dev_obs(obs)
+    ref_v = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm)
+    ref_i = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, y, w, obs.nx, obs.ny, obs.dl, obs.dm, obs.nband)
+    out = {}
+    for name, g in (("on", g_on), ("off", g_off)):
+        v = ctx.pfb_degrid(g, *d, real_t(x, 32)).cpu().numpy()
+        img = ctx.pfb_grid(g, *d, cx_t(y, 32), real_t(w, 32)).cpu().numpy()
+        assert rel_l2(v, ref_v) <= TOL32, name
+        for b in range(obs.nband):
+            assert rel_l2(img[b], ref_i[b]) <= TOL32, (name, b)
+        out[name] = (v, img)
+    assert rel_l2(out["off"][0], out["on"][0]) <= 1e-6
+    assert rel_l2(out["off"][1], out["on"][1]) <= 1e-6
+
+
 @pytest.mark.parametrize("prec,eps,tol", PRECS)
 def test_dirty_psf_hessian(ctx, prec, eps, tol):
     obs = synth.tiny_observation(nx=32, ny=32)

@@ -223,6 +223,15 @@ int pfb_timing_names(pfb_ctx *ctx, char *buf, size_t len);
 int pfb_wsum_static(int device, pfb_prec prec, int64_t nrow, int32_t nchan, int32_t nband,
                     const int32_t *band_of_chan, const void *wgt, double *wsum_out, void *stream);
 
+/* Support W (taps per axis, in u, v and w) of the ES kernel that the library picks
+ * for a requested accuracy epsilon (Section 2; the smallest W whose worst-case
+ * aliasing bound is <= epsilon at 2x oversampling).  Each visibility then costs
+ * W^2 W_w multiply-adds per gridding or degridding pass (W_w = W with w-stacking,
+ * 1 without).  Returns W (4..16), or PFB_ERR_EPS when epsilon is below what
+ * `prec` reaches (1e-6 for PFB_F32, 1e-12 for PFB_F64) and PFB_ERR_ARG when it
+ * is not positive and finite.  No device work. */
+int pfb_kernel_support(double epsilon, pfb_prec prec);
+
 /* Library version string. */
 const char *pfb_version(void);
 

@@ -21,7 +21,7 @@ ERRORS = {
 # every function the header declares (the CPU test checks the library exports them)
 EXPORTS = ["pfb_create", "pfb_destroy", "pfb_last_error", "pfb_plan_reset", "pfb_degrid", "pfb_grid",
            "pfb_dirty", "pfb_psf", "pfb_hessian", "pfb_psf_conv", "pfb_step", "pfb_version",
-           "pfb_timing", "pfb_timing_read", "pfb_timing_names", "pfb_wsum_static"]
+           "pfb_timing", "pfb_timing_read", "pfb_timing_names", "pfb_wsum_static", "pfb_kernel_support"]
 
 
 class pfb_geom(ctypes.Structure):
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     lib.pfb_timing_read.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.pfb_timing_names.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     lib.pfb_wsum_static.argtypes = [ctypes.c_int, ctypes.c_int, I64, I32, I32, P, P, P, P]
+    lib.pfb_kernel_support.argtypes = [D, ctypes.c_int]
     for f in EXPORTS:
         if f not in ("pfb_destroy", "pfb_last_error", "pfb_version", "pfb_create"):
             getattr(lib, f).restype = ctypes.c_int

@@ -223,6 +223,12 @@ extern "C" {
 
 const char *pfb_version(void) { return "pfb-gb300 0.1 (sm_103a)"; }
 
+int pfb_kernel_support(double epsilon, pfb_prec prec) {
+    if (!(epsilon > 0.0) || !std::isfinite(epsilon) || (prec != PFB_F32 && prec != PFB_F64)) return PFB_ERR_ARG;
+    if (epsilon < (prec == PFB_F32 ? 1e-6 : 1e-12)) return PFB_ERR_EPS;
+    return kernel_support(epsilon);
+}
+
 int pfb_timing(pfb_ctx *ctx, int enable) {
     return guarded(ctx, [&](Ctx &c) {
         c.timing.clear();

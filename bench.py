@@ -493,19 +493,23 @@ def run_serve(args):
     __graft_entry__.build()
     from paper_2101_08072_gb300.serve import Server
     reqs = serve_requests(args.serve_requests, max_pix=args.serve_max_pix, max_rows=args.serve_max_rows)
-    # offered load: a Poisson stream at 0.8 of the sequential capacity, estimated from the
-    # service times of the first FP32 and FP64 requests run alone
+    # offered load: a Poisson stream at 0.8 of the sequential capacity.  The service time of a
+    # request is modelled as (seconds per visibility-step of its precision) x visibilities x
+    # (steps + 3, for the dirty image and the PSF); the per-precision rate comes from the first
+    # FP32 and the first FP64 request, each run alone.
     srv = Server(0, max_active=1)
-    svc = []
-    for r in reqs[:2]:          # one FP32 and one FP64 request, each alone
+    per_vis_step = {}
+    for prec in ("f32", "f64"):
+        r = next(q for q in reqs if q.precision == prec)
         t0 = time.perf_counter()
         try:
             srv.submit(r).result()
         except Exception:
             pass
-        svc.append(time.perf_counter() - t0)
+        per_vis_step[prec] = (time.perf_counter() - t0) / (r.nvis * (r.n_iter + 3))
     srv.close()
-    rate = 0.8 / max(float(np.mean(svc)), 1e-3)
+    predicted = [per_vis_step[q.precision] * q.nvis * (q.n_iter + 3) for q in reqs]
+    rate = 0.8 / max(float(np.mean(predicted)), 1e-3)
     from paper_2101_08072_gb300 import synth
     arrivals = synth.poisson_arrivals(np.random.default_rng(4), len(reqs), rate)
     srv = Server(0, max_active=8)
@@ -528,7 +532,8 @@ def run_serve(args):
     m = srv.metrics()
     line = {"metric": "serving latency (pfb-clean requests, 10 steps each)", "value": m["p50_s"], "unit": "s",
             "higher_is_better": False, "p50_s": m["p50_s"], "p99_s": m["p99_s"], "mvis_per_s": m["mvis_per_s"],
-            "completed": m["completed"], "errors": errors, "error_messages": messages, "requests": len(reqs), "arrival_rate_per_s": rate,
+            "completed": m["completed"], "errors": errors, "error_messages": messages, "requests": len(reqs),
+            "arrival_rate_per_s": rate, "predicted_sequential_s": float(np.sum(predicted)),
             "data": "synthetic (seeded)", "n_gpus": 1,
             "config": {"workload": f"Poisson stream of mixed-size requests: 512^2-{args.serve_max_pix}^2, "
                                    f"1e4-{args.serve_max_rows:.0e} rows, 8-128 channels, 1-4 bands, "

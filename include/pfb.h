@@ -118,8 +118,11 @@ void pfb_destroy(pfb_ctx *ctx);
  * of a context-free call (pfb_wsum_static) on the calling thread. */
 const char *pfb_last_error(const pfb_ctx *ctx);
 
-/* Drop cached plans and PSF spectra (call after changing uvw/freq/band contents
- * or PSF contents in place). */
+/* Drop cached plans, PSF spectra and scratch buffers (w-plane blocks and the
+ * like), returning their memory to the context's budget; the next call rebuilds
+ * what it needs.  Call it after changing uvw/freq/band or PSF contents in place,
+ * or between the phases of a solve that use different geometries (the PSF's 2x
+ * field, then the image).  Synchronises the device. */
 int pfb_plan_reset(pfb_ctx *ctx);
 
 /* R, degridding (Section 2, Eq. 1): image [nband][nx][ny] -> vis_out [nrow][nchan].

@@ -99,6 +99,9 @@ void Ctx::reset() {
     plans.clear();
     for (auto &s : spectra) dfree(s.spec, s.bytes);
     spectra.clear();
+    for (auto &b : bufs)
+        if (b.second.ptr) dfree(b.second.ptr, b.second.bytes);
+    bufs.clear();
 }
 
 cufftHandle Ctx::fft(int n0, int n1, int batch, cufftType type) {

@@ -67,8 +67,8 @@ class Request:
 
 
 def footprint_bytes(r: Request) -> int:
-    """HBM reserved for a request: its data, images, the plan's item lists and
-    pixel tables, and w-plane stacks for the operator and the PSF grid (the
+    """HBM reserved for a request: its data, images, the plan's item lists, item
+    records and pixel tables, and w-plane stacks for the operator and the PSF grid (the
     library processes plane blocks within whatever budget it is given, so the
     stacks are sized for a handful of planes, not the whole stack)."""
     rs = 4 if r.precision == "f32" else 8
@@ -78,6 +78,8 @@ def footprint_bytes(r: Request) -> int:
     img = r.nband * r.nx * r.ny
     images = img * rs * 10 + 4 * img * rs * 2 + 4 * img * cs                # x, dual, dirty, CG vectors, PSF, spectra
     tables = img * 16 + 4 * img * 16 + 2 * (1 << 25) * 12                  # pixel tables, bucket offsets
+    if r.precision == "f32":
+        tables += int(1.4 * nvis) * 24                                    # per-item geometry records
     grid = 4 * r.nx * r.ny * cs                                             # one oversampled plane
     planes = 12 * grid + 4 * 12 * grid                                      # operator and PSF plane blocks + FFT work
     return int(1.15 * (data + images + tables + planes)) + (64 << 20)
@@ -151,8 +153,11 @@ class _Slot:
             nb = bin(self.params.basis_mask).count("1")
             self.x = torch.zeros((req.nband, req.nx, req.ny), dtype=rdt, device=self.dev)
             self.dual = torch.zeros((nb, req.nband, req.nx, req.ny), dtype=rdt, device=self.dev)
-            self.dirty, self.wsum = self.ctx.pfb_dirty(self.geom, self.uvw, self.freq, self.band, self.vis, self.wgt)
+            # PSF first (2x field), then its plan and plane block go before the image-sized
+            # plan that the dirty image and the steps share is built
             self.psf, _ = self.ctx.pfb_psf(self.geom, self.uvw, self.freq, self.band, self.wgt)
+            self.ctx.pfb_plan_reset()
+            self.dirty, self.wsum = self.ctx.pfb_dirty(self.geom, self.uvw, self.freq, self.band, self.vis, self.wgt)
 
     def issue_step(self):
         import torch

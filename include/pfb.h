@@ -103,7 +103,17 @@ typedef struct {
     int32_t nlevel;      /* wavelet decomposition levels (wavelet bases) */
     uint32_t basis_mask; /* bit 0 Dirac; bits 1..6 Daubechies db1..db6 (Eq. 9's dictionary) */
     double unorm;        /* ||U|| for the primal step; <= 0: max |PSF spectrum| + sigma */
+    uint32_t flags;      /* PFB_STEP_* bits; 0 = the exact-gradient step */
 } pfb_params;
+
+/* pfb_params.flags */
+/* Approximate gradient (Eq. 4): the step takes IR = I^d - I^psf * x_k, the PSF
+   convolution standing in for the Hessian, instead of the exact IR = I^d - H x_k
+   (Eq. 3).  No visibility is touched: the step costs only image-sized FFTs.  The
+   paper notes that this gradient is inexact for wide fields (the w term breaks the
+   convolution structure); it is offered as the cheap inner gradient of a major /
+   minor cycle scheme, not as a replacement for the exact step. */
+#define PFB_STEP_APPROX_GRADIENT 1u
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the scratch
  * (w-plane stacks, sort tables); 0 means 85% of the device memory free at creation.
@@ -175,7 +185,9 @@ int pfb_psf_conv(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const void *
  * dirty [nband][nx][ny] and psf [nband][2nx][2ny] as written by pfb_dirty / pfb_psf;
  * wsum (host, [nband]) the weight sums they returned; x_inout [nband][nx][ny];
  * dual_inout [nbasis][nband][nx][ny] (nbasis = bits set in basis_mask), zero on
- * the first step.  n_hessian_out (host, may be NULL) receives 1; stats_out (host,
+ * the first step.  n_hessian_out (host, may be NULL) receives 1 (0 with
+ * PFB_STEP_APPROX_GRADIENT, where IR = I^d - I^psf * x_k and the objective's data
+ * term uses I^psf * x_k in place of H x_k); stats_out (host,
  * [3], may be NULL) receives [objective at x_k without the data constant,
  * ||x_{k+1} - x_k|| / ||x_{k+1}||, largest CG relative residual]; when stats_out
  * is given the call returns after synchronising the stream, otherwise it only
@@ -185,6 +197,31 @@ int pfb_step(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_params
              const int32_t *band_of_chan, const void *wgt, const void *dirty, const void *psf,
              const double *wsum, void *x_inout, void *dual_inout, int64_t *n_hessian_out,
              double *stats_out, void *stream);
+
+/* A whole pfb-clean solve from the data (Section 3: the PSF and dirty image, then
+ * preconditioned forward-backward steps until the iterates settle):
+ *   1. psf_out = I^psf on the 2nx x 2ny grid and wsum_out (host, [nband]) the
+ *      per-band weight sums, exactly as pfb_psf writes them;
+ *   2. the context's plans and scratch buffers are dropped (as pfb_plan_reset:
+ *      the PSF's 2x-field plan is not reused), then dirty_out = I^d as pfb_dirty;
+ *   3. up to max_outer calls of the step of pfb_step on x_inout / dual_inout (their
+ *      contents on entry are the starting point: zeros for a cold start), stopping
+ *      after the first step whose relative update ||x_{k+1} - x_k|| / ||x_{k+1}||
+ *      is <= tol (tol <= 0: always max_outer steps).
+ * params as for pfb_step (PFB_STEP_APPROX_GRADIENT makes every step use Eq. 4).
+ * n_outer_out (host) receives the steps taken; n_hessian_out (host) the count of
+ * full R^dagger Sigma^-1 R applications: one per exact-gradient step plus one for
+ * the dirty image and the PSF together (each is one half: a gridding pass without
+ * the degridding).  history_out (host, [max_outer][3], may be NULL) receives each
+ * step's stats as pfb_step's stats_out.  Synchronises the device (step 2) and the
+ * stream after every step (the stopping test reads the update on the host).
+ * Arrays: vis, wgt as pfb_dirty; dirty_out [nband][nx][ny]; psf_out
+ * [nband][2nx][2ny]; x_inout [nband][nx][ny]; dual_inout [nbasis][nband][nx][ny]. */
+int pfb_clean(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_params *params, int32_t max_outer,
+              double tol, int64_t nrow, int32_t nchan, const double *uvw, const double *freq,
+              const int32_t *band_of_chan, const void *vis, const void *wgt, void *dirty_out, void *psf_out,
+              double *wsum_out, void *x_inout, void *dual_inout, int32_t *n_outer_out, int64_t *n_hessian_out,
+              double *history_out, void *stream);
 
 /* Per-kernel device timing (tracing; not part of the paper's method).
  * pfb_timing(ctx, 1) clears the totals and starts recording CUDA events around

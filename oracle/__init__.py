@@ -16,14 +16,19 @@ interferometric data"):
   psf_conv    I^psf * x as a linear convolution (Eq. 4): direct sum or padded FFT
   cg          conjugate gradient for U delta = IR, U = I^psf* + sigma Id (Eq. 6, Eq. 8)
   prox        Condat-Vu primal-dual for Eq. 7 with r(x) of Eq. 9
-  step        one preconditioned forward-backward step (Eqs. 6-7)
+  step        one preconditioned forward-backward step (Eqs. 6-7); optionally with
+              the approximate gradient of Eq. 4 (I^psf * x in place of H x)
+  clean       a whole solve: PSF, dirty image, then steps until the relative update
+              reaches a tolerance
   daubechies  db1..db6 filters by spectral factorisation, periodised DWT (Eq. 9's Psi)
 
 Parity status: R, R^dagger, I^d, I^psf, the Hessian, the PSF convolution, CG,
 the prox, the wavelets and the gradient are pinned by tests/test_oracle_pins.py
 (closed forms, library-routine special cases, invariants, brute force).  The
-composed step at fixed iteration counts has no printed value in the paper to
-pin it: its parts are pinned, the composition itself is "parity unpinned".
+composed step and the clean driver at fixed iteration counts have no printed
+value in the paper to pin them: their parts are pinned, and so are the fixed
+point at the true image, the reduction of the approximate gradient to the exact
+one at w = 0 and the stopping rule; the iterates themselves are "parity unpinned".
 """
 from __future__ import annotations
 
@@ -334,6 +339,7 @@ class Params:
     nlevel: int = 3
     basis_mask: int = 1
     unorm: float = 0.0          # ||U||; <= 0 means max|Re spectrum| + sigma
+    approx_gradient: bool = False   # Eq. 4: I^psf * x stands in for H x
 
 
 def unorm_of(spec_sym, sigma):
@@ -374,7 +380,8 @@ def step(uvw, freq, band_of_chan, wgt, dirty_img, psf_img, wsum_b, x, v, dl, dm,
     """One preconditioned forward-backward step.
 
       wbar = mean_b wsum_b      (one scalar: I^d, I^psf and the Hessian are divided by it)
-      IR   = I^d - H x_k        (one Hessian application = the exact -grad f, Eq. 3)
+      IR   = I^d - H x_k        (one Hessian application = the exact -grad f, Eq. 3;
+                                 with p.approx_gradient I^d - I^psf * x_k, Eq. 4)
       delta = CG(U, IR)         (U = I^psf_sym * + sigma Id, Eq. 8)
       xbar = x_k + gamma delta  (Eq. 6)
       x_{k+1}, v = prox(xbar)   (Eq. 7)
@@ -384,8 +391,12 @@ def step(uvw, freq, band_of_chan, wgt, dirty_img, psf_img, wsum_b, x, v, dl, dm,
     (tests of the composition at sizes where the direct DFT is too slow)."""
     nband = x.shape[0]
     wbar = float(np.mean(wsum_b))
-    hx = (hessian(uvw, freq, band_of_chan, wgt, x, dl, dm, flags) if hessian_fn is None
-          else hessian_fn(x)) / wbar
+    if p.approx_gradient:
+        # Eq. 4: the PSF convolution (plain, not symmetrised) replaces the Hessian
+        hx = psf_conv(np.asarray(psf_img, dtype=np.float64), x) / wbar
+    else:
+        hx = (hessian(uvw, freq, band_of_chan, wgt, x, dl, dm, flags) if hessian_fn is None
+              else hessian_fn(x)) / wbar
     idn = np.asarray(dirty_img, dtype=np.float64) / wbar
     psfn = np.asarray(psf_img, dtype=np.float64) / wbar
     ir = idn - hx
@@ -399,3 +410,28 @@ def step(uvw, freq, band_of_chan, wgt, dirty_img, psf_img, wsum_b, x, v, dl, dm,
     nx1 = float(np.linalg.norm(x1))
     rel = float(np.linalg.norm(x1 - x)) / nx1 if nx1 > 0 else 0.0
     return x1, v1, np.array([obj, rel, float(cgres.max()) if nband else 0.0])
+
+
+# ------------------------------------------------------------------ whole solve
+def clean(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, p: Params, max_outer, tol,
+          x0=None, v0=None, flags=0):
+    """A pfb-clean solve: I^psf on the 2x field and I^d from the data (Eqs. 3-4), then
+    preconditioned forward-backward steps (Eqs. 6-7) from x0 (zeros by default) and the
+    dual v0, stopping after the first step whose relative update is <= tol (tol <= 0:
+    max_outer steps).  n_hessian counts full R^dagger Sigma^-1 R applications: one per
+    exact-gradient step and one for I^d and I^psf together (one half each)."""
+    psf_img, wsum_b = psf(uvw, freq, band_of_chan, wgt, nx, ny, dl, dm, nband, flags)
+    dirty_img, _ = dirty(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, flags)
+    nbasis = len(basis_list(p.basis_mask))
+    x = np.zeros((nband, nx, ny)) if x0 is None else np.array(x0, dtype=np.float64)
+    v = np.zeros((nbasis, nband, nx, ny)) if v0 is None else np.array(v0, dtype=np.float64)
+    hist = []
+    n_hessian = 1
+    while len(hist) < max_outer:
+        x, v, st = step(uvw, freq, band_of_chan, wgt, dirty_img, psf_img, wsum_b, x, v, dl, dm, p, flags)
+        hist.append(st)
+        n_hessian += 0 if p.approx_gradient else 1
+        if tol > 0 and st[1] <= tol:
+            break
+    return {"x": x, "dual": v, "dirty": dirty_img, "psf": psf_img, "wsum": wsum_b, "n_outer": len(hist),
+            "n_hessian": n_hessian, "history": np.array(hist).reshape(len(hist), 3)}

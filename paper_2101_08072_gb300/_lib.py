@@ -12,6 +12,7 @@ PFB_F64 = 1
 PFB_NO_DIVIDE_BY_N = 1
 PFB_NO_WTERM = 2
 PFB_NO_ITEM_RECORDS = 4
+PFB_STEP_APPROX_GRADIENT = 1
 
 ERRORS = {
     0: "PFB_OK", -1: "PFB_ERR_ARG", -2: "PFB_ERR_OOM", -3: "PFB_ERR_CUDA", -4: "PFB_ERR_EPS",
@@ -20,7 +21,7 @@ ERRORS = {
 
 # every function the header declares (the CPU test checks the library exports them)
 EXPORTS = ["pfb_create", "pfb_destroy", "pfb_last_error", "pfb_plan_reset", "pfb_degrid", "pfb_grid",
-           "pfb_dirty", "pfb_psf", "pfb_hessian", "pfb_psf_conv", "pfb_step", "pfb_version",
+           "pfb_dirty", "pfb_psf", "pfb_hessian", "pfb_psf_conv", "pfb_step", "pfb_clean", "pfb_version",
            "pfb_timing", "pfb_timing_read", "pfb_timing_names", "pfb_wsum_static", "pfb_kernel_support"]
 
 
@@ -34,7 +35,7 @@ class pfb_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("sigma", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("cg_tol", ctypes.c_double), ("pd_tol", ctypes.c_double), ("cg_iters", ctypes.c_int32),
                 ("pd_iters", ctypes.c_int32), ("nlevel", ctypes.c_int32), ("basis_mask", ctypes.c_uint32),
-                ("unorm", ctypes.c_double)]
+                ("unorm", ctypes.c_double), ("flags", ctypes.c_uint32)]
 
 
 class PfbError(RuntimeError):
@@ -74,6 +75,9 @@ def load(path: str = LIB_PATH):
     lib.pfb_psf_conv.argtypes = [P, G, ctypes.c_int, P, P, P, P]
     lib.pfb_step.argtypes = [P, G, ctypes.c_int, ctypes.POINTER(pfb_params), *data, P, P, P,
                              ctypes.POINTER(D), P, P, ctypes.POINTER(I64), ctypes.POINTER(D), P]
+    lib.pfb_clean.argtypes = [P, G, ctypes.c_int, ctypes.POINTER(pfb_params), I32, D, *data, P, P, P, P,
+                              ctypes.POINTER(D), P, P, ctypes.POINTER(I32), ctypes.POINTER(I64),
+                              ctypes.POINTER(D), P]
     lib.pfb_timing.argtypes = [P, ctypes.c_int]
     lib.pfb_timing_read.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.pfb_timing_names.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]

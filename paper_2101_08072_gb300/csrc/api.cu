@@ -220,6 +220,29 @@ void check_data(int64_t nrow, int32_t nchan, const double *uvw, const double *fr
 
 cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+void check_params(const pfb_params *prm, const pfb_geom *g) {
+    PFB_REQUIRE(prm, "params is NULL");
+    PFB_REQUIRE(prm->gamma > 0 && prm->sigma > 0 && prm->lambda >= 0, "need gamma > 0, sigma > 0, lambda >= 0");
+    PFB_REQUIRE(prm->cg_iters >= 0 && prm->pd_iters >= 0, "iteration counts must be >= 0");
+    PFB_REQUIRE(prm->basis_mask >= 1u && prm->basis_mask < 128u, "basis_mask must select bits 0..6");
+    PFB_REQUIRE((prm->flags & ~PFB_STEP_APPROX_GRADIENT) == 0, "unknown params flag bits");
+    if (prm->basis_mask != 1u) {
+        PFB_REQUIRE(prm->nlevel >= 1 && prm->nlevel <= 12, "nlevel must be in [1, 12]");
+        PFB_REQUIRE(g->nx % (1 << prm->nlevel) == 0 && g->ny % (1 << prm->nlevel) == 0,
+                    "wavelet bases need nx, ny divisible by 2^nlevel (periodised transform)");
+    }
+}
+
+void run_step(Ctx &c, const Plan &p, pfb_prec prec, const pfb_params &prm, const void *wgt, const void *dirty,
+              const void *psf, const double *wsum, void *x, void *dual, double *stats, cudaStream_t st) {
+    if (prec == PFB_F64)
+        op_step<double>(c, p, prm, (const double *)wgt, (const double *)dirty, (const double *)psf, wsum,
+                        (double *)x, (double *)dual, stats, st);
+    else
+        op_step<float>(c, p, prm, (const float *)wgt, (const float *)dirty, (const float *)psf, wsum, (float *)x,
+                       (float *)dual, stats, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -414,24 +437,57 @@ int pfb_step(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const pfb_params *p
     return guarded(ctx, [&](Ctx &c) {
         check_geom(g, prec);
         check_data(nrow, nchan, uvw, freq, band);
-        PFB_REQUIRE(prm, "params is NULL");
+        check_params(prm, g);
         PFB_REQUIRE(dirty && psf && wsum && x_inout && dual_inout, "dirty, psf, wsum, x and dual must not be NULL");
-        PFB_REQUIRE(prm->gamma > 0 && prm->sigma > 0 && prm->lambda >= 0, "need gamma > 0, sigma > 0, lambda >= 0");
-        PFB_REQUIRE(prm->cg_iters >= 0 && prm->pd_iters >= 0, "iteration counts must be >= 0");
-        PFB_REQUIRE(prm->basis_mask >= 1u && prm->basis_mask < 128u, "basis_mask must select bits 0..6");
-        if (prm->basis_mask != 1u) {
-            PFB_REQUIRE(prm->nlevel >= 1 && prm->nlevel <= 12, "nlevel must be in [1, 12]");
-            PFB_REQUIRE(g->nx % (1 << prm->nlevel) == 0 && g->ny % (1 << prm->nlevel) == 0,
-                        "wavelet bases need nx, ny divisible by 2^nlevel (periodised transform)");
-        }
         Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, S(stream));
+        run_step(c, p, prec, *prm, wgt, dirty, psf, wsum, x_inout, dual_inout, stats_out, S(stream));
+        // known on the host: no synchronisation
+        if (n_hessian_out) *n_hessian_out = (prm->flags & PFB_STEP_APPROX_GRADIENT) ? 0 : 1;
+    });
+}
+
+int pfb_clean(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const pfb_params *prm, int32_t max_outer, double tol,
+              int64_t nrow, int32_t nchan, const double *uvw, const double *freq, const int32_t *band,
+              const void *vis, const void *wgt, void *dirty_out, void *psf_out, double *wsum_out, void *x_inout,
+              void *dual_inout, int32_t *n_outer_out, int64_t *n_hessian_out, double *history_out, void *stream) {
+    return guarded(ctx, [&](Ctx &c) {
+        check_geom(g, prec);
+        check_data(nrow, nchan, uvw, freq, band);
+        check_params(prm, g);
+        PFB_REQUIRE(max_outer >= 0, "max_outer must be >= 0");
+        PFB_REQUIRE(std::isfinite(tol), "tol must be finite");
+        PFB_REQUIRE(vis && dirty_out && psf_out && wsum_out && x_inout && dual_inout && n_outer_out && n_hessian_out,
+                    "vis, dirty_out, psf_out, wsum_out, x, dual, n_outer_out and n_hessian_out must not be NULL");
+        PFB_REQUIRE(2 * g->nx <= 65536 && 2 * g->ny <= 65536, "PSF grid too large");
+        const cudaStream_t st = S(stream);
+        // 1. I^psf on the 2x field and the weight sums
+        {
+            Plan &pp = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, true, st);
+            if (prec == PFB_F64) op_grid<double>(c, pp, nullptr, (const double *)wgt, true, (double *)psf_out, st);
+            else op_grid<float>(c, pp, nullptr, (const float *)wgt, true, (float *)psf_out, st);
+            wsum_to_host(c, pp, prec, wgt, wsum_out, st);
+        }
+        // 2. the 2x-field plan and its plane stack give their memory back; then I^d
+        c.reset();
+        Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, st);
         if (prec == PFB_F64)
-            op_step<double>(c, p, *prm, (const double *)wgt, (const double *)dirty, (const double *)psf, wsum,
-                            (double *)x_inout, (double *)dual_inout, stats_out, S(stream));
+            op_grid<double>(c, p, (const double2 *)vis, (const double *)wgt, false, (double *)dirty_out, st);
         else
-            op_step<float>(c, p, *prm, (const float *)wgt, (const float *)dirty, (const float *)psf, wsum,
-                           (float *)x_inout, (float *)dual_inout, stats_out, S(stream));
-        if (n_hessian_out) *n_hessian_out = 1;   // known on the host: no synchronisation
+            op_grid<float>(c, p, (const float2 *)vis, (const float *)wgt, false, (float *)dirty_out, st);
+        // 3. outer steps until the relative update reaches tol
+        const bool exact = !(prm->flags & PFB_STEP_APPROX_GRADIENT);
+        int32_t k = 0;
+        int64_t nh = 1;   // I^d and I^psf: one half each
+        while (k < max_outer) {
+            double stats[3];
+            run_step(c, p, prec, *prm, wgt, dirty_out, psf_out, wsum_out, x_inout, dual_inout, stats, st);
+            if (history_out) std::copy(stats, stats + 3, history_out + 3 * (size_t)k);
+            ++k;
+            nh += exact ? 1 : 0;
+            if (tol > 0 && stats[1] <= tol) break;
+        }
+        *n_outer_out = k;
+        *n_hessian_out = nh;
     });
 }
 

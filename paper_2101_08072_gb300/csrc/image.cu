@@ -643,8 +643,15 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
     ctx.fft((int)NX, (int)NY, nb, RFft<T>::c2r);
     if (prm.basis_mask != 1u)
         for (const char *nm : {"st_wa", "st_wb", "st_psiv", "st_u"}) ctx.scratch(nm, img);
-    // 1. one exact Hessian application: H x_k = R^dagger W R x_k (Eq. 3)
-    {
+    // 1. one exact Hessian application: H x_k = R^dagger W R x_k (Eq. 3), or with
+    //    PFB_STEP_APPROX_GRADIENT its stand-in of Eq. 4, I^psf * x_k (plain, not symmetrised)
+    if (prm.flags & PFB_STEP_APPROX_GRADIENT) {
+        k_pad<T><<<(unsigned)((nbig + 255) / 256), 256, 0, st>>>(nx, ny, nb, x, (const T *)nullptr, padded);
+        check_launch("approx_pad");
+        conv_padded<T>(ctx, nx, ny, nb, padded, S, (T)(1.0 / (double)(NX * NY)), false, st);
+        k_crop<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nx, ny, nb, padded, hx);
+        check_launch("approx_crop");
+    } else {
         cx_t<T> *vis = (cx_t<T> *)ctx.scratch("st_vis", (size_t)p.nrow * p.nchan * sizeof(cx_t<T>));
         op_degrid<T>(ctx, p, x, vis, st);
         op_grid<T>(ctx, p, vis, wgt, false, hx, st);

@@ -288,6 +288,11 @@ static void exclusive_scan(Ctx &ctx, const In *in, int64_t n, int64_t *out, cuda
 // a shared-memory histogram and scan per bucket, a scatter into tmp and a copy back.
 constexpr int FINE_BINS = 4 * TILE * TILE;
 
+// bucket keys (band x tile x w bucket) a plan may use; beyond it w planes are grouped q to a bucket
+#ifndef PFB_KEY_CAP_LOG2
+#define PFB_KEY_CAP_LOG2 27
+#endif
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_fine_sort(CoordSrc src, const int64_t *__restrict__ off, int ntiles,
                                                    int nkq, const BandGeom *__restrict__ bgs, int nchan,
@@ -463,7 +468,7 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     p.ntu = p.Nu / TILE;
     p.ntv = p.Nv / TILE;
     const int64_t ntiles = (int64_t)p.ntu * p.ntv;
-    const int64_t key_cap = int64_t(1) << 27;   // 1 GiB of bucket offsets at most
+    const int64_t key_cap = int64_t(1) << PFB_KEY_CAP_LOG2;   // 1 GiB of bucket offsets at most
     p.q = 1;
     while ((int64_t)p.nband * ntiles * ((p.Pmax + p.q - 1) / p.q) > key_cap) ++p.q;
     p.nkq = (p.Pmax + p.q - 1) / p.q;

@@ -47,10 +47,12 @@ class StepParams:
     nlevel: int = 3
     basis_mask: int = 1
     unorm: float = 0.0
+    approx_gradient: bool = False   # Eq. 4 (I^psf * x) in place of the Hessian (PFB_STEP_APPROX_GRADIENT)
 
     def c(self) -> _lib.pfb_params:
         return _lib.pfb_params(self.gamma, self.sigma, self.lam, self.cg_tol, self.pd_tol, self.cg_iters,
-                               self.pd_iters, self.nlevel, self.basis_mask, self.unorm)
+                               self.pd_iters, self.nlevel, self.basis_mask, self.unorm,
+                               _lib.PFB_STEP_APPROX_GRADIENT if self.approx_gradient else 0)
 
 
 def _ptr(t):
@@ -241,6 +243,40 @@ class Context:
                                       _ptr(x), _ptr(dual), ctypes.byref(nh), st if stats else None,
                                       self._stream()))
         return int(nh.value), np.array(st[:]) if stats else None
+
+    def pfb_clean(self, geom: Geometry, params: StepParams, uvw, freq, band_of_chan, vis, wgt=None,
+                  max_outer: int = 20, tol: float = 0.0, x=None, dual=None):
+        """A whole solve: I^psf (2x field), I^d, then up to max_outer steps until the relative
+        update is <= tol.  x and dual (zeros if None) are updated in place.  Returns a dict with
+        x, dual, dirty, psf, wsum, n_outer, n_hessian and history ([n_outer][3] step stats)."""
+        nrow, nchan = self._data(uvw, freq, band_of_chan)
+        prec = _prec_cx(vis.dtype)
+        rdt = _RDT[prec]
+        self._t(vis, "vis", _CDT[prec], (nrow, nchan))
+        if wgt is not None:
+            self._t(wgt, "wgt", rdt, (nrow, nchan))
+        img = (geom.nband, geom.nx, geom.ny)
+        nb = bin(params.basis_mask).count("1")
+        if x is None:
+            x = torch.zeros(img, dtype=rdt, device=self.device)
+        if dual is None:
+            dual = torch.zeros((nb,) + img, dtype=rdt, device=self.device)
+        self._t(x, "x", rdt, img)
+        self._t(dual, "dual", rdt, (nb,) + img)
+        dirty = torch.empty(img, dtype=rdt, device=self.device)
+        psf = torch.empty((geom.nband, 2 * geom.nx, 2 * geom.ny), dtype=rdt, device=self.device)
+        ws = (ctypes.c_double * geom.nband)()
+        hist = (ctypes.c_double * (3 * max(max_outer, 1)))()
+        no, nh = ctypes.c_int32(0), ctypes.c_int64(0)
+        g, p = geom.c(), params.c()
+        self._check(self.lib.pfb_clean(self.h, ctypes.byref(g), prec, ctypes.byref(p), int(max_outer), float(tol),
+                                       nrow, nchan, _ptr(uvw), _ptr(freq), _ptr(band_of_chan), _ptr(vis),
+                                       _ptr(wgt), _ptr(dirty), _ptr(psf), ws, _ptr(x), _ptr(dual),
+                                       ctypes.byref(no), ctypes.byref(nh), hist, self._stream()))
+        k = int(no.value)
+        return {"x": x, "dual": dual, "dirty": dirty, "psf": psf, "wsum": np.array(ws[:], dtype=np.float64),
+                "n_outer": k, "n_hessian": int(nh.value),
+                "history": np.array(hist[:3 * k], dtype=np.float64).reshape(k, 3)}
 
     def pfb_plan_reset(self):
         """Drop cached plans (after changing uvw/freq/band_of_chan in place)."""

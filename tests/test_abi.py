@@ -46,10 +46,36 @@ def test_version_and_no_device(lib):
         assert lib.pfb_create(ctypes.byref(h), 0, 0) == -1   # no device: argument error, no crash
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """Sizes and field offsets of the ctypes structs against the C compiler's view of
+    include/pfb.h."""
+    import shutil
+    import subprocess
     from paper_2101_08072_gb300 import _lib
     assert ctypes.sizeof(_lib.pfb_geom) == 56
-    assert ctypes.sizeof(_lib.pfb_params) == 64
+    assert ctypes.sizeof(_lib.pfb_params) == 72
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pfb.h"', 'int main(void) {']
+    for st in (_lib.pfb_geom, _lib.pfb_params):
+        cname = st.__name__
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in st._fields_:
+            cf = "lambda" if f == "lambda_" else f
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {cf}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in (_lib.pfb_geom, _lib.pfb_params):
+        assert got[(st.__name__, "size")] == ctypes.sizeof(st)
+        for f, _ in st._fields_:
+            assert got[(st.__name__, f)] == getattr(st, f).offset, (st.__name__, f)
 
 
 def test_binding_fails_loudly_without_library(tmp_path):

@@ -445,3 +445,97 @@ def test_step_decreases_objective():
         objs.append(st[0])
     assert x.min() >= 0
     assert objs[-1] < objs[0]
+
+
+# ------------------------------------------------------------------ approximate gradient (Eq. 4)
+def test_approx_gradient_step_equals_exact_at_w0():
+    """For a coplanar array (w = 0) without the 1/n factor the Hessian is exactly the
+    PSF convolution, so the step with the approximate gradient of Eq. 4 must equal
+    the exact-gradient step: a wrong normalisation, sign or PSF orientation in the
+    Eq. 4 branch breaks this."""
+    obs = synth.tiny_observation(nx=16, ny=16)
+    uvw = obs.uvw.copy(); uvw[:, 2] = 0.0
+    rng = np.random.default_rng(41)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    a = (uvw, obs.freq, obs.band_of_chan)
+    f = oracle.NO_DIVIDE_BY_N
+    xt = synth.point_source_image(rng, 1, 16, 16, 4)
+    V = oracle.degrid(*a, xt, obs.dl, obs.dm, flags=f) + synth.complex_noise(rng, (obs.nrow, obs.nchan), 1e-3)
+    d, ws = oracle.dirty(*a, V, w, 16, 16, obs.dl, obs.dm, 1, flags=f)
+    p, _ = oracle.psf(*a, w, 16, 16, obs.dl, obs.dm, 1, flags=f)
+    x0 = 0.3 * xt
+    v0 = np.zeros((1, 1, 16, 16))
+    prm = oracle.Params(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=10, pd_iters=20)
+    xe, ve, se = oracle.step(*a, w, d, p, ws, x0, v0, obs.dl, obs.dm, prm, f)
+    prm.approx_gradient = True
+    xa, va, sa = oracle.step(*a, w, d, p, ws, x0, v0, obs.dl, obs.dm, prm, f)
+    assert np.abs(xa - xe).max() < 1e-10 * np.abs(xe).max()
+    assert np.abs(va - ve).max() < 1e-10 * max(np.abs(ve).max(), 1e-30) + 1e-15
+    assert sa[0] == pytest.approx(se[0], rel=1e-10)
+
+
+def test_approx_gradient_error_grows_with_field():
+    """The wide-field error of Eq. 4: ||H x - I^psf * x|| / ||H x|| vanishes (to
+    rounding) for a coplanar array without 1/n and grows with the field of view as
+    the w (n - 1) phase grows."""
+    obs = synth.tiny_observation(nx=16, ny=16)
+    rng = np.random.default_rng(42)
+    x = rng.uniform(0, 1, (1, 16, 16))
+    uvw = obs.uvw
+
+    def err(dl, flags=0, coplanar=False):
+        u = uvw.copy()
+        if coplanar:
+            u[:, 2] = 0.0
+        hx = oracle.hessian(u, obs.freq, obs.band_of_chan, None, x, dl, dl, flags=flags)
+        p, _ = oracle.psf(u, obs.freq, obs.band_of_chan, None, 16, 16, dl, dl, 1, flags=flags)
+        return np.linalg.norm(hx - oracle.psf_conv(p, x)) / np.linalg.norm(hx)
+
+    assert err(obs.dl * 8, oracle.NO_DIVIDE_BY_N, coplanar=True) < 1e-12
+    e = [err(obs.dl * s) for s in (1, 4, 16)]
+    assert e[0] < e[1] < e[2]
+    assert e[0] < 1e-3 and e[2] > 1e-2
+
+
+# ------------------------------------------------------------------ whole solve
+def _clean_case(seed, noise):
+    obs = synth.tiny_observation(nx=16, ny=16)
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    a = (obs.uvw, obs.freq, obs.band_of_chan)
+    xt = synth.sparse_random_image(rng, 1, 16, 16, 0.2)
+    V = oracle.degrid(*a, xt, obs.dl, obs.dm)
+    if noise:
+        V = V + synth.complex_noise(rng, (obs.nrow, obs.nchan), noise)
+    return obs, a, w, xt, V
+
+
+def test_clean_stops_at_truth():
+    """Started at the true image with noiseless data and lam = 0, the first step is a
+    fixed point (the exact residual of Eq. 3 vanishes), so the stopping rule ends the
+    solve after one step; the count is that step plus the dirty image and PSF."""
+    obs, a, w, xt, V = _clean_case(43, 0.0)
+    prm = oracle.Params(gamma=1.0, sigma=1e-2, lam=0.0, cg_iters=20, pd_iters=50)
+    r = oracle.clean(*a, V, w, 16, 16, obs.dl, obs.dm, 1, prm, max_outer=5, tol=1e-8, x0=xt)
+    assert r["n_outer"] == 1 and r["n_hessian"] == 2
+    assert np.abs(r["x"] - xt).max() < 1e-9
+    assert r["history"][0, 1] < 1e-9
+
+
+def test_clean_driver_counts_and_composition():
+    """tol <= 0 runs max_outer steps, each the step of Eqs. 6-7 applied to the
+    previous iterate; with the approximate gradient no step counts as a Hessian."""
+    obs, a, w, xt, V = _clean_case(44, 1e-3)
+    prm = oracle.Params(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=8, pd_iters=10)
+    r = oracle.clean(*a, V, w, 16, 16, obs.dl, obs.dm, 1, prm, max_outer=3, tol=0.0)
+    assert r["n_outer"] == 3 and r["n_hessian"] == 4
+    assert r["history"].shape == (3, 3)
+    x = np.zeros((1, 16, 16)); v = np.zeros((1, 1, 16, 16))
+    for k in range(3):
+        x, v, st = oracle.step(*a, w, r["dirty"], r["psf"], r["wsum"], x, v, obs.dl, obs.dm, prm)
+        assert np.array_equal(st, r["history"][k])
+    assert np.array_equal(x, r["x"])
+    assert r["history"][-1, 0] < r["history"][0, 0]
+    prm.approx_gradient = True
+    ra = oracle.clean(*a, V, w, 16, 16, obs.dl, obs.dm, 1, prm, max_outer=2, tol=0.0)
+    assert ra["n_outer"] == 2 and ra["n_hessian"] == 1

@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--clean-outer", type=int, default=20)
     ap.add_argument("--clean-pd", type=int, default=10, help="primal-dual iterations per step")
     ap.add_argument("--clean-cg", type=int, default=10, help="CG iterations per step")
+    ap.add_argument("--clean-gamma", type=float, default=1.0)
+    ap.add_argument("--clean-sigma", type=float, default=1e-3)
+    ap.add_argument("--clean-lambda", type=float, default=1e-4)
+    ap.add_argument("--clean-basis", type=int, default=0b1111111, help="basis mask (bit 0 Dirac, 1..6 db1..db6)")
     ap.add_argument("--fp64", action="store_true", help="also time the FP64 path (eps 1e-9) on the same workload")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-entry-point timings")
     return ap.parse_args()
@@ -600,8 +604,8 @@ def run_clean(args):
                          torch.randn(vis.shape, dtype=rdt, device=dev, generator=gen) * sd).to(cdt)
     del sd
     ctx.pfb_plan_reset()
-    prm = StepParams(gamma=1.0, sigma=1e-3, lam=1e-4, cg_iters=args.clean_cg, pd_iters=args.clean_pd, nlevel=3,
-                     basis_mask=0b1111111)
+    prm = StepParams(gamma=args.clean_gamma, sigma=args.clean_sigma, lam=args.clean_lambda, cg_iters=args.clean_cg,
+                     pd_iters=args.clean_pd, nlevel=3, basis_mask=args.clean_basis)
     torch.cuda.synchronize(dev)
     ctx.lib.pfb_timing(ctx.h, 1)
     t0 = time.perf_counter()
@@ -618,14 +622,16 @@ def run_clean(args):
             "mvis_per_s_hessian_equivalent": r["n_hessian"] * obs.nvis / wall / 1e6,
             "objective_first_last": [float(hist[0, 0]), float(hist[-1, 0])] if len(hist) else None,
             "rel_update_last": float(hist[-1, 1]) if len(hist) else None,
+            "history": [[float(v) for v in h] for h in hist],
             "rel_error_vs_true_sky": model_err,
             "kernels_ms": {k: round(v, 2) for k, v in sorted(kern.items(), key=lambda kv: -kv[1])[:16]},
             "dtype": args.prec, "data": "synthetic (seeded)", "n_gpus": 1,
             "config": {"workload": f"full pfb-clean: {obs.nx}^2 image at 1.5 arcsec (PSF {2 * obs.nx}^2), "
                                    f"{obs.nband} bands, {obs.nchan} channels over 0.856-1.712 GHz, {obs.nrow} rows, "
-                                   "5000 point + 20 Gaussian sources, Dirac + db1..db6, "
+                                   f"5000 point + 20 Gaussian sources, basis mask {args.clean_basis:#b}, "
                                    f"{args.clean_outer} outer steps ({args.clean_cg} CG, {args.clean_pd} "
-                                   "primal-dual iterations each)",
+                                   f"primal-dual iterations each), gamma {args.clean_gamma:g}, "
+                                   f"sigma {args.clean_sigma:g}, lambda {args.clean_lambda:g}",
                        "visibilities": obs.nvis, "epsilon": eps, "precision": args.prec}}
     ctx.close()
     print(json.dumps(line))

@@ -383,106 +383,216 @@ static WavFilt wav_filter(int N) {
     return f;
 }
 
-// One level of the periodised DWT of the [n x m] block at the top-left of each
-// band image (row stride ny) along axis 0 (rows, i) or 1 (columns, j):
-//   a[k] = sum_t h[t] x[(2k + t) mod n_ax],  d[k] = sum_t g[t] x[(2k + t) mod n_ax]
-// with a stored in [0, n_ax/2) and d in [n_ax/2, n_ax) of that axis.
-template <typename T>
-__global__ void k_dwt_level(int nx, int ny, int nband, int n, int m, int axis, WavTaps<T> f,
-                            const T *__restrict__ in, T *__restrict__ out) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t per = (int64_t)n * m;
-    if (e >= per * nband) return;
-    const int b = (int)(e / per);
-    const int r = (int)(e - (int64_t)b * per);
-    const int i = r / m, j = r - i * m;
-    const T *src = in + (int64_t)b * nx * ny;
-    const int N = axis == 0 ? n : m;
-    const int pos = axis == 0 ? i : j;
-    const int half = N / 2;
-    const bool hi = pos >= half;
-    const int k = hi ? pos - half : pos;
-    T acc = 0;
-    int q = 2 * k;
-    for (int t = 0; t < f.L; ++t, ++q) {
-        q -= q >= N ? N : 0;
-        const T xv = axis == 0 ? src[(int64_t)q * ny + j] : src[(int64_t)i * ny + q];
-        acc += (hi ? f.g[t] : f.h[t]) * xv;
+// ---- periodised 2-D DWT, one level per launch, both axes in shared memory
+// One level maps an [n x m] block x to its four half-size subbands (Mallat layout):
+//   along an axis of length N:  a[k] = sum_t h[t] x[(2k + t) mod N],  d[k] = sum_t g[t] x[(2k + t) mod N]
+// applied along axis 0 (rows, i) and axis 1 (columns, j): (a,a) is the coarse band LL at (k, q),
+// (a,d) sits at (k, q + m/2), (d,a) at (k + n/2, q) and (d,d) at (k + n/2, q + m/2).  Its transpose
+// (= inverse, the filters being orthonormal) is, along an axis,
+//   x[p] = sum_{t = p mod 2} h[t] a[((p - t) mod N) / 2] + g[t] d[((p - t) mod N) / 2].
+// A CTA owns a tile: the forward kernel a 32 x 32 tile of every subband, whose (2*32 + L - 2)^2 input
+// region (with the periodic halo) it stages once; the inverse kernel a 64 x 64 tile of x, staging the
+// (32 + L/2 - 1)^2 coefficients of each subband it needs.  The coarse band goes to / comes from its own
+// strided view, so a multi-level transform needs no copies (coarse bands ping-pong through scratch).
+template <typename T> struct View2 {
+    T *p;
+    int64_t bs;   // band stride (elements)
+    int rs;       // row stride (elements)
+};
+constexpr int DWT_TO = 32;   // forward: coefficients per tile edge, each subband
+constexpr int DWT_TX = 64;   // inverse: pixels per tile edge
+__host__ __device__ constexpr int dwt_edge(int L) { return 2 * DWT_TO + L - 2; }
+__host__ __device__ constexpr int idwt_edge(int L) { return DWT_TX / 2 + L / 2 - 1; }
+template <typename T> constexpr size_t dwt_smem(int L) {
+    return sizeof(T) * ((size_t)dwt_edge(L) * dwt_edge(L) + 2 * (size_t)DWT_TO * dwt_edge(L));
+}
+template <typename T> constexpr size_t idwt_smem(int L) {
+    return sizeof(T) * (4 * (size_t)idwt_edge(L) * idwt_edge(L) + 2 * (size_t)idwt_edge(L) * DWT_TX);
+}
+
+__device__ __forceinline__ int pmod(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(256) k_dwt2_tile(int n, int m, int tiles_q, View2<T> src, View2<T> ll,
+                                                   View2<T> det, WavTaps<T> f) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    constexpr int E = dwt_edge(L);
+    T *xs = reinterpret_cast<T *>(sm_raw);   // [E][E] input region
+    T *ts = xs + E * E;                      // [2 DWT_TO][E]: a and d along axis 0
+    const int b = blockIdx.y;
+    const int tk = blockIdx.x / tiles_q, tq = blockIdx.x - tk * tiles_q;
+    const int K0 = tk * DWT_TO, Q0 = tq * DWT_TO;
+    const int nh = n / 2, mh = m / 2;
+    const T *sp = src.p + b * src.bs;
+    for (int e = threadIdx.x; e < E * E; e += blockDim.x) {
+        const int r = e / E, c = e - r * E;
+        xs[e] = sp[(int64_t)pmod(2 * K0 + r, n) * src.rs + pmod(2 * Q0 + c, m)];
     }
-    out[(int64_t)b * nx * ny + (int64_t)i * ny + j] = acc;
-}
-
-// Transpose (= inverse) of k_dwt_level:
-//   x[p] = sum_{t = p mod 2} h[t] a[((p - t) mod N)/2] + g[t] d[((p - t) mod N)/2]
-template <typename T>
-__global__ void k_idwt_level(int nx, int ny, int nband, int n, int m, int axis, WavTaps<T> f,
-                             const T *__restrict__ in, T *__restrict__ out) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t per = (int64_t)n * m;
-    if (e >= per * nband) return;
-    const int b = (int)(e / per);
-    const int r = (int)(e - (int64_t)b * per);
-    const int i = r / m, j = r - i * m;
-    const T *src = in + (int64_t)b * nx * ny;
-    const int N = axis == 0 ? n : m;
-    const int pos = axis == 0 ? i : j;
-    const int half = N / 2;
-    T acc = 0;
-    for (int t = 0; t < f.L; ++t) {
-        int q = pos - t;
-        q %= N;
-        q += q < 0 ? N : 0;
-        if (q & 1) continue;
-        const int k = q >> 1;
-        const T av = axis == 0 ? src[(int64_t)k * ny + j] : src[(int64_t)i * ny + k];
-        const T dv = axis == 0 ? src[(int64_t)(k + half) * ny + j] : src[(int64_t)i * ny + k + half];
-        acc += f.h[t] * av + f.g[t] * dv;
+    __syncthreads();
+    for (int e = threadIdx.x; e < DWT_TO * E; e += blockDim.x) {
+        const int kk = e / E, c = e - kk * E;
+        const T *col = xs + 2 * kk * E + c;
+        T lo = 0, hi = 0;
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+            const T v = col[t * E];
+            lo += f.h[t] * v;
+            hi += f.g[t] * v;
+        }
+        ts[kk * E + c] = lo;
+        ts[(DWT_TO + kk) * E + c] = hi;
     }
-    out[(int64_t)b * nx * ny + (int64_t)i * ny + j] = acc;
+    __syncthreads();
+    T *lp = ll.p + b * ll.bs;
+    T *dp = det.p + b * det.bs;
+    for (int e = threadIdx.x; e < DWT_TO * DWT_TO; e += blockDim.x) {
+        const int kk = e / DWT_TO, qq = e - kk * DWT_TO;
+        const int k = K0 + kk, q = Q0 + qq;
+        if (k >= nh || q >= mh) continue;
+        const T *lo = ts + kk * E + 2 * qq, *hi = ts + (DWT_TO + kk) * E + 2 * qq;
+        T aa = 0, ad = 0, da = 0, dd = 0;
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+            aa += f.h[t] * lo[t];
+            ad += f.g[t] * lo[t];
+            da += f.h[t] * hi[t];
+            dd += f.g[t] * hi[t];
+        }
+        lp[(int64_t)k * ll.rs + q] = aa;
+        dp[(int64_t)k * det.rs + q + mh] = ad;
+        dp[(int64_t)(k + nh) * det.rs + q] = da;
+        dp[(int64_t)(k + nh) * det.rs + q + mh] = dd;
+    }
 }
 
-// copy the [n x m] top-left block of each band image
-template <typename T>
-__global__ void k_copy_block(int nx, int ny, int nband, int n, int m, const T *__restrict__ in, T *__restrict__ out) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t per = (int64_t)n * m;
-    if (e >= per * nband) return;
-    const int b = (int)(e / per);
-    const int r = (int)(e - (int64_t)b * per);
-    const int i = r / m, j = r - i * m;
-    const int64_t o = (int64_t)b * nx * ny + (int64_t)i * ny + j;
-    out[o] = in[o];
+template <typename T, int L>
+__global__ void __launch_bounds__(256) k_idwt2_tile(int n, int m, int tiles_s, View2<T> ll, View2<T> det,
+                                                    View2<T> dst, WavTaps<T> f) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    constexpr int C = idwt_edge(L);
+    constexpr int H = L / 2 - 1;   // offset of coefficient k = p/2 in the staged region
+    T *cs = reinterpret_cast<T *>(sm_raw);   // [4][C][C]: (a,a) (a,d) (d,a) (d,d)
+    T *us = cs + 4 * C * C;                  // [2][C][DWT_TX]: axis-1 inverse of the a and d rows
+    const int b = blockIdx.y;
+    const int tp = blockIdx.x / tiles_s, tsi = blockIdx.x - tp * tiles_s;
+    const int P0 = tp * DWT_TX, S0 = tsi * DWT_TX;
+    const int nh = n / 2, mh = m / 2;
+    const int kb0 = P0 / 2 - H, kb1 = S0 / 2 - H;
+    const T *lp = ll.p + b * ll.bs;
+    const T *dp = det.p + b * det.bs;
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+        const int r = e / C, c = e - r * C;
+        const int k = pmod(kb0 + r, nh), q = pmod(kb1 + c, mh);
+        cs[e] = lp[(int64_t)k * ll.rs + q];
+        cs[C * C + e] = dp[(int64_t)k * det.rs + q + mh];
+        cs[2 * C * C + e] = dp[(int64_t)(k + nh) * det.rs + q];
+        cs[3 * C * C + e] = dp[(int64_t)(k + nh) * det.rs + q + mh];
+    }
+    __syncthreads();
+    // axis 1: rows r of the a (resp. d) half of axis 0
+    for (int e = threadIdx.x; e < 2 * C * DWT_TX; e += blockDim.x) {
+        const int half = e / (C * DWT_TX), rem = e - half * C * DWT_TX;
+        const int r = rem / DWT_TX, ss = rem - r * DWT_TX;
+        const T *ra = cs + (2 * half) * C * C + r * C;   // a along axis 1
+        const T *rd = ra + C * C;                         // d along axis 1
+        const bool odd = ss & 1;
+        const int base = (ss >> 1) + H;
+        T acc = 0;
+#pragma unroll
+        for (int u = 0; u < L / 2; ++u) {   // taps t = 2u + (ss mod 2)
+            const T hv = odd ? f.h[2 * u + 1] : f.h[2 * u], gv = odd ? f.g[2 * u + 1] : f.g[2 * u];
+            acc += hv * ra[base - u] + gv * rd[base - u];
+        }
+        us[e] = acc;
+    }
+    __syncthreads();
+    T *op = dst.p + b * dst.bs;
+    for (int e = threadIdx.x; e < DWT_TX * DWT_TX; e += blockDim.x) {
+        const int pp = e / DWT_TX, ss = e - pp * DWT_TX;
+        const int p = P0 + pp, s2 = S0 + ss;
+        if (p >= n || s2 >= m) continue;
+        const bool odd = pp & 1;
+        const int base = (pp >> 1) + H;
+        T acc = 0;
+#pragma unroll
+        for (int u = 0; u < L / 2; ++u) {   // taps t = 2u + (pp mod 2)
+            const T hv = odd ? f.h[2 * u + 1] : f.h[2 * u], gv = odd ? f.g[2 * u + 1] : f.g[2 * u];
+            acc += hv * us[(base - u) * DWT_TX + ss] + gv * us[(C + base - u) * DWT_TX + ss];
+        }
+        op[(int64_t)p * dst.rs + s2] = acc;
+    }
 }
 
-// coef = multi-level 2-D DWT of img (Mallat layout); tmp is scratch of the same size
+template <typename T, int L>
+static void dwt_level_launch(int nband, int n, int m, View2<T> src, View2<T> ll, View2<T> det, const WavFilt &f,
+                             cudaStream_t st) {
+    const int tk = (n / 2 + DWT_TO - 1) / DWT_TO, tq = (m / 2 + DWT_TO - 1) / DWT_TO;
+    const size_t sm = dwt_smem<T>(L);
+    PFB_CUDA(cudaFuncSetAttribute(k_dwt2_tile<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_dwt2_tile<T, L><<<dim3((unsigned)(tk * tq), (unsigned)nband), 256, sm, st>>>(n, m, tq, src, ll, det,
+                                                                                  WavTaps<T>(f));
+    check_launch("dwt");
+}
+
+template <typename T, int L>
+static void idwt_level_launch(int nband, int n, int m, View2<T> ll, View2<T> det, View2<T> dst, const WavFilt &f,
+                              cudaStream_t st) {
+    const int tp = (n + DWT_TX - 1) / DWT_TX, ts = (m + DWT_TX - 1) / DWT_TX;
+    const size_t sm = idwt_smem<T>(L);
+    PFB_CUDA(cudaFuncSetAttribute(k_idwt2_tile<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_idwt2_tile<T, L><<<dim3((unsigned)(tp * ts), (unsigned)nband), 256, sm, st>>>(n, m, ts, ll, det, dst,
+                                                                                   WavTaps<T>(f));
+    check_launch("idwt");
+}
+
+#define PFB_TAPS_SWITCH(LV, CALL)                                          \
+    switch (LV) {                                                          \
+        case 2: CALL(2); break;                                            \
+        case 4: CALL(4); break;                                            \
+        case 6: CALL(6); break;                                            \
+        case 8: CALL(8); break;                                            \
+        case 10: CALL(10); break;                                          \
+        case 12: CALL(12); break;                                          \
+        default: throw Error(PFB_ERR_ARG, "unsupported wavelet filter length"); \
+    }
+
+// coef = multi-level 2-D DWT of img (Mallat layout, [nband][nx][ny]).  tmp (>= nband nx ny / 2
+// elements) holds the coarse bands between levels.
 template <typename T>
 static void dwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, const T *img, T *coef, T *tmp,
                  cudaStream_t st) {
-    PFB_CUDA(cudaMemcpyAsync(coef, img, (size_t)nband * nx * ny * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    int n = nx, m = ny;
+    const int64_t full = (int64_t)nx * ny, quarter = (int64_t)(nx / 2) * (ny / 2);
+    View2<T> src{const_cast<T *>(img), full, ny};
+    const View2<T> det{coef, full, ny};
     for (int lv = 0; lv < nlevel; ++lv) {
-        const int64_t cnt = (int64_t)n * m * nband;
-        const unsigned gb = (unsigned)((cnt + 255) / 256);
-        k_dwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 0, WavTaps<T>(f), coef, tmp);
-        k_dwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 1, WavTaps<T>(f), tmp, coef);
-        check_launch("dwt");
-        n /= 2;
-        m /= 2;
+        const int n = nx >> lv, m = ny >> lv;
+        const View2<T> ll = lv == nlevel - 1 ? det : View2<T>{tmp + (lv & 1) * nband * quarter, quarter, m / 2};
+#define PFB_DWT_CALL(LV) dwt_level_launch<T, LV>(nband, n, m, src, ll, det, f, st)
+        PFB_TAPS_SWITCH(f.L, PFB_DWT_CALL)
+#undef PFB_DWT_CALL
+        src = ll;
+        if (lv < nlevel - 1) src.bs = (int64_t)(n / 2) * (m / 2);
     }
 }
 
-// img = inverse of dwt2 (coef is overwritten)
+// out = inverse multi-level DWT of coef (Mallat layout); tmp as for dwt2.
 template <typename T>
-static void idwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, T *coef, T *tmp, cudaStream_t st) {
-    int n = nx >> (nlevel - 1), m = ny >> (nlevel - 1);
-    for (int lv = 0; lv < nlevel; ++lv) {
-        const int64_t cnt = (int64_t)n * m * nband;
-        const unsigned gb = (unsigned)((cnt + 255) / 256);
-        k_idwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 1, WavTaps<T>(f), coef, tmp);
-        k_idwt_level<T><<<gb, 256, 0, st>>>(nx, ny, nband, n, m, 0, WavTaps<T>(f), tmp, coef);
-        check_launch("idwt");
-        n *= 2;
-        m *= 2;
+static void idwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, const T *coef, T *out, T *tmp,
+                  cudaStream_t st) {
+    const int64_t full = (int64_t)nx * ny, quarter = (int64_t)(nx / 2) * (ny / 2);
+    const View2<T> det{const_cast<T *>(coef), full, ny};
+    View2<T> ll = det;
+    for (int lv = nlevel - 1; lv >= 0; --lv) {
+        const int n = nx >> lv, m = ny >> lv;
+        const View2<T> dst = lv == 0 ? View2<T>{out, full, ny}
+                                     : View2<T>{tmp + (lv & 1) * nband * quarter, (int64_t)n * m, m};
+#define PFB_IDWT_CALL(LV) idwt_level_launch<T, LV>(nband, n, m, ll, det, dst, f, st)
+        PFB_TAPS_SWITCH(f.L, PFB_IDWT_CALL)
+#undef PFB_IDWT_CALL
+        ll = dst;
     }
 }
 
@@ -579,6 +689,9 @@ static void conv_padded(Ctx &ctx, int nx, int ny, int nband, T *padded, const cx
                         cudaStream_t st) {
     const int64_t NX = 2 * nx, NY = 2 * ny, NH = NY / 2 + 1;
     cx_t<T> *X = (cx_t<T> *)ctx.scratch("img_spec", (size_t)nband * NX * NH * sizeof(cx_t<T>));
+    // algorithmic bytes: the padded image in and out, the half spectrum written, read twice and the cached
+    // PSF spectrum read
+    KTimer tm(ctx, "img_conv", st, (double)nband * NX * (2.0 * NY * sizeof(T) + 4.0 * NH * sizeof(cx_t<T>)), 1);
     cufftHandle hf = ctx.fft((int)NX, (int)NY, nband, RFft<T>::r2c);
     PFB_CUFFT(cufftSetStream(hf, st));
     PFB_CUFFT(RFft<T>::fwd(hf, padded, X));
@@ -668,6 +781,10 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
         if (prm.basis_mask >> k & 1u) bases.push_back(k);
     const int K = (int)bases.size();
     const double inv_sqrt_k = 1.0 / std::sqrt((double)K);
+    // algorithmic bytes of one multi-level transform: every level reads its input band and writes it back
+    double dwt_bytes = 0;
+    for (int lv = 0; lv < std::max(0, prm.nlevel); ++lv)
+        dwt_bytes += 2.0 * (double)(nx >> lv) * (double)(ny >> lv) * nb * sizeof(T);
     T *wa = nullptr, *wb = nullptr;
     if (prm.basis_mask != 1u) {
         wa = (T *)ctx.scratch("st_wa", img);
@@ -676,6 +793,7 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
     for (int k : bases) {
         const T *coef = x;
         if (k > 0) {
+            KTimer tm(ctx, "dwt", st, dwt_bytes, prm.nlevel);
             dwt2<T>(nx, ny, nb, prm.nlevel, wav_filter(k), x, wa, wb, st);
             coef = wa;
         }
@@ -735,8 +853,10 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
             if (bases[t] == 0) {
                 k_axpy<T><<<gn, 256, 0, st>>>(n, (T)inv_sqrt_k, vk, psiv);
             } else {
-                PFB_CUDA(cudaMemcpyAsync(wa, vk, img, cudaMemcpyDeviceToDevice, st));
-                idwt2<T>(nx, ny, nb, prm.nlevel, wav_filter(bases[t]), wa, wb, st);
+                {
+                    KTimer tm(ctx, "idwt", st, dwt_bytes, prm.nlevel);
+                    idwt2<T>(nx, ny, nb, prm.nlevel, wav_filter(bases[t]), vk, wa, wb, st);
+                }
                 k_axpy<T><<<gn, 256, 0, st>>>(n, (T)inv_sqrt_k, wa, psiv);
             }
             check_launch("psi");
@@ -748,6 +868,7 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
         for (int t = 0; t < K; ++t) {
             const T *c = ubuf;
             if (bases[t] != 0) {
+                KTimer tm(ctx, "dwt", st, dwt_bytes, prm.nlevel);
                 dwt2<T>(nx, ny, nb, prm.nlevel, wav_filter(bases[t]), ubuf, wa, wb, st);
                 c = wa;
             }

@@ -312,7 +312,7 @@ __host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
         L.rv[s] = o; o += ch * W * (int)sizeof(float2);
         L.wy[s] = o; o += ch * res_ws(Ww) * (int)sizeof(float2);
     }
-    L.meta = o; o += 2 * (int)sizeof(int4);
+    L.meta = o; o += 4 * (int)sizeof(int4);
     L.total = o;
     return L;
 }
@@ -388,6 +388,9 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     constexpr int SLOT = TILE * RSTRIDE;
     constexpr int WS = res_ws(Ww);
     constexpr int CH = res_ch(W);
+    constexpr int G = W * W;         // consumer threads of a group (one per residue class)
+    constexpr int NG = GRID_NC / G;  // consumer groups
+    constexpr int RPG = CH / NG;     // records of one group in a chunk
     const ResSmem L = res_layout(R, W, Ww);
     float2 *ring = reinterpret_cast<float2 *>(smem_raw);
     int4 *meta = reinterpret_cast<int4 *>(smem_raw + L.meta);
@@ -446,11 +449,39 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             }
             return lo;
         };
-        // chunk after [c0, c1) starting in bucket kq: at most CH items of one bucket
-        auto next_chunk = [&](int64_t c0, int &kq, int64_t &c1) {
-            if (c0 >= wi.end) { c1 = c0; return; }
-            if (c0 >= off[kbase + kq + 1]) kq = bucket_of(c0);
-            c1 = min(min((int64_t)wi.end, off[kbase + kq + 1]), c0 + CH);
+        // A bucket's items (its part of this work item) are split into NG contiguous parts, one per
+        // consumer group; chunk c of the bucket holds records [c RPG, c RPG + RPG) of every part, so
+        // a group walks its part in order and its register runs break only where the cell changes.
+        struct CPos {
+            int kq, P, c, nch;   // bucket, part length, chunk within the bucket, chunks of the bucket
+            int64_t s, e;        // the bucket's item range within this work item
+            bool end;
+        };
+        auto init_bucket = [&](CPos &q) {
+            q.s = max(off[kbase + q.kq], (int64_t)wi.begin);
+            q.e = min(off[kbase + q.kq + 1], (int64_t)wi.end);
+            q.P = (int)((q.e - q.s + NG - 1) / NG);
+            q.nch = (q.P + RPG - 1) / RPG;
+            q.c = 0;
+        };
+        auto advance = [&](CPos &q) {
+            if (q.end) return;
+            if (++q.c < q.nch) return;
+            do {
+                ++q.kq;
+                if (q.kq >= g.nkq || off[kbase + q.kq] >= wi.end) {
+                    q.end = true;
+                    return;
+                }
+                init_bucket(q);
+            } while (q.e <= q.s);
+        };
+        // this producer thread's item in chunk q (record slot pt), or -1
+        auto item_of = [&](const CPos &q) -> int64_t {
+            if (q.end || pt >= NG * RPG) return -1;
+            const int gq = pt / RPG, j = pt - gq * RPG;
+            const int64_t idx = q.s + (int64_t)gq * q.P + (int64_t)q.c * RPG + j;
+            return idx < min(q.s + (int64_t)(gq + 1) * q.P, q.e) ? idx : -1;
         };
         auto load_raw = [&](RawRec &q, int64_t idx) {
             const uint32_t v = q.code & VIS_MASK;
@@ -551,35 +582,42 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             }
         };
 
-        // chunk i = [c0, c1) in bucket kq; chunk i+1 = [n0, n1) in kq_n; chunk i+2 starts at n1
-        int kq = bucket_of(wi.begin);
-        int64_t c0 = wi.begin, c1;
-        next_chunk(c0, kq, c1);
+        // chunk i at cp, i+1 at np_, i+2 at mp: raw inputs of i+1 and item codes of i+2 are in flight
+        // while chunk i is staged
+        CPos cp;
+        cp.kq = bucket_of(wi.begin);
+        cp.end = false;
+        init_bucket(cp);
         RawRec raw;
-        raw.code = pt < c1 - c0 ? items[c0 + pt] : 0u;
-        if (pt < c1 - c0) load_raw(raw, c0 + pt);
-        int kq_n = kq;
-        int64_t n0 = c1, n1;
-        next_chunk(n0, kq_n, n1);
+        int64_t ic = item_of(cp);
+        raw.code = ic >= 0 ? items[ic] : 0u;
+        if (ic >= 0) load_raw(raw, ic);
+        CPos np_ = cp;
+        advance(np_);
+        int64_t in_ = item_of(np_);
         RawRec nxt;
-        nxt.code = pt < n1 - n0 ? items[n0 + pt] : 0u;
+        nxt.code = in_ >= 0 ? items[in_] : 0u;
         int i = 0;
-        while (c0 < wi.end) {
+        while (!cp.end) {
             const int sb = i & 1;
-            // raw inputs of chunk i+1 and item codes of chunk i+2: in flight during this stage
-            if (pt < n1 - n0) load_raw(nxt, n0 + pt);
-            int kq_m = kq_n;
-            int64_t m0 = n1, m1;
-            next_chunk(m0, kq_m, m1);
-            const uint32_t code2 = pt < m1 - m0 ? items[m0 + pt] : 0u;
+            if (in_ >= 0) load_raw(nxt, in_);
+            CPos mp = np_;
+            advance(mp);
+            const int64_t im = item_of(mp);
+            const uint32_t code2 = im >= 0 ? items[im] : 0u;
             if (i >= 2) pair_sync<BAR_EMPTY>(sb);   // buffer sb released (chunk i-2)
-            if (pt < c1 - c0) stage(raw, pt, sb);
-            if (pt == 0) meta[sb] = make_int4((int)(c1 - c0), kq, n0 >= wi.end ? 1 : 0, kq_n);
+            if (ic >= 0) stage(raw, pt, sb);
+            if (pt == 0) {
+                meta[2 * sb] = make_int4(cp.kq, np_.end ? 1 : 0, np_.end ? -1 : np_.kq, 0);
+                meta[2 * sb + 1] = make_int4(cp.P, (int)(cp.e - cp.s), cp.c, 0);
+            }
             __threadfence_block();
             pair_arrive<BAR_FULL>(sb);
             raw = nxt;
-            c0 = n0; c1 = n1; kq = kq_n;
-            n0 = m0; n1 = m1; kq_n = kq_m;
+            ic = in_;
+            cp = np_;
+            np_ = mp;
+            in_ = im;
             nxt.code = code2;
             ++i;
         }
@@ -588,8 +626,6 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     } else {
         // ================================================================ consumers
         const int ct = threadIdx.x - GRID_NP;
-        constexpr int G = W * W;
-        constexpr int NG = GRID_NC / G;
         const int grp = ct / G, lid = ct - grp * G;
         const int ta = lid / W, tb = lid - ta * W;
         const bool in_group = grp < NG;
@@ -620,22 +656,24 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         for (int i = 0;; ++i) {
             const int sb = i & 1;
             pair_sync<BAR_FULL>(sb);
-            const int4 m = meta[sb];   // records, bucket, last chunk, bucket of the next chunk
-            if (m.y != prev_kq) {
+            const int4 m = meta[2 * sb];        // bucket, last chunk, bucket of the next chunk
+            const int4 mc = meta[2 * sb + 1];   // part length, items of the bucket, chunk in the bucket
+            if (m.x != prev_kq) {
                 // planes below this bucket's first plane are complete (the sums of the previous
                 // bucket were added to the ring at the end of its last chunk)
                 named_sync<BAR_CONS, GRID_NC>();
-                flush_planes(max(m.y * g.q, k_lo), ct, GRID_NC);
+                flush_planes(max(m.x * g.q, k_lo), ct, GRID_NC);
                 named_sync<BAR_CONS, GRID_NC>();
-                prev_kq = m.y;
+                prev_kq = m.x;
             }
             if (in_group) {
                 const float2 *ru = reinterpret_cast<const float2 *>(smem_raw + L.ru[sb]);
                 const float2 *rv = reinterpret_cast<const float2 *>(smem_raw + L.rv[sb]);
                 const float2 *rwy = reinterpret_cast<const float2 *>(smem_raw + L.wy[sb]);
-                const int cnt = m.x;
-                const int per = (cnt + NG - 1) / NG;
-                const int r0 = grp * per, r1 = min(cnt, r0 + per);
+                // this group's records of the chunk: the next ones of its contiguous part
+                const int part = min(mc.x, max(0, mc.y - grp * mc.x));
+                const int cnt = min(RPG, max(0, part - mc.z * RPG));
+                const int r0 = grp * RPG, r1 = r0 + cnt;
                 const float2 *pu = ru + ta, *pv = rv + tb;
                 for (int r = r0; r < r1; ++r) {
                     const float2 a = pu[r * W], b = pv[r * W];
@@ -664,11 +702,11 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                     }
                 }
                 // the sums stay in registers while the next chunk continues this bucket
-                if (m.z || m.w != m.y) flush_acc();
+                if (m.y || m.z != m.x) flush_acc();
             }
             __threadfence_block();
             pair_arrive<BAR_EMPTY>(sb);
-            if (m.z) break;
+            if (m.y) break;
         }
         // remaining planes: all of the block for an owned tile, the touched ones for a chunk
         named_sync<BAR_CONS, GRID_NC>();

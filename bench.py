@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--clean-outer", type=int, default=20)
     ap.add_argument("--clean-pd", type=int, default=10, help="primal-dual iterations per step")
     ap.add_argument("--clean-cg", type=int, default=10, help="CG iterations per step")
-    ap.add_argument("--clean-gamma", type=float, default=1.0)
+    ap.add_argument("--clean-gamma", type=float, default=0.5,
+                    help="step size; at the 8192^2 field gamma = 1 diverges slowly (see DESIGN.md)")
     ap.add_argument("--clean-sigma", type=float, default=1e-3)
     ap.add_argument("--clean-lambda", type=float, default=1e-4)
     ap.add_argument("--clean-basis", type=int, default=0b1111111, help="basis mask (bit 0 Dirac, 1..6 db1..db6)")

@@ -570,16 +570,25 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
             }
         }
         p.work_heavy_end[b] = (int64_t)work.size();
+        // owned tiles with items, largest first (no long tile starts at the end of the launch); tiles
+        // without items join the heavy ones in the list whose planes are zeroed by a plain kernel
+        const size_t l0 = work.size();
         for (int64_t t = 0; t < ntiles; ++t) {
             const int64_t s = tb[b * ntiles + t], e = tb[b * ntiles + t + 1];
-            if (e - s <= chunk) work.push_back({(int)t, 0, s, e});
+            if (e == s) heavy.push_back((int)t);
+            else if (e - s <= chunk) work.push_back({(int)t, 0, s, e});
         }
+        std::stable_sort(work.begin() + l0, work.end(), [](const WorkItem &x, const WorkItem &y) {
+            return x.end - x.begin > y.end - y.begin;
+        });
     }
     p.work_begin[p.nband] = (int64_t)work.size();
     p.heavy_begin[p.nband] = (int64_t)heavy.size();
-    p.d_work = (WorkItem *)ctx.dalloc(work.size() * sizeof(WorkItem));
+    p.d_work = (WorkItem *)ctx.dalloc(std::max<size_t>(work.size(), 1) * sizeof(WorkItem));
     p.bytes += work.size() * sizeof(WorkItem);
-    PFB_CUDA(cudaMemcpyAsync(p.d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
+    if (!work.empty())
+        PFB_CUDA(cudaMemcpyAsync(p.d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                                 st));
     if (!heavy.empty()) {
         p.d_heavy = (int *)ctx.dalloc(heavy.size() * sizeof(int));
         p.bytes += heavy.size() * sizeof(int);

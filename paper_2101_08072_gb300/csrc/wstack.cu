@@ -1176,7 +1176,7 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                         PFB_W_SWITCH(p.W, p.wstack, PFB_GRID_CALL)
 #undef PFB_GRID_CALL
                     }
-                } else {
+                } else if (w1 > w0) {
                     k_grid_tiles<T><<<(unsigned)(w1 - w0), 256, smem, st>>>(p.d_work + w0, p.d_items, p.d_off,
                                                                              p.coords(), vis, wgt,
                                                                              unit_vis ? 1 : 0, g, k_lo, k_hi, planes);

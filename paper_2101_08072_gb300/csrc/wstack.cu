@@ -638,11 +638,13 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             const int ck = (int)(ckey & ((1u << KEY_PLANE_BITS) - 1u));
             if ((unsigned)cu < (unsigned)TILE && (unsigned)cv < (unsigned)TILE) {
                 float2 *cell = ring + cu * RSTRIDE + cv;
+                const int s0 = ck % R;
 #pragma unroll
                 for (int c = 0; c < Ww; ++c) {
                     const int k = ck + c;
                     if (k >= k_lo && k < k_hi) {
-                        float2 *dst = cell + (k % R) * SLOT;
+                        const int sl = s0 + c - (s0 + c >= R ? R : 0);
+                        float2 *dst = cell + sl * SLOT;
                         atomicAdd(&dst->x, acc[c].x);
                         atomicAdd(&dst->y, acc[c].y);
                     }
@@ -673,33 +675,58 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                 // this group's records of the chunk: the next ones of its contiguous part
                 const int part = min(mc.x, max(0, mc.y - grp * mc.x));
                 const int cnt = min(RPG, max(0, part - mc.z * RPG));
-                const int r0 = grp * RPG, r1 = r0 + cnt;
-                const float2 *pu = ru + ta, *pv = rv + tb;
-                for (int r = r0; r < r1; ++r) {
-                    const float2 a = pu[r * W], b = pv[r * W];
-                    float4 q[Ww / 2 > 0 ? Ww / 2 : 1];
-                    float2 qo;
-                    const float4 *wy4 = reinterpret_cast<const float4 *>(rwy + r * WS);
+                constexpr int NQ = WS / 2;   // float4 per w-tap row (odd W_w: the last half is padding)
+                const float2 *pa = ru + grp * RPG * W + ta, *pb = rv + grp * RPG * W + tb;
+                const float4 *pw = reinterpret_cast<const float4 *>(rwy + grp * RPG * WS);
+                auto add = [&](float wuv, const float4 *q) {
 #pragma unroll
-                    for (int c2 = 0; c2 < Ww / 2; ++c2) q[c2] = wy4[c2];
-                    if (Ww & 1) qo = rwy[r * WS + Ww - 1];
-                    const uint32_t key = __float_as_uint(a.y) | __float_as_uint(b.y);
-                    if (key != ckey) {
+                    for (int c = 0; c < Ww; ++c) {
+                        const float4 v = q[c >> 1];
+                        acc[c].x = fmaf(wuv, (c & 1) ? v.z : v.x, acc[c].x);
+                        acc[c].y = fmaf(wuv, (c & 1) ? v.w : v.y, acc[c].y);
+                    }
+                };
+                // two records per step (W_w <= 6: both w-tap rows fit in registers); one test covers
+                // both run breaks, which are rare in dense tiles
+                int n = cnt;
+                constexpr int PAIR = Ww <= 6 ? 2 : 1 << 30;
+                for (; n >= PAIR; n -= 2, pa += 2 * W, pb += 2 * W, pw += 2 * NQ) {
+                    const float2 a0 = pa[0], b0 = pb[0], a1 = pa[W], b1 = pb[W];
+                    float4 q0[NQ], q1[NQ];
+#pragma unroll
+                    for (int c2 = 0; c2 < NQ; ++c2) {
+                        q0[c2] = pw[c2];
+                        q1[c2] = pw[NQ + c2];
+                    }
+                    const uint32_t k0 = __float_as_uint(a0.y) | __float_as_uint(b0.y);
+                    const uint32_t k1 = __float_as_uint(a1.y) | __float_as_uint(b1.y);
+                    if (((k0 ^ ckey) | (k1 ^ ckey)) != 0u) {
+                        if (k0 != ckey) {
+                            flush_acc();
+                            ckey = k0;
+                        }
+                        add(a0.x * b0.x, q0);
+                        if (k1 != ckey) {
+                            flush_acc();
+                            ckey = k1;
+                        }
+                        add(a1.x * b1.x, q1);
+                    } else {
+                        add(a0.x * b0.x, q0);
+                        add(a1.x * b1.x, q1);
+                    }
+                }
+                for (; n > 0; --n, pa += W, pb += W, pw += NQ) {
+                    const float2 a0 = pa[0], b0 = pb[0];
+                    float4 q0[NQ];
+#pragma unroll
+                    for (int c2 = 0; c2 < NQ; ++c2) q0[c2] = pw[c2];
+                    const uint32_t k0 = __float_as_uint(a0.y) | __float_as_uint(b0.y);
+                    if (k0 != ckey) {
                         flush_acc();
-                        ckey = key;
+                        ckey = k0;
                     }
-                    const float wuv = a.x * b.x;
-#pragma unroll
-                    for (int c2 = 0; c2 < Ww / 2; ++c2) {
-                        acc[2 * c2].x = fmaf(wuv, q[c2].x, acc[2 * c2].x);
-                        acc[2 * c2].y = fmaf(wuv, q[c2].y, acc[2 * c2].y);
-                        acc[2 * c2 + 1].x = fmaf(wuv, q[c2].z, acc[2 * c2 + 1].x);
-                        acc[2 * c2 + 1].y = fmaf(wuv, q[c2].w, acc[2 * c2 + 1].y);
-                    }
-                    if (Ww & 1) {
-                        acc[Ww - 1].x = fmaf(wuv, qo.x, acc[Ww - 1].x);
-                        acc[Ww - 1].y = fmaf(wuv, qo.y, acc[Ww - 1].y);
-                    }
+                    add(a0.x * b0.x, q0);
                 }
                 // the sums stay in registers while the next chunk continues this bucket
                 if (m.y || m.z != m.x) flush_acc();

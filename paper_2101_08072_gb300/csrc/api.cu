@@ -48,6 +48,7 @@ void Ctx::dfree(void *p, size_t bytes) {
 void *Ctx::scratch(const std::string &name, size_t bytes) {
     DevBuf &b = bufs[name];
     if (b.bytes >= bytes && b.ptr) return b.ptr;
+    zero_tag.erase(name);
     if (b.ptr) {
         dfree(b.ptr, b.bytes);
         b.ptr = nullptr;
@@ -59,6 +60,7 @@ void *Ctx::scratch(const std::string &name, size_t bytes) {
 }
 
 void Ctx::release(const std::string &name) {
+    zero_tag.erase(name);
     auto it = bufs.find(name);
     if (it == bufs.end()) return;
     dfree(it->second.ptr, it->second.bytes);
@@ -102,6 +104,7 @@ void Ctx::reset() {
     for (auto &b : bufs)
         if (b.second.ptr) dfree(b.second.ptr, b.second.bytes);
     bufs.clear();
+    zero_tag.clear();
 }
 
 cufftHandle Ctx::fft(int n0, int n1, int batch, cufftType type) {

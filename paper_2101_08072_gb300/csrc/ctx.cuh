@@ -25,6 +25,7 @@ struct Plan {
     int nchan = 0;
     const void *uvw = nullptr, *freq = nullptr, *band = nullptr;
     uint64_t last_use = 0;
+    uint64_t id = 0;   // unique per context: tags buffers whose zero pattern belongs to this plan
 
     // ---- geometry
     int Nu = 0, Nv = 0, Ww = 1, ntu = 0, ntv = 0, q = 1, nkq = 1, Pmax = 1;
@@ -38,6 +39,7 @@ struct Plan {
     std::vector<int64_t> work_begin; // per band offset into d_work (size nband + 1)
     std::vector<int64_t> work_heavy_end; // per band: end of the heavy-tile chunks (they come first)
     std::vector<int64_t> heavy_begin; // per band offset into d_heavy (size nband + 1)
+    std::vector<int64_t> empty_begin; // per band: the tiles without items follow the heavy ones in d_heavy
 
     // ---- device
     double *d_scale = nullptr;
@@ -130,6 +132,10 @@ struct Ctx {
     uint64_t clock = 0;
     std::vector<std::unique_ptr<Plan>> plans;
     std::map<std::string, DevBuf> bufs;
+    // named buffers whose zeros are kept between calls: the plan id (and plane count) they were
+    // cleared for; dropped whenever the buffer is reallocated
+    std::map<std::string, std::pair<uint64_t, int>> zero_tag;
+    uint64_t plan_serial = 0;
     std::map<FftKey, cufftHandle> ffts;
     std::vector<PsfSpec> spectra;
     Timing timing;

@@ -286,7 +286,9 @@ static void exclusive_scan(Ctx &ctx, const In *in, int64_t n, int64_t *out, cuda
 // Items that start on the same cell then sit next to each other, so the gridding
 // kernel's per-thread accumulators rarely change cell.  One CTA per (band, tile):
 // a shared-memory histogram and scan per bucket, a scatter into tmp and a copy back.
-constexpr int FINE_BINS = 4 * TILE * TILE;
+// first-tap cell of the item relative to its tile (4 TILE^2 positions: home and spill copies), home
+// items first: bin = spill * 4 TILE^2 + (lu + TILE) * 2 TILE + (lv + TILE)
+constexpr int FINE_BINS = 8 * TILE * TILE;
 
 // bucket keys (band x tile x w bucket) a plan may use; beyond it w planes are grouped q to a bucket
 #ifndef PFB_KEY_CAP_LOG2
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(256) k_fine_sort(CoordSrc src, const int64_t *
         const VisCoord<T> c = vis_coord<T>(src, row, ch, g);
         const int lu = (c.gu0 & (TILE - 1)) - du * TILE + TILE;
         const int lv = (c.gv0 & (TILE - 1)) - dv * TILE + TILE;
-        return lu * 2 * TILE + lv;
+        return ((du | dv) ? 4 * TILE * TILE : 0) + lu * 2 * TILE + lv;
     };
     for (int kq = 0; kq < nkq; ++kq) {
         const int64_t s = off[(int64_t)bt * nkq + kq], e = off[(int64_t)bt * nkq + kq + 1];
@@ -553,6 +555,7 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     p.work_begin.assign(p.nband + 1, 0);
     p.work_heavy_end.assign(p.nband, 0);
     p.heavy_begin.assign(p.nband + 1, 0);
+    p.empty_begin.assign(p.nband, 0);
     p.band_items_begin.assign(p.nband, 0);
     p.band_items_end.assign(p.nband, 0);
     for (int b = 0; b < p.nband; ++b) {
@@ -571,8 +574,9 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
         }
         p.work_heavy_end[b] = (int64_t)work.size();
         // owned tiles with items, largest first (no long tile starts at the end of the launch); tiles
-        // without items join the heavy ones in the list whose planes are zeroed by a plain kernel
+        // without items follow the heavy ones in the list of tiles that a plain kernel zeroes
         const size_t l0 = work.size();
+        p.empty_begin[b] = (int64_t)heavy.size();
         for (int64_t t = 0; t < ntiles; ++t) {
             const int64_t s = tb[b * ntiles + t], e = tb[b * ntiles + t + 1];
             if (e == s) heavy.push_back((int)t);
@@ -671,6 +675,7 @@ Plan &get_plan(Ctx &ctx, const pfb_geom &g, int prec, int64_t nrow, int nchan, c
         PFB_REQUIRE(p.band_h[c] >= 0 && p.band_h[c] < g.nband, "band_of_chan entry outside [0, nband)");
         p.scale[c] = fh[c] / C_LIGHT;
     }
+    p.id = ++ctx.plan_serial;
     p.Nu = good_size(std::max(2 * nx, 2 * MAX_W));
     p.Nv = good_size(std::max(2 * ny, 2 * MAX_W));
     try {

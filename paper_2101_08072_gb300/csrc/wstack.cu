@@ -805,15 +805,46 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
         __syncthreads();
         if (loaded && threadIdx.x == 0)
             for (int k = pa; k < pb; ++k) slot_plane[k % R] = k;
-        for (int64_t it = s + threadIdx.x; it < e; it += blockDim.x) {
-            const uint32_t code = items[it];
-            if (code >> 30) continue;
+        // the bucket lists its home items first (the plan's fine sort), then spill copies of
+        // neighbours' items, which this tile does not degrid: find the end of the home items
+        int64_t he = s;
+        {
+            int64_t lo = s, hi = e;   // first index in [s, e) with spill bits, or e
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (items[mid] >> 30) hi = mid; else lo = mid + 1;
+            }
+            he = lo;
+        }
+        // each thread's next item is loaded while the current one is interpolated
+        int64_t it = s + threadIdx.x;
+        uint32_t code_n = 0;
+        float4 rec_n = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 ph_n = make_float2(1.f, 0.f);
+        if (it < he) {
+            code_n = items[it];
+            if constexpr (REC) {
+                rec_n = recs[it];
+                ph_n = rph[it];
+            }
+        }
+        for (; it < he; it += blockDim.x) {
+            const uint32_t code = code_n;
+            const float4 r4 = rec_n;
+            const float2 ph = ph_n;
+            const int64_t nx_it = it + blockDim.x;
+            if (nx_it < he) {
+                code_n = items[nx_it];
+                if constexpr (REC) {
+                    rec_n = recs[nx_it];
+                    ph_n = rph[nx_it];
+                }
+            }
             const uint32_t v = code;
             VisCoord<float> c;
             int lu, lv;
             float cs = 1.f, sn = 0.f;
             if constexpr (REC) {
-                const float4 r4 = recs[it];
                 const uint32_t bits = __float_as_uint(r4.w);
                 c.ou = r4.x;
                 c.ov = r4.y;
@@ -822,7 +853,6 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
                 lv = (int)((bits >> 6) & 63u) - 32;
                 c.flip = (bits >> 12) & 1u;
                 c.k0 = (int)(bits >> 13);
-                const float2 ph = rph[it];
                 cs = ph.x;
                 sn = ph.y;
             } else {
@@ -959,14 +989,14 @@ __global__ void k_wsum(const T *__restrict__ wgt, int64_t nrow, int nchan, const
 template <typename T> struct FftT;
 template <> struct FftT<float> {
     static constexpr cufftType c2c = CUFFT_C2C;
-    static cufftResult exec(cufftHandle h, float2 *d, int dir) {
-        return cufftExecC2C(h, (cufftComplex *)d, (cufftComplex *)d, dir);
+    static cufftResult exec(cufftHandle h, float2 *in, float2 *out, int dir) {
+        return cufftExecC2C(h, (cufftComplex *)in, (cufftComplex *)out, dir);
     }
 };
 template <> struct FftT<double> {
     static constexpr cufftType c2c = CUFFT_Z2Z;
-    static cufftResult exec(cufftHandle h, double2 *d, int dir) {
-        return cufftExecZ2Z(h, (cufftDoubleComplex *)d, (cufftDoubleComplex *)d, dir);
+    static cufftResult exec(cufftHandle h, double2 *in, double2 *out, int dir) {
+        return cufftExecZ2Z(h, (cufftDoubleComplex *)in, (cufftDoubleComplex *)out, dir);
     }
 };
 
@@ -983,7 +1013,8 @@ static size_t fft_work_estimate(int Nu, int Nv, int batch) {
 // FFT of nplanes planes in batches of up to 8, smaller when the work area would not
 // fit the context's HBM budget
 template <typename T>
-static void fft_planes(Ctx &ctx, cx_t<T> *data, int nplanes, int Nu, int Nv, int dir, cudaStream_t st) {
+static void fft_planes(Ctx &ctx, cx_t<T> *data, int nplanes, int Nu, int Nv, int dir, cudaStream_t st,
+                       cx_t<T> *out = nullptr) {
     int maxb = 8;
     const size_t room = ctx.available() + ctx.scratch_bytes("fftwork");
     const size_t plane_bytes = (size_t)Nu * Nv * sizeof(cx_t<T>);
@@ -995,7 +1026,7 @@ static void fft_planes(Ctx &ctx, cx_t<T> *data, int nplanes, int Nu, int Nv, int
         const int b = std::min(maxb, nplanes - k);
         cufftHandle h = ctx.fft(Nu, Nv, b, FftT<T>::c2c);
         PFB_CUFFT(cufftSetStream(h, st));
-        PFB_CUFFT(FftT<T>::exec(h, data + k * plane_sz, dir));
+        PFB_CUFFT(FftT<T>::exec(h, data + k * plane_sz, (out ? out : data) + k * plane_sz, dir));
     }
 }
 
@@ -1016,6 +1047,35 @@ static int plane_block(Ctx &ctx, const Plan &p, size_t cxs, size_t reserve_unuse
     if (blk < 1) throw Error(PFB_ERR_OOM, "HBM budget too small for one w-plane of " +
                                               std::to_string(p.Nu) + "x" + std::to_string(p.Nv));
     return blk;
+}
+
+// Kept zero padding.  The zeros of a plane block (the padding around the image in degridding, the tiles
+// without visibilities in gridding) are the same in every call with a plan, so when every band fits one
+// block and the budget has room, the transform input gets buffers of its own that only the pre-pass or
+// the tile kernels write, cleared once per plan, and the FFT writes the shared block out of place.
+// Degridding keeps one input buffer, gridding one per band (each band has its own empty tiles).
+static bool keep_zeros_fits(Ctx &ctx, const Plan &p, size_t cxs, int blk, int nbuf, const char *prefix) {
+    if (blk < p.Pmax) return false;
+    const size_t need = (size_t)nbuf * blk * p.Nu * p.Nv * cxs;
+    size_t have = 0;
+    for (int i = 0; i < nbuf; ++i) have += ctx.scratch_bytes(std::string(prefix) + std::to_string(i));
+    const size_t others = (size_t)p.nrow * p.nchan * cxs + 16 * (size_t)p.nband * p.nx * p.ny * (cxs / 2) +
+                          (256u << 20);
+    return ctx.available() + have >= need + others;
+}
+
+// A kept-zero input buffer: cleared on `st` unless it already holds this plan's zeros.
+template <typename T>
+static cx_t<T> *kept_zero_buffer(Ctx &ctx, const Plan &p, const std::string &name, int blk, cudaStream_t st) {
+    const size_t bytes = (size_t)blk * p.Nu * p.Nv * sizeof(cx_t<T>);
+    cx_t<T> *buf = (cx_t<T> *)ctx.scratch(name, bytes);
+    auto it = ctx.zero_tag.find(name);
+    if (it == ctx.zero_tag.end() || it->second != std::make_pair(p.id, blk)) {
+        KTimer t(ctx, "memset_planes", st, (double)bytes, 0);
+        PFB_CUDA(cudaMemsetAsync(buf, 0, bytes, st));
+        ctx.zero_tag[name] = std::make_pair(p.id, blk);
+    }
+    return buf;
 }
 
 static unsigned grid_blocks(int64_t n, int threads, int cap) {
@@ -1116,6 +1176,8 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
     // room for cuFFT work areas is taken from the same budget
     const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
     cx_t<T> *planes = (cx_t<T> *)ctx.scratch("planes", (size_t)blk * p.Nu * p.Nv * cxs);
+    const bool keep = keep_zeros_fits(ctx, p, cxs, blk, 1, "dg_in");
+    cx_t<T> *in = keep ? kept_zero_buffer<T>(ctx, p, "dg_in0", blk, st) : planes;
     const int64_t npix = (int64_t)p.nx * p.ny;
     const double plane_bytes = (double)p.Nu * p.Nv * cxs;
     for (int b = 0; b < p.nband; ++b) {
@@ -1125,19 +1187,19 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
         for (int k_lo = 0; k_lo < g.P; k_lo += blk) {
             const int k_hi = std::min(g.P, k_lo + blk);
             const int nk = k_hi - k_lo;
-            {
+            if (!keep) {
                 KTimer t(ctx, "memset_planes", st, nk * plane_bytes, 0);
                 PFB_CUDA(cudaMemsetAsync(planes, 0, (size_t)nk * p.Nu * p.Nv * cxs, st));
             }
             {
                 KTimer t(ctx, "prepass", st, npix * (2.0 * sizeof(T) + 8.0 + nk * (double)cxs));
                 k_prepass<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
-                    p.nx, p.ny, image + b * npix, (const T *)p.d_corr, p.d_tp, g, k_lo, k_hi, p.dw, planes);
+                    p.nx, p.ny, image + b * npix, (const T *)p.d_corr, p.d_tp, g, k_lo, k_hi, p.dw, in);
                 check_launch("prepass");
             }
             {
                 KTimer t(ctx, "fft_fwd", st, 2.0 * nk * plane_bytes, 0);
-                fft_planes<T>(ctx, planes, nk, p.Nu, p.Nv, CUFFT_FORWARD, st);
+                fft_planes<T>(ctx, in, nk, p.Nu, p.Nv, CUFFT_FORWARD, st, keep ? planes : nullptr);
             }
             if (i1 > i0 && sizeof(T) == 4 && degrid_tiles_fit(p)) {
                 KTimer t(ctx, "degrid_tiles", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
@@ -1165,6 +1227,7 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
     const size_t cxs = sizeof(cx_t<T>);
     const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
     cx_t<T> *planes = (cx_t<T> *)ctx.scratch("planes", (size_t)blk * p.Nu * p.Nv * cxs);
+    const bool keep = keep_zeros_fits(ctx, p, cxs, blk, p.nband, "gr_in");
     const int64_t npix = (int64_t)p.nx * p.ny;
     const int R = p.Ww + p.q - 1;
     const size_t smem = (size_t)R * TILE * TILE * cxs;
@@ -1173,16 +1236,19 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
     for (int b = 0; b < p.nband; ++b) {
         const BandGeom g = p.geom(b);
         const int64_t w0 = p.work_begin[b], w1 = p.work_begin[b + 1];
-        const int64_t h0 = p.heavy_begin[b], h1 = p.heavy_begin[b + 1];
+        // tiles zeroed per call: the heavy ones (filled by reductions), and the empty ones unless kept
+        const int64_t h0 = p.heavy_begin[b], h1 = keep ? p.empty_begin[b] : p.heavy_begin[b + 1];
         const double nvb = (double)band_nvis(p, b);
         const double nit = (double)(p.band_items_end[b] - p.band_items_begin[b]);
+        cx_t<T> *const out = planes;
+        cx_t<T> *const in = keep ? kept_zero_buffer<T>(ctx, p, "gr_in" + std::to_string(b), blk, st) : planes;
         for (int k_lo = 0; k_lo < g.P; k_lo += blk) {
             const int k_hi = std::min(g.P, k_lo + blk);
             const int nk = k_hi - k_lo;
             if (h1 > h0) {
                 KTimer t(ctx, "zero_tiles", st, (double)(h1 - h0) * nk * TILE * TILE * cxs);
                 k_zero_tiles<T><<<(unsigned)((h1 - h0) * nk), 256, 0, st>>>(
-                    p.d_heavy + h0, (int)(h1 - h0), p.ntv, p.Nv, (int64_t)p.Nu * p.Nv, nk, planes);
+                    p.d_heavy + h0, (int)(h1 - h0), p.ntv, p.Nv, (int64_t)p.Nu * p.Nv, nk, in);
                 check_launch("zero_tiles");
             }
             {
@@ -1199,25 +1265,25 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                         KTimer tp(ctx, part == 0 ? "grid_dense" : "grid_light", st, 0.0, 0);
 #define PFB_GRID_CALL(WV, WWV)                                                                            \
     launch_grid_res_t<WV, WWV>((unsigned)(a1 - a0), R, st, p.d_work + a0, p, (const float2 *)vis,          \
-                               (const float *)wgt, unit_vis ? 1 : 0, g, k_lo, k_hi, (float2 *)planes)
+                               (const float *)wgt, unit_vis ? 1 : 0, g, k_lo, k_hi, (float2 *)in)
                         PFB_W_SWITCH(p.W, p.wstack, PFB_GRID_CALL)
 #undef PFB_GRID_CALL
                     }
                 } else if (w1 > w0) {
                     k_grid_tiles<T><<<(unsigned)(w1 - w0), 256, smem, st>>>(p.d_work + w0, p.d_items, p.d_off,
                                                                              p.coords(), vis, wgt,
-                                                                             unit_vis ? 1 : 0, g, k_lo, k_hi, planes);
+                                                                             unit_vis ? 1 : 0, g, k_lo, k_hi, in);
                 }
                 check_launch("grid_tiles");
             }
             {
                 KTimer t(ctx, "fft_inv", st, 2.0 * nk * plane_bytes, 0);
-                fft_planes<T>(ctx, planes, nk, p.Nu, p.Nv, CUFFT_INVERSE, st);
+                fft_planes<T>(ctx, in, nk, p.Nu, p.Nv, CUFFT_INVERSE, st, keep ? out : nullptr);
             }
             {
                 KTimer t(ctx, "postpass", st, npix * (nk * (double)cxs + 2.0 * sizeof(T) + 8.0));
                 k_postpass<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
-                    p.nx, p.ny, (const T *)p.d_corr, p.d_tp, g, k_lo, k_hi, p.dw, planes, k_lo > 0 ? 1 : 0,
+                    p.nx, p.ny, (const T *)p.d_corr, p.d_tp, g, k_lo, k_hi, p.dw, out, k_lo > 0 ? 1 : 0,
                     image + b * npix);
                 check_launch("postpass");
             }

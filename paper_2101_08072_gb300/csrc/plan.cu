@@ -287,8 +287,31 @@ static void exclusive_scan(Ctx &ctx, const In *in, int64_t n, int64_t *out, cuda
 // kernel's per-thread accumulators rarely change cell.  One CTA per (band, tile):
 // a shared-memory histogram and scan per bucket, a scatter into tmp and a copy back.
 // first-tap cell of the item relative to its tile (4 TILE^2 positions: home and spill copies), home
-// items first: bin = spill * 4 TILE^2 + (lu + TILE) * 2 TILE + (lv + TILE)
+// items first, cells along a Hilbert curve (neighbouring cells stay close in the order, so the register
+// runs of the gridding consumers break less often than in row order):
+//   bin = spill * 4 TILE^2 + hilbert(lu + TILE, lv + TILE)
 constexpr int FINE_BINS = 8 * TILE * TILE;
+
+// position of (x, y) along the Hilbert curve that fills an n x n grid (n a power of two): at each scale
+// s the quadrant contributes s^2 times its rank (0, 1, 2, 3 along the curve), and the remaining
+// coordinates are reflected and transposed into that quadrant's orientation
+__device__ __forceinline__ int hilbert_index(int n, int x, int y) {
+    int d = 0;
+    for (int s = n >> 1; s > 0; s >>= 1) {
+        const int rx = (x & s) ? 1 : 0, ry = (y & s) ? 1 : 0;
+        d += s * s * ((3 * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = n - 1 - x;
+                y = n - 1 - y;
+            }
+            const int t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
+}
 
 // bucket keys (band x tile x w bucket) a plan may use; beyond it w planes are grouped q to a bucket
 #ifndef PFB_KEY_CAP_LOG2
@@ -311,7 +334,7 @@ __global__ void __launch_bounds__(256) k_fine_sort(CoordSrc src, const int64_t *
         const VisCoord<T> c = vis_coord<T>(src, row, ch, g);
         const int lu = (c.gu0 & (TILE - 1)) - du * TILE + TILE;
         const int lv = (c.gv0 & (TILE - 1)) - dv * TILE + TILE;
-        return ((du | dv) ? 4 * TILE * TILE : 0) + lu * 2 * TILE + lv;
+        return ((du | dv) ? 4 * TILE * TILE : 0) + hilbert_index(2 * TILE, lu, lv);
     };
     for (int kq = 0; kq < nkq; ++kq) {
         const int64_t s = off[(int64_t)bt * nkq + kq], e = off[(int64_t)bt * nkq + kq + 1];

@@ -132,12 +132,17 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ measured traffic
+# sources that shape the gridding and degridding kernels and their item order (a profiled traffic
+# figure is only valid for them)
+TRAFFIC_SOURCES = ["common.cuh", "ctx.cuh", "plan.cu", "wstack.cu"]
+
+
 def source_digest() -> str:
-    """Digest of the CUDA sources (a profiled traffic figure is only valid for them)."""
+    """Digest of the sources of the profiled kernels."""
     import hashlib
     d = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2101_08072_gb300", "csrc")
-    for f in sorted(os.listdir(src)):
+    for f in TRAFFIC_SOURCES:
         d.update(open(os.path.join(src, f), "rb").read())
     return d.hexdigest()[:16]
 

@@ -68,8 +68,8 @@ def _load():
         lib = ctypes.CDLL(_LIB)
         P = ctypes.c_void_p
         i32, i64, f64, u32 = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_uint
-        lib.oracle_degrid.argtypes = [i32, i32, f64, f64, i32, i64, i32, P, P, P, P, u32, i64, P, P]
-        lib.oracle_grid.argtypes = [i32, i32, f64, f64, i32, i64, i32, P, P, P, P, P, u32, i64, P, P]
+        lib.oracle_degrid.argtypes = [i32, i32, f64, f64, f64, f64, i32, i64, i32, P, P, P, P, u32, i64, P, P]
+        lib.oracle_grid.argtypes = [i32, i32, f64, f64, f64, f64, i32, i64, i32, P, P, P, P, P, u32, i64, P, P]
         lib.oracle_wsum.argtypes = [i32, i64, i32, P, P, P]
         lib.oracle_psf_conv_direct.argtypes = [i32, i32, i32, P, P, P]
         lib.oracle_num_threads.restype = i32
@@ -90,9 +90,10 @@ def _c(a, dtype):
 
 
 # ------------------------------------------------------------------ R and R^dagger
-def degrid(uvw, freq, band_of_chan, image, dl, dm, flags=0, rows=None):
+def degrid(uvw, freq, band_of_chan, image, dl, dm, flags=0, rows=None, l0=0.0, m0=0.0):
     """R x (Eq. 1).  image [nband][nx][ny] -> vis [nrow][nchan] complex128.
-    rows: optional row indices; then only those rows are returned, [len(rows)][nchan]."""
+    rows: optional row indices; then only those rows are returned, [len(rows)][nchan].
+    (l0, m0): direction cosines of the image centre (a facet away from the phase centre)."""
     lib = _load()
     uvw, freq = _c(uvw, np.float64), _c(freq, np.float64)
     boc, image = _c(band_of_chan, np.int32), _c(image, np.float64)
@@ -101,14 +102,15 @@ def degrid(uvw, freq, band_of_chan, image, dl, dm, flags=0, rows=None):
     sel = None if rows is None else _c(rows, np.int64)
     nout = nrow if sel is None else sel.shape[0]
     out = np.zeros((nout, nchan, 2), dtype=np.float64)
-    lib.oracle_degrid(nx, ny, dl, dm, nband, nrow, nchan, _p(uvw), _p(freq), _p(boc), _p(image),
+    lib.oracle_degrid(nx, ny, dl, dm, l0, m0, nband, nrow, nchan, _p(uvw), _p(freq), _p(boc), _p(image),
                       flags, 0 if sel is None else sel.shape[0], _p(sel), _p(out))
     return out[..., 0] + 1j * out[..., 1]
 
 
-def grid(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, flags=0, pix=None):
+def grid(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, flags=0, pix=None, l0=0.0, m0=0.0):
     """R^dagger Sigma^-1 y (Eq. 3).  vis [nrow][nchan] complex, wgt same shape or None.
-    pix: optional flat indices b*nx*ny + i*ny + j; then returns [len(pix)]."""
+    pix: optional flat indices b*nx*ny + i*ny + j; then returns [len(pix)].
+    (l0, m0): direction cosines of the image centre (a facet away from the phase centre)."""
     lib = _load()
     uvw, freq = _c(uvw, np.float64), _c(freq, np.float64)
     boc = _c(band_of_chan, np.int32)
@@ -117,7 +119,7 @@ def grid(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, flags=0, pix=
     nrow, nchan = uvw.shape[0], freq.shape[0]
     sel = None if pix is None else _c(pix, np.int64)
     out = np.zeros(nband * nx * ny if sel is None else sel.shape[0], dtype=np.float64)
-    lib.oracle_grid(nx, ny, dl, dm, nband, nrow, nchan, _p(uvw), _p(freq), _p(boc), _p(v), _p(w),
+    lib.oracle_grid(nx, ny, dl, dm, l0, m0, nband, nrow, nchan, _p(uvw), _p(freq), _p(boc), _p(v), _p(w),
                     flags, 0 if sel is None else sel.shape[0], _p(sel), _p(out))
     return out.reshape(nband, nx, ny) if sel is None else out
 
@@ -131,25 +133,26 @@ def wsum(band_of_chan, wgt, nrow, nband):
     return out
 
 
-def dirty(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, flags=0):
+def dirty(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, flags=0, l0=0.0, m0=0.0):
     """I^d = R^dagger Sigma^-1 V (Eq. 3) and the per-band weight sums."""
-    img = grid(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, flags)
+    img = grid(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, flags, l0=l0, m0=m0)
     return img, wsum(band_of_chan, wgt, uvw.shape[0], nband)
 
 
-def psf(uvw, freq, band_of_chan, wgt, nx, ny, dl, dm, nband, flags=0):
+def psf(uvw, freq, band_of_chan, wgt, nx, ny, dl, dm, nband, flags=0, l0=0.0, m0=0.0):
     """I^psf: the adjoint applied to Sigma^-1 1 on a 2nx x 2ny grid with the same
-    pixel size, centre pixel (nx, ny).  Unnormalised: peak = per-band weight sum."""
+    pixel size, centre pixel (nx, ny) at (l0, m0).  Unnormalised: at the phase
+    centre its peak is the per-band weight sum."""
     ones = np.ones((uvw.shape[0], freq.shape[0]), dtype=np.complex128)
-    img = grid(uvw, freq, band_of_chan, ones, wgt, 2 * nx, 2 * ny, dl, dm, nband, flags)
+    img = grid(uvw, freq, band_of_chan, ones, wgt, 2 * nx, 2 * ny, dl, dm, nband, flags, l0=l0, m0=m0)
     return img, wsum(band_of_chan, wgt, uvw.shape[0], nband)
 
 
-def hessian(uvw, freq, band_of_chan, wgt, x, dl, dm, flags=0):
+def hessian(uvw, freq, band_of_chan, wgt, x, dl, dm, flags=0, l0=0.0, m0=0.0):
     """R^dagger Sigma^-1 R x (Eq. 3)."""
     nband, nx, ny = x.shape
-    rx = degrid(uvw, freq, band_of_chan, x, dl, dm, flags)
-    return grid(uvw, freq, band_of_chan, rx, wgt, nx, ny, dl, dm, nband, flags)
+    rx = degrid(uvw, freq, band_of_chan, x, dl, dm, flags, l0=l0, m0=m0)
+    return grid(uvw, freq, band_of_chan, rx, wgt, nx, ny, dl, dm, nband, flags, l0=l0, m0=m0)
 
 
 # ------------------------------------------------------------------ PSF convolution

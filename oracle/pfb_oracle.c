@@ -7,8 +7,8 @@
  *
  *     V[d,nu] = sum_{i,j} x[b(nu),i,j] / n_ij * exp(-2 pi i (u l_i + v m_j + w (n_ij - 1)))
  *
- * with (u,v,w) = uvw_d * f_nu / c (wavelengths), l_i = (i - nx/2) dl,
- * m_j = (j - ny/2) dm, n_ij = sqrt(1 - l_i^2 - m_j^2), and b(nu) the imaging
+ * with (u,v,w) = uvw_d * f_nu / c (wavelengths), l_i = l0 + (i - nx/2) dl,
+ * m_j = m0 + (j - ny/2) dm, n_ij = sqrt(1 - l_i^2 - m_j^2), and b(nu) the imaging
  * band of channel nu (Section 2: n_b bands, n_b << n_nu).  The adjoint
  * R^dagger used in Eq. 3 is the transpose under the real inner products
  * <a,b> = Re sum conj(a) b on visibilities and <x,z> = sum x z on images:
@@ -20,6 +20,11 @@
  *
  * Flags: bit 0 drops the 1/n factor, bit 1 drops the w (n-1) term.  Both are
  * test switches that turn the operator into a plain 2-D non-uniform DFT.
+ *
+ * (l0, m0) places the image centre away from the phase centre: the image is then
+ * one facet of a larger field, and the operator is still the definition above with
+ * the facet's absolute l, m (the phase centre of the data does not move).  With
+ * l0 = m0 = 0 the image is centred on the phase centre.
  */
 #include <math.h>
 #include <stdint.h>
@@ -40,10 +45,10 @@ static inline void cis_cycles(double phi, double sign, double *re, double *im) {
     *im = sign * sin(a);
 }
 
-static inline void pixel_lmn(int i, int j, int nx, int ny, double dl, double dm, unsigned flags,
-                             double *l, double *m, double *nm1, double *ninv) {
-    *l = (double)(i - nx / 2) * dl;
-    *m = (double)(j - ny / 2) * dm;
+static inline void pixel_lmn(int i, int j, int nx, int ny, double dl, double dm, double l0, double m0,
+                             unsigned flags, double *l, double *m, double *nm1, double *ninv) {
+    *l = l0 + (double)(i - nx / 2) * dl;
+    *m = m0 + (double)(j - ny / 2) * dm;
     double s = 1.0 - (*l) * (*l) - (*m) * (*m);
     double n = sqrt(s);
     /* n - 1 written as -(l^2+m^2)/(1+n): no cancellation near the phase centre */
@@ -55,7 +60,7 @@ static inline void pixel_lmn(int i, int j, int nx, int ny, double dl, double dm,
  * R (Eq. 1): image [nband][nx][ny] -> vis [nrow][nchan] complex (re,im pairs).
  * If rows != NULL only the nsel listed rows are evaluated and vis is [nsel][nchan].
  */
-void oracle_degrid(int nx, int ny, double dl, double dm, int nband, int64_t nrow, int nchan,
+void oracle_degrid(int nx, int ny, double dl, double dm, double l0, double m0, int nband, int64_t nrow, int nchan,
                    const double *uvw, const double *freq, const int32_t *band_of_chan,
                    const double *image, unsigned flags, int64_t nsel, const int64_t *rows,
                    double *vis) {
@@ -74,7 +79,7 @@ void oracle_degrid(int nx, int ny, double dl, double dm, int nband, int64_t nrow
             if (xv == 0.0) continue;
             int i = (int)(p / ny), j = (int)(p % ny);
             double l, m, nm1, ninv;
-            pixel_lmn(i, j, nx, ny, dl, dm, flags, &l, &m, &nm1, &ninv);
+            pixel_lmn(i, j, nx, ny, dl, dm, l0, m0, flags, &l, &m, &nm1, &ninv);
             tab[b][4 * k + 0] = l;
             tab[b][4 * k + 1] = m;
             tab[b][4 * k + 2] = nm1;
@@ -113,7 +118,7 @@ void oracle_degrid(int nx, int ny, double dl, double dm, int nband, int64_t nrow
  * -> image.  If pix != NULL only the npix listed flat indices b*nx*ny + i*ny + j are
  * evaluated and out is [npix]; otherwise out is the full [nband][nx][ny] cube.
  */
-void oracle_grid(int nx, int ny, double dl, double dm, int nband, int64_t nrow, int nchan,
+void oracle_grid(int nx, int ny, double dl, double dm, double l0, double m0, int nband, int64_t nrow, int nchan,
                  const double *uvw, const double *freq, const int32_t *band_of_chan,
                  const double *vis, const double *wgt, unsigned flags, int64_t npix,
                  const int64_t *pix, double *out) {
@@ -127,7 +132,7 @@ void oracle_grid(int nx, int ny, double dl, double dm, int nband, int64_t nrow, 
         const int64_t pp = p % ((int64_t)nx * ny);
         const int i = (int)(pp / ny), j = (int)(pp % ny);
         double l, m, nm1, ninv;
-        pixel_lmn(i, j, nx, ny, dl, dm, flags, &l, &m, &nm1, &ninv);
+        pixel_lmn(i, j, nx, ny, dl, dm, l0, m0, flags, &l, &m, &nm1, &ninv);
         double acc = 0.0;
         for (int c = 0; c < nchan; ++c) {
             if (band_of_chan[c] != b) continue;

@@ -539,3 +539,50 @@ def test_clean_driver_counts_and_composition():
     prm.approx_gradient = True
     ra = oracle.clean(*a, V, w, 16, 16, obs.dl, obs.dm, 1, prm, max_outer=2, tol=0.0)
     assert ra["n_outer"] == 2 and ra["n_hessian"] == 1
+
+
+# ------------------------------------------------------------------ facets (image centre away from the phase centre)
+def _facets(nx, ny, fx, fy, dl, dm):
+    """(i0, j0, l0, m0) of the fx x fy facets that tile an nx x ny image centred on the phase centre."""
+    out = []
+    for i0 in range(0, nx, fx):
+        for j0 in range(0, ny, fy):
+            out.append((i0, j0, (i0 + fx // 2 - nx // 2) * dl, (j0 + fy // 2 - ny // 2) * dm))
+    return out
+
+
+def test_facets_sum_to_the_full_image():
+    """R of an image equals the sum of R over facets that tile it, each facet an image of
+    its own centred at its (l0, m0); R^dagger of a facet is the full image's R^dagger on
+    the facet's pixels.  Both follow from Eq. 1 being a sum over pixels at absolute l, m."""
+    obs = synth.tiny_observation(nx=32, ny=24)
+    rng = np.random.default_rng(51)
+    a = (obs.uvw * 8.0, obs.freq, obs.band_of_chan)
+    dl, dm = obs.dl * 3, obs.dm * 3          # a wide field: the w term matters
+    x = rng.uniform(0, 1, (1, 32, 24))
+    y = synth.random_vis(rng, (obs.nrow, obs.nchan))
+    v_full = oracle.degrid(*a, x, dl, dm)
+    i_full = oracle.grid(*a, y, None, 32, 24, dl, dm, 1)
+    v_sum = np.zeros_like(v_full)
+    for i0, j0, l0, m0 in _facets(32, 24, 16, 12, dl, dm):
+        xf = x[:, i0:i0 + 16, j0:j0 + 12]
+        v_sum += oracle.degrid(*a, xf, dl, dm, l0=l0, m0=m0)
+        i_f = oracle.grid(*a, y, None, 16, 12, dl, dm, 1, l0=l0, m0=m0)
+        assert np.abs(i_f - i_full[:, i0:i0 + 16, j0:j0 + 12]).max() < 1e-10 * np.abs(i_full).max()
+    assert np.abs(v_sum - v_full).max() < 1e-10 * np.abs(v_full).max()
+
+
+def test_facet_offset_is_a_shift_when_coplanar():
+    """Without the w term and 1/n the offset is the shift theorem:
+    R_(l0,m0) x = exp(-2 pi i (u l0 + v m0)) R_(0,0) x."""
+    obs = synth.tiny_observation(nx=16, ny=16)
+    rng = np.random.default_rng(52)
+    a = (obs.uvw, obs.freq, obs.band_of_chan)
+    x = rng.uniform(0, 1, (1, 16, 16))
+    f = oracle.NO_WTERM | oracle.NO_DIVIDE_BY_N
+    l0, m0 = 7.5 * obs.dl, -3.25 * obs.dm
+    v0 = oracle.degrid(*a, x, obs.dl, obs.dm, flags=f)
+    v1 = oracle.degrid(*a, x, obs.dl, obs.dm, flags=f, l0=l0, m0=m0)
+    s = obs.freq[None, :] / synth.C_LIGHT
+    ph = np.exp(-2j * np.pi * (obs.uvw[:, 0:1] * s * l0 + obs.uvw[:, 1:2] * s * m0))
+    assert np.abs(v1 - ph * v0).max() < 1e-12 * np.abs(v0).max()

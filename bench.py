@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--clean-sigma", type=float, default=1e-3)
     ap.add_argument("--clean-lambda", type=float, default=1e-4)
     ap.add_argument("--clean-basis", type=int, default=0b1111111, help="basis mask (bit 0 Dirac, 1..6 db1..db6)")
+    ap.add_argument("--facets", type=int, default=0,
+                    help="faceted Hessian instead: the image split into F x F facets (R = sum of the facets' R)")
     ap.add_argument("--fp64", action="store_true", help="also time the FP64 path (eps 1e-9) on the same workload")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-entry-point timings")
     return ap.parse_args()
@@ -644,6 +646,97 @@ def run_clean(args):
     return 0
 
 
+# ------------------------------------------------------------------ faceted Hessian
+def run_facets(args):
+    """The Hessian of the MeerKAT-like workload with the image split into F x F facets, each
+    an image of its own centred at (l0, m0): V = sum_f R_f x_f (the first facet writes the
+    visibilities, the others accumulate into them), then R_f^dagger (W V) per facet.  It is
+    timed against the whole-image Hessian on the same data and compared with it."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2101_08072_gb300 import Context, Geometry, _lib
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    obs, x_np = workload(args)
+    F = args.facets
+    fx, fy = obs.nx // F, obs.ny // F
+    uvw = torch.from_numpy(obs.uvw).to(dev)
+    freq = torch.from_numpy(obs.freq).to(dev)
+    band = torch.from_numpy(obs.band_of_chan.astype(np.int32)).to(dev)
+    x = torch.from_numpy(x_np).to(dev, torch.float32)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(9)
+    wgt = torch.empty((obs.nrow, obs.nchan), dtype=torch.float32, device=dev).uniform_(0.5, 1.5, generator=gen)
+    ctx = Context(0)
+    stream = torch.cuda.current_stream(dev)
+    g_full = Geometry(nx=obs.nx, ny=obs.ny, dl=obs.dl, dm=obs.dm, nband=obs.nband, epsilon=args.eps)
+    facets = []
+    for i0 in range(0, obs.nx, fx):
+        for j0 in range(0, obs.ny, fy):
+            l0 = (i0 + fx // 2 - obs.nx // 2) * obs.dl
+            m0 = (j0 + fy // 2 - obs.ny // 2) * obs.dm
+            gf = Geometry(nx=fx, ny=fy, dl=obs.dl, dm=obs.dm, nband=obs.nband, epsilon=args.eps, l0=l0, m0=m0)
+            ga = Geometry(nx=fx, ny=fy, dl=obs.dl, dm=obs.dm, nband=obs.nband, epsilon=args.eps, l0=l0, m0=m0,
+                          flags=_lib.PFB_ACCUMULATE)
+            facets.append((i0, j0, gf, ga, x[:, i0:i0 + fx, j0:j0 + fy].contiguous(),
+                           torch.empty((obs.nband, fx, fy), dtype=torch.float32, device=dev)))
+    vis = torch.empty((obs.nrow, obs.nchan), dtype=torch.complex64, device=dev)
+    y_full = torch.empty_like(x)
+
+    def faceted():
+        for k, (i0, j0, gf, ga, xf, yf) in enumerate(facets):
+            ctx.pfb_degrid(ga if k else gf, uvw, freq, band, xf, out=vis)
+        for i0, j0, gf, ga, xf, yf in facets:
+            ctx.pfb_grid(gf, uvw, freq, band, vis, wgt, out=yf)
+
+    def full():
+        ctx.pfb_hessian(g_full, uvw, freq, band, x, wgt, out=y_full)
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / n
+
+    ms_full = timed(full, args.steps)
+    ms_fac = timed(faceted, args.steps)
+    # planes per facet and for the whole image, from the forward-FFT bytes the library records
+    def planes(fn, nx, ny):
+        ctx.lib.pfb_timing(ctx.h, 1)
+        fn()
+        import ctypes
+        n, ms, by = ctypes.c_int64(0), ctypes.c_double(0), ctypes.c_double(0)
+        ctx.lib.pfb_timing_read(ctx.h, b"fft_fwd", ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by))
+        ctx.lib.pfb_timing(ctx.h, 0)
+        return by.value / (2.0 * (2 * nx) * (2 * ny) * 8)
+    pl_full = planes(lambda: ctx.pfb_degrid(g_full, uvw, freq, band, x, out=vis), obs.nx, obs.ny)
+    pl_fac = [planes(lambda f=f: ctx.pfb_degrid(f[2], uvw, freq, band, f[4], out=vis), fx, fy) for f in facets]
+    faceted()
+    full()
+    torch.cuda.synchronize(dev)
+    y_fac = torch.empty_like(x)
+    for i0, j0, gf, ga, xf, yf in facets:
+        y_fac[:, i0:i0 + fx, j0:j0 + fy] = yf
+    diff = float(torch.linalg.vector_norm(y_fac - y_full) / torch.linalg.vector_norm(y_full))
+    line = {"metric": "faceted Hessian R^dagger Sigma^-1 R x", "value": obs.nvis / (ms_fac * 1e-3) / 1e6,
+            "unit": "Mvis/s", "ms_per_step": ms_fac, "whole_image_ms_per_step": ms_full,
+            "whole_image_mvis_per_s": obs.nvis / (ms_full * 1e-3) / 1e6,
+            "w_planes_whole_image": pl_full, "w_planes_per_facet": pl_fac,
+            "rel_l2_vs_whole_image": diff, "facets": F * F, "dtype": "f32", "data": "synthetic (seeded)",
+            "n_gpus": 1, "steps": args.steps,
+            "config": {"workload": f"MeerKAT-like Hessian, {obs.nx}^2 image as {F}x{F} facets of {fx}x{fy}",
+                       "visibilities": obs.nvis, "epsilon": args.eps}}
+    ctx.close()
+    print(json.dumps(line))
+    return 0
+
+
 def kernel_totals(ctx):
     """ms per kernel group recorded by the library's timing since it was enabled."""
     import ctypes
@@ -665,6 +758,8 @@ def main():
         return run_serve(args)
     if args.clean:
         return run_clean(args)
+    if args.facets:
+        return run_facets(args)
     return run_ours(args)
 
 

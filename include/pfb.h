@@ -23,8 +23,14 @@
  *  - wgt     [nrow][nchan] real >= 0 (float32 for PFB_F32, float64 for PFB_F64),
  *    the diagonal of Sigma^-1; NULL means all ones.
  *  - image   [nband][nx][ny] real (float32 / float64).  Pixel (i, j) sits at
- *    l = (i - nx/2) dl, m = (j - ny/2) dm; n = sqrt(1 - l^2 - m^2).  The first
- *    image axis pairs with u, the second with v.
+ *    l = l0 + (i - nx/2) dl, m = m0 + (j - ny/2) dm; n = sqrt(1 - l^2 - m^2).  The
+ *    first image axis pairs with u, the second with v.  (l0, m0) = (0, 0) centres the
+ *    image on the phase centre; otherwise the image is a facet of a wider field (the
+ *    paper's route to cheaper wide-field operators): R of an image is the sum of R
+ *    over facets that tile it, and R^dagger of a facet is the image's R^dagger on the
+ *    facet's pixels.  A facet's w-stack spans only the facet (the part of n - 1 that is
+ *    linear across it is applied as a shift of u and v by w dn/dl, w dn/dm at the
+ *    facet centre), and its PSF (pfb_psf) is the PSF at the facet centre.
  *  - R x [d, nu] = sum_{i,j} x[b(nu),i,j] / n_ij exp(-2 pi i (u l_i + v m_j + w (n_ij - 1)))
  *    with (u, v, w) = uvw_d f_nu / c.  R^dagger is the transpose under the real
  *    inner products Re sum conj(a) b (visibilities) and sum x z (images).
@@ -81,6 +87,9 @@ enum {
    gridding and degridding kernels stream instead of recomputing it from uvw.  With
    this flag the plan never keeps them. */
 #define PFB_NO_ITEM_RECORDS 4u
+/* pfb_degrid adds R x into vis_out instead of overwriting it (vis_out += R x), so that
+   R of a faceted image is the sum of the facets' calls.  Other entry points ignore it. */
+#define PFB_ACCUMULATE 8u
 
 typedef struct {
     int32_t nx, ny;      /* image pixels per band (even); the PSF is 2nx x 2ny */
@@ -88,7 +97,8 @@ typedef struct {
     double fov_l, fov_m; /* field of view in radians: 0 = derive, else must equal nx*dl, ny*dm */
     double epsilon;      /* requested relative L2 accuracy of R and R^dagger */
     int32_t nband;       /* n_b imaging bands */
-    uint32_t flags;      /* PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM | PFB_NO_ITEM_RECORDS */
+    uint32_t flags;      /* PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM | PFB_NO_ITEM_RECORDS | PFB_ACCUMULATE */
+    double l0, m0;       /* direction cosines of the image centre (facets); 0, 0 = the phase centre */
 } pfb_geom;
 
 /* Parameters of one pfb-clean step (Eqs. 6-9). */

@@ -12,6 +12,7 @@ PFB_F64 = 1
 PFB_NO_DIVIDE_BY_N = 1
 PFB_NO_WTERM = 2
 PFB_NO_ITEM_RECORDS = 4
+PFB_ACCUMULATE = 8
 PFB_STEP_APPROX_GRADIENT = 1
 
 ERRORS = {
@@ -28,7 +29,8 @@ EXPORTS = ["pfb_create", "pfb_destroy", "pfb_last_error", "pfb_plan_reset", "pfb
 class pfb_geom(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dl", ctypes.c_double),
                 ("dm", ctypes.c_double), ("fov_l", ctypes.c_double), ("fov_m", ctypes.c_double),
-                ("epsilon", ctypes.c_double), ("nband", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+                ("epsilon", ctypes.c_double), ("nband", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("l0", ctypes.c_double), ("m0", ctypes.c_double)]
 
 
 class pfb_params(ctypes.Structure):

@@ -205,7 +205,9 @@ void check_geom(const pfb_geom *g, pfb_prec prec) {
     PFB_REQUIRE(g->nx <= 65536 && g->ny <= 65536, "nx, ny must be <= 65536");
     PFB_REQUIRE(g->nband >= 1 && g->nband <= 32, "nband must be in [1, 32]");
     PFB_REQUIRE(std::isfinite(g->dl) && std::isfinite(g->dm) && g->dl > 0 && g->dm > 0, "dl, dm must be > 0");
-    PFB_REQUIRE((g->flags & ~(PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM | PFB_NO_ITEM_RECORDS)) == 0, "unknown flag bits");
+    PFB_REQUIRE((g->flags & ~(PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM | PFB_NO_ITEM_RECORDS | PFB_ACCUMULATE)) == 0,
+                "unknown flag bits");
+    PFB_REQUIRE(std::isfinite(g->l0) && std::isfinite(g->m0), "l0, m0 must be finite");
     if (g->fov_l != 0)
         PFB_REQUIRE(std::fabs(g->fov_l - g->nx * g->dl) <= 1e-9 * std::fabs(g->fov_l), "fov_l != nx * dl");
     if (g->fov_m != 0)
@@ -335,8 +337,9 @@ int pfb_degrid(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int
         check_data(nrow, nchan, uvw, freq, band);
         PFB_REQUIRE(image && vis_out, "image and vis_out must not be NULL");
         Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, S(stream));
-        if (prec == PFB_F64) op_degrid<double>(c, p, (const double *)image, (double2 *)vis_out, S(stream));
-        else op_degrid<float>(c, p, (const float *)image, (float2 *)vis_out, S(stream));
+        const bool acc = g->flags & PFB_ACCUMULATE;
+        if (prec == PFB_F64) op_degrid<double>(c, p, (const double *)image, (double2 *)vis_out, S(stream), acc);
+        else op_degrid<float>(c, p, (const float *)image, (float2 *)vis_out, S(stream), acc);
     });
 }
 

@@ -116,7 +116,11 @@ struct BandGeom {
     int nchan;
     double u2cell, v2cell;  // dl * Nu, dm * Nv: wavelengths -> grid cells
     double inv_dw, w0;      // w -> plane coordinate z_w = (w - w0) / dw
-    double tc;              // centre of (n - 1) over the image; removed per visibility
+    double tc;              // centre of t = n - 1 - fa dl - fb dm over the image; removed per visibility
+    // facet terms: u' = u + fa w, v' = v + fb w on the grid, and the phase u l0 + v m0 per visibility
+    int facet;
+    double fa, fb, l0, m0;
+    int accumulate;         // degridding adds into the visibilities instead of writing them
     double beta;
     double inv_halfw;       // 2 / W
     // FP32 path: first-tap offsets O = W/2 (uv) and W/2 + w0/dw (w), split into
@@ -142,6 +146,11 @@ struct ChanDF {
     float sv_hi, sv_lo;   // f/c * dm * Nv
     float sw_hi, sw_lo;   // f/c / dw       (metres -> w-plane coordinate)
     float sp_hi, sp_lo;   // f/c * t_c      (metres -> turns of exp(-2 pi i w t_c))
+    // facets only
+    float sa_hi, sa_lo;   // f/c * fa * dl * Nu  (metres of w -> u cells)
+    float sb_hi, sb_lo;   // f/c * fb * dm * Nv  (metres of w -> v cells)
+    float sl_hi, sl_lo;   // f/c * l0            (metres of u -> turns)
+    float sm_hi, sm_lo;   // f/c * m0            (metres of v -> turns)
 };
 
 // Grid coordinates of one visibility.
@@ -163,7 +172,7 @@ __device__ __forceinline__ VisCoord<double> vis_coord64(const double *__restrict
     c.flip = w < 0.0;
     if (c.flip) { u = -u; v = -v; w = -w; }
     const double hw = 0.5 * g.W;
-    double xu = u * g.u2cell, xv = v * g.v2cell;
+    double xu = (g.facet ? u + g.fa * w : u) * g.u2cell, xv = (g.facet ? v + g.fb * w : v) * g.v2cell;
     xu -= g.Nu * floor(xu / g.Nu);            // periodic grid: wrap into [0, Nu)
     xv -= g.Nv * floor(xv / g.Nv);
     double fu = ceil(xu - hw), fv = ceil(xv - hw);
@@ -177,6 +186,11 @@ __device__ __forceinline__ VisCoord<double> vis_coord64(const double *__restrict
     c.gu0 = gu;
     c.gv0 = gv;
     double ph = w * g.tc;
+    ph -= rint(ph);
+    if (g.facet) {
+        double pu = u * g.l0, pv = v * g.m0;
+        ph += (pu - rint(pu)) + (pv - rint(pv));
+    }
     c.ph = ph - rint(ph);
     if (g.Ww > 1) {
         double zw = (w - g.w0) * g.inv_dw;
@@ -200,6 +214,18 @@ __device__ __forceinline__ void df_mul(float a_hi, float a_lo, float s_hi, float
     e = fmaf(a_hi, s_hi, -p) + fmaf(a_hi, s_lo, a_lo * s_hi);
 }
 
+// (p + e) += a * s in double-float: the new product by TwoProduct, the two high parts by TwoSum
+// (Knuth), every rounding error gathered into e.
+__device__ __forceinline__ void df_add_mul(float a_hi, float a_lo, float s_hi, float s_lo, float &p, float &e) {
+    float q, f;
+    df_mul(a_hi, a_lo, s_hi, s_lo, q, f);
+    const float t = p + q;
+    const float bb = t - p;
+    const float err = (p - (t - bb)) + (q - bb);
+    p = t;
+    e = e + f + err;
+}
+
 // First tap g0 = ceil(x - O) and offset g0 - x for x = p + e, O = oi + of.
 __device__ __forceinline__ void df_tap(float p, float e, int oi, float of, float hw, int &g0, float &off) {
     const float r = floorf(p);
@@ -220,13 +246,22 @@ __device__ __forceinline__ VisCoord<float> vis_coord32(const float2 *__restrict_
     float p, e;
     int g0;
     df_mul(u.x, u.y, cs.su_hi, cs.su_lo, p, e);
+    if (g.facet) df_add_mul(w.x, w.y, cs.sa_hi, cs.sa_lo, p, e);
     df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ou);
     c.gu0 = wrap_mod(g0, g.Nu, g.inv_Nu);
     df_mul(v.x, v.y, cs.sv_hi, cs.sv_lo, p, e);
+    if (g.facet) df_add_mul(w.x, w.y, cs.sb_hi, cs.sb_lo, p, e);
     df_tap(p, e, g.uv_oi, g.uv_of, g.hw, g0, c.ov);
     c.gv0 = wrap_mod(g0, g.Nv, g.inv_Nv);
     df_mul(w.x, w.y, cs.sp_hi, cs.sp_lo, p, e);
     c.ph = (p - rintf(p)) + e;
+    if (g.facet) {
+        df_mul(u.x, u.y, cs.sl_hi, cs.sl_lo, p, e);
+        c.ph += (p - rintf(p)) + e;
+        df_mul(v.x, v.y, cs.sm_hi, cs.sm_lo, p, e);
+        c.ph += (p - rintf(p)) + e;
+        c.ph -= rintf(c.ph);
+    }
     if (g.Ww > 1) {
         df_mul(w.x, w.y, cs.sw_hi, cs.sw_lo, p, e);
         df_tap(p, e, g.w_oi, g.w_of, g.hw, g0, c.ow);

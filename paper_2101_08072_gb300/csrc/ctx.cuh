@@ -18,6 +18,8 @@ struct Plan {
     // ---- key
     int nx = 0, ny = 0, nband = 0;
     double dl = 0, dm = 0;
+    double l0 = 0, m0 = 0;    // image centre (facets)
+    double fa = 0, fb = 0;    // dn/dl, dn/dm at the image centre (0 without w term)
     uint32_t flags = 0;
     int prec = 0;
     int W = 0;
@@ -68,6 +70,9 @@ struct Plan {
         g.inv_dw = wstack ? 1.0 / dw : 0.0;
         g.w0 = w0[b];
         g.tc = tc; g.beta = beta; g.inv_halfw = 2.0 / W;
+        g.facet = (l0 != 0.0 || m0 != 0.0) ? 1 : 0;
+        g.fa = fa; g.fb = fb; g.l0 = l0; g.m0 = m0;
+        g.accumulate = 0;
         const double hw = 0.5 * W;
         g.hw = (float)hw;
         g.uv_oi = (int)std::floor(hw);
@@ -187,7 +192,7 @@ int kernel_support(double eps);
 // wstack.cu
 void build_item_records(Ctx &ctx, Plan &p, cudaStream_t st);
 template <typename T>
-void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st);
+void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st, bool accumulate = false);
 template <typename T>
 void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool unit_vis, T *image,
              cudaStream_t st);

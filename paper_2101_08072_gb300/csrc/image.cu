@@ -427,9 +427,18 @@ __global__ void __launch_bounds__(256) k_dwt2_tile(int n, int m, int tiles_q, Vi
     const int K0 = tk * DWT_TO, Q0 = tq * DWT_TO;
     const int nh = n / 2, mh = m / 2;
     const T *sp = src.p + b * src.bs;
-    for (int e = threadIdx.x; e < E * E; e += blockDim.x) {
-        const int r = e / E, c = e - r * E;
-        xs[e] = sp[(int64_t)pmod(2 * K0 + r, n) * src.rs + pmod(2 * Q0 + c, m)];
+    if (2 * K0 + E <= n && 2 * Q0 + E <= m) {
+        // interior tile: the region does not wrap
+        const T *base = sp + (int64_t)(2 * K0) * src.rs + 2 * Q0;
+        for (int e = threadIdx.x; e < E * E; e += blockDim.x) {
+            const int r = e / E, c = e - r * E;
+            xs[e] = base[(int64_t)r * src.rs + c];
+        }
+    } else {
+        for (int e = threadIdx.x; e < E * E; e += blockDim.x) {
+            const int r = e / E, c = e - r * E;
+            xs[e] = sp[(int64_t)pmod(2 * K0 + r, n) * src.rs + pmod(2 * Q0 + c, m)];
+        }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < DWT_TO * E; e += blockDim.x) {
@@ -483,9 +492,10 @@ __global__ void __launch_bounds__(256) k_idwt2_tile(int n, int m, int tiles_s, V
     const int kb0 = P0 / 2 - H, kb1 = S0 / 2 - H;
     const T *lp = ll.p + b * ll.bs;
     const T *dp = det.p + b * det.bs;
+    const bool inner = kb0 >= 0 && kb1 >= 0 && kb0 + C <= nh && kb1 + C <= mh;   // no wrap
     for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
         const int r = e / C, c = e - r * C;
-        const int k = pmod(kb0 + r, nh), q = pmod(kb1 + c, mh);
+        const int k = inner ? kb0 + r : pmod(kb0 + r, nh), q = inner ? kb1 + c : pmod(kb1 + c, mh);
         cs[e] = lp[(int64_t)k * ll.rs + q];
         cs[C * C + e] = dp[(int64_t)k * det.rs + q + mh];
         cs[2 * C * C + e] = dp[(int64_t)(k + nh) * det.rs + q];

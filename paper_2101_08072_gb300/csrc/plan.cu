@@ -402,17 +402,19 @@ __global__ void k_tile_begin(const int64_t *__restrict__ off, int64_t ntb, int n
 // Per-pixel tables: t = n - 1 - t_c (FP64) and the correction
 // 1 / (n psihat_u psihat_v psihat_w(dw t)) in the working precision.
 template <typename T>
-__global__ void k_pixel_tables(int nx, int ny, double dl, double dm, uint32_t flags, double tc, double dw,
+__global__ void k_pixel_tables(int nx, int ny, double dl, double dm, double l0, double m0, double fa, double fb,
+                               uint32_t flags, double tc, double dw,
                                int wstack, const double *__restrict__ psiu, const double *__restrict__ psiv,
                                const double *__restrict__ tab, int M, double xi0, double inv_h,
                                double *__restrict__ tp, T *__restrict__ corr) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= (int64_t)nx * ny) return;
     int i = (int)(p / ny), j = (int)(p - (int64_t)i * ny);
-    double l = (i - nx / 2) * dl, m = (j - ny / 2) * dm;
+    const double dli = (i - nx / 2) * dl, dmj = (j - ny / 2) * dm;
+    double l = l0 + dli, m = m0 + dmj;
     double r2 = l * l + m * m;
     double n = sqrt(1.0 - r2);
-    double nm1 = (flags & PFB_NO_WTERM) ? 0.0 : -r2 / (1.0 + n);
+    double nm1 = (flags & PFB_NO_WTERM) ? 0.0 : -r2 / (1.0 + n) - fa * dli - fb * dmj;
     double t = nm1 - tc;
     double c = psiu[i] * psiv[j];
     if (!(flags & PFB_NO_DIVIDE_BY_N)) c *= n;
@@ -455,14 +457,26 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
         std::memcpy(&h[1], &hb[1], 8);
         double wmax = h[0], wmin = h[1];
         if (!(wmin <= wmax)) wmin = wmax = 0.0;
-        // ---- geometry of the image: range of n - 1
-        double lmax = (nx / 2) * p.dl, mmax = (ny / 2) * p.dm;
-        double r2 = lmax * lmax + mmax * mmax;
-        PFB_REQUIRE(r2 < 1.0, "field of view reaches the horizon (l^2 + m^2 >= 1)");
-        double tmin = -r2 / (1.0 + std::sqrt(1.0 - r2));
-        bool nowterm = p.flags & PFB_NO_WTERM;
-        p.tc = nowterm ? 0.0 : 0.5 * tmin;
-        p.Thalf = nowterm ? 0.0 : -0.5 * tmin;
+        // ---- geometry of the image: range of t = n - 1 - fa dl - fb dm over the pixels, where
+        // (dl, dm) is the offset from the image centre (l0, m0) and (fa, fb) = grad n there.
+        // t is concave with its maximum n0 - 1 at the centre, so its minimum is at a corner.
+        const bool nowterm = p.flags & PFB_NO_WTERM;
+        const double r20 = p.l0 * p.l0 + p.m0 * p.m0;
+        PFB_REQUIRE(r20 < 1.0, "image centre beyond the horizon (l0^2 + m0^2 >= 1)");
+        const double n0 = std::sqrt(1.0 - r20);
+        p.fa = nowterm ? 0.0 : -p.l0 / n0;
+        p.fb = nowterm ? 0.0 : -p.m0 / n0;
+        auto t_at = [&](double dl_, double dm_) {
+            const double l = p.l0 + dl_, m = p.m0 + dm_, r2 = l * l + m * m;
+            PFB_REQUIRE(r2 < 1.0, "field of view reaches the horizon (l^2 + m^2 >= 1)");
+            return -r2 / (1.0 + std::sqrt(1.0 - r2)) - p.fa * dl_ - p.fb * dm_;
+        };
+        const double tmax = -r20 / (1.0 + n0);
+        double tmin = tmax;
+        for (int ci : {-(nx / 2), nx - 1 - nx / 2})
+            for (int cj : {-(ny / 2), ny - 1 - ny / 2}) tmin = std::min(tmin, t_at(ci * p.dl, cj * p.dm));
+        p.tc = nowterm ? 0.0 : 0.5 * (tmin + tmax);
+        p.Thalf = nowterm ? 0.0 : 0.5 * (tmax - tmin);
         p.wstack = !nowterm && p.Thalf > 0.0;
         p.Ww = p.wstack ? p.W : 1;
         p.dw = p.wstack ? 1.0 / (4.0 * p.Thalf) : 0.0;   // dw * max|t| = 1/(2 sigma), sigma = 2
@@ -516,6 +530,10 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
         split_df(p.scale[c] * p.dm * p.Nv, cdf[c].sv_hi, cdf[c].sv_lo);
         split_df(p.wstack ? p.scale[c] / p.dw : 0.0, cdf[c].sw_hi, cdf[c].sw_lo);
         split_df(p.scale[c] * p.tc, cdf[c].sp_hi, cdf[c].sp_lo);
+        split_df(p.scale[c] * p.fa * p.dl * p.Nu, cdf[c].sa_hi, cdf[c].sa_lo);
+        split_df(p.scale[c] * p.fb * p.dm * p.Nv, cdf[c].sb_hi, cdf[c].sb_lo);
+        split_df(p.scale[c] * p.l0, cdf[c].sl_hi, cdf[c].sl_lo);
+        split_df(p.scale[c] * p.m0, cdf[c].sm_hi, cdf[c].sm_lo);
     }
     PFB_CUDA(cudaMemcpyAsync(p.d_scale, p.scale.data(), p.nchan * sizeof(double), cudaMemcpyHostToDevice, st));
     PFB_CUDA(cudaMemcpyAsync(p.d_band, p.band_h.data(), p.nchan * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -645,11 +663,13 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     p.bytes += npix * (sizeof(double) + rs);
     const unsigned pb = (unsigned)((npix + 255) / 256);
     if (p.prec == PFB_F64)
-        k_pixel_tables<double><<<pb, 256, 0, st>>>(nx, ny, p.dl, p.dm, p.flags, p.tc, p.dw, p.wstack, d_psiu,
+        k_pixel_tables<double><<<pb, 256, 0, st>>>(nx, ny, p.dl, p.dm, p.l0, p.m0, p.fa, p.fb, p.flags, p.tc,
+                                                   p.dw, p.wstack, d_psiu,
                                                    d_psiv, d_tab, M, -xi_max, 1.0 / h, p.d_tp,
                                                    (double *)p.d_corr);
     else
-        k_pixel_tables<float><<<pb, 256, 0, st>>>(nx, ny, p.dl, p.dm, p.flags, p.tc, p.dw, p.wstack, d_psiu,
+        k_pixel_tables<float><<<pb, 256, 0, st>>>(nx, ny, p.dl, p.dm, p.l0, p.m0, p.fa, p.fb, p.flags, p.tc,
+                                                  p.dw, p.wstack, d_psiu,
                                                   d_psiv, d_tab, M, -xi_max, 1.0 / h, p.d_tp,
                                                   (float *)p.d_corr);
     check_launch("pixel_tables");
@@ -666,15 +686,18 @@ Plan &get_plan(Ctx &ctx, const pfb_geom &g, int prec, int64_t nrow, int nchan, c
     const int W = kernel_support(g.epsilon);
     for (auto &pp : ctx.plans) {
         Plan &p = *pp;
-        if (p.nx == nx && p.ny == ny && p.nband == g.nband && p.dl == g.dl && p.dm == g.dm &&
-            p.flags == g.flags && p.prec == prec && p.W == W && p.nrow == nrow && p.nchan == nchan &&
+        if (p.nx == nx && p.ny == ny && p.nband == g.nband && p.dl == g.dl && p.dm == g.dm && p.l0 == g.l0 &&
+            p.m0 == g.m0 &&
+            p.flags == (g.flags & ~PFB_ACCUMULATE) && p.prec == prec && p.W == W && p.nrow == nrow && p.nchan == nchan &&
             p.uvw == uvw && p.freq == freq && p.band == band) {
             p.last_use = ++ctx.clock;
             return p;
         }
     }
-    // evict the least recently used plan beyond four
-    while (ctx.plans.size() >= 4) {
+    // evict the least recently used plans beyond sixteen (a faceted image keeps one plan per facet), and
+    // while the budget could not hold another plan of this size (items, records and tables)
+    const size_t plan_need = (size_t)nrow * nchan * 48 + (size_t)nx * ny * 16 + (256u << 20);
+    while (ctx.plans.size() >= 16 || (!ctx.plans.empty() && ctx.available() < plan_need)) {
         auto it = std::min_element(ctx.plans.begin(), ctx.plans.end(),
                                    [](const std::unique_ptr<Plan> &a, const std::unique_ptr<Plan> &b) {
                                        return a->last_use < b->last_use;
@@ -684,7 +707,9 @@ Plan &get_plan(Ctx &ctx, const pfb_geom &g, int prec, int64_t nrow, int nchan, c
     }
     auto pp = std::make_unique<Plan>();
     Plan &p = *pp;
-    p.nx = nx; p.ny = ny; p.nband = g.nband; p.dl = g.dl; p.dm = g.dm; p.flags = g.flags; p.prec = prec;
+    p.nx = nx; p.ny = ny; p.nband = g.nband; p.dl = g.dl; p.dm = g.dm; p.flags = g.flags & ~PFB_ACCUMULATE;
+    p.prec = prec;
+    p.l0 = g.l0; p.m0 = g.m0;
     p.W = W; p.beta = es_beta(W); p.nrow = nrow; p.nchan = nchan; p.uvw = uvw; p.freq = freq; p.band = band;
     PFB_REQUIRE(nrow * (int64_t)nchan < (int64_t)VIS_MASK, "more than 2^30 visibilities in one call");
     std::vector<double> fh(nchan);

@@ -104,12 +104,12 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ ite
         }
         // exp(-2 pi i w t_c)
         T cs = 1, sn = 0;
-        if (g.tc != 0.0) sincos_turns(c.ph, &sn, &cs);
+        if (g.tc != 0.0 || g.facet) sincos_turns(c.ph, &sn, &cs);
         T vr = ar * cs + ai * sn;
         T vi = ai * cs - ar * sn;
         if (c.flip) vi = -vi;
         cx_t<T> out;
-        if (c.k0 < k_lo) {
+        if (g.accumulate || c.k0 < k_lo) {
             out = vis[v];
             out.x += vr;
             out.y += vi;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
             if (wgt) { const T w = wgt[v]; yr *= w; yi *= w; }
             if (c.flip) yi = -yi;
             // multiply by exp(+2 pi i w t_c) (adjoint of the degridding phase)
-            if (g.tc != 0.0) {
+            if (g.tc != 0.0 || g.facet) {
                 T cs, sn;
                 sincos_turns(c.ph, &sn, &cs);
                 const T r0 = yr * cs - yi * sn;
@@ -372,7 +372,7 @@ __global__ void k_item_records(const uint32_t *__restrict__ items, int64_t i0, i
         const int lv = (c.gv0 & (TILE - 1)) - dv * TILE;
         rec[i] = make_float4(c.ou, c.ov, c.ow, __uint_as_float(rec_bits(lu, lv, c.flip, c.k0)));
         float cs = 1.f, sn = 0.f;
-        if (g.tc != 0.0) sincos_turns(c.ph, &sn, &cs);
+        if (g.tc != 0.0 || g.facet) sincos_turns(c.ph, &sn, &cs);
         rph[i] = make_float2(cs, sn);
     }
 }
@@ -547,7 +547,7 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                 }
                 lu = (c.gu0 & (TILE - 1)) - du * TILE;
                 lv = (c.gv0 & (TILE - 1)) - dv * TILE;
-                if (g.tc != 0.0) sincos_turns(c.ph, &sn, &cs2);
+                if (g.tc != 0.0 || g.facet) sincos_turns(c.ph, &sn, &cs2);
             }
             float yr = q.y.x * q.wt, yi = q.y.y * q.wt;
             if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) {
@@ -861,7 +861,7 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
                 c = vis_coord<float>(src, row, ch, g);
                 lu = c.gu0 - tu * TILE;
                 lv = c.gv0 - tv * TILE;
-                if (g.tc != 0.0) sincos_turns(c.ph, &sn, &cs);
+                if (g.tc != 0.0 || g.facet) sincos_turns(c.ph, &sn, &cs);
             }
             if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) continue;
             const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
@@ -904,7 +904,7 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
             float vi = ai * cs - ar * sn;
             if (c.flip) vi = -vi;
             float2 out;
-            if (c.k0 < k_lo) {
+            if (g.accumulate || c.k0 < k_lo) {
                 out = vis[v];
                 out.x += vr;
                 out.y += vi;
@@ -1171,7 +1171,7 @@ static int64_t band_nvis(const Plan &p, int b) {
 }
 
 template <typename T>
-void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st) {
+void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st, bool accumulate) {
     const size_t cxs = sizeof(cx_t<T>);
     // room for cuFFT work areas is taken from the same budget
     const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
@@ -1181,7 +1181,8 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
     const int64_t npix = (int64_t)p.nx * p.ny;
     const double plane_bytes = (double)p.Nu * p.Nv * cxs;
     for (int b = 0; b < p.nband; ++b) {
-        const BandGeom g = p.geom(b);
+        BandGeom g = p.geom(b);
+        g.accumulate = accumulate ? 1 : 0;
         const int64_t i0 = p.band_items_begin[b], i1 = p.band_items_end[b];
         const double nvb = (double)band_nvis(p, b);
         for (int k_lo = 0; k_lo < g.P; k_lo += blk) {
@@ -1300,8 +1301,8 @@ void op_wsum(Ctx &ctx, const Plan &p, const T *wgt, double *d_wsum, cudaStream_t
     check_launch("wsum");
 }
 
-template void op_degrid<float>(Ctx &, const Plan &, const float *, float2 *, cudaStream_t);
-template void op_degrid<double>(Ctx &, const Plan &, const double *, double2 *, cudaStream_t);
+template void op_degrid<float>(Ctx &, const Plan &, const float *, float2 *, cudaStream_t, bool);
+template void op_degrid<double>(Ctx &, const Plan &, const double *, double2 *, cudaStream_t, bool);
 template void op_grid<float>(Ctx &, const Plan &, const float2 *, const float *, bool, float *, cudaStream_t);
 template void op_grid<double>(Ctx &, const Plan &, const double2 *, const double *, bool, double *, cudaStream_t);
 template void op_wsum<float>(Ctx &, const Plan &, const float *, double *, cudaStream_t);

@@ -29,9 +29,12 @@ class Geometry:
     nband: int = 1
     epsilon: float = 1e-5
     flags: int = 0
+    l0: float = 0.0   # direction cosines of the image centre: a facet of a wider field
+    m0: float = 0.0
 
     def c(self) -> _lib.pfb_geom:
-        return _lib.pfb_geom(self.nx, self.ny, self.dl, self.dm, 0.0, 0.0, self.epsilon, self.nband, self.flags)
+        return _lib.pfb_geom(self.nx, self.ny, self.dl, self.dm, 0.0, 0.0, self.epsilon, self.nband, self.flags,
+                             self.l0, self.m0)
 
 
 @dataclasses.dataclass
@@ -93,7 +96,7 @@ class Context:
         # Inputs of the plans cached by libpfb, most recent last.  libpfb keys its
         # plans on device pointers; holding the tensors keeps torch's caching
         # allocator from handing the same addresses to different data while a plan
-        # that points at them may still be cached (libpfb keeps at most 4 plans).
+        # that points at them may still be cached (libpfb keeps at most 16 plans).
         self._keep: list[tuple] = []
 
     def close(self):

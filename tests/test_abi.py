@@ -52,7 +52,7 @@ def test_struct_layouts_match_header(tmp_path):
     import shutil
     import subprocess
     from paper_2101_08072_gb300 import _lib
-    assert ctypes.sizeof(_lib.pfb_geom) == 56
+    assert ctypes.sizeof(_lib.pfb_geom) == 72
     assert ctypes.sizeof(_lib.pfb_params) == 72
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:

@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--clean-basis", type=int, default=0b1111111, help="basis mask (bit 0 Dirac, 1..6 db1..db6)")
     ap.add_argument("--facets", type=int, default=0,
                     help="faceted Hessian instead: the image split into F x F facets (R = sum of the facets' R)")
+    ap.add_argument("--facets-wide", action="store_true",
+                    help="with --facets: the full pfb-clean field (8192^2, 64 channels, --clean-rows rows)")
     ap.add_argument("--fp64", action="store_true", help="also time the FP64 path (eps 1e-9) on the same workload")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-entry-point timings")
     return ap.parse_args()
@@ -658,7 +660,7 @@ def run_facets(args):
     from paper_2101_08072_gb300 import Context, Geometry, _lib
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    obs, x_np = workload(args)
+    obs, x_np = clean_workload(args) if args.facets_wide else workload(args)
     F = args.facets
     fx, fy = obs.nx // F, obs.ny // F
     uvw = torch.from_numpy(obs.uvw).to(dev)
@@ -730,7 +732,9 @@ def run_facets(args):
             "w_planes_whole_image": pl_full, "w_planes_per_facet": pl_fac,
             "rel_l2_vs_whole_image": diff, "facets": F * F, "dtype": "f32", "data": "synthetic (seeded)",
             "n_gpus": 1, "steps": args.steps,
-            "config": {"workload": f"MeerKAT-like Hessian, {obs.nx}^2 image as {F}x{F} facets of {fx}x{fy}",
+            "config": {"workload": f"{'full pfb-clean field' if args.facets_wide else 'MeerKAT-like'} Hessian "
+                                   f"({obs.nrow} rows x {obs.nchan} channels), {obs.nx}^2 image as {F}x{F} facets "
+                                   f"of {fx}x{fy}",
                        "visibilities": obs.nvis, "epsilon": args.eps}}
     ctx.close()
     print(json.dumps(line))

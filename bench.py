@@ -12,7 +12,7 @@ step touches tens of GB of w-plane stacks, far more than the 129 MB L2.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With N > 1 (torchrun) each rank runs an independent replica of the workload
-(the path shards only with an image all-reduce that this build does not use);
+(the path shards only with an image all-reduce, which this program does not use);
 value is the sum over ranks, timed as the max over ranks.
 """
 from __future__ import annotations
@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--clean-pd", type=int, default=10, help="primal-dual iterations per step")
     ap.add_argument("--clean-cg", type=int, default=10, help="CG iterations per step")
     ap.add_argument("--clean-gamma", type=float, default=0.5,
-                    help="step size; at the 8192^2 field gamma = 1 diverges slowly (see DESIGN.md)")
+                    help="step size; at the 8192^2 field gamma = 1 diverges slowly: the PSF-based preconditioner "
+                         "underestimates the wide-field Hessian in some directions by more than 2x")
     ap.add_argument("--clean-sigma", type=float, default=1e-3)
     ap.add_argument("--clean-lambda", type=float, default=1e-4)
     ap.add_argument("--clean-basis", type=int, default=0b1111111, help="basis mask (bit 0 Dirac, 1..6 db1..db6)")

@@ -249,7 +249,7 @@ def oracle_sample(obs, x, wgt_rows, rows, pix):
     return 1e-6 / sec_per_vis, t2 - t0, oracle.num_threads()
 
 
-def cpu_baseline(obs, x, wgt_np_fn, n_rows=8192, n_pix=2048, seed=5):
+def cpu_baseline(obs, x, wgt_np_fn, n_rows=24576, n_pix=6144, seed=5):
     rng = np.random.default_rng(seed)
     rows = np.sort(rng.choice(obs.nrow, n_rows, replace=False))
     pix = np.sort(rng.choice(obs.nband * obs.nx * obs.ny, n_pix, replace=False))
@@ -274,7 +274,7 @@ def run_reference(args):
     vals = []
     info = None
     for i in range(args.warmup + args.steps):
-        info = cpu_baseline(obs, x, wgt, n_rows=256, n_pix=128, seed=100 + i)
+        info = cpu_baseline(obs, x, wgt, n_rows=2048, n_pix=1024, seed=100 + i)
         if i >= args.warmup:
             vals.append(info["value"])
     value = statistics.median(vals)

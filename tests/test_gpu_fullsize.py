@@ -97,3 +97,28 @@ def test_hessian_row_subset_vs_oracle(big):
                       obs.dm, obs.nband, pix=pix)
     got = hx.reshape(-1)[torch.from_numpy(pix).to(dev)].cpu().numpy()
     assert rel_l2(got, ref) <= 3 * TOL
+
+
+def test_fp64_path_full_size_sampled(big):
+    """The FP64 path (epsilon = 1e-10) at the full size: R at sampled rows and R^dagger at
+    sampled pixels against the oracle, within the FP64 tolerance 1e-9."""
+    from paper_2101_08072_gb300 import Geometry
+    obs, ctx, dev = big["obs"], big["ctx"], big["dev"]
+    g64 = Geometry(nx=obs.nx, ny=obs.ny, dl=obs.dl, dm=obs.dm, nband=obs.nband, epsilon=1e-10)
+    a = (g64, big["uvw"], big["freq"], big["band"])
+    x64 = big["xt"].double()
+    v = ctx.pfb_degrid(*a, x64)
+    rows = np.sort(np.random.default_rng(18).choice(obs.nrow, 16, replace=False))
+    ref = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x64.cpu().numpy(), obs.dl, obs.dm, rows=rows)
+    got = v[torch.from_numpy(rows).to(dev)].cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-9
+    del v
+    rng = np.random.default_rng(19)
+    y = synth.random_vis(rng, (obs.nrow, obs.nchan))
+    img = ctx.pfb_grid(*a, torch.from_numpy(y).to(dev))
+    npx = obs.nband * obs.nx * obs.ny
+    pix = np.sort(np.random.default_rng(20).choice(npx, 8, replace=False))
+    ref = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, y, None, obs.nx, obs.ny, obs.dl, obs.dm, obs.nband,
+                      pix=pix)
+    got = img.reshape(-1)[torch.from_numpy(pix).to(dev)].cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-9

@@ -48,56 +48,75 @@ __global__ void k_ifftshift(int nx, int ny, int nband, const T *__restrict__ psf
 }
 
 // zero-padded copy of (a - b) (b may be null) into [nband][2nx][2ny]
+// (blockIdx.y = band, blocks stride over the 2 nx padded rows)
 template <typename T>
-__global__ void k_pad(int nx, int ny, int nband, const T *__restrict__ a, const T *__restrict__ b,
-                      T *__restrict__ out) {
-    const int64_t NX = 2 * nx, NY = 2 * ny;
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= nband * NX * NY) return;
-    const int64_t bb = e / (NX * NY), r = e - bb * NX * NY;
-    const int64_t i = r / NY, j = r - i * NY;
-    T v = 0;
-    if (i < nx && j < ny) {
-        const int64_t s = (bb * nx + i) * ny + j;
-        v = b ? a[s] - b[s] : a[s];
+__global__ void k_pad(int nx, int ny, const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out) {
+    const int bb = blockIdx.y;
+    const int NX = 2 * nx, NY = 2 * ny;
+    for (int i = blockIdx.x; i < NX; i += gridDim.x) {
+        T *orow = out + ((int64_t)bb * NX + i) * NY;
+        if (i < nx) {
+            const int64_t s0 = ((int64_t)bb * nx + i) * ny;
+#pragma unroll 4
+            for (int j = threadIdx.x; j < ny; j += blockDim.x) orow[j] = b ? a[s0 + j] - b[s0 + j] : a[s0 + j];
+            for (int j = ny + threadIdx.x; j < NY; j += blockDim.x) orow[j] = 0;
+        } else {
+            for (int j = threadIdx.x; j < NY; j += blockDim.x) orow[j] = 0;
+        }
     }
-    out[e] = v;
 }
 
-// X *= S * scale (complex S), or X *= Re(S) * scale (symmetric part)
+// X *= S * scale (complex S)
 template <typename T>
-__global__ void k_spec_mul(int64_t n, const cx_t<T> *__restrict__ S, T scale, int sym, cx_t<T> *__restrict__ X) {
+__global__ void k_spec_mul(int64_t n, const cx_t<T> *__restrict__ S, T scale, cx_t<T> *__restrict__ X) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n) return;
     const cx_t<T> s = S[e];
     cx_t<T> x = X[e];
-    if (sym) {
-        x.x *= s.x * scale;
-        x.y *= s.x * scale;
-    } else {
-        const T r = (x.x * s.x - x.y * s.y) * scale;
-        const T i = (x.x * s.y + x.y * s.x) * scale;
-        x.x = r;
-        x.y = i;
-    }
+    const T r = (x.x * s.x - x.y * s.y) * scale;
+    const T i = (x.x * s.y + x.y * s.x) * scale;
+    x.x = r;
+    x.y = i;
+    X[e] = x;
+}
+
+// X *= Re(S) * scale (the spectrum of the symmetrised PSF, Eq. 8)
+template <typename T>
+__global__ void k_spec_mul_re(int64_t n, const T *__restrict__ Sre, T scale, cx_t<T> *__restrict__ X) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const T s = Sre[e] * scale;
+    cx_t<T> x = X[e];
+    x.x *= s;
+    x.y *= s;
     X[e] = x;
 }
 
 template <typename T>
-__global__ void k_crop(int nx, int ny, int nband, const T *__restrict__ big, T *__restrict__ y) {
+__global__ void k_real_part(int64_t n, const cx_t<T> *__restrict__ S, T *__restrict__ re) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= (int64_t)nband * nx * ny) return;
-    const int64_t b = e / ((int64_t)nx * ny), r = e - b * nx * ny;
-    const int64_t i = r / ny, j = r - i * ny;
-    y[e] = big[(b * 2 * nx + i) * 2 * ny + j];
+    if (e < n) re[e] = S[e].x;
 }
 
-// max |Re S| over the spectrum (bits of a non-negative double)
+// top-left [nx][ny] corner of each padded band (blockIdx.y = band, blocks stride over rows)
 template <typename T>
-__global__ void k_absmax_re(int64_t n, const cx_t<T> *__restrict__ S, unsigned long long *out) {
-    double m = 0;
+__global__ void k_crop(int nx, int ny, const T *__restrict__ big, T *__restrict__ y) {
+    const int b = blockIdx.y;
+    for (int i = blockIdx.x; i < nx; i += gridDim.x) {
+        const T *brow = big + ((int64_t)b * 2 * nx + i) * 2 * ny;
+        T *yrow = y + ((int64_t)b * nx + i) * ny;
+#pragma unroll 4
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) yrow[j] = brow[j];
+    }
+}
+
+// max |v| over n values (bits of a non-negative double)
+template <typename T>
+__global__ void k_absmax(int64_t n, const T *__restrict__ v, unsigned long long *out) {
+    T mt = 0;   // the maximum of the working-precision values is exact in that precision
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        m = fmax(m, fabs((double)S[e].x));
+        mt = fmax(mt, fabs(v[e]));
+    double m = (double)mt;
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
@@ -117,6 +136,35 @@ __device__ __forceinline__ void block_sum_atomic(double v, double *dst) {
     __syncthreads();
 }
 
+// Sum of products per thread.  FP64 arithmetic runs at a small fraction of the FP32
+// rate on this GPU, so FP32 work keeps its sums as an unevaluated float pair: each
+// product split exactly into p + e (e by FMA) and each addition by Knuth's TwoSum,
+// which keeps about 48 bits; the pair becomes a double once per thread.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float hi = 0, lo = 0;
+    __device__ __forceinline__ void add(float v) {
+        const float s = __fadd_rn(hi, v);
+        const float vb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, vb)), __fsub_rn(v, vb));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        add(p);
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Scalar slots of one step (device doubles)
 enum {
     S_XHX = 0,      // x_k . H x_k
@@ -125,30 +173,33 @@ enum {
     S_DX2,          // ||x_{k+1} - x_k||^2
     S_X2,           // ||x_{k+1}||^2
     S_L21,          // ||Psi^dagger x_k||_{2,1}
+    S_TAU,          // primal step size of the Condat-Vu iteration
     S_COUNT
 };
 // per-band arrays follow: BB[nb] (||IR||^2), then RR[(iters+1)][nb], PAP[iters][nb]
 #define S_UNORM_IDX S_UNORM
 
-// IR = (I^d - H x) * inv_wbar; objective pieces (per band blocks, blockIdx.y = band)
+// IR = (I^d - H x) * inv_wbar; objective pieces (per band blocks, blockIdx.y = band):
+// x . H x and x . I^d (both scaled by inv_wbar), ||IR||^2 per band
 template <typename T>
 __global__ void k_residual(int64_t npix, const T *__restrict__ dirty, const T *__restrict__ hx,
                            const T *__restrict__ x, double inv_wbar, T *__restrict__ ir, double *__restrict__ sc,
                            double *__restrict__ bb) {
     const int b = blockIdx.y;
-    double xhx = 0, xd = 0, rr = 0;
+    const T w = (T)inv_wbar;
+    Acc<T> xhx, xd, rr;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = b * npix + p;
-        const double d = (double)dirty[e] * inv_wbar, h = (double)hx[e] * inv_wbar, xv = (double)x[e];
-        const T r = (T)(d - h);
+        const T d = dirty[e], h = hx[e], xv = x[e];
+        const T r = (d - h) * w;
         ir[e] = r;
-        xhx += xv * h;
-        xd += xv * d;
-        rr += (double)r * (double)r;
+        xhx.add_prod(xv, h);
+        xd.add_prod(xv, d);
+        rr.add_prod(r, r);
     }
-    block_sum_atomic(xhx, &sc[S_XHX]);
-    block_sum_atomic(xd, &sc[S_XD]);
-    block_sum_atomic(rr, &bb[b]);
+    block_sum_atomic(xhx.value() * inv_wbar, &sc[S_XHX]);
+    block_sum_atomic(xd.value() * inv_wbar, &sc[S_XD]);
+    block_sum_atomic(rr.value(), &bb[b]);
 }
 
 // CG start: delta = 0, r = p = IR, RR[0] = BB
@@ -165,21 +216,24 @@ __global__ void k_cg_init(int64_t n, const T *__restrict__ ir, T *__restrict__ d
 
 __device__ __forceinline__ bool cg_active(double rr, double bb, double tol2) { return rr > 0.0 && rr > tol2 * bb; }
 
-// Ap = crop(conv) + sigma p, pap[b] += p . Ap
+// Ap = crop(conv) + sigma p, pap[b] += p . Ap   (blockIdx.y = band, blocks stride over rows)
 template <typename T>
 __global__ void k_cg_ap(int nx, int ny, const T *__restrict__ big, const T *__restrict__ p, T sigma,
                         T *__restrict__ ap, double *__restrict__ pap) {
     const int b = blockIdx.y;
-    const int64_t npix = (int64_t)nx * ny;
-    double acc = 0;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npix; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q / ny, j = q - i * ny;
-        const int64_t e = b * npix + q;
-        const T v = big[((int64_t)b * 2 * nx + i) * 2 * ny + j] + sigma * p[e];
-        ap[e] = v;
-        acc += (double)p[e] * (double)v;
+    Acc<T> acc;
+    for (int i = blockIdx.x; i < nx; i += gridDim.x) {
+        const T *brow = big + ((int64_t)b * 2 * nx + i) * 2 * ny;
+        const int64_t e0 = ((int64_t)b * nx + i) * ny;
+#pragma unroll 4
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+            const T pv = p[e0 + j];
+            const T v = brow[j] + sigma * pv;
+            ap[e0 + j] = v;
+            acc.add_prod(pv, v);
+        }
     }
-    block_sum_atomic(acc, &pap[b]);
+    block_sum_atomic(acc.value(), &pap[b]);
 }
 
 // delta += alpha p; r -= alpha Ap; rr_next[b] += r . r
@@ -189,37 +243,50 @@ __global__ void k_cg_update(int64_t npix, const T *__restrict__ p, const T *__re
                             const double *__restrict__ bb, double tol2, T *__restrict__ delta, T *__restrict__ r,
                             double *__restrict__ rr_next) {
     const int b = blockIdx.y;
-    const bool act = cg_active(rr[b], bb[b], tol2) && pap[b] > 0.0;
-    const T alpha = act ? (T)(rr[b] / pap[b]) : (T)0;
-    double acc = 0;
+    __shared__ T s_alpha;
+    if (threadIdx.x == 0) {
+        const bool act = cg_active(rr[b], bb[b], tol2) && pap[b] > 0.0;
+        s_alpha = act ? (T)(rr[b] / pap[b]) : (T)0;
+    }
+    __syncthreads();
+    const T alpha = s_alpha;
+    Acc<T> acc;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npix; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = b * npix + q;
         delta[e] += alpha * p[e];
         const T rv = r[e] - alpha * ap[e];
         r[e] = rv;
-        acc += (double)rv * (double)rv;
+        acc.add_prod(rv, rv);
     }
-    block_sum_atomic(acc, &rr_next[b]);
+    block_sum_atomic(acc.value(), &rr_next[b]);
 }
 
 // p = r + beta p, beta = rr_next / rr (0 once converged), written padded for the next U p
+// (blockIdx.y = band, blocks stride over the 2 nx padded rows)
 template <typename T>
 __global__ void k_cg_dir(int nx, int ny, const T *__restrict__ r, const double *__restrict__ rr,
                          const double *__restrict__ rr_next, const double *__restrict__ bb, double tol2,
                          T *__restrict__ p, T *__restrict__ padded) {
     const int b = blockIdx.y;
-    const int64_t NX = 2 * nx, NY = 2 * ny;
-    const bool act = cg_active(rr[b], bb[b], tol2);
-    const T beta = act ? (T)(rr_next[b] / rr[b]) : (T)0;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < NX * NY; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q / NY, j = q - i * NY;
-        T v = 0;
-        if (i < nx && j < ny) {
-            const int64_t e = ((int64_t)b * nx + i) * ny + j;
-            v = r[e] + beta * p[e];
-            p[e] = v;
+    const int NX = 2 * nx, NY = 2 * ny;
+    __shared__ T s_beta;
+    if (threadIdx.x == 0) s_beta = cg_active(rr[b], bb[b], tol2) ? (T)(rr_next[b] / rr[b]) : (T)0;
+    __syncthreads();
+    const T beta = s_beta;
+    for (int i = blockIdx.x; i < NX; i += gridDim.x) {
+        T *prow = padded + ((int64_t)b * NX + i) * NY;
+        if (i < nx) {
+            const int64_t e0 = ((int64_t)b * nx + i) * ny;
+#pragma unroll 4
+            for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+                const T v = r[e0 + j] + beta * p[e0 + j];
+                p[e0 + j] = v;
+                prow[j] = v;
+            }
+            for (int j = ny + threadIdx.x; j < NY; j += blockDim.x) prow[j] = 0;
+        } else {
+            for (int j = threadIdx.x; j < NY; j += blockDim.x) prow[j] = 0;
         }
-        padded[(int64_t)b * NX * NY + q] = v;
     }
 }
 
@@ -233,61 +300,64 @@ __global__ void k_axpy_clamp(int64_t n, const T *__restrict__ x, const T *__rest
     xpd[e] = v > 0 ? v : 0;
 }
 
-// One Condat-Vu iteration with Psi = Dirac (one thread per pixel, all bands):
+// Condat-Vu primal step size, once per step: tau = 0.98 / (||U|| / (2 gamma) + 1) with
+// ||U|| = max |Re S| / wbar + sigma unless given (sc[S_UNORM] holds max |Re S|)
+__global__ void k_pd_tau(double *__restrict__ sc, double inv_wbar, double sigma, double gamma,
+                         double unorm_fixed) {
+    const double unorm = unorm_fixed > 0 ? unorm_fixed : sc[S_UNORM] * inv_wbar + sigma;
+    sc[S_TAU] = 0.98 / (0.5 * unorm / gamma + 1.0);
+}
+
+// One Condat-Vu iteration with Psi = Dirac (one thread per pixel, all bands; blocks stride over rows):
 //   x~ = max(0, x - tau (grad + Psi v)),  grad = (conv + sigma (x - xbar)) / gamma
 //   v~ = v + Psi^dagger (2 x~ - x);  v = v~ min(1, lam / ||v~||_bands);  x = x~
 template <typename T>
 __global__ void k_pd_dirac(int nx, int ny, int nband, const T *__restrict__ big, const T *__restrict__ xbar,
-                           T sigma, T gamma, T lam, const double *__restrict__ sc, double inv_wbar,
-                           double unorm_fixed, T *__restrict__ x, T *__restrict__ v) {
+                           T sigma, T gamma, T lam, const double *__restrict__ sc, T *__restrict__ x,
+                           T *__restrict__ v) {
     const int64_t npix = (int64_t)nx * ny;
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= npix) return;
-    // ||U|| = max |Re S| / wbar + sigma unless given (sc[S_UNORM] holds max |Re S|)
-    const double unorm = unorm_fixed > 0 ? unorm_fixed : sc[S_UNORM] * inv_wbar + (double)sigma;
-    const T tau = (T)(0.98 / (0.5 * unorm / (double)gamma + 1.0));
-    const int64_t i = q / ny, j = q - i * ny;
-    T xt[32], vt[32];
-    T nrm2 = 0;
-    for (int b = 0; b < nband; ++b) {
-        const int64_t e = b * npix + q;
-        const T xv = x[e];
-        const T grad = (big[((int64_t)b * 2 * nx + i) * 2 * ny + j] + sigma * (xv - xbar[e])) / gamma;
-        T xn = xv - tau * (grad + v[e]);
-        xn = xn > 0 ? xn : 0;
-        xt[b] = xn;
-        const T vn = v[e] + (2 * xn - xv);
-        vt[b] = vn;
-        nrm2 += vn * vn;
-    }
-    const T nrm = sqrt(nrm2);
-    const T s = nrm > lam ? lam / nrm : (T)1;
-    for (int b = 0; b < nband; ++b) {
-        const int64_t e = b * npix + q;
-        x[e] = xt[b];
-        v[e] = vt[b] * s;
+    const T tau = (T)sc[S_TAU];
+    for (int i = blockIdx.x; i < nx; i += gridDim.x) {
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+            const int64_t q = (int64_t)i * ny + j;
+            T xt[32], vt[32];
+            T nrm2 = 0;
+            for (int b = 0; b < nband; ++b) {
+                const int64_t e = b * npix + q;
+                const T xv = x[e];
+                const T grad = (big[((int64_t)b * 2 * nx + i) * 2 * ny + j] + sigma * (xv - xbar[e])) / gamma;
+                T xn = xv - tau * (grad + v[e]);
+                xn = xn > 0 ? xn : 0;
+                xt[b] = xn;
+                const T vn = v[e] + (2 * xn - xv);
+                vt[b] = vn;
+                nrm2 += vn * vn;
+            }
+            const T nrm = sqrt(nrm2);
+            const T s = nrm > lam ? lam / nrm : (T)1;
+            for (int b = 0; b < nband; ++b) {
+                const int64_t e = b * npix + q;
+                x[e] = xt[b];
+                v[e] = vt[b] * s;
+            }
+        }
     }
 }
 
-// final statistics: ||x1 - x0||^2, ||x1||^2, sum_p ||x0[:, p]||_2 ; copy x1 to the output
+// final statistics: ||x1 - x0||^2, ||x1||^2; copy x1 to the output (blockIdx.y = band)
 template <typename T>
-__global__ void k_finish(int64_t npix, int nband, const T *__restrict__ x1, T *__restrict__ x0_out,
-                         double *__restrict__ sc) {
-    double dx2 = 0, x2 = 0;
+__global__ void k_finish(int64_t npix, const T *__restrict__ x1, T *__restrict__ x0_out, double *__restrict__ sc) {
+    const int64_t off = (int64_t)blockIdx.y * npix;
+    Acc<T> dx2, x2;
+#pragma unroll 4
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npix; q += (int64_t)gridDim.x * blockDim.x) {
-        double g2 = 0;
-        for (int b = 0; b < nband; ++b) {
-            const int64_t e = b * npix + q;
-            const double a = (double)x0_out[e], c = (double)x1[e];
-            dx2 += (c - a) * (c - a);
-            x2 += c * c;
-            g2 += a * a;
-            x0_out[e] = x1[e];
-        }
-        (void)g2;
+        const T a = x0_out[off + q], c = x1[off + q];
+        dx2.add_prod(c - a, c - a);
+        x2.add_prod(c, c);
+        x0_out[off + q] = c;
     }
-    block_sum_atomic(dx2, &sc[S_DX2]);
-    block_sum_atomic(x2, &sc[S_X2]);
+    block_sum_atomic(dx2.value(), &sc[S_DX2]);
+    block_sum_atomic(x2.value(), &sc[S_X2]);
 }
 
 // ------------------------------------------------------------------ Daubechies dictionary (Eq. 9's Psi)
@@ -479,7 +549,7 @@ __global__ void __launch_bounds__(256) k_dwt2_tile(int n, int m, int tiles_q, Vi
 
 template <typename T, int L>
 __global__ void __launch_bounds__(256) k_idwt2_tile(int n, int m, int tiles_s, View2<T> ll, View2<T> det,
-                                                    View2<T> dst, WavTaps<T> f) {
+                                                    View2<T> dst, WavTaps<T> f, T alpha, int accumulate) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     constexpr int C = idwt_edge(L);
     constexpr int H = L / 2 - 1;   // offset of coefficient k = p/2 in the staged region
@@ -532,7 +602,8 @@ __global__ void __launch_bounds__(256) k_idwt2_tile(int n, int m, int tiles_s, V
             const T hv = odd ? f.h[2 * u + 1] : f.h[2 * u], gv = odd ? f.g[2 * u + 1] : f.g[2 * u];
             acc += hv * us[(base - u) * DWT_TX + ss] + gv * us[(C + base - u) * DWT_TX + ss];
         }
-        op[(int64_t)p * dst.rs + s2] = acc;
+        T *o = op + (int64_t)p * dst.rs + s2;
+        *o = accumulate ? *o + alpha * acc : alpha * acc;
     }
 }
 
@@ -549,12 +620,12 @@ static void dwt_level_launch(int nband, int n, int m, View2<T> src, View2<T> ll,
 
 template <typename T, int L>
 static void idwt_level_launch(int nband, int n, int m, View2<T> ll, View2<T> det, View2<T> dst, const WavFilt &f,
-                              cudaStream_t st) {
+                              T alpha, int accumulate, cudaStream_t st) {
     const int tp = (n + DWT_TX - 1) / DWT_TX, ts = (m + DWT_TX - 1) / DWT_TX;
     const size_t sm = idwt_smem<T>(L);
     PFB_CUDA(cudaFuncSetAttribute(k_idwt2_tile<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_idwt2_tile<T, L><<<dim3((unsigned)(tp * ts), (unsigned)nband), 256, sm, st>>>(n, m, ts, ll, det, dst,
-                                                                                   WavTaps<T>(f));
+                                                                                   WavTaps<T>(f), alpha, accumulate);
     check_launch("idwt");
 }
 
@@ -588,10 +659,11 @@ static void dwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, const 
     }
 }
 
-// out = inverse multi-level DWT of coef (Mallat layout); tmp as for dwt2.
+// out = alpha * inverse multi-level DWT of coef (Mallat layout), or out += that with accumulate;
+// tmp as for dwt2.
 template <typename T>
-static void idwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, const T *coef, T *out, T *tmp,
-                  cudaStream_t st) {
+static void idwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, const T *coef, T *out, T *tmp, T alpha,
+                  bool accumulate, cudaStream_t st) {
     const int64_t full = (int64_t)nx * ny, quarter = (int64_t)(nx / 2) * (ny / 2);
     const View2<T> det{const_cast<T *>(coef), full, ny};
     View2<T> ll = det;
@@ -599,7 +671,8 @@ static void idwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, const
         const int n = nx >> lv, m = ny >> lv;
         const View2<T> dst = lv == 0 ? View2<T>{out, full, ny}
                                      : View2<T>{tmp + (lv & 1) * nband * quarter, (int64_t)n * m, m};
-#define PFB_IDWT_CALL(LV) idwt_level_launch<T, LV>(nband, n, m, ll, det, dst, f, st)
+#define PFB_IDWT_CALL(LV) \
+    idwt_level_launch<T, LV>(nband, n, m, ll, det, dst, f, lv == 0 ? alpha : (T)1, lv == 0 && accumulate, st)
         PFB_TAPS_SWITCH(f.L, PFB_IDWT_CALL)
 #undef PFB_IDWT_CALL
         ll = dst;
@@ -607,24 +680,27 @@ static void idwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, const
 }
 
 // primal update for a general dictionary: x~ = max(0, x - tau (grad + psiv)),
-// u = 2 x~ - x (kept for the dual update), x = x~
+// u = 2 x~ - x (kept for the dual update), x = x~   (blockIdx.y = band, blocks stride over rows)
 template <typename T>
-__global__ void k_pd_primal(int nx, int ny, int nband, const T *__restrict__ big, const T *__restrict__ xbar,
+__global__ void k_pd_primal(int nx, int ny, const T *__restrict__ big, const T *__restrict__ xbar,
                             const T *__restrict__ psiv, T sigma, T gamma, const double *__restrict__ sc,
-                            double inv_wbar, double unorm_fixed, T *__restrict__ x, T *__restrict__ u) {
-    const int64_t npix = (int64_t)nx * ny;
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= npix * nband) return;
-    const double unorm = unorm_fixed > 0 ? unorm_fixed : sc[S_UNORM_IDX] * inv_wbar + (double)sigma;
-    const T tau = (T)(0.98 / (0.5 * unorm / (double)gamma + 1.0));
-    const int64_t b = e / npix, q = e - b * npix;
-    const int64_t i = q / ny, j = q - i * ny;
-    const T xv = x[e];
-    const T grad = (big[(b * 2 * nx + i) * 2 * ny + j] + sigma * (xv - xbar[e])) / gamma;
-    T xn = xv - tau * (grad + psiv[e]);
-    xn = xn > 0 ? xn : 0;
-    u[e] = 2 * xn - xv;
-    x[e] = xn;
+                            T *__restrict__ x, T *__restrict__ u) {
+    const int b = blockIdx.y;
+    const T tau = (T)sc[S_TAU];
+    for (int i = blockIdx.x; i < nx; i += gridDim.x) {
+        const T *brow = big + ((int64_t)b * 2 * nx + i) * 2 * ny;
+        const int64_t e0 = ((int64_t)b * nx + i) * ny;
+#pragma unroll 4
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+            const int64_t e = e0 + j;
+            const T xv = x[e];
+            const T grad = (brow[j] + sigma * (xv - xbar[e])) / gamma;
+            T xn = xv - tau * (grad + psiv[e]);
+            xn = xn > 0 ? xn : 0;
+            u[e] = 2 * xn - xv;
+            x[e] = xn;
+        }
+    }
 }
 
 // dual update of one basis: v~ = v + c * s (s = 1/sqrt(K)), projected onto the l2
@@ -645,25 +721,26 @@ __global__ void k_pd_dual(int64_t npix, int nband, const T *__restrict__ c, T s,
     for (int b = 0; b < nband; ++b) v[b * npix + q] = vt[b] * f;
 }
 
+// y = a x, or y += a x with accumulate
 template <typename T>
-__global__ void k_axpy(int64_t n, T a, const T *__restrict__ x, T *__restrict__ y) {
+__global__ void k_axpy(int64_t n, T a, const T *__restrict__ x, int accumulate, T *__restrict__ y) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < n) y[e] += a * x[e];
+    if (e < n) y[e] = accumulate ? y[e] + a * x[e] : a * x[e];
 }
 
 // sum_q ||coef[:, q]||_2 over bands (for the l2,1 term of the objective)
 template <typename T>
 __global__ void k_l21(int64_t npix, int nband, const T *__restrict__ c, double scale, double *__restrict__ out) {
-    double acc = 0;
+    Acc<T> acc;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npix; q += (int64_t)gridDim.x * blockDim.x) {
-        double g2 = 0;
+        T g2 = 0;
         for (int b = 0; b < nband; ++b) {
-            const double v = (double)c[b * npix + q];
+            const T v = c[b * npix + q];
             g2 += v * v;
         }
-        acc += sqrt(g2);
+        acc.add(sqrt(g2));
     }
-    block_sum_atomic(acc * scale, out);
+    block_sum_atomic(acc.value() * scale, out);
 }
 
 // ------------------------------------------------------------------ spectrum cache
@@ -676,7 +753,10 @@ static cx_t<T> *psf_spectrum(Ctx &ctx, int nx, int ny, int nband, const T *psf, 
     const int64_t NX = 2 * nx, NY = 2 * ny, NH = NY / 2 + 1;
     PsfSpec s;
     s.psf = psf; s.nx = nx; s.ny = ny; s.nband = nband; s.prec = prec;
-    s.bytes = (size_t)nband * NX * NH * sizeof(cx_t<T>);
+    // the complex spectrum, then its real part (the spectrum of the symmetrised PSF, which is
+    // all that U and ||U|| read)
+    const int64_t ns = nband * NX * NH;
+    s.bytes = (size_t)ns * (sizeof(cx_t<T>) + sizeof(T));
     s.spec = ctx.dalloc(s.bytes);
     T *shifted = (T *)ctx.scratch("img_pad", (size_t)nband * NX * NY * sizeof(T));
     const int64_t n = nband * NX * NY;
@@ -685,6 +765,9 @@ static cx_t<T> *psf_spectrum(Ctx &ctx, int nx, int ny, int nband, const T *psf, 
     cufftHandle h = ctx.fft((int)NX, (int)NY, nband, RFft<T>::r2c);
     PFB_CUFFT(cufftSetStream(h, st));
     PFB_CUFFT(RFft<T>::fwd(h, shifted, (cx_t<T> *)s.spec));
+    k_real_part<T><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(ns, (const cx_t<T> *)s.spec,
+                                                                 (T *)((cx_t<T> *)s.spec + ns));
+    check_launch("real_part");
     if (ctx.spectra.size() >= 4) {
         ctx.dfree(ctx.spectra.front().spec, ctx.spectra.front().bytes);
         ctx.spectra.erase(ctx.spectra.begin());
@@ -693,24 +776,40 @@ static cx_t<T> *psf_spectrum(Ctx &ctx, int nx, int ny, int nband, const T *psf, 
     return (cx_t<T> *)s.spec;
 }
 
-// padded real [nband][2nx][2ny] -> (conv with S) -> padded real, in place
+// real part of the cached spectrum S of [nband][2nx][ny+1] values (stored right after S)
+template <typename T> static const T *spec_re(const cx_t<T> *S, int nx, int ny, int nband) {
+    return (const T *)(S + (int64_t)nband * 2 * nx * (ny + 1));
+}
+
+// padded real [nband][2nx][2ny] -> (conv with S, or with Re S when sym) -> padded real, in place
 template <typename T>
 static void conv_padded(Ctx &ctx, int nx, int ny, int nband, T *padded, const cx_t<T> *S, T scale, bool sym,
                         cudaStream_t st) {
     const int64_t NX = 2 * nx, NY = 2 * ny, NH = NY / 2 + 1;
     cx_t<T> *X = (cx_t<T> *)ctx.scratch("img_spec", (size_t)nband * NX * NH * sizeof(cx_t<T>));
-    // algorithmic bytes: the padded image in and out, the half spectrum written, read twice and the cached
-    // PSF spectrum read
-    KTimer tm(ctx, "img_conv", st, (double)nband * NX * (2.0 * NY * sizeof(T) + 4.0 * NH * sizeof(cx_t<T>)), 1);
+    // algorithmic bytes: the padded image in and out, the half spectrum written and read twice, and the
+    // cached PSF spectrum read (its real part alone when sym)
+    KTimer tm(ctx, "img_conv", st,
+              (double)nband * NX * (2.0 * NY * sizeof(T) + 3.0 * NH * sizeof(cx_t<T>) +
+                                    NH * (sym ? sizeof(T) : sizeof(cx_t<T>))), 1);
     cufftHandle hf = ctx.fft((int)NX, (int)NY, nband, RFft<T>::r2c);
     PFB_CUFFT(cufftSetStream(hf, st));
     PFB_CUFFT(RFft<T>::fwd(hf, padded, X));
     const int64_t ns = nband * NX * NH;
-    k_spec_mul<T><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(ns, S, scale, sym ? 1 : 0, X);
+    if (sym)
+        k_spec_mul_re<T><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(ns, spec_re<T>(S, nx, ny, nband), scale, X);
+    else
+        k_spec_mul<T><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(ns, S, scale, X);
     check_launch("spec_mul");
     cufftHandle hi = ctx.fft((int)NX, (int)NY, nband, RFft<T>::c2r);
     PFB_CUFFT(cufftSetStream(hi, st));
     PFB_CUFFT(RFft<T>::inv(hi, X, padded));
+}
+
+// grid of the row kernels: blockIdx.y = band, about 8 CTAs per SM in all, each striding over rows
+static dim3 row_grid(const Ctx &ctx, int rows, int nband) {
+    const int per_band = std::max(1, (8 * ctx.num_sms + nband - 1) / nband);
+    return dim3((unsigned)std::min(rows, per_band), (unsigned)nband);
 }
 
 template <typename T>
@@ -719,15 +818,19 @@ void op_psf_conv(Ctx &ctx, int nx, int ny, int nband, const T *psf, const T *x, 
     cx_t<T> *S = psf_spectrum<T>(ctx, nx, ny, nband, psf, st);
     T *padded = (T *)ctx.scratch("img_pad", (size_t)nband * NX * NY * sizeof(T));
     const int64_t nb = nband * NX * NY;
-    k_pad<T><<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(nx, ny, nband, x, (const T *)nullptr, padded);
+    k_pad<T><<<row_grid(ctx, 2 * nx, nband), 256, 0, st>>>(nx, ny, x, (const T *)nullptr, padded);
     check_launch("pad");
     conv_padded<T>(ctx, nx, ny, nband, padded, S, (T)(1.0 / (double)(NX * NY)), false, st);
     const int64_t n = (int64_t)nband * nx * ny;
-    k_crop<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nx, ny, nband, padded, y);
+    k_crop<T><<<row_grid(ctx, nx, nband), 256, 0, st>>>(nx, ny, padded, y);
     check_launch("crop");
 }
 
 static unsigned rblocks(int64_t n, int cap) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, cap)); }
+// grid of the per-band reductions: blockIdx.y = band, about 8 CTAs of 256 threads per SM in all
+static dim3 band_grid(const Ctx &ctx, int64_t npix, int nband) {
+    return dim3(rblocks(npix, std::max(1, 8 * ctx.num_sms / nband)), (unsigned)nband);
+}
 
 template <typename T>
 void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const T *dirty, const T *psf,
@@ -769,10 +872,10 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
     // 1. one exact Hessian application: H x_k = R^dagger W R x_k (Eq. 3), or with
     //    PFB_STEP_APPROX_GRADIENT its stand-in of Eq. 4, I^psf * x_k (plain, not symmetrised)
     if (prm.flags & PFB_STEP_APPROX_GRADIENT) {
-        k_pad<T><<<(unsigned)((nbig + 255) / 256), 256, 0, st>>>(nx, ny, nb, x, (const T *)nullptr, padded);
+        k_pad<T><<<row_grid(ctx, 2 * nx, nb), 256, 0, st>>>(nx, ny, x, (const T *)nullptr, padded);
         check_launch("approx_pad");
         conv_padded<T>(ctx, nx, ny, nb, padded, S, (T)(1.0 / (double)(NX * NY)), false, st);
-        k_crop<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nx, ny, nb, padded, hx);
+        k_crop<T><<<row_grid(ctx, nx, nb), 256, 0, st>>>(nx, ny, padded, hx);
         check_launch("approx_crop");
     } else {
         cx_t<T> *vis = (cx_t<T> *)ctx.scratch("st_vis", (size_t)p.nrow * p.nchan * sizeof(cx_t<T>));
@@ -781,8 +884,7 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
     }
     // 2. IR = (I^d - H x_k) / wbar
     {
-        dim3 gr(rblocks(npix, 2 * ctx.num_sms), nb);
-        k_residual<T><<<gr, 256, 0, st>>>(npix, dirty, hx, x, inv_wbar, ir, sc, bb);
+        k_residual<T><<<band_grid(ctx, npix, nb), 256, 0, st>>>(npix, dirty, hx, x, inv_wbar, ir, sc, bb);
         check_launch("residual");
     }
     // objective's l2,1 term at x_k: ||Psi^dagger x_k||_{2,1} (Psi normalised by 1/sqrt(K))
@@ -807,7 +909,7 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
             dwt2<T>(nx, ny, nb, prm.nlevel, wav_filter(k), x, wa, wb, st);
             coef = wa;
         }
-        k_l21<T><<<rblocks(npix, 2 * ctx.num_sms), 256, 0, st>>>(npix, nb, coef, inv_sqrt_k, &sc[S_L21]);
+        k_l21<T><<<rblocks(npix, 8 * ctx.num_sms), 256, 0, st>>>(npix, nb, coef, inv_sqrt_k, &sc[S_L21]);
         check_launch("l21");
     }
     // 3. CG for U delta = IR (per band)
@@ -816,18 +918,16 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
     k_cg_init<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ir, delta, r, pp);
     check_launch("cg_init");
     PFB_CUDA(cudaMemcpyAsync(RR, bb, nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    k_pad<T><<<(unsigned)((nbig + 255) / 256), 256, 0, st>>>(nx, ny, nb, pp, (const T *)nullptr, padded);
+    k_pad<T><<<row_grid(ctx, 2 * nx, nb), 256, 0, st>>>(nx, ny, pp, (const T *)nullptr, padded);
     check_launch("cg_pad");
     for (int it = 0; it < iters; ++it) {
         double *rr = RR + (size_t)it * nb, *rrn = RR + (size_t)(it + 1) * nb, *pap = PAP + (size_t)it * nb;
         conv_padded<T>(ctx, nx, ny, nb, padded, S, conv_scale, true, st);
-        dim3 g1(rblocks(npix, 2 * ctx.num_sms), nb);
-        k_cg_ap<T><<<g1, 256, 0, st>>>(nx, ny, padded, pp, sigma, ap, pap);
+        k_cg_ap<T><<<row_grid(ctx, nx, nb), 256, 0, st>>>(nx, ny, padded, pp, sigma, ap, pap);
         check_launch("cg_ap");
-        k_cg_update<T><<<g1, 256, 0, st>>>(npix, pp, ap, rr, pap, bb, tol2, delta, r, rrn);
+        k_cg_update<T><<<band_grid(ctx, npix, nb), 256, 0, st>>>(npix, pp, ap, rr, pap, bb, tol2, delta, r, rrn);
         check_launch("cg_update");
-        dim3 gp(rblocks(NX * NY, 4 * ctx.num_sms), nb);
-        k_cg_dir<T><<<gp, 256, 0, st>>>(nx, ny, r, rr, rrn, bb, tol2, pp, padded);
+        k_cg_dir<T><<<row_grid(ctx, 2 * nx, nb), 256, 0, st>>>(nx, ny, r, rr, rrn, bb, tol2, pp, padded);
         check_launch("cg_dir");
     }
     // 4. x_{k+1/2} = x_k + gamma delta; primal start max(x_{k+1/2}, 0)
@@ -836,10 +936,13 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
     // 5. prox (Eq. 7) by Condat-Vu
     if (prm.unorm <= 0) {
         const int64_t ns = nb * NX * (NY / 2 + 1);
-        k_absmax_re<T><<<rblocks(ns, 4 * ctx.num_sms), 256, 0, st>>>(ns, S, (unsigned long long *)&sc[S_UNORM]);
+        k_absmax<T><<<rblocks(ns, 4 * ctx.num_sms), 256, 0, st>>>(ns, spec_re<T>(S, nx, ny, nb),
+                                                                   (unsigned long long *)&sc[S_UNORM]);
         check_launch("absmax");
     }
     const double unorm_fixed = prm.unorm > 0 ? prm.unorm : -1.0;
+    k_pd_tau<<<1, 1, 0, st>>>(sc, inv_wbar, (double)sigma, prm.gamma, unorm_fixed);
+    check_launch("pd_tau");
     T *psiv = nullptr, *ubuf = nullptr;
     if (prm.basis_mask != 1u) {
         psiv = (T *)ctx.scratch("st_psiv", img);
@@ -847,32 +950,28 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
     }
     const unsigned gn = (unsigned)((n + 255) / 256);
     for (int it = 0; it < prm.pd_iters; ++it) {
-        k_pad<T><<<(unsigned)((nbig + 255) / 256), 256, 0, st>>>(nx, ny, nb, xk1, xbar, padded);
+        k_pad<T><<<row_grid(ctx, 2 * nx, nb), 256, 0, st>>>(nx, ny, xk1, xbar, padded);
         check_launch("pd_pad");
         conv_padded<T>(ctx, nx, ny, nb, padded, S, conv_scale, true, st);
         if (prm.basis_mask == 1u) {   // Dirac only: one fused kernel
-            k_pd_dirac<T><<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(
-                nx, ny, nb, padded, xbar, sigma, (T)prm.gamma, (T)prm.lambda, sc, inv_wbar, unorm_fixed, xk1, dual);
+            k_pd_dirac<T><<<row_grid(ctx, nx, 1), 256, 0, st>>>(nx, ny, nb, padded, xbar, sigma, (T)prm.gamma,
+                                                                (T)prm.lambda, sc, xk1, dual);
             check_launch("pd_dirac");
             continue;
         }
-        // Psi v = sum_k Psi_k v_k / sqrt(K)
-        PFB_CUDA(cudaMemsetAsync(psiv, 0, img, st));
+        // Psi v = sum_k Psi_k v_k / sqrt(K): the first basis writes psiv, the others add to it
         for (int t = 0; t < K; ++t) {
             T *vk = dual + (size_t)t * n;
             if (bases[t] == 0) {
-                k_axpy<T><<<gn, 256, 0, st>>>(n, (T)inv_sqrt_k, vk, psiv);
+                k_axpy<T><<<gn, 256, 0, st>>>(n, (T)inv_sqrt_k, vk, t > 0 ? 1 : 0, psiv);
+                check_launch("psi");
             } else {
-                {
-                    KTimer tm(ctx, "idwt", st, dwt_bytes, prm.nlevel);
-                    idwt2<T>(nx, ny, nb, prm.nlevel, wav_filter(bases[t]), vk, wa, wb, st);
-                }
-                k_axpy<T><<<gn, 256, 0, st>>>(n, (T)inv_sqrt_k, wa, psiv);
+                KTimer tm(ctx, "idwt", st, dwt_bytes + (t > 0 ? (double)img : 0.0), prm.nlevel);
+                idwt2<T>(nx, ny, nb, prm.nlevel, wav_filter(bases[t]), vk, psiv, wa, (T)inv_sqrt_k, t > 0, st);
             }
-            check_launch("psi");
         }
-        k_pd_primal<T><<<gn, 256, 0, st>>>(nx, ny, nb, padded, xbar, psiv, sigma, (T)prm.gamma, sc, inv_wbar,
-                                           unorm_fixed, xk1, ubuf);
+        k_pd_primal<T><<<row_grid(ctx, nx, nb), 256, 0, st>>>(nx, ny, padded, xbar, psiv, sigma, (T)prm.gamma, sc,
+                                                              xk1, ubuf);
         check_launch("pd_primal");
         // v_k = proj(v_k + Psi_k^dagger (2 x~ - x) / sqrt(K))
         for (int t = 0; t < K; ++t) {
@@ -888,7 +987,7 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
         }
     }
     // 6. statistics and output
-    k_finish<T><<<rblocks(npix, 2 * ctx.num_sms), 256, 0, st>>>(npix, nb, xk1, x, sc);
+    k_finish<T><<<band_grid(ctx, npix, nb), 256, 0, st>>>(npix, xk1, x, sc);
     check_launch("finish");
     if (stats_h) {
         std::vector<double> h(nsc);

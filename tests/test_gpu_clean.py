@@ -1,5 +1,7 @@
 """The whole solve (pfb_clean) and the approximate-gradient step (Eq. 4) through the
 C ABI against the FP64 oracle, on the same seeded inputs and iteration counts."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -57,6 +59,48 @@ def test_approx_gradient_step(ctx, prec):
     assert rel_l2(xg.cpu().numpy(), x1) <= tol
     assert rel_l2(vg.cpu().numpy(), v1) <= tol
     assert stg[0] == pytest.approx(st[0], rel=tol)
+
+
+@functools.lru_cache(maxsize=None)
+def _large_case(mask):
+    nx, ny, nb = 1288, 1000, 2
+    obs = synth.tiny_observation(nx=32, ny=32, nband=nb)
+    rng = np.random.default_rng(203)
+    ws = np.array([1.0, 1.25])
+    ii = np.arange(2 * nx)[:, None] - nx
+    jj = np.arange(2 * ny)[None, :] - ny
+    beam = np.exp(-(ii * ii + jj * jj) / (2.0 * 2.5 ** 2))
+    p = ws[:, None, None] * beam[None]
+    xt = synth.point_source_image(rng, nb, nx, ny, 60)
+    d = oracle.psf_conv(p, xt) + 1e-3 * rng.normal(size=(nb, nx, ny))
+    x0 = 0.5 * xt
+    v0 = np.zeros((bin(mask).count("1"), nb, nx, ny))
+    w = synth.uniform_weights(rng, (obs.nrow, obs.nchan))
+    _, op = _params(approx_gradient=True, cg_iters=4, pd_iters=4, basis_mask=mask)
+    ref = oracle.step(obs.uvw, obs.freq, obs.band_of_chan, w, d, p, ws, x0, v0, obs.dl, obs.dm, op)
+    return obs, w, ws, p, d, x0, v0, ref
+
+
+@pytest.mark.parametrize("prec,mask", [(32, 1), (32, 0b1111111), (64, 0b1111111)])
+def test_approx_gradient_step_large(ctx, prec, mask):
+    """The image side of a step (PSF convolution, CG, primal-dual with Dirac + db1..db6) at
+    1288 x 1000 pixels: more rows than the image kernels launch CTAs per band, so every
+    CTA strides over several rows, and 1000-pixel rows leave a ragged tail of 232 threads.
+    The PSF is a Gaussian beam (a positive spectrum, so U is positive definite); the
+    dirty image its convolution with point sources plus noise."""
+    nx, ny, nb = 1288, 1000, 2
+    obs, w, ws, p, d, x0, v0, (x1, v1, st) = _large_case(mask)
+    gp, _ = _params(approx_gradient=True, cg_iters=4, pd_iters=4, basis_mask=mask)
+    from paper_2101_08072_gb300 import Geometry
+    g = Geometry(nx=nx, ny=ny, dl=obs.dl, dm=obs.dm, nband=nb, epsilon=EPS32 if prec == 32 else EPS64)
+    xg, vg = real_t(x0, prec), real_t(v0, prec)
+    nh, stg = ctx.pfb_step(g, gp, *dev_obs(obs), real_t(w, prec), real_t(d, prec), real_t(p, prec), ws, xg, vg)
+    tol = 1e-4 if prec == 32 else 1e-8
+    assert nh == 0
+    assert rel_l2(xg.cpu().numpy(), x1) <= tol
+    assert rel_l2(vg.cpu().numpy(), v1) <= tol
+    assert stg[0] == pytest.approx(st[0], rel=tol)
+    assert stg[1] == pytest.approx(st[1], rel=10 * tol)
 
 
 @pytest.mark.parametrize("prec,mask", [(32, 1), (64, 1), (64, 0b101)])

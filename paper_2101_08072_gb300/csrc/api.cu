@@ -116,7 +116,7 @@ cufftHandle Ctx::fft(int n0, int n1, int batch, cufftType type) {
         PFB_CUFFT(cufftCreate(&h));
         PFB_CUFFT(cufftSetAutoAllocation(h, 0));
         int n[2] = {n0, n1};
-        cufftResult r = cufftMakePlanMany(h, 2, n, nullptr, 1, 0, nullptr, 1, 0, type, batch, &ws);
+        cufftResult r = cufftMakePlanMany(h, n1 > 0 ? 2 : 1, n, nullptr, 1, 0, nullptr, 1, 0, type, batch, &ws);
         if (r != CUFFT_SUCCESS) {
             cufftDestroy(h);
             throw Error(PFB_ERR_CUDA, "cufftMakePlanMany failed: " + std::to_string((int)r));

@@ -1,0 +1,260 @@
+// Column pass of the FP32 w-plane transforms.  A 2-D DFT of a plane is a pass of 1-D DFTs along the
+// rows and one along the columns.  cuFFT's 2-D plans take two passes over the plane for the columns;
+// this kernel takes one, and it touches only the image region: the pre-pass puts pixel (i, j) at
+// ((i - nx/2) mod Nu, (j - ny/2) mod Nv), so only the columns [0, ny/2) and [Nv - ny/2, Nv) and the rows
+// [0, nx/2) and [Nu - nx/2, Nu) carry data into the forward transform, and the post-pass reads back
+// only that region of the inverse transform.
+//   forward (degridding): this pass first, reading the image rows of the image columns (the other rows
+//            are zero) and writing whole columns; then the row pass (cuFFT, all rows);
+//   inverse (gridding): the row pass first (cuFFT, all rows); then this pass, reading whole image
+//            columns and writing back their image rows only.
+// One CTA transforms two adjacent columns of one plane (a 16-byte element per row) of length N = 2^L,
+// 10 <= L <= 13, with N/16 threads.  The algorithm is the mixed-radix Stockham autosort DFT (radix-16
+// stages, the last of radix 2, 4 or 8 when L is not a multiple of 4) in the formulation of Govindaraju
+// et al., "High performance discrete Fourier transforms on graphics processors" (SC 2008): stage s with
+// radix R and Ns = product of the earlier radices takes, for butterfly j < N/R, the inputs
+// x[j + r N/R] (r < R), multiplies input r by exp(-/+ 2 pi i r (j mod Ns) / (Ns R)), applies an R-point
+// DFT and writes output r to y[(j div Ns) Ns R + (j mod Ns) + r Ns].  The first stage reads the plane,
+// the last writes it; the stages between go through shared memory (one buffer, the reads of a stage
+// finished before its writes, indexed i + i/16 so that the strided writes of the first stage do not
+// conflict on banks).  The R-point DFTs run in registers: 16 = 4 x 4 and 8 = 4 x 2 by the Cooley-Tukey
+// split n = R2 n1 + n2, k = k1 + R1 k2 with the twiddles exp(-/+ 2 pi i n2 k1 / R) in between.
+#include "ctx.cuh"
+
+namespace pfb {
+namespace {
+
+__device__ __forceinline__ float4 c_add(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 c_sub(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+// both complex values of a times w
+__device__ __forceinline__ float4 c_mul(float4 a, float2 w) {
+    return make_float4(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x, a.z * w.x - a.w * w.y, a.z * w.y + a.w * w.x);
+}
+// times -i (forward sign) or +i (inverse sign)
+template <bool INV> __device__ __forceinline__ float4 c_rot(float4 a) {
+    return INV ? make_float4(-a.y, a.x, -a.w, a.z) : make_float4(a.y, -a.x, a.w, -a.z);
+}
+
+// cos(2 pi e / 16), from cos(pi/8), sin(pi/8) and sqrt(1/2); sin(2 pi e / 16) = cos16(e - 4)
+constexpr double kC8 = 0.92387953251128675613, kS8 = 0.38268343236508977173, kR2 = 0.70710678118654752440;
+__host__ __device__ constexpr double cos16(int e) {
+    return (e & 15) == 0 ? 1.0 : (e & 15) == 1 ? kC8 : (e & 15) == 2 ? kR2 : (e & 15) == 3 ? kS8
+         : (e & 15) == 4 ? 0.0 : (e & 15) == 5 ? -kS8 : (e & 15) == 6 ? -kR2 : (e & 15) == 7 ? -kC8
+         : (e & 15) == 8 ? -1.0 : (e & 15) == 9 ? -kC8 : (e & 15) == 10 ? -kR2 : (e & 15) == 11 ? -kS8
+         : (e & 15) == 12 ? 0.0 : (e & 15) == 13 ? kS8 : (e & 15) == 14 ? kR2 : kC8;
+}
+
+// a times exp(-/+ 2 pi i e / R), R in {8, 16}; e is a compile-time constant once the loops unroll
+template <int R, bool INV> __device__ __forceinline__ float4 c_tw(float4 a, int e) {
+    const int f = (e * (16 / R)) & 15;
+    if (f == 0) return a;
+    if (f == 8) return make_float4(-a.x, -a.y, -a.z, -a.w);
+    if (f == 4) return c_rot<INV>(a);
+    if (f == 12) return c_rot<!INV>(a);
+    const float c = (float)cos16(f), s = (float)cos16(f - 4);
+    return c_mul(a, make_float2(c, INV ? s : -s));
+}
+
+template <bool INV> __device__ __forceinline__ void dft2(float4 &x0, float4 &x1) {
+    const float4 a = c_add(x0, x1);
+    x1 = c_sub(x0, x1);
+    x0 = a;
+}
+template <bool INV> __device__ __forceinline__ void dft4(float4 &x0, float4 &x1, float4 &x2, float4 &x3) {
+    const float4 a0 = c_add(x0, x2), a1 = c_sub(x0, x2), a2 = c_add(x1, x3), a3 = c_rot<INV>(c_sub(x1, x3));
+    x0 = c_add(a0, a2);
+    x1 = c_add(a1, a3);
+    x2 = c_sub(a0, a2);
+    x3 = c_sub(a1, a3);
+}
+
+// R-point DFT of x[0..R) in registers; output k ends up in x[operm<R>(k)]
+template <int R> __device__ __forceinline__ constexpr int operm(int k) {
+    return R == 16 ? 4 * (k & 3) + (k >> 2) : R == 8 ? 2 * (k & 3) + (k >> 2) : k;
+}
+template <int R, bool INV> __device__ __forceinline__ void dft_reg(float4 *x) {
+    if constexpr (R == 2) {
+        dft2<INV>(x[0], x[1]);
+    } else if constexpr (R == 4) {
+        dft4<INV>(x[0], x[1], x[2], x[3]);
+    } else if constexpr (R == 8) {   // n = 2 n1 + n2: DFT4 over n1, twiddle W8^(n2 k1), DFT2 over n2
+#pragma unroll
+        for (int n2 = 0; n2 < 2; ++n2) dft4<INV>(x[n2], x[2 + n2], x[4 + n2], x[6 + n2]);
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1) x[2 * k1 + 1] = c_tw<8, INV>(x[2 * k1 + 1], k1);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) dft2<INV>(x[2 * k1], x[2 * k1 + 1]);
+    } else {   // 16: n = 4 n1 + n2: DFT4 over n1, twiddle W16^(n2 k1), DFT4 over n2
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
+#pragma unroll
+        for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+            for (int k1 = 1; k1 < 4; ++k1) x[4 * k1 + n2] = c_tw<16, INV>(x[4 * k1 + n2], n2 * k1);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+    }
+}
+
+__host__ __device__ constexpr int spad(int i) { return i + (i >> 4); }
+
+// twiddle exp(-/+ 2 pi i m / N) from the table of exp(-2 pi i m / N)
+template <bool INV> __device__ __forceinline__ float2 twiddle(const float2 *__restrict__ W, int m) {
+    float2 w = __ldg(W + m);
+    if (INV) w.y = -w.y;
+    return w;
+}
+__device__ __forceinline__ float2 c_mul1(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Inputs r = 1..R-1 of a butterfly times w^r, w = exp(-/+ 2 pi i k step / N).  w and (for R >= 8) w^4
+// come from the table, the other powers from products of at most three of them (w^r = w^h w^(r-h),
+// h the largest power of two below r): two gathered loads instead of R - 1, and a twiddle error of a
+// few units in the last place, about the table's own rounding.
+template <int R, bool INV>
+__device__ __forceinline__ void apply_twiddles(float4 *v, const float2 *__restrict__ W, int k, int step) {
+    float2 w[R];
+    w[1] = twiddle<INV>(W, k * step);
+    if (R >= 8) w[4 % R] = twiddle<INV>(W, 4 * k * step);
+#pragma unroll
+    for (int r = 2; r < R; ++r) {
+        if (R >= 8 && r == 4) continue;
+        const int h = r >= 8 ? 8 : r >= 4 ? 4 : 2;
+        w[r] = h == r ? c_mul1(w[r / 2], w[r / 2]) : c_mul1(w[h], w[r - h]);
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], w[r]);
+}
+
+// Forward: rows outside the image rows read as zero, all rows written; inverse: all rows read, the
+// image rows written.  A CTA takes its column pair through all planes in turn, so the stores of one
+// plane drain while the loads of the next are in flight.
+template <int L, bool INV>
+__global__ void __launch_bounds__((1 << L) / 16) k_colfft(float2 *__restrict__ data, int nplanes, int Nv,
+                                                          int64_t plane_sz, int nx, int ny,
+                                                          const float2 *__restrict__ W) {
+    constexpr int N = 1 << L, T = N / 16;
+    constexpr int NST16 = L / 4, RL = (L % 4) ? (1 << (L % 4)) : 16, BPT = 16 / RL;
+    constexpr int NMID = NST16 - 1 - ((L % 4) ? 0 : 1);   // radix-16 stages between the first and last
+    extern __shared__ float4 sm[];
+    const int tid = threadIdx.x;
+    const int q = blockIdx.x, hq = ny / 4;
+    const int c = q < hq ? 2 * q : Nv - ny / 2 + 2 * (q - hq);
+    const int rlo = nx / 2, rhi = N - nx / 2;
+    float4 v[16];
+
+    for (int pl = 0; pl < nplanes; ++pl) {
+        float2 *base = data + (int64_t)pl * plane_sz + c;
+        // first stage (radix 16, Ns = 1: no twiddles), from the plane
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int row = tid + r * T;
+            v[r] = (!INV && row >= rlo && row < rhi) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                     : *reinterpret_cast<const float4 *>(base + (int64_t)row * Nv);
+        }
+        dft_reg<16, INV>(v);
+        __syncthreads();   // the previous plane's last stage has read the buffer
+#pragma unroll
+        for (int r = 0; r < 16; ++r) sm[spad(tid * 16 + r)] = v[operm<16>(r)];
+        __syncthreads();
+
+        int Ns = 16;
+#pragma unroll
+        for (int s = 0; s < NMID; ++s) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = sm[spad(tid + r * T)];
+            const int k = tid & (Ns - 1);
+            apply_twiddles<16, INV>(v, W, k, N / (Ns * 16));
+            dft_reg<16, INV>(v);
+            __syncthreads();
+            const int d = (tid / Ns) * Ns * 16 + k;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) sm[spad(d + r * Ns)] = v[operm<16>(r)];
+            __syncthreads();
+            Ns *= 16;
+        }
+
+        // last stage (radix RL, BPT butterflies per thread), to the plane
+#pragma unroll
+        for (int b = 0; b < BPT; ++b)
+#pragma unroll
+            for (int r = 0; r < RL; ++r) v[b * RL + r] = sm[spad(tid + b * T + r * (N / RL))];
+        const int step = N / (Ns * RL);
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int j = tid + b * T, k = j & (Ns - 1);
+            apply_twiddles<RL, INV>(v + b * RL, W, k, step);
+            dft_reg<RL, INV>(v + b * RL);
+        }
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int j = tid + b * T, k = j & (Ns - 1);
+            const int d = (j / Ns) * Ns * RL + k;
+#pragma unroll
+            for (int r = 0; r < RL; ++r) {
+                const int row = d + r * Ns;
+                if (INV && row >= rlo && row < rhi) continue;
+                *reinterpret_cast<float4 *>(base + (int64_t)row * Nv) = v[b * RL + operm<RL>(r)];
+            }
+        }
+    }
+}
+
+// W[m] = exp(-2 pi i m / n), rounded from double
+__global__ void k_colfft_table(int n, float2 *W) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)m / (double)n, &s, &c);
+    W[m] = make_float2((float)c, (float)-s);
+}
+
+template <int L, bool INV>
+void launch_colfft(float2 *data, int nplanes, int Nv, int64_t plane_sz, int nx, int ny, const float2 *W,
+                   cudaStream_t st) {
+    constexpr int N = 1 << L;
+    const size_t smem = (size_t)(spad(N - 1) + 1) * sizeof(float4);
+    PFB_CUDA(cudaFuncSetAttribute(k_colfft<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_colfft<L, INV><<<(unsigned)(ny / 2), N / 16, smem, st>>>(data, nplanes, Nv, plane_sz, nx, ny, W);
+    check_launch("colfft");
+}
+
+}  // namespace
+
+bool colfft_fits(int Nu, int Nv, int nx, int ny) {
+    int L = 0;
+    while ((1 << L) < Nu) ++L;
+    return (1 << L) == Nu && L >= 10 && L <= 13 && ny % 4 == 0 && nx % 2 == 0 && nx <= Nu && ny <= Nv &&
+           Nv % 2 == 0;
+}
+
+void colfft_planes(Ctx &ctx, float2 *data, int nplanes, int Nu, int Nv, int nx, int ny, bool inverse,
+                   cudaStream_t st) {
+    PFB_REQUIRE(colfft_fits(Nu, Nv, nx, ny), "column transform: unsupported plane shape");
+    const std::string name = "colfft_w" + std::to_string(Nu);
+    float2 *W = (float2 *)ctx.scratch(name, (size_t)Nu * sizeof(float2));
+    auto tag = ctx.zero_tag.find(name);
+    if (tag == ctx.zero_tag.end() || tag->second.first != (uint64_t)Nu) {
+        k_colfft_table<<<(unsigned)((Nu + 255) / 256), 256, 0, st>>>(Nu, W);
+        check_launch("colfft_table");
+        ctx.zero_tag[name] = {(uint64_t)Nu, 1};
+    }
+    const int64_t plane_sz = (int64_t)Nu * Nv;
+#define PFB_COLFFT(LV)                                                                                  \
+    (inverse ? launch_colfft<LV, true>(data, nplanes, Nv, plane_sz, nx, ny, W, st)                      \
+             : launch_colfft<LV, false>(data, nplanes, Nv, plane_sz, nx, ny, W, st))
+    switch (Nu) {
+        case 1024: PFB_COLFFT(10); break;
+        case 2048: PFB_COLFFT(11); break;
+        case 4096: PFB_COLFFT(12); break;
+        default: PFB_COLFFT(13); break;
+    }
+#undef PFB_COLFFT
+}
+
+}  // namespace pfb

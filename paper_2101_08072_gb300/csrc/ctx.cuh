@@ -137,8 +137,9 @@ struct Ctx {
     uint64_t clock = 0;
     std::vector<std::unique_ptr<Plan>> plans;
     std::map<std::string, DevBuf> bufs;
-    // named buffers whose zeros are kept between calls: the plan id (and plane count) they were
-    // cleared for; dropped whenever the buffer is reallocated
+    // named buffers whose contents are kept between calls: for kept zeros the plan id (and plane
+    // count) they were cleared for, for a twiddle table its length; dropped whenever the buffer is
+    // reallocated
     std::map<std::string, std::pair<uint64_t, int>> zero_tag;
     uint64_t plan_serial = 0;
     std::map<FftKey, cufftHandle> ffts;
@@ -154,8 +155,15 @@ struct Ctx {
     size_t available() const { return budget > used ? budget - used : 0; }
     void free_plan(Plan &p);
     void reset();
+    // cached cuFFT plan of `batch` contiguous n0 x n1 transforms (1-D of length n0 when n1 == 0),
+    // bound to the shared work area
     cufftHandle fft(int n0, int n1, int batch, cufftType type);
 };
+
+// colfft.cu: the FP32 column pass of the w-plane transforms over the image region (see there)
+bool colfft_fits(int Nu, int Nv, int nx, int ny);
+void colfft_planes(Ctx &ctx, float2 *data, int nplanes, int Nu, int Nv, int nx, int ny, bool inverse,
+                   cudaStream_t st);
 
 // Scoped timer: records events around the enclosed launches when timing is on.
 // `bytes` is the algorithmic traffic of the enclosed work; `launches` the number

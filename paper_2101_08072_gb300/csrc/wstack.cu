@@ -1030,6 +1030,19 @@ static void fft_planes(Ctx &ctx, cx_t<T> *data, int nplanes, int Nu, int Nv, int
     }
 }
 
+// Row pass of a plane block: 1-D DFTs of length Nv along all nplanes * Nu rows (in -> out, or in place)
+template <typename T>
+static void fft_rows(Ctx &ctx, cx_t<T> *in, cx_t<T> *out, int nplanes, int Nu, int Nv, int dir, cudaStream_t st) {
+    cufftHandle h = ctx.fft(Nv, 0, nplanes * Nu, FftT<T>::c2c);
+    PFB_CUFFT(cufftSetStream(h, st));
+    PFB_CUFFT(FftT<T>::exec(h, in, out, dir));
+}
+
+// FP32 planes whose column pass colfft.cu takes: power-of-two Nu up to 8192, image region aligned
+template <typename T> static bool split_fft(const Plan &p) {
+    return sizeof(T) == 4 && colfft_fits(p.Nu, p.Nv, p.nx, p.ny);
+}
+
 static int plane_block(Ctx &ctx, const Plan &p, size_t cxs, size_t reserve_unused) {
     // keep room for the cuFFT work area of a single-plane transform
     (void)reserve_unused;
@@ -1199,8 +1212,13 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
                 check_launch("prepass");
             }
             {
-                KTimer t(ctx, "fft_fwd", st, 2.0 * nk * plane_bytes, 0);
-                fft_planes<T>(ctx, in, nk, p.Nu, p.Nv, CUFFT_FORWARD, st, keep ? planes : nullptr);
+                KTimer t(ctx, "fft_fwd", st, 2.0 * nk * plane_bytes, split_fft<T>(p) ? 1 : 0);
+                if (split_fft<T>(p)) {   // columns of the image region (in place), then all rows
+                    colfft_planes(ctx, (float2 *)in, nk, p.Nu, p.Nv, p.nx, p.ny, false, st);
+                    fft_rows<T>(ctx, in, planes, nk, p.Nu, p.Nv, CUFFT_FORWARD, st);
+                } else {
+                    fft_planes<T>(ctx, in, nk, p.Nu, p.Nv, CUFFT_FORWARD, st, keep ? planes : nullptr);
+                }
             }
             if (i1 > i0 && sizeof(T) == 4 && degrid_tiles_fit(p)) {
                 KTimer t(ctx, "degrid_tiles", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
@@ -1278,8 +1296,13 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                 check_launch("grid_tiles");
             }
             {
-                KTimer t(ctx, "fft_inv", st, 2.0 * nk * plane_bytes, 0);
-                fft_planes<T>(ctx, in, nk, p.Nu, p.Nv, CUFFT_INVERSE, st, keep ? out : nullptr);
+                KTimer t(ctx, "fft_inv", st, 2.0 * nk * plane_bytes, split_fft<T>(p) ? 1 : 0);
+                if (split_fft<T>(p)) {   // all rows, then the image columns of the image rows (in place)
+                    fft_rows<T>(ctx, in, out, nk, p.Nu, p.Nv, CUFFT_INVERSE, st);
+                    colfft_planes(ctx, (float2 *)out, nk, p.Nu, p.Nv, p.nx, p.ny, true, st);
+                } else {
+                    fft_planes<T>(ctx, in, nk, p.Nu, p.Nv, CUFFT_INVERSE, st, keep ? out : nullptr);
+                }
             }
             {
                 KTimer t(ctx, "postpass", st, npix * (nk * (double)cxs + 2.0 * sizeof(T) + 8.0));

@@ -177,6 +177,20 @@ int pfb_hessian(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, int64_t nrow,
                 const double *uvw, const double *freq, const int32_t *band_of_chan,
                 const void *wgt, const void *x, void *y_out, void *stream);
 
+/* The Hessian of pfb_hessian (Eq. 3) from HOST buffers: uvw, freq, band_of_chan, wgt (may be NULL:
+ * unit weights) and x are read from host memory, y_out is written to host memory; layouts as in
+ * pfb_hessian.  The copies overlap the computation: x goes in first, the weights go in on an internal
+ * copy stream while R x is computed, and each band of y_out comes back as soon as it is gridded.  With
+ * page-locked (pinned) host memory the copies are asynchronous; pageable memory works but loses the
+ * overlap.  The call enqueues work on `stream` (the copy stream is joined back to it); y_out holds the
+ * result once `stream` has been synchronised, and the host buffers must stay valid until then.  The
+ * device copies live in the context's scratch and the plan is built on them; it is reused while the
+ * host pointers of uvw, freq and band_of_chan (and nrow, nchan) stay the same, so call
+ * pfb_plan_reset() when their contents change under the same pointers.  Errors as pfb_hessian. */
+int pfb_hessian_host(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, int64_t nrow, int32_t nchan,
+                     const double *uvw, const double *freq, const int32_t *band_of_chan,
+                     const void *wgt, const void *x, void *y_out, void *stream);
+
 /* PSF convolution (Eq. 4): y_out[b,i,j] = sum_{i',j'} psf[b, i-i'+nx, j-j'+ny] x[b,i',j']
  * (linear convolution, psf [nband][2nx][2ny] as written by pfb_psf).  Uses the
  * geometry's nx, ny, nband only.  The PSF spectrum is cached per psf pointer. */

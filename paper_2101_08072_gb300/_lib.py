@@ -22,7 +22,8 @@ ERRORS = {
 
 # every function the header declares (the CPU test checks the library exports them)
 EXPORTS = ["pfb_create", "pfb_destroy", "pfb_last_error", "pfb_plan_reset", "pfb_degrid", "pfb_grid",
-           "pfb_dirty", "pfb_psf", "pfb_hessian", "pfb_psf_conv", "pfb_step", "pfb_clean", "pfb_version",
+           "pfb_dirty", "pfb_psf", "pfb_hessian", "pfb_hessian_host", "pfb_psf_conv", "pfb_step", "pfb_clean",
+           "pfb_version",
            "pfb_timing", "pfb_timing_read", "pfb_timing_names", "pfb_wsum_static", "pfb_kernel_support"]
 
 
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH):
     lib.pfb_dirty.argtypes = [P, G, ctypes.c_int, *data, P, P, P, ctypes.POINTER(D), P]
     lib.pfb_psf.argtypes = [P, G, ctypes.c_int, *data, P, P, ctypes.POINTER(D), P]
     lib.pfb_hessian.argtypes = [P, G, ctypes.c_int, *data, P, P, P, P]
+    lib.pfb_hessian_host.argtypes = [P, G, ctypes.c_int, *data, P, P, P, P]
     lib.pfb_psf_conv.argtypes = [P, G, ctypes.c_int, P, P, P, P]
     lib.pfb_step.argtypes = [P, G, ctypes.c_int, ctypes.POINTER(pfb_params), *data, P, P, P,
                              ctypes.POINTER(D), P, P, ctypes.POINTER(I64), ctypes.POINTER(D), P]

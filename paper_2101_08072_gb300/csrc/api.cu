@@ -21,6 +21,24 @@ Ctx::~Ctx() {
     bufs.clear();
     for (auto &kv : ffts) cufftDestroy(kv.second);
     ffts.clear();
+    for (cudaEvent_t e : copy_events) cudaEventDestroy(e);
+    copy_events.clear();
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    copy_stream = nullptr;
+}
+
+cudaStream_t Ctx::copy_stream_get() {
+    if (!copy_stream) PFB_CUDA(cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking));
+    return copy_stream;
+}
+
+cudaEvent_t Ctx::copy_event(size_t i) {
+    while (copy_events.size() <= i) {
+        cudaEvent_t e;
+        PFB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        copy_events.push_back(e);
+    }
+    return copy_events[i];
 }
 
 void *Ctx::dalloc(size_t bytes) {
@@ -250,6 +268,67 @@ void run_step(Ctx &c, const Plan &p, pfb_prec prec, const pfb_params &prm, const
 
 }  // namespace
 
+namespace pfb {
+
+// The Hessian from host buffers, with the copies overlapping the computation.  On the caller's stream:
+// uvw, freq, band and x in, the plan, R x of every band, then R^dagger Sigma^-1 band by band.  On the
+// copy stream: the weights once x is in (they are needed only after R x), and band b of the result as
+// soon as its last post-pass has run.  The caller's stream then waits for the copy stream, so work queued
+// after this call (or a synchronisation of the stream) sees the finished result.
+template <typename T>
+static void hessian_host(Ctx &c, const pfb_geom *g, int prec, int64_t nrow, int32_t nchan, const double *uvw,
+                         const double *freq, const int32_t *band, const T *wgt, const T *x, T *y, cudaStream_t st) {
+    const int64_t npix = (int64_t)g->nx * g->ny, nimg = npix * g->nband;
+    double *d_uvw = (double *)c.scratch("host_uvw", (size_t)nrow * 3 * sizeof(double));
+    double *d_freq = (double *)c.scratch("host_freq", (size_t)nchan * sizeof(double));
+    int32_t *d_band = (int32_t *)c.scratch("host_band", (size_t)nchan * sizeof(int32_t));
+    // plans built on the scratch copies belong to the host pointers they were copied from
+    const void *key[3] = {uvw, freq, band};
+    if (std::memcmp(key, c.host_data, sizeof(key)) != 0 || c.host_nrow != nrow || c.host_nchan != nchan) {
+        PFB_CUDA(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < c.plans.size();) {
+            if (c.plans[i]->uvw == d_uvw) {
+                c.free_plan(*c.plans[i]);
+                c.plans.erase(c.plans.begin() + i);
+            } else {
+                ++i;
+            }
+        }
+        std::memcpy(c.host_data, key, sizeof(key));
+        c.host_nrow = nrow;
+        c.host_nchan = nchan;
+    }
+    T *d_x = (T *)c.scratch("host_x", (size_t)nimg * sizeof(T));
+    T *d_y = (T *)c.scratch("host_y", (size_t)nimg * sizeof(T));
+    T *d_w = wgt ? (T *)c.scratch("host_wgt", (size_t)nrow * nchan * sizeof(T)) : nullptr;
+    cudaStream_t cs = c.copy_stream_get();
+    PFB_CUDA(cudaMemcpyAsync(d_uvw, uvw, (size_t)nrow * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    PFB_CUDA(cudaMemcpyAsync(d_freq, freq, (size_t)nchan * sizeof(double), cudaMemcpyHostToDevice, st));
+    PFB_CUDA(cudaMemcpyAsync(d_band, band, (size_t)nchan * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    PFB_CUDA(cudaMemcpyAsync(d_x, x, (size_t)nimg * sizeof(T), cudaMemcpyHostToDevice, st));
+    cudaEvent_t e_in = c.copy_event(0), e_w = c.copy_event(1), e_out = c.copy_event(2);
+    PFB_CUDA(cudaEventRecord(e_in, st));
+    PFB_CUDA(cudaStreamWaitEvent(cs, e_in, 0));
+    if (wgt)
+        PFB_CUDA(cudaMemcpyAsync(d_w, wgt, (size_t)nrow * nchan * sizeof(T), cudaMemcpyHostToDevice, cs));
+    PFB_CUDA(cudaEventRecord(e_w, cs));
+    Plan &p = get_plan(c, *g, prec, nrow, nchan, d_uvw, d_freq, d_band, false, st);
+    cx_t<T> *vis = (cx_t<T> *)c.scratch("hess_vis", (size_t)nrow * nchan * sizeof(cx_t<T>));
+    op_degrid<T>(c, p, d_x, vis, st);
+    PFB_CUDA(cudaStreamWaitEvent(st, e_w, 0));
+    op_grid<T>(c, p, vis, d_w, false, d_y, st, [&](int b) {
+        cudaEvent_t e = c.copy_event(3 + (size_t)b);
+        PFB_CUDA(cudaEventRecord(e, st));
+        PFB_CUDA(cudaStreamWaitEvent(cs, e, 0));
+        PFB_CUDA(cudaMemcpyAsync(y + b * npix, d_y + b * npix, (size_t)npix * sizeof(T), cudaMemcpyDeviceToHost,
+                                 cs));
+    });
+    PFB_CUDA(cudaEventRecord(e_out, cs));
+    PFB_CUDA(cudaStreamWaitEvent(st, e_out, 0));
+}
+
+}  // namespace pfb
+
 extern "C" {
 
 const char *pfb_version(void) { return "pfb-gb300 0.1 (sm_103a)"; }
@@ -416,6 +495,22 @@ int pfb_hessian(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, in
             op_degrid<float>(c, p, (const float *)x, (float2 *)vis, S(stream));
             op_grid<float>(c, p, (const float2 *)vis, (const float *)wgt, false, (float *)y_out, S(stream));
         }
+    });
+}
+
+int pfb_hessian_host(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
+                     const double *freq, const int32_t *band, const void *wgt, const void *x, void *y_out,
+                     void *stream) {
+    return guarded(ctx, [&](Ctx &c) {
+        check_geom(g, prec);
+        check_data(nrow, nchan, uvw, freq, band);
+        PFB_REQUIRE(x && y_out, "x and y_out must not be NULL");
+        if (prec == PFB_F64)
+            hessian_host<double>(c, g, prec, nrow, nchan, uvw, freq, band, (const double *)wgt, (const double *)x,
+                                 (double *)y_out, S(stream));
+        else
+            hessian_host<float>(c, g, prec, nrow, nchan, uvw, freq, band, (const float *)wgt, (const float *)x,
+                                (float *)y_out, S(stream));
     });
 }
 

@@ -3,6 +3,8 @@
 
 #include "common.cuh"
 
+#include <functional>
+
 namespace pfb {
 
 // One gridding work item: a uv tile of one band, either the tile's whole item
@@ -145,6 +147,15 @@ struct Ctx {
     std::map<FftKey, cufftHandle> ffts;
     std::vector<PsfSpec> spectra;
     Timing timing;
+    // pfb_hessian_host: a copy stream joined to the caller's stream by events, and the host
+    // pointers whose contents the scratch copies (and the plans built on them) hold
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> copy_events;
+    const void *host_data[3] = {nullptr, nullptr, nullptr};
+    int64_t host_nrow = -1;
+    int host_nchan = -1;
+    cudaStream_t copy_stream_get();
+    cudaEvent_t copy_event(size_t i);
 
     ~Ctx();
     void *dalloc(size_t bytes);            // counted against the budget
@@ -201,9 +212,10 @@ int kernel_support(double eps);
 void build_item_records(Ctx &ctx, Plan &p, cudaStream_t st);
 template <typename T>
 void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st, bool accumulate = false);
+// band_done (may be empty) is called after the last launch that writes band b of image, on st
 template <typename T>
 void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool unit_vis, T *image,
-             cudaStream_t st);
+             cudaStream_t st, const std::function<void(int)> &band_done = {});
 template <typename T>
 void op_wsum(Ctx &ctx, const Plan &p, const T *wgt, double *d_wsum, cudaStream_t st);
 

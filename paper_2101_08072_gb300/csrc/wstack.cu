@@ -1242,7 +1242,7 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
 
 template <typename T>
 void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool unit_vis, T *image,
-             cudaStream_t st) {
+             cudaStream_t st, const std::function<void(int)> &band_done) {
     const size_t cxs = sizeof(cx_t<T>);
     const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
     cx_t<T> *planes = (cx_t<T> *)ctx.scratch("planes", (size_t)blk * p.Nu * p.Nv * cxs);
@@ -1312,6 +1312,7 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                 check_launch("postpass");
             }
         }
+        if (band_done) band_done(b);
     }
 }
 
@@ -1326,8 +1327,10 @@ void op_wsum(Ctx &ctx, const Plan &p, const T *wgt, double *d_wsum, cudaStream_t
 
 template void op_degrid<float>(Ctx &, const Plan &, const float *, float2 *, cudaStream_t, bool);
 template void op_degrid<double>(Ctx &, const Plan &, const double *, double2 *, cudaStream_t, bool);
-template void op_grid<float>(Ctx &, const Plan &, const float2 *, const float *, bool, float *, cudaStream_t);
-template void op_grid<double>(Ctx &, const Plan &, const double2 *, const double *, bool, double *, cudaStream_t);
+template void op_grid<float>(Ctx &, const Plan &, const float2 *, const float *, bool, float *, cudaStream_t,
+                             const std::function<void(int)> &);
+template void op_grid<double>(Ctx &, const Plan &, const double2 *, const double *, bool, double *, cudaStream_t,
+                              const std::function<void(int)> &);
 template void op_wsum<float>(Ctx &, const Plan &, const float *, double *, cudaStream_t);
 template void op_wsum<double>(Ctx &, const Plan &, const double *, double *, cudaStream_t);
 

@@ -211,6 +211,36 @@ class Context:
                                          _ptr(band_of_chan), _ptr(wgt), _ptr(x), _ptr(out), self._stream()))
         return out
 
+    def pfb_hessian_host(self, geom: Geometry, uvw, freq, band_of_chan, x, wgt=None, out=None):
+        """R^dagger Sigma^-1 R x (Eq. 3) from CPU tensors (pinned for overlapped copies): the library
+        copies the inputs in and the result out, overlapped with the computation.  out (a CPU tensor,
+        pinned when allocated here) holds the result once the current CUDA stream is synchronised."""
+        for name, t, dt in (("uvw", uvw, torch.float64), ("freq", freq, torch.float64),
+                            ("band_of_chan", band_of_chan, torch.int32)):
+            if t.dtype != dt or not t.is_contiguous() or t.device.type != "cpu":
+                raise TypeError(f"{name} must be a contiguous {dt} CPU tensor")
+        if uvw.ndim != 2 or uvw.shape[1] != 3:
+            raise ValueError("uvw must be [nrow, 3]")
+        nrow, nchan = uvw.shape[0], freq.shape[0]
+        prec = _prec_real(x.dtype)
+        shape = (geom.nband, geom.nx, geom.ny)
+        for name, t, shp in (("x", x, shape), ("wgt", wgt, (nrow, nchan))):
+            if t is not None and (t.dtype != _RDT[prec] or not t.is_contiguous() or t.device.type != "cpu"
+                                  or tuple(t.shape) != tuple(shp)):
+                raise TypeError(f"{name} must be a contiguous {_RDT[prec]} CPU tensor of shape {shp}")
+        if out is None:
+            out = torch.empty(shape, dtype=_RDT[prec], pin_memory=True)
+        if out.dtype != _RDT[prec] or not out.is_contiguous() or out.device.type != "cpu" or \
+                tuple(out.shape) != tuple(shape):
+            raise TypeError(f"y_out must be a contiguous {_RDT[prec]} CPU tensor of shape {shape}")
+        # the plan is keyed on these host pointers: hold the arrays so that their memory is not handed
+        # to new arrays with other contents while the plan lives
+        self._keep_host = (uvw, freq, band_of_chan)
+        g = geom.c()
+        self._check(self.lib.pfb_hessian_host(self.h, ctypes.byref(g), prec, nrow, nchan, _ptr(uvw), _ptr(freq),
+                                              _ptr(band_of_chan), _ptr(wgt), _ptr(x), _ptr(out), self._stream()))
+        return out
+
     def pfb_psf_conv(self, geom: Geometry, psf, x, out=None):
         """I^psf * x (Eq. 4), linear convolution."""
         prec = _prec_real(x.dtype)

@@ -128,7 +128,26 @@ struct BandGeom {
     int uv_oi, w_oi;
     float uv_of, w_of, hw;
     float inv_Nu, inv_Nv;
+    // FP32 path: w0 and the plane spacing dw as unevaluated float pairs (hi + lo) for the per-pixel
+    // plane phases of the pre- and post-pass
+    float w0_hi, w0_lo, dw_hi, dw_lo;
 };
+
+// frac(a t) in turns for a = a_hi + a_lo and t = t_hi + t_lo (unevaluated float pairs), as hi + lo.
+// The leading product is split exactly by FMA (TwoProduct) and its integer part removed (exact for
+// |a t| < 2^23); the cross terms a_hi t_lo + a_lo t_hi are added and the sum renormalised by TwoSum.
+// The dropped a_lo t_lo and the rounding of the cross terms leave about 2^-46 |a t| of error, so the
+// reduced phase is good to ~1e-12 turns for the phases of the w-stack (|a t| of a few hundred turns).
+__device__ __forceinline__ void frac_prod_df(float a_hi, float a_lo, float t_hi, float t_lo, float *hi, float *lo) {
+    const float p = a_hi * t_hi;
+    const float e = fmaf(a_hi, t_hi, -p);
+    const float q = p - rintf(p);
+    const float s = e + fmaf(a_hi, t_lo, a_lo * t_hi);
+    const float h = q + s;
+    const float z = h - q;
+    *hi = h;
+    *lo = (q - (h - z)) + (s - z);
+}
 
 // x mod n in [0, n) for |x| < 2^24, by a float reciprocal and one correction
 __device__ __forceinline__ int wrap_mod(int x, int n, float inv_n) {

@@ -55,7 +55,7 @@ struct Plan {
     int64_t nitems = 0;
     int64_t *d_off = nullptr;
     int64_t nkeys = 0;
-    double *d_tp = nullptr;   // n - 1 - tc per pixel
+    double *d_tp = nullptr;   // n - 1 - tc per pixel (FP32 plans: the same 8 bytes as a float pair hi, lo)
     void *d_corr = nullptr;   // 1 / (n psi_u psi_v psi_w) per pixel, working precision
     WorkItem *d_work = nullptr;
     int *d_heavy = nullptr;
@@ -84,6 +84,11 @@ struct Plan {
         g.w_of = (float)(O - std::floor(O));
         g.inv_Nu = 1.0f / (float)Nu;
         g.inv_Nv = 1.0f / (float)Nv;
+        g.w0_hi = (float)w0[b];
+        g.w0_lo = (float)(w0[b] - (double)g.w0_hi);
+        const double dws = wstack ? dw : 0.0;
+        g.dw_hi = (float)dws;
+        g.dw_lo = (float)(dws - (double)g.dw_hi);
         return g;
     }
     CoordSrc coords() const { return CoordSrc{(const double *)uvw, d_scale, d_rowdf, d_chandf}; }

@@ -430,7 +430,12 @@ __global__ void k_pixel_tables(int nx, int ny, double dl, double dm, double l0, 
         double a3 = (f + 1.0) * f * (f - 1.0) / 6.0;
         c *= a0 * tab[k - 1] + a1 * tab[k] + a2 * tab[k + 1] + a3 * tab[k + 2];
     }
-    tp[p] = t;
+    if constexpr (sizeof(T) == 4) {   // FP32 plans: t as an unevaluated float pair
+        const float hi = (float)t;
+        reinterpret_cast<float2 *>(tp)[p] = make_float2(hi, (float)(t - (double)hi));
+    } else {
+        tp[p] = t;
+    }
     corr[p] = (T)(1.0 / c);
 }
 

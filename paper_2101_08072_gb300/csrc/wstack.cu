@@ -18,6 +18,28 @@ namespace pfb {
 // ------------------------------------------------------------------ pre-pass (R)
 // Writes x corr exp(-2 pi i w_k t) for planes [k_lo, k_hi) at the pixel's grid
 // position (i - nx/2 mod N_u, j - ny/2 mod N_v); the rest of each plane was zeroed.
+// Per-pixel base of the plane phases: th0 = frac(w0 t) and dth = frac(dw t) = dth_hi + dth_lo.  FP64
+// plans reduce in FP64 (t a double); FP32 plans hold t as a float pair and reduce in float-float
+// arithmetic, since FP64 runs at a small fraction of the FP32 rate on this GPU.
+__device__ __forceinline__ void plane_phase_base(const double *__restrict__ tp, int64_t p, const BandGeom &g,
+                                                 double dw, double *th0, double *dth_hi, double *dth_lo) {
+    const double t = tp[p];
+    const double a0 = g.w0 * t, a1 = dw * t;
+    const double d1 = a1 - rint(a1);
+    *th0 = a0 - rint(a0);
+    *dth_hi = d1;
+    *dth_lo = 0.0;
+}
+__device__ __forceinline__ void plane_phase_base(const double *__restrict__ tp, int64_t p, const BandGeom &g,
+                                                 double dw, float *th0, float *dth_hi, float *dth_lo) {
+    (void)dw;
+    const float2 t = reinterpret_cast<const float2 *>(tp)[p];
+    float h, l;
+    frac_prod_df(g.w0_hi, g.w0_lo, t.x, t.y, &h, &l);
+    *th0 = h + l;
+    frac_prod_df(g.dw_hi, g.dw_lo, t.x, t.y, dth_hi, dth_lo);
+}
+
 template <typename T>
 __global__ void k_prepass(int nx, int ny, const T *__restrict__ x, const T *__restrict__ corr,
                           const double *__restrict__ tp, BandGeom g, int k_lo, int k_hi, double dw,
@@ -31,12 +53,10 @@ __global__ void k_prepass(int nx, int ny, const T *__restrict__ x, const T *__re
     gv += gv < 0 ? g.Nv : 0;
     const int64_t pos = (int64_t)gu * g.Nv + gv;
     const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
-    const double t = tp[p];
-    // phase of plane k in turns: (w0 + k dw) t = th0 + k dth, both reduced mod 1 in
-    // FP64 once per pixel; the per-plane sum is formed in the working precision
-    const double a0 = g.w0 * t, a1 = dw * t;
-    const double d1 = a1 - rint(a1);
-    const T th0 = (T)(a0 - rint(a0)), dth_hi = (T)d1, dth_lo = (T)(d1 - (double)dth_hi);
+    // phase of plane k in turns: (w0 + k dw) t = th0 + k dth, both reduced mod 1 once per
+    // pixel; the per-plane sum is formed in the working precision
+    T th0, dth_hi, dth_lo;
+    plane_phase_base(tp, p, g, dw, &th0, &dth_hi, &dth_lo);
     for (int k = k_lo; k < k_hi; ++k) {
         T cs = 1, sn = 0;
         if (g.Ww > 1) sincos_turns(plane_turns(k, th0, dth_hi, dth_lo), &sn, &cs);
@@ -946,10 +966,8 @@ __global__ void k_postpass(int nx, int ny, const T *__restrict__ corr, const dou
     gv += gv < 0 ? g.Nv : 0;
     const int64_t pos = (int64_t)gu * g.Nv + gv;
     const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
-    const double t = tp[p];
-    const double a0 = g.w0 * t, a1 = dw * t;
-    const double d1 = a1 - rint(a1);
-    const T th0 = (T)(a0 - rint(a0)), dth_hi = (T)d1, dth_lo = (T)(d1 - (double)dth_hi);
+    T th0, dth_hi, dth_lo;
+    plane_phase_base(tp, p, g, dw, &th0, &dth_hi, &dth_lo);
     T acc = 0;
     for (int k = k_lo; k < k_hi; ++k) {
         const cx_t<T> h = planes[(int64_t)(k - k_lo) * plane_sz + pos];

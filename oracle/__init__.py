@@ -25,10 +25,13 @@ interferometric data"):
 Parity status: R, R^dagger, I^d, I^psf, the Hessian, the PSF convolution, CG,
 the prox, the wavelets and the gradient are pinned by tests/test_oracle_pins.py
 (closed forms, library-routine special cases, invariants, brute force).  The
-composed step and the clean driver at fixed iteration counts have no printed
-value in the paper to pin them: their parts are pinned, and so are the fixed
-point at the true image, the reduction of the approximate gradient to the exact
-one at w = 0 and the stopping rule; the iterates themselves are "parity unpinned".
+composed step is pinned at lam = 0 with CG run to convergence, where the prox is
+the identity, against a dense computation of x + gamma U^-1 (I^d - H x) / wbar;
+so are the fixed point at the true image, the reduction of the approximate
+gradient to the exact one at w = 0 and the stopping rule.  With lam > 0 and at
+fixed, unconverged iteration counts the primal-dual and CG iterates, and so the
+step and clean iterates, have no printed value in the paper and no closed form:
+those iterates are "parity unpinned" (their parts are pinned).
 """
 from __future__ import annotations
 

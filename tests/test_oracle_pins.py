@@ -428,6 +428,50 @@ def test_step_fixed_point_at_truth():
     assert st[1] < 1e-9
 
 
+def test_step_equals_dense_preconditioned_step():
+    """lam = 0 and an iterate well inside the positive orthant: the prox of Eq. 7 is the identity and
+    the dual stays 0, so a step with CG run to convergence is x + gamma U^-1 (I^d - H x) / wbar
+    (Eqs. 6-8).  Built here from dense matrices: H column by column from the Hessian of unit images,
+    U = (M + M^T) / 2 + sigma Id with M[(i,j),(i',j')] = I^psf[i - i' + nx, j - j' + ny] / wbar (the
+    linear PSF convolution, symmetrised), solved by numpy.  The statistics follow the same formulas:
+    objective x.Hx / (2 wbar) - x.I^d / wbar and relative update ||x1 - x|| / ||x1||."""
+    nx = ny = 8
+    obs = synth.tiny_observation(nx=nx, ny=ny)
+    rng = np.random.default_rng(28)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    a = (obs.uvw, obs.freq, obs.band_of_chan)
+    xt = synth.point_source_image(rng, 1, nx, ny, 4)
+    V = oracle.degrid(*a, xt, obs.dl, obs.dm) + synth.complex_noise(rng, (obs.nrow, obs.nchan), 1e-2)
+    d, ws = oracle.dirty(*a, V, w, nx, ny, obs.dl, obs.dm, 1)
+    p, _ = oracle.psf(*a, w, nx, ny, obs.dl, obs.dm, 1)
+    x0 = 2.0 + rng.uniform(0.0, 1.0, (1, nx, ny))
+    gamma, sigma = 0.5, 0.3
+    prm = oracle.Params(gamma=gamma, sigma=sigma, lam=0.0, cg_iters=100, pd_iters=5)
+    x1, v1, st = oracle.step(*a, w, d, p, ws, x0, np.zeros((1, 1, nx, ny)), obs.dl, obs.dm, prm)
+    # dense H and U
+    n = nx * ny
+    wbar = float(np.mean(ws))
+    Hd = np.zeros((n, n))
+    M = np.zeros((n, n))
+    for k in range(n):
+        i, j = divmod(k, ny)
+        Hd[:, k] = oracle.hessian(*a, w, _unit_image(nx, ny, i, j), obs.dl, obs.dm).ravel()
+        for k2 in range(n):
+            i2, j2 = divmod(k2, ny)
+            M[k2, k] = p[0, i2 - i + nx, j2 - j + ny]
+    U = 0.5 * (M + M.T) / wbar + sigma * np.eye(n)
+    xv = x0.ravel()
+    ir = (d.ravel() - Hd @ xv) / wbar
+    xbar = xv + gamma * np.linalg.solve(U, ir)
+    assert xbar.min() > 0.1   # the prox is the identity there
+    assert np.abs(x1.ravel() - xbar).max() <= 1e-9 * np.abs(xbar).max()
+    assert np.abs(v1).max() == 0.0
+    obj = 0.5 * xv @ (Hd @ xv) / wbar - xv @ d.ravel() / wbar
+    assert st[0] == pytest.approx(obj, rel=1e-10)
+    assert st[1] == pytest.approx(np.linalg.norm(xbar - xv) / np.linalg.norm(xbar), rel=1e-9)
+    assert st[2] < 1e-8
+
+
 def test_step_decreases_objective():
     obs = synth.tiny_observation(nx=16, ny=16)
     rng = np.random.default_rng(26)

@@ -28,10 +28,11 @@ the prox, the wavelets and the gradient are pinned by tests/test_oracle_pins.py
 composed step is pinned at lam = 0 with CG run to convergence, where the prox is
 the identity, against a dense computation of x + gamma U^-1 (I^d - H x) / wbar;
 so are the fixed point at the true image, the reduction of the approximate
-gradient to the exact one at w = 0 and the stopping rule.  With lam > 0 and at
-fixed, unconverged iteration counts the primal-dual and CG iterates, and so the
-step and clean iterates, have no printed value in the paper and no closed form:
-those iterates are "parity unpinned" (their parts are pinned).
+gradient to the exact one at w = 0 and the stopping rule; CG at a fixed
+iteration count k is pinned as the U-norm minimiser over the k-dimensional
+Krylov space.  With lam > 0 the primal-dual iterates at a fixed, unconverged
+count, and so the step and clean iterates, have no printed value in the paper
+and no closed form: those iterates are "parity unpinned" (their parts are pinned).
 """
 from __future__ import annotations
 

@@ -324,6 +324,31 @@ def test_cg_matches_dense_solve():
     assert res[0] < 1e-12
 
 
+def test_cg_iterates_minimise_over_krylov_spaces():
+    """CG at a fixed, unconverged iteration count k: its iterate is the minimiser of the U-norm error
+    (delta - U^-1 b)^T U (delta - U^-1 b) over the Krylov space span{b, U b, ..., U^(k-1) b} (Hestenes
+    and Stiefel 1952).  The minimiser is computed here from an orthonormal basis Q of that space:
+    delta_k = Q (Q^T U Q)^-1 Q^T b.  Also the reported relative residual ||b - U delta_k|| / ||b||."""
+    nx = ny = 8
+    p = _test_psf(nx, ny)
+    spec = np.real(oracle.psf_spectrum(p))
+    sigma = 0.05
+    n = nx * ny
+    U = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros((1, nx, ny)); e.reshape(-1)[k] = 1.0
+        U[:, k] = oracle.u_apply(spec, sigma, e).reshape(-1)
+    b = np.random.default_rng(27).normal(size=(1, nx, ny))
+    bv = b.reshape(-1)
+    for k in (1, 2, 3, 5):
+        delta, res = oracle.cg(spec, sigma, b, iters=k, tol=0.0)
+        K = np.stack([np.linalg.matrix_power(U, m) @ bv for m in range(k)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        ref = Q @ np.linalg.solve(Q.T @ U @ Q, Q.T @ bv)
+        assert np.abs(delta.reshape(-1) - ref).max() <= 1e-9 * np.abs(ref).max(), k
+        assert res[0] == pytest.approx(np.linalg.norm(bv - U @ ref) / np.linalg.norm(bv), rel=1e-7), k
+
+
 def test_symmetrised_psf_operator_is_symmetric_part():
     """U uses Re(spectrum): the convolution with the PSF symmetrised about its
     centre, i.e. (M + M^T)/2 for M the PSF-convolution matrix."""

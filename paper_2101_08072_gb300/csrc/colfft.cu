@@ -21,6 +21,8 @@
 // split n = R2 n1 + n2, k = k1 + R1 k2 with the twiddles exp(-/+ 2 pi i n2 k1 / R) in between.
 #include "ctx.cuh"
 
+#include <cuda.h>
+
 namespace pfb {
 namespace {
 
@@ -134,14 +136,23 @@ __device__ __forceinline__ void apply_twiddles(float4 *v, const float2 *__restri
 // Forward: rows outside the image rows read as zero, all rows written; inverse: all rows read, the
 // image rows written.  A CTA takes its column pair through all planes in turn, so the stores of one
 // plane drain while the loads of the next are in flight.
-template <int L, bool INV>
+// TMA: the last stage writes the transformed columns densely into shared memory and one thread stores
+// them with tiled bulk copies (boxes of 2 cells x 256 rows), which keeps the 16-byte row stores off the
+// load/store pipe.  Copies are issued by thread 0, which waits (a hardware wait) until they have read
+// shared memory before the buffer is written again, and until they are complete before it exits.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+template <int L, bool INV, bool TMA>
 __global__ void __launch_bounds__((1 << L) / 16) k_colfft(float2 *__restrict__ data, int nplanes, int Nv,
                                                           int64_t plane_sz, int nx, int ny,
-                                                          const float2 *__restrict__ W) {
+                                                          const float2 *__restrict__ W,
+                                                          const __grid_constant__ CUtensorMap tmap) {
     constexpr int N = 1 << L, T = N / 16;
     constexpr int NST16 = L / 4, RL = (L % 4) ? (1 << (L % 4)) : 16, BPT = 16 / RL;
     constexpr int NMID = NST16 - 1 - ((L % 4) ? 0 : 1);   // radix-16 stages between the first and last
-    extern __shared__ float4 sm[];
+    extern __shared__ __align__(1024) float4 sm[];
     const int tid = threadIdx.x;
     const int q = blockIdx.x, hq = ny / 4;
     const int c = q < hq ? 2 * q : Nv - ny / 2 + 2 * (q - hq);
@@ -191,18 +202,44 @@ __global__ void __launch_bounds__((1 << L) / 16) k_colfft(float2 *__restrict__ d
             apply_twiddles<RL, INV>(v + b * RL, W, k, step);
             dft_reg<RL, INV>(v + b * RL);
         }
+        if constexpr (TMA) {
+            __syncthreads();   // every thread has read the buffer
 #pragma unroll
-        for (int b = 0; b < BPT; ++b) {
-            const int j = tid + b * T, k = j & (Ns - 1);
-            const int d = (j / Ns) * Ns * RL + k;
+            for (int b = 0; b < BPT; ++b) {
+                const int j = tid + b * T, k = j & (Ns - 1);
+                const int d = (j / Ns) * Ns * RL + k;
 #pragma unroll
-            for (int r = 0; r < RL; ++r) {
-                const int row = d + r * Ns;
-                if (INV && row >= rlo && row < rhi) continue;
-                *reinterpret_cast<float4 *>(base + (int64_t)row * Nv) = v[b * RL + operm<RL>(r)];
+                for (int r = 0; r < RL; ++r) sm[d + r * Ns] = v[b * RL + operm<RL>(r)];   // row-major, dense
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                for (int r0 = 0; r0 < N; r0 += 256) {
+                    if (INV && r0 >= rlo && r0 + 256 <= rhi) continue;   // no image row in this box
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                            reinterpret_cast<uint64_t>(&tmap)),
+                        "r"(c), "r"(r0), "r"(pl), "r"(smem_u32(sm + r0))
+                        : "memory");
+                }
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < BPT; ++b) {
+                const int j = tid + b * T, k = j & (Ns - 1);
+                const int d = (j / Ns) * Ns * RL + k;
+#pragma unroll
+                for (int r = 0; r < RL; ++r) {
+                    const int row = d + r * Ns;
+                    if (INV && row >= rlo && row < rhi) continue;
+                    *reinterpret_cast<float4 *>(base + (int64_t)row * Nv) = v[b * RL + operm<RL>(r)];
+                }
             }
         }
     }
+    if (TMA && tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // W[m] = exp(-2 pi i m / n), rounded from double
@@ -214,13 +251,59 @@ __global__ void k_colfft_table(int n, float2 *W) {
     W[m] = make_float2((float)c, (float)-s);
 }
 
+// Tensor map of a plane block for the TMA stores: [nplanes][Nu][Nv] cells of 8 bytes, box 2 x 256 x 1.
+// Returns false (plain stores) when the driver's encoder is not available or a layout rule of the copy
+// is not met: 16-byte base and strides, a 16-byte inner box extent, and x coordinates (2 q or
+// Nv - ny/2 + 2 q) that are even, i.e. 16-byte aligned.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+static bool colfft_tensor_map(CUtensorMap *map, float2 *data, int Nu, int Nv, int nplanes, int ny) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || Nu < 256 || Nu % 256 || Nv % 2 || (Nv - ny / 2) % 2 || (ny / 2) % 2) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)Nv, (cuuint64_t)Nu, (cuuint64_t)nplanes};
+    const cuuint64_t strides[2] = {(cuuint64_t)Nv * 8, (cuuint64_t)Nu * Nv * 8};
+    const cuuint32_t box[3] = {2, 256, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (reinterpret_cast<uintptr_t>(data) % 16 || strides[0] % 16 || strides[1] % 16) return false;
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, data, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int L, bool INV>
 void launch_colfft(float2 *data, int nplanes, int Nv, int64_t plane_sz, int nx, int ny, const float2 *W,
                    cudaStream_t st) {
     constexpr int N = 1 << L;
     const size_t smem = (size_t)(spad(N - 1) + 1) * sizeof(float4);
-    PFB_CUDA(cudaFuncSetAttribute(k_colfft<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_colfft<L, INV><<<(unsigned)(ny / 2), N / 16, smem, st>>>(data, nplanes, Nv, plane_sz, nx, ny, W);
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    if (colfft_tensor_map(&map, data, N, Nv, nplanes, ny)) {
+        PFB_CUDA(cudaFuncSetAttribute(k_colfft<L, INV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        k_colfft<L, INV, true><<<(unsigned)(ny / 2), N / 16, smem, st>>>(data, nplanes, Nv, plane_sz, nx, ny, W,
+                                                                          map);
+    } else {
+        PFB_CUDA(cudaFuncSetAttribute(k_colfft<L, INV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        k_colfft<L, INV, false><<<(unsigned)(ny / 2), N / 16, smem, st>>>(data, nplanes, Nv, plane_sz, nx, ny, W,
+                                                                           map);
+    }
     check_launch("colfft");
 }
 

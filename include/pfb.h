@@ -179,10 +179,9 @@ int pfb_hessian(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, int64_t nrow,
 
 /* The Hessian of pfb_hessian (Eq. 3) from HOST buffers: uvw, freq, band_of_chan, wgt (may be NULL:
  * unit weights) and x are read from host memory, y_out is written to host memory; layouts as in
- * pfb_hessian.  The copies overlap the computation: x goes in first, the weights go in on an internal
- * copy stream while R x is computed, and each band of y_out comes back as soon as it is gridded.  With
- * page-locked (pinned) host memory the copies are asynchronous; pageable memory works but loses the
- * overlap.  The call enqueues work on `stream` (the copy stream is joined back to it); y_out holds the
+ * pfb_hessian.  The inputs go in on `stream` before the computation; each band of y_out comes back on an
+ * internal copy stream as soon as it is gridded, overlapping the later bands.  With page-locked (pinned)
+ * host memory the copies are asynchronous; pageable memory works but loses the overlap.  The call enqueues work on `stream` (the copy stream is joined back to it); y_out holds the
  * result once `stream` has been synchronised, and the host buffers must stay valid until then.  The
  * device copies live in the context's scratch and the plan is built on them; it is reused while the
  * host pointers of uvw, freq and band_of_chan (and nrow, nchan) stay the same, so call

@@ -270,11 +270,10 @@ void run_step(Ctx &c, const Plan &p, pfb_prec prec, const pfb_params &prm, const
 
 namespace pfb {
 
-// The Hessian from host buffers, with the copies overlapping the computation.  On the caller's stream:
-// uvw, freq, band and x in, the plan, R x of every band, then R^dagger Sigma^-1 band by band.  On the
-// copy stream: the weights once x is in (they are needed only after R x), and band b of the result as
-// soon as its last post-pass has run.  The caller's stream then waits for the copy stream, so work queued
-// after this call (or a synchronisation of the stream) sees the finished result.
+// The Hessian from host buffers.  On the caller's stream: uvw, freq, band, x and the weights in, the
+// plan, R x of every band, then R^dagger Sigma^-1 band by band.  On the copy stream: band b of the result
+// as soon as its last post-pass has run, overlapping the later bands.  The caller's stream then waits for
+// the copy stream, so work queued after this call (or a synchronisation of the stream) sees the result.
 template <typename T>
 static void hessian_host(Ctx &c, const pfb_geom *g, int prec, int64_t nrow, int32_t nchan, const double *uvw,
                          const double *freq, const int32_t *band, const T *wgt, const T *x, T *y, cudaStream_t st) {
@@ -306,16 +305,14 @@ static void hessian_host(Ctx &c, const pfb_geom *g, int prec, int64_t nrow, int3
     PFB_CUDA(cudaMemcpyAsync(d_freq, freq, (size_t)nchan * sizeof(double), cudaMemcpyHostToDevice, st));
     PFB_CUDA(cudaMemcpyAsync(d_band, band, (size_t)nchan * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     PFB_CUDA(cudaMemcpyAsync(d_x, x, (size_t)nimg * sizeof(T), cudaMemcpyHostToDevice, st));
-    cudaEvent_t e_in = c.copy_event(0), e_w = c.copy_event(1), e_out = c.copy_event(2);
-    PFB_CUDA(cudaEventRecord(e_in, st));
-    PFB_CUDA(cudaStreamWaitEvent(cs, e_in, 0));
+    // the weights go in before R x on the same stream: a host-to-device copy next to the transforms was
+    // measured to slow them by more than the copy takes
     if (wgt)
-        PFB_CUDA(cudaMemcpyAsync(d_w, wgt, (size_t)nrow * nchan * sizeof(T), cudaMemcpyHostToDevice, cs));
-    PFB_CUDA(cudaEventRecord(e_w, cs));
+        PFB_CUDA(cudaMemcpyAsync(d_w, wgt, (size_t)nrow * nchan * sizeof(T), cudaMemcpyHostToDevice, st));
+    cudaEvent_t e_out = c.copy_event(2);
     Plan &p = get_plan(c, *g, prec, nrow, nchan, d_uvw, d_freq, d_band, false, st);
     cx_t<T> *vis = (cx_t<T> *)c.scratch("hess_vis", (size_t)nrow * nchan * sizeof(cx_t<T>));
     op_degrid<T>(c, p, d_x, vis, st);
-    PFB_CUDA(cudaStreamWaitEvent(st, e_w, 0));
     op_grid<T>(c, p, vis, d_w, false, d_y, st, [&](int b) {
         cudaEvent_t e = c.copy_event(3 + (size_t)b);
         PFB_CUDA(cudaEventRecord(e, st));

@@ -212,9 +212,10 @@ class Context:
         return out
 
     def pfb_hessian_host(self, geom: Geometry, uvw, freq, band_of_chan, x, wgt=None, out=None):
-        """R^dagger Sigma^-1 R x (Eq. 3) from CPU tensors (pinned for overlapped copies): the library
-        copies the inputs in and the result out, overlapped with the computation.  out (a CPU tensor,
-        pinned when allocated here) holds the result once the current CUDA stream is synchronised."""
+        """R^dagger Sigma^-1 R x (Eq. 3) from CPU tensors (pinned for asynchronous copies): the library
+        copies the inputs in and each band of the result out while the later bands are computed.  out (a
+        CPU tensor, pinned when allocated here) holds the result once the current CUDA stream is
+        synchronised."""
         for name, t, dt in (("uvw", uvw, torch.float64), ("freq", freq, torch.float64),
                             ("band_of_chan", band_of_chan, torch.int32)):
             if t.dtype != dt or not t.is_contiguous() or t.device.type != "cpu":

@@ -374,11 +374,18 @@ def prox(xbar, v, spec_sym, p: Params):
         grad = u_apply(spec_sym, p.sigma, x - xbar) / p.gamma
         xt = np.maximum(0.0, x - tau * (grad + psi(v, bases, p.nlevel)))
         vt = v + psi_adjoint(2.0 * xt - x, bases, p.nlevel)
-        nrm = np.sqrt((vt ** 2).sum(axis=1, keepdims=True))
-        scale = np.where(nrm > p.lam, p.lam / np.maximum(nrm, 1e-300), 1.0)
-        v = vt * scale
+        v = project_l2inf(vt, p.lam)
         x = xt
     return x, v
+
+
+def project_l2inf(vt, lam):
+    """Projection onto the l2,inf ball of radius lam (groups over bands, axis 1):
+    v_g = vt_g min(1, lam / ||vt_g||_2).  By Moreau's identity this is the prox of
+    the convex conjugate of lam ||.||_{2,1} (Eq. 9's norm)."""
+    nrm = np.sqrt((vt ** 2).sum(axis=1, keepdims=True))
+    scale = np.where(nrm > lam, lam / np.maximum(nrm, 1e-300), 1.0)
+    return vt * scale
 
 
 # ------------------------------------------------------------------ one pfb step (Eqs. 6-7)

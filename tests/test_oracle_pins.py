@@ -395,6 +395,79 @@ def test_dwt_orthonormal_and_haar_closed_form():
     assert np.abs(c - ref).max() < 1e-14
 
 
+def _dwt_constant_failures(dwt2_fn):
+    """Failures of the multi-level DWT on constant images (Eq. 9's Psi_k, Mallat layout).
+    A constant c has zero detail at every level (the high-pass filter sums to 0, the
+    first vanishing moment) and a low-pass output of sqrt(2) c per axis and level, so
+    after L levels of the 2-D transform only the coarsest approximation block
+    [0:n/2^L, 0:m/2^L] is non-zero and it holds c 2^L.  A recursion on the wrong
+    quadrant, a wrong block size or a skipped level breaks this."""
+    bad = []
+    c0 = 1.7
+    for N in range(1, 7):
+        h = oracle.daubechies(N)
+        for L in (1, 2, 3):
+            img = np.full((16, 32), c0)
+            got = dwt2_fn(img, h, L)
+            ref = np.zeros_like(img)
+            ref[: 16 >> L, : 32 >> L] = c0 * 2.0 ** L
+            err = float(np.abs(got - ref).max())
+            if err > 1e-12:
+                bad.append((N, L, err))
+    return bad
+
+
+def _haar_two_level_expected():
+    """Two levels of the 2-D Haar DWT of the separable 8 x 8 image x = a b^T, worked by
+    hand.  One 1-D Haar level maps x to ((x0+x1), (x2+x3), ... | (x0-x1), (x2-x3), ...)/sqrt2.
+      a = [1..8]:              level 1 A1 = [3, 7, 11, 15]/sqrt2, D1 = [-1, -1, -1, -1]/sqrt2
+                               level 2 (on A1) A2 = [10, 26]/2 = [5, 13], D2 = [-4, -4]/2 = [-2, -2]
+      b = [1,0,0,2,3,1,0,1]:   level 1 A1 = [1, 2, 4, 1]/sqrt2, D1 = [1, -2, 2, -1]/sqrt2
+                               level 2 A2 = [3, 5]/2, D2 = [-1, 3]/2
+    A 2-D level on a separable block gives the four outer products of the 1-D halves, and
+    the second level transforms only the approximation block [0:4, 0:4]."""
+    r2 = math.sqrt(2.0)
+    a_A1, a_D1 = np.array([3, 7, 11, 15]) / r2, np.array([-1, -1, -1, -1]) / r2
+    a_A2, a_D2 = np.array([5.0, 13.0]), np.array([-2.0, -2.0])
+    b_A1, b_D1 = np.array([1, 2, 4, 1]) / r2, np.array([1, -2, 2, -1]) / r2
+    b_A2, b_D2 = np.array([1.5, 2.5]), np.array([-0.5, 1.5])
+    c = np.zeros((8, 8))
+    c[0:2, 0:2] = np.outer(a_A2, b_A2)
+    c[0:2, 2:4] = np.outer(a_A2, b_D2)
+    c[2:4, 0:2] = np.outer(a_D2, b_A2)
+    c[2:4, 2:4] = np.outer(a_D2, b_D2)
+    c[0:4, 4:8] = np.outer(a_A1, b_D1)
+    c[4:8, 0:4] = np.outer(a_D1, b_A1)
+    c[4:8, 4:8] = np.outer(a_D1, b_D1)
+    return np.outer(np.arange(1.0, 9.0), [1, 0, 0, 2, 3, 1, 0, 1]), c
+
+
+def _wrong_quadrant_dwt2(img, h, nlevel):
+    """A planted mistake: the recursion continues on the detail block [n/2:n, 0:m/2]
+    instead of the approximation block [0:n/2, 0:m/2]."""
+    c = np.array(img, dtype=np.float64)
+    g = oracle.highpass(h)
+    r0, n, m = 0, c.shape[0], c.shape[1]
+    for _ in range(nlevel):
+        blk = oracle._dwt1(c[r0:r0 + n, :m], h, g, 0)
+        c[r0:r0 + n, :m] = oracle._dwt1(blk, h, g, 1)
+        r0, n, m = r0 + n // 2, n // 2, m // 2
+    return c
+
+
+def test_dwt_multilevel_recursion_constant_images():
+    assert _dwt_constant_failures(oracle.dwt2) == []
+    # the pin rejects a recursion on the wrong quadrant (planted, CPU only)
+    assert len(_dwt_constant_failures(_wrong_quadrant_dwt2)) > 0
+
+
+def test_dwt_two_level_haar_hand_worked():
+    x, ref = _haar_two_level_expected()
+    assert np.abs(oracle.dwt2(x, oracle.daubechies(1), 2) - ref).max() < 1e-13
+    assert np.abs(oracle.idwt2(ref, oracle.daubechies(1), 2) - x).max() < 1e-13
+    assert np.abs(_wrong_quadrant_dwt2(x, oracle.daubechies(1), 2) - ref).max() > 0.1
+
+
 def test_psi_tight_frame():
     rng = np.random.default_rng(22)
     x = rng.normal(size=(2, 16, 16))
@@ -432,6 +505,60 @@ def test_prox_lambda0_kkt():
     assert x.min() >= 0
     assert g.min() > -1e-7
     assert np.abs(x * g).max() < 1e-7
+
+
+def _prox_kkt(x, v, xbar, spec, p):
+    """Optimality of Eq. 7 with r of Eq. 9 at (x, v): x is the minimiser of
+    lam ||Psi^dagger x||_{2,1} + iota_+(x) + (1/2 gamma)(x - xbar)^T U (x - xbar) and v a
+    dual certificate when
+      x >= 0;  ||v_g|| <= lam for every group g (bands of one basis coefficient);
+      v_g = lam c_g / ||c_g|| wherever c_g = (Psi^dagger x)_g != 0  (v in lam d||.||_{2,1}(c));
+      g = U (x - xbar) / gamma + Psi v >= 0 and x . g = 0  (-g in the normal cone of x >= 0).
+    Returns the largest violation of each condition, scaled by lam or |g|."""
+    bases = oracle.basis_list(p.basis_mask)
+    c = oracle.psi_adjoint(x, bases, p.nlevel)
+    cn = np.sqrt((c ** 2).sum(axis=1, keepdims=True))
+    vn = np.sqrt((v ** 2).sum(axis=1))
+    act = np.broadcast_to(cn > 1e-9, v.shape)
+    dirn = np.abs(v - p.lam * c / np.maximum(cn, 1e-300))[act]
+    g = oracle.u_apply(spec, p.sigma, x - xbar) / p.gamma + oracle.psi(v, bases, p.nlevel)
+    return {"neg_x": float(max(0.0, -x.min())),
+            "ball": float(max(0.0, vn.max() - p.lam)) / p.lam,
+            "subgrad": float(dirn.max()) / p.lam if dirn.size else 0.0,
+            "neg_g": float(max(0.0, -g.min())),
+            "compl": float(np.abs(x * g).max())}
+
+
+def _kkt_case():
+    nx = ny = 8
+    spec1 = np.real(oracle.psf_spectrum(_test_psf(nx, ny)))
+    spec = 0.3 * np.concatenate([spec1, 0.5 * spec1])     # two bands, U = PSF_sym* + sigma Id
+    xbar = np.random.default_rng(25).normal(size=(2, nx, ny))
+    p = oracle.Params(gamma=1.0, sigma=1.0, lam=0.2, pd_iters=400, basis_mask=0b1111111, nlevel=2)
+    return xbar, spec, p
+
+
+def test_prox_lambda_positive_kkt_full_dictionary():
+    """The converged Condat-Vu prox (lam > 0, full Dirac + db1..db6 dictionary, U metric)
+    satisfies the optimality conditions of Eq. 7; a planted projection radius of 2 lam
+    or lam / 2 in the dual update (CPU only) violates them."""
+    xbar, spec, p = _kkt_case()
+    nb = xbar.shape[0]
+    x, v = oracle.prox(xbar, np.zeros((7, nb) + xbar.shape[1:]), spec, p)
+    k = _prox_kkt(x, v, xbar, spec, p)
+    assert k["neg_x"] == 0.0
+    assert k["ball"] < 1e-12 and k["subgrad"] < 1e-6, k
+    assert k["neg_g"] < 1e-9 and k["compl"] < 1e-9, k
+    assert 0.2 < float((x > 0).mean()) < 0.8          # both sides of the positivity constraint occur
+    proj = oracle.project_l2inf
+    for wrong in (2.0, 0.5):
+        try:
+            oracle.project_l2inf = lambda vt, lam, f=wrong: proj(vt, f * lam)
+            xw, vw = oracle.prox(xbar, np.zeros((7, nb) + xbar.shape[1:]), spec, p)
+        finally:
+            oracle.project_l2inf = proj
+        kw = _prox_kkt(xw, vw, xbar, spec, p)
+        assert max(kw["ball"], kw["subgrad"]) > 0.1, (wrong, kw)
 
 
 # ------------------------------------------------------------------ step (Eqs. 6-7)

@@ -270,19 +270,23 @@ int pfb_timing_names(pfb_ctx *ctx, char *buf, size_t len);
  * could synchronise the device.
  *   wsum_out[b] = sum over rows and the channels c of band b of wgt[row][c]
  *   (1 per visibility when wgt is NULL).
- * device: CUDA device to run on; band_of_chan [nchan] int32 (device), ids outside
- * [0, nband) are skipped; wgt [nrow][nchan] float32 (PFB_F32) / float64 (PFB_F64)
- * (device) or NULL; wsum_out [nband] float64, DEVICE memory owned by the caller,
- * valid once `stream` has completed the work.
- * The accumulators are a fixed device array of 32 doubles inside the library
- * (every GPU that loads the library holds it until the process exits): nband > 32
- * returns PFB_ERR_ARG.  The call clears them on `stream` before use.  All calls on
- * a device share that array, so calls whose work overlaps on the GPU (different
- * streams, or host threads without ordering) race: order them on one stream.  The
- * first call on a device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  Errors: PFB_ERR_ARG
- * for bad sizes or pointers, PFB_ERR_CUDA for a failed launch; pfb_last_error(NULL)
- * gives the message. */
+ * device: CUDA device to run on; the calling thread's current device is restored
+ * before the call returns.  band_of_chan [nchan] int32 (device memory); an id outside
+ * [0, nband) makes the call return PFB_ERR_ARG, as pfb_dirty does.  wgt
+ * [nrow][nchan] float32 (PFB_F32) / float64 (PFB_F64) (device memory) or NULL.
+ * wsum_out [nband] float64, host or device memory owned by the caller (the result is
+ * copied out with cudaMemcpyDefault); the call returns after `stream` has completed
+ * its work, so wsum_out is valid on return (as with pfb_dirty's host wsum_out).
+ * The accumulators are a fixed device array of 33 doubles inside the library (every
+ * GPU that loads the library holds it until the process exits): nband > 32 returns
+ * PFB_ERR_ARG.  The call clears them on `stream` before use.  All calls on a device
+ * share that array, so calls whose work overlaps on the GPU (different streams, or
+ * host threads without ordering) race: order them on one stream.  The first call on
+ * a device looks up the array's device address (with that device current), which
+ * may also load the library's device code on that device; make that first call
+ * before any stream capture.  Errors: PFB_ERR_ARG for bad sizes, host pointers where
+ * device memory is required, or out-of-range band ids; PFB_ERR_CUDA for a failed
+ * launch; pfb_last_error(NULL) gives the message. */
 int pfb_wsum_static(int device, pfb_prec prec, int64_t nrow, int32_t nchan, int32_t nband,
                     const int32_t *band_of_chan, const void *wgt, double *wsum_out, void *stream);
 

@@ -16,14 +16,19 @@ namespace pfb {
 // Accumulators shared by every call of pfb_wsum_static on a device, held by every
 // GPU that loads the library until the process exits.
 constexpr int NOALLOC_MAX_BANDS = 32;
-static __device__ __align__(256) double g_wsum_scratch[NOALLOC_MAX_BANDS];
+// (one more slot: the count of out-of-range band ids)
+static __device__ __align__(256) double g_wsum_scratch[NOALLOC_MAX_BANDS + 1];
 
+// Slot NOALLOC_MAX_BANDS counts the channels whose band id lies outside [0, nband).
 template <typename T>
 __global__ void k_wsum_static(const T *__restrict__ wgt, int64_t n, int nchan, int nband,
                               const int *__restrict__ band, double *__restrict__ acc) {
     __shared__ double sacc[NOALLOC_MAX_BANDS];
     for (int b = threadIdx.x; b < NOALLOC_MAX_BANDS; b += blockDim.x) sacc[b] = 0.0;
     __syncthreads();
+    if (blockIdx.x == 0)
+        for (int c = threadIdx.x; c < nchan; c += blockDim.x)
+            if (band[c] < 0 || band[c] >= nband) atomicAdd(&acc[NOALLOC_MAX_BANDS], 1.0);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int b = band[(int)(i % nchan)];
         if (b >= 0 && b < nband) atomicAdd(&sacc[b], wgt ? (double)wgt[i] : 1.0);
@@ -31,11 +36,6 @@ __global__ void k_wsum_static(const T *__restrict__ wgt, int64_t n, int nchan, i
     __syncthreads();
     for (int b = threadIdx.x; b < nband; b += blockDim.x)
         if (sacc[b] != 0.0) atomicAdd(&acc[b], sacc[b]);
-}
-
-__global__ void k_wsum_static_out(const double *__restrict__ acc, int nband, double *__restrict__ out) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nband) out[b] = acc[b];
 }
 
 // Device address of g_wsum_scratch, looked up once per device with that device
@@ -54,6 +54,32 @@ static double *scratch_address(int device) {
 
 // message of the last failure of a context-free call on this thread
 thread_local std::string g_free_error;
+
+// Restores the calling thread's current device when the call returns.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != device) PFB_CUDA(cudaSetDevice(device));
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// True when the GPU can dereference p as device memory (device or managed allocations).
+static bool device_pointer(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
 
 }  // namespace pfb
 
@@ -75,10 +101,14 @@ extern "C" int pfb_wsum_static(int device, pfb_prec prec, int64_t nrow, int32_t 
         return PFB_ERR_ARG;
     }
     try {
-        PFB_CUDA(cudaSetDevice(device));
+        DeviceGuard dg(device);
+        if (!device_pointer(band_of_chan) || (wgt && !device_pointer(wgt))) {
+            g_free_error = "pfb_wsum_static: band_of_chan and wgt must be device (or managed) memory";
+            return PFB_ERR_ARG;
+        }
         double *acc = scratch_address(device);
         cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-        PFB_CUDA(cudaMemsetAsync(acc, 0, NOALLOC_MAX_BANDS * sizeof(double), st));
+        PFB_CUDA(cudaMemsetAsync(acc, 0, (NOALLOC_MAX_BANDS + 1) * sizeof(double), st));
         const int64_t n = nrow * (int64_t)nchan;
         int sms = 0;
         PFB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
@@ -88,8 +118,16 @@ extern "C" int pfb_wsum_static(int device, pfb_prec prec, int64_t nrow, int32_t 
         else
             k_wsum_static<float><<<blocks, 256, 0, st>>>((const float *)wgt, n, nchan, nband, band_of_chan, acc);
         check_launch("wsum_static");
-        k_wsum_static_out<<<1, NOALLOC_MAX_BANDS, 0, st>>>(acc, nband, wsum_out);
-        check_launch("wsum_static_out");
+        // cudaMemcpyDefault takes a host or a device destination; the count of bad band ids
+        // comes back to the stack, so the call returns after `stream` has done its work
+        double bad = 0.0;
+        PFB_CUDA(cudaMemcpyAsync(wsum_out, acc, (size_t)nband * sizeof(double), cudaMemcpyDefault, st));
+        PFB_CUDA(cudaMemcpyAsync(&bad, acc + NOALLOC_MAX_BANDS, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PFB_CUDA(cudaStreamSynchronize(st));
+        if (bad != 0.0) {
+            g_free_error = "pfb_wsum_static: band_of_chan entry outside [0, nband)";
+            return PFB_ERR_ARG;
+        }
         return PFB_OK;
     } catch (const Error &e) {
         g_free_error = e.what();

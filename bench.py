@@ -71,7 +71,8 @@ def parse():
                     help="faceted Hessian instead: the image split into F x F facets (R = sum of the facets' R)")
     ap.add_argument("--facets-wide", action="store_true",
                     help="with --facets: the full pfb-clean field (8192^2, 64 channels, --clean-rows rows)")
-    ap.add_argument("--fp64", action="store_true", help="also time the FP64 path (eps 1e-9) on the same workload")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64 path (eps 1e-9) on the same workload (run by default, after the rest)")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-entry-point timings")
     return ap.parse_args()
 
@@ -239,25 +240,53 @@ def oracle_sample(obs, x, wgt_rows, rows, pix):
     t0 = time.perf_counter()
     v = oracle.degrid(sub_uvw, obs.freq, obs.band_of_chan, x, obs.dl, obs.dm)
     t1 = time.perf_counter()
-    oracle.grid(sub_uvw, obs.freq, obs.band_of_chan, v, wgt_rows, obs.nx, obs.ny, obs.dl, obs.dm, obs.nband,
-                pix=pix)
+    img = oracle.grid(sub_uvw, obs.freq, obs.band_of_chan, v, wgt_rows, obs.nx, obs.ny, obs.dl, obs.dm,
+                      obs.nband, pix=pix)
     t2 = time.perf_counter()
     nvis = len(rows) * obs.nchan
     npix_total = obs.nband * obs.nx * obs.ny
     # R^dagger at one pixel of band b reads only band b's channels: scale by pixels per band
     sec_per_vis = (t1 - t0) / nvis + (t2 - t1) / nvis * (npix_total / len(pix))
-    return 1e-6 / sec_per_vis, t2 - t0, oracle.num_threads()
+    return 1e-6 / sec_per_vis, t2 - t0, oracle.num_threads(), (v, img)
 
 
-def cpu_baseline(obs, x, wgt_np_fn, n_rows=24576, n_pix=6144, seed=5):
+def cpu_baseline(obs, x, wgt_np_fn, n_rows=24576, n_pix=6144, seed=5, want_sample=False):
     rng = np.random.default_rng(seed)
     rows = np.sort(rng.choice(obs.nrow, n_rows, replace=False))
     pix = np.sort(rng.choice(obs.nband * obs.nx * obs.ny, n_pix, replace=False))
-    value, secs, threads = oracle_sample(obs, x, wgt_np_fn(rows), rows, pix)
-    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+    wrows = wgt_np_fn(rows)
+    value, secs, threads, (v, img) = oracle_sample(obs, x, wrows, rows, pix)
+    info = {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"FP64 direct sum: R x on {n_rows} random rows x {obs.nchan} channels (1000 sources), "
                       f"R^dagger at {n_pix} random pixels; cost extrapolated linearly to the full "
                       f"{obs.nband}x{obs.nx}^2 Hessian ({secs:.1f} s of CPU work)"}
+    if want_sample:
+        return info, {"rows": rows, "pix": pix, "wgt": wrows, "vis": v, "img": img}
+    return info
+
+
+def accuracy(ctx, g, obs, uvw, freq, band, x, smp, dev, rdt):
+    """Relative L2 error of the GPU operators against the FP64 oracle on its sample: R x at the
+    sampled rows (all channels), taken from one pfb_degrid of the whole workload, and R^dagger
+    Sigma^-1 of the oracle's visibilities of those rows (with their weights) at the sampled pixels,
+    from pfb_grid on the same rows.  The error bound epsilon applies to each."""
+    import torch
+    cdt = torch.complex64 if rdt == torch.float32 else torch.complex128
+    vis = ctx.pfb_degrid(g, uvw, freq, band, x)
+    rows_t = torch.from_numpy(smp["rows"]).to(dev)
+    v_gpu = vis.index_select(0, rows_t).cpu().numpy().astype(np.complex128)
+    del vis
+    v_or = smp["vis"]
+    e_r = float(np.linalg.norm(v_gpu - v_or) / np.linalg.norm(v_or))
+    sub_uvw = uvw.index_select(0, rows_t).contiguous()
+    img = ctx.pfb_grid(g, sub_uvw, freq, band, torch.from_numpy(v_or).to(dev, cdt),
+                       torch.from_numpy(smp["wgt"]).to(dev, rdt))
+    got = img.reshape(-1).index_select(0, torch.from_numpy(smp["pix"]).to(dev)).cpu().numpy().astype(np.float64)
+    ref = smp["img"]
+    e_g = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return {"R": e_r, "R_dagger": e_g, "epsilon": g.epsilon,
+            "sample": f"R x at {len(smp['rows'])} random rows x {obs.nchan} channels; R^dagger Sigma^-1 of the "
+                      f"oracle's visibilities of those rows at {len(smp['pix'])} random pixels"}
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
@@ -429,36 +458,52 @@ def run_ours(args):
                          "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                                  "peak_source": peak_src}})
 
-    # ---- the FP64 path on the same workload (eps 1e-9), for the FP32-vs-FP64 comparison
-    fp64 = None
-    if args.fp64:
-        x64 = x.double()
-        w64 = wgt.double()
-        y64 = torch.empty_like(x64)
-        g64 = Geometry(nx=obs.nx, ny=obs.ny, dl=obs.dl, dm=obs.dm, nband=obs.nband, epsilon=1e-9)
-        ctx.pfb_hessian(g64, uvw, freq, band, x64, w64, out=y64)
-        torch.cuda.synchronize(dev)
-        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n64 = max(1, min(args.steps, 2))
-        h0.record(stream)
-        for _ in range(n64):
-            ctx.pfb_hessian(g64, uvw, freq, band, x64, w64, out=y64)
-        h1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms64 = h0.elapsed_time(h1) / n64
-        fp64 = {"value": obs.nvis / (ms64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms64, "epsilon": 1e-9,
-                "steps": n64}
-        del x64, w64, y64
-
     # ---- every entry point of the path on the same workload (one warm call, then timed calls)
     rows = None
     if not args.no_rows:
         rows = time_rows(ctx, lib, g, obs, uvw, freq, band, x, wgt, stream, dev)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    # ---- the oracle on the host cores (bounded sample), and the GPU operators' error on that sample
+    cpu, acc = None, None
+    if rank == 0 and world == 1:
         wnp = wgt.cpu().numpy().astype(np.float64)
-        cpu = cpu_baseline(obs, x_np, lambda rows: wnp[rows])
+        if args.no_cpu:
+            _, smp = cpu_baseline(obs, x_np, lambda rows: wnp[rows], n_rows=1024, n_pix=256, want_sample=True)
+        else:
+            cpu, smp = cpu_baseline(obs, x_np, lambda rows: wnp[rows], want_sample=True)
+        acc = accuracy(ctx, g, obs, uvw, freq, band, x, smp, dev, rdt)
+
+    # ---- the FP64 path on the same workload (eps 1e-9), for the FP32-vs-FP64 comparison; last,
+    # after the FP32 plans have given their memory back
+    fp64 = None
+    if not args.no_fp64 and args.prec == "f32":
+        try:
+            ctx.pfb_plan_reset()
+            x64 = x.double()
+            w64 = wgt.double()
+            y64 = torch.empty_like(x64)
+            g64 = Geometry(nx=obs.nx, ny=obs.ny, dl=obs.dl, dm=obs.dm, nband=obs.nband, epsilon=1e-9)
+            t64 = time.perf_counter()
+            ctx.pfb_hessian(g64, uvw, freq, band, x64, w64, out=y64)
+            torch.cuda.synchronize(dev)
+            t64 = time.perf_counter() - t64
+            h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h0.record(stream)
+            ctx.pfb_hessian(g64, uvw, freq, band, x64, w64, out=y64)
+            h1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms64 = h0.elapsed_time(h1)
+            # the FP32 Hessian against the FP64 one (same x and weights)
+            ctx.pfb_plan_reset()
+            ctx.pfb_hessian(g, uvw, freq, band, x, wgt, out=y)
+            torch.cuda.synchronize(dev)
+            d32 = float(torch.linalg.vector_norm(y.double() - y64) / torch.linalg.vector_norm(y64))
+            fp64 = {"value": obs.nvis / (ms64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms64, "epsilon": 1e-9,
+                    "steps": 1, "first_call_s_with_plan": t64, "fp32_over_fp64": value / (obs.nvis / ms64 / 1e3),
+                    "rel_l2_fp32_vs_fp64_hessian": d32}
+            del x64, w64, y64
+        except Exception as e:   # reported, not fatal: the FP32 line stands on its own
+            fp64 = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -466,6 +511,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded)",
                 "config": config(args, obs), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": own_launches, "clocks": clk, "fp64_path": fp64, "rows": rows,
+                "rel_l2": acc,
                 "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                             for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms"])},

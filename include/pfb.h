@@ -90,6 +90,11 @@ enum {
 /* pfb_degrid adds R x into vis_out instead of overwriting it (vis_out += R x), so that
    R of a faceted image is the sum of the facets' calls.  Other entry points ignore it. */
 #define PFB_ACCUMULATE 8u
+/* Speed switch, no effect on the result beyond rounding: FP32 plans whose w-planes are
+   powers of two of 1024..8192 cells per side transform only the image region and the
+   32 x 32 uv tiles that some visibility touches, with the pre- and post-pass folded
+   into the column transforms.  With this flag they take the full-plane transforms. */
+#define PFB_NO_PRUNED_FFT 16u
 
 typedef struct {
     int32_t nx, ny;      /* image pixels per band (even); the PSF is 2nx x 2ny */
@@ -97,7 +102,8 @@ typedef struct {
     double fov_l, fov_m; /* field of view in radians: 0 = derive, else must equal nx*dl, ny*dm */
     double epsilon;      /* requested relative L2 accuracy of R and R^dagger */
     int32_t nband;       /* n_b imaging bands */
-    uint32_t flags;      /* PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM | PFB_NO_ITEM_RECORDS | PFB_ACCUMULATE */
+    uint32_t flags;      /* PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM | PFB_NO_ITEM_RECORDS | PFB_ACCUMULATE |
+                            PFB_NO_PRUNED_FFT */
     double l0, m0;       /* direction cosines of the image centre (facets); 0, 0 = the phase centre */
 } pfb_geom;
 

@@ -13,6 +13,7 @@ PFB_NO_DIVIDE_BY_N = 1
 PFB_NO_WTERM = 2
 PFB_NO_ITEM_RECORDS = 4
 PFB_ACCUMULATE = 8
+PFB_NO_PRUNED_FFT = 16
 PFB_STEP_APPROX_GRADIENT = 1
 
 ERRORS = {

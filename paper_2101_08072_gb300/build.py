@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpfb.so")
-SOURCES = ["api.cu", "plan.cu", "wstack.cu", "image.cu", "colfft.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "plan.cu", "wstack.cu", "image.cu", "colfft.cu", "planefft.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -109,6 +109,17 @@ void Ctx::free_plan(Plan &p) {
     fr(p.d_rph, (size_t)p.nitems * sizeof(float2));
     p.d_rec = nullptr;
     p.d_rph = nullptr;
+    fr(p.d_occ, (size_t)p.nband * p.Pmax * p.ntu * (p.ntv / 32) * sizeof(uint32_t));
+    fr(p.d_rowocc, (size_t)p.nband * p.Pmax * (p.ntu / 32) * sizeof(uint32_t));
+    if (p.d_rowlist) fr(p.d_rowlist, std::max<size_t>((size_t)p.rowlist_off.back(), 1) * sizeof(int));
+    fr(p.d_tT, (size_t)p.nx * p.ny * sizeof(float2));
+    fr(p.d_wk, (size_t)p.nband * p.Pmax * sizeof(float2));
+    p.d_occ = nullptr;
+    p.d_rowocc = nullptr;
+    p.d_rowlist = nullptr;
+    p.d_tT = nullptr;
+    p.d_wk = nullptr;
+    p.pruned = false;
     p.d_scale = nullptr; p.d_rowdf = nullptr; p.d_chandf = nullptr; p.d_band = nullptr; p.d_bg = nullptr; p.d_items = nullptr; p.d_off = nullptr;
     p.d_tp = nullptr; p.d_corr = nullptr; p.d_work = nullptr; p.d_heavy = nullptr;
 }
@@ -223,7 +234,8 @@ void check_geom(const pfb_geom *g, pfb_prec prec) {
     PFB_REQUIRE(g->nx <= 65536 && g->ny <= 65536, "nx, ny must be <= 65536");
     PFB_REQUIRE(g->nband >= 1 && g->nband <= 32, "nband must be in [1, 32]");
     PFB_REQUIRE(std::isfinite(g->dl) && std::isfinite(g->dm) && g->dl > 0 && g->dm > 0, "dl, dm must be > 0");
-    PFB_REQUIRE((g->flags & ~(PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM | PFB_NO_ITEM_RECORDS | PFB_ACCUMULATE)) == 0,
+    PFB_REQUIRE((g->flags & ~(PFB_NO_DIVIDE_BY_N | PFB_NO_WTERM | PFB_NO_ITEM_RECORDS | PFB_ACCUMULATE |
+                                PFB_NO_PRUNED_FFT)) == 0,
                 "unknown flag bits");
     PFB_REQUIRE(std::isfinite(g->l0) && std::isfinite(g->m0), "l0, m0 must be finite");
     if (g->fov_l != 0)

@@ -20,118 +20,13 @@
 // conflict on banks).  The R-point DFTs run in registers: 16 = 4 x 4 and 8 = 4 x 2 by the Cooley-Tukey
 // split n = R2 n1 + n2, k = k1 + R1 k2 with the twiddles exp(-/+ 2 pi i n2 k1 / R) in between.
 #include "ctx.cuh"
+#include "fftcore.cuh"
 
 #include <cuda.h>
 
 namespace pfb {
 namespace {
-
-__device__ __forceinline__ float4 c_add(float4 a, float4 b) {
-    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-}
-__device__ __forceinline__ float4 c_sub(float4 a, float4 b) {
-    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-}
-// both complex values of a times w
-__device__ __forceinline__ float4 c_mul(float4 a, float2 w) {
-    return make_float4(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x, a.z * w.x - a.w * w.y, a.z * w.y + a.w * w.x);
-}
-// times -i (forward sign) or +i (inverse sign)
-template <bool INV> __device__ __forceinline__ float4 c_rot(float4 a) {
-    return INV ? make_float4(-a.y, a.x, -a.w, a.z) : make_float4(a.y, -a.x, a.w, -a.z);
-}
-
-// cos(2 pi e / 16), from cos(pi/8), sin(pi/8) and sqrt(1/2); sin(2 pi e / 16) = cos16(e - 4)
-constexpr double kC8 = 0.92387953251128675613, kS8 = 0.38268343236508977173, kR2 = 0.70710678118654752440;
-__host__ __device__ constexpr double cos16(int e) {
-    return (e & 15) == 0 ? 1.0 : (e & 15) == 1 ? kC8 : (e & 15) == 2 ? kR2 : (e & 15) == 3 ? kS8
-         : (e & 15) == 4 ? 0.0 : (e & 15) == 5 ? -kS8 : (e & 15) == 6 ? -kR2 : (e & 15) == 7 ? -kC8
-         : (e & 15) == 8 ? -1.0 : (e & 15) == 9 ? -kC8 : (e & 15) == 10 ? -kR2 : (e & 15) == 11 ? -kS8
-         : (e & 15) == 12 ? 0.0 : (e & 15) == 13 ? kS8 : (e & 15) == 14 ? kR2 : kC8;
-}
-
-// a times exp(-/+ 2 pi i e / R), R in {8, 16}; e is a compile-time constant once the loops unroll
-template <int R, bool INV> __device__ __forceinline__ float4 c_tw(float4 a, int e) {
-    const int f = (e * (16 / R)) & 15;
-    if (f == 0) return a;
-    if (f == 8) return make_float4(-a.x, -a.y, -a.z, -a.w);
-    if (f == 4) return c_rot<INV>(a);
-    if (f == 12) return c_rot<!INV>(a);
-    const float c = (float)cos16(f), s = (float)cos16(f - 4);
-    return c_mul(a, make_float2(c, INV ? s : -s));
-}
-
-template <bool INV> __device__ __forceinline__ void dft2(float4 &x0, float4 &x1) {
-    const float4 a = c_add(x0, x1);
-    x1 = c_sub(x0, x1);
-    x0 = a;
-}
-template <bool INV> __device__ __forceinline__ void dft4(float4 &x0, float4 &x1, float4 &x2, float4 &x3) {
-    const float4 a0 = c_add(x0, x2), a1 = c_sub(x0, x2), a2 = c_add(x1, x3), a3 = c_rot<INV>(c_sub(x1, x3));
-    x0 = c_add(a0, a2);
-    x1 = c_add(a1, a3);
-    x2 = c_sub(a0, a2);
-    x3 = c_sub(a1, a3);
-}
-
-// R-point DFT of x[0..R) in registers; output k ends up in x[operm<R>(k)]
-template <int R> __device__ __forceinline__ constexpr int operm(int k) {
-    return R == 16 ? 4 * (k & 3) + (k >> 2) : R == 8 ? 2 * (k & 3) + (k >> 2) : k;
-}
-template <int R, bool INV> __device__ __forceinline__ void dft_reg(float4 *x) {
-    if constexpr (R == 2) {
-        dft2<INV>(x[0], x[1]);
-    } else if constexpr (R == 4) {
-        dft4<INV>(x[0], x[1], x[2], x[3]);
-    } else if constexpr (R == 8) {   // n = 2 n1 + n2: DFT4 over n1, twiddle W8^(n2 k1), DFT2 over n2
-#pragma unroll
-        for (int n2 = 0; n2 < 2; ++n2) dft4<INV>(x[n2], x[2 + n2], x[4 + n2], x[6 + n2]);
-#pragma unroll
-        for (int k1 = 1; k1 < 4; ++k1) x[2 * k1 + 1] = c_tw<8, INV>(x[2 * k1 + 1], k1);
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) dft2<INV>(x[2 * k1], x[2 * k1 + 1]);
-    } else {   // 16: n = 4 n1 + n2: DFT4 over n1, twiddle W16^(n2 k1), DFT4 over n2
-#pragma unroll
-        for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
-#pragma unroll
-        for (int n2 = 1; n2 < 4; ++n2)
-#pragma unroll
-            for (int k1 = 1; k1 < 4; ++k1) x[4 * k1 + n2] = c_tw<16, INV>(x[4 * k1 + n2], n2 * k1);
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
-    }
-}
-
-__host__ __device__ constexpr int spad(int i) { return i + (i >> 4); }
-
-// twiddle exp(-/+ 2 pi i m / N) from the table of exp(-2 pi i m / N)
-template <bool INV> __device__ __forceinline__ float2 twiddle(const float2 *__restrict__ W, int m) {
-    float2 w = __ldg(W + m);
-    if (INV) w.y = -w.y;
-    return w;
-}
-__device__ __forceinline__ float2 c_mul1(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// Inputs r = 1..R-1 of a butterfly times w^r, w = exp(-/+ 2 pi i k step / N).  w and (for R >= 8) w^4
-// come from the table, the other powers from products of at most three of them (w^r = w^h w^(r-h),
-// h the largest power of two below r): two gathered loads instead of R - 1, and a twiddle error of a
-// few units in the last place, about the table's own rounding.
-template <int R, bool INV>
-__device__ __forceinline__ void apply_twiddles(float4 *v, const float2 *__restrict__ W, int k, int step) {
-    float2 w[R];
-    w[1] = twiddle<INV>(W, k * step);
-    if (R >= 8) w[4 % R] = twiddle<INV>(W, 4 * k * step);
-#pragma unroll
-    for (int r = 2; r < R; ++r) {
-        if (R >= 8 && r == 4) continue;
-        const int h = r >= 8 ? 8 : r >= 4 ? 4 : 2;
-        w[r] = h == r ? c_mul1(w[r / 2], w[r / 2]) : c_mul1(w[h], w[r - h]);
-    }
-#pragma unroll
-    for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], w[r]);
-}
+using namespace fft;
 
 // Forward: rows outside the image rows read as zero, all rows written; inverse: all rows read, the
 // image rows written.  A CTA takes its column pair through all planes in turn, so the stores of one
@@ -140,9 +35,6 @@ __device__ __forceinline__ void apply_twiddles(float4 *v, const float2 *__restri
 // them with tiled bulk copies (boxes of 2 cells x 256 rows), which keeps the 16-byte row stores off the
 // load/store pipe.  Copies are issued by thread 0, which waits (a hardware wait) until they have read
 // shared memory before the buffer is written again, and until they are complete before it exits.
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 template <int L, bool INV, bool TMA>
 __global__ void __launch_bounds__((1 << L) / 16) k_colfft(float2 *__restrict__ data, int nplanes, int Nv,
@@ -251,14 +143,14 @@ __global__ void k_colfft_table(int n, float2 *W) {
     W[m] = make_float2((float)c, (float)-s);
 }
 
-// Tensor map of a plane block for the TMA stores: [nplanes][Nu][Nv] cells of 8 bytes, box 2 x 256 x 1.
+// Tensor map of a plane block for the TMA stores: [nplanes][Nu][Nv] cells of 8 bytes, box 2 x box_rows x 1.
 // Returns false (plain stores) when the driver's encoder is not available or a layout rule of the copy
 // is not met: 16-byte base and strides, a 16-byte inner box extent, and x coordinates (2 q or
 // Nv - ny/2 + 2 q) that are even, i.e. 16-byte aligned.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-static EncodeTiledFn encode_tiled() {
+static EncodeTiledFn encode_tiled_fn() {
     static EncodeTiledFn fn = [] {
         void *f = nullptr;
         cudaDriverEntryPointQueryResult q{};
@@ -273,19 +165,6 @@ static EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-static bool colfft_tensor_map(CUtensorMap *map, float2 *data, int Nu, int Nv, int nplanes, int ny) {
-    EncodeTiledFn enc = encode_tiled();
-    if (!enc || Nu < 256 || Nu % 256 || Nv % 2 || (Nv - ny / 2) % 2 || (ny / 2) % 2) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)Nv, (cuuint64_t)Nu, (cuuint64_t)nplanes};
-    const cuuint64_t strides[2] = {(cuuint64_t)Nv * 8, (cuuint64_t)Nu * Nv * 8};
-    const cuuint32_t box[3] = {2, 256, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    if (reinterpret_cast<uintptr_t>(data) % 16 || strides[0] % 16 || strides[1] % 16) return false;
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, data, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int L, bool INV>
 void launch_colfft(float2 *data, int nplanes, int Nv, int64_t plane_sz, int nx, int ny, const float2 *W,
                    cudaStream_t st) {
@@ -293,7 +172,7 @@ void launch_colfft(float2 *data, int nplanes, int Nv, int64_t plane_sz, int nx, 
     const size_t smem = (size_t)(spad(N - 1) + 1) * sizeof(float4);
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
-    if (colfft_tensor_map(&map, data, N, Nv, nplanes, ny)) {
+    if (plane_tensor_map(&map, data, N, Nv, nplanes, ny, 256)) {
         PFB_CUDA(cudaFuncSetAttribute(k_colfft<L, INV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         k_colfft<L, INV, true><<<(unsigned)(ny / 2), N / 16, smem, st>>>(data, nplanes, Nv, plane_sz, nx, ny, W,
@@ -309,6 +188,31 @@ void launch_colfft(float2 *data, int nplanes, int Nv, int64_t plane_sz, int nx, 
 
 }  // namespace
 
+bool plane_tensor_map(CUtensorMap *map, float2 *data, int Nu, int Nv, int nplanes, int ny, int box_rows) {
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc || Nu < box_rows || Nu % box_rows || Nv % 2 || (Nv - ny / 2) % 2 || (ny / 2) % 2) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)Nv, (cuuint64_t)Nu, (cuuint64_t)nplanes};
+    const cuuint64_t strides[2] = {(cuuint64_t)Nv * 8, (cuuint64_t)Nu * Nv * 8};
+    const cuuint32_t box[3] = {2, (cuuint32_t)box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (reinterpret_cast<uintptr_t>(data) % 16 || strides[0] % 16 || strides[1] % 16) return false;
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, data, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+const float2 *fft_twiddles(Ctx &ctx, int n, cudaStream_t st) {
+    const std::string name = "colfft_w" + std::to_string(n);
+    float2 *W = (float2 *)ctx.scratch(name, (size_t)n * sizeof(float2));
+    auto tag = ctx.zero_tag.find(name);
+    if (tag == ctx.zero_tag.end() || tag->second.first != (uint64_t)n) {
+        k_colfft_table<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, W);
+        check_launch("colfft_table");
+        ctx.zero_tag[name] = {(uint64_t)n, 1};
+    }
+    return W;
+}
+
 bool colfft_fits(int Nu, int Nv, int nx, int ny) {
     int L = 0;
     while ((1 << L) < Nu) ++L;
@@ -319,14 +223,7 @@ bool colfft_fits(int Nu, int Nv, int nx, int ny) {
 void colfft_planes(Ctx &ctx, float2 *data, int nplanes, int Nu, int Nv, int nx, int ny, bool inverse,
                    cudaStream_t st) {
     PFB_REQUIRE(colfft_fits(Nu, Nv, nx, ny), "column transform: unsupported plane shape");
-    const std::string name = "colfft_w" + std::to_string(Nu);
-    float2 *W = (float2 *)ctx.scratch(name, (size_t)Nu * sizeof(float2));
-    auto tag = ctx.zero_tag.find(name);
-    if (tag == ctx.zero_tag.end() || tag->second.first != (uint64_t)Nu) {
-        k_colfft_table<<<(unsigned)((Nu + 255) / 256), 256, 0, st>>>(Nu, W);
-        check_launch("colfft_table");
-        ctx.zero_tag[name] = {(uint64_t)Nu, 1};
-    }
+    const float2 *W = fft_twiddles(ctx, Nu, st);
     const int64_t plane_sz = (int64_t)Nu * Nv;
 #define PFB_COLFFT(LV)                                                                                  \
     (inverse ? launch_colfft<LV, true>(data, nplanes, Nv, plane_sz, nx, ny, W, st)                      \

@@ -3,6 +3,8 @@
 
 #include "common.cuh"
 
+#include <cuda.h>
+
 #include <functional>
 
 namespace pfb {
@@ -62,6 +64,16 @@ struct Plan {
     // FP32 tile kernels: per-item geometry records in item order (optional)
     float4 *d_rec = nullptr;
     float2 *d_rph = nullptr;
+    // Pruned plane transforms (planefft.cu), FP32 plans with power-of-two planes of 1024..8192 cells:
+    // which 32 x 32 tiles of each w-plane any visibility touches, the tile-rows holding at least one such
+    // tile, and t per pixel transposed to the column-pair order of the column kernels.
+    bool pruned = false;
+    uint32_t *d_occ = nullptr;       // [nband][Pmax][ntu][ntv / 32] bit tv of tile (tu, tv) in plane k
+    uint32_t *d_rowocc = nullptr;    // [nband][Pmax][ntu / 32] bit tu: tile-row tu holds a touched tile
+    int *d_rowlist = nullptr;        // occupied (plane, tile-row) pairs as k << 16 | tu, by band, then k
+    std::vector<int64_t> rowlist_off;  // [nband][Pmax + 1]: first list entry of (b, k)
+    float4 *d_tT = nullptr;          // [ny / 2][nx]: t of the column pair q at image row i (two float pairs)
+    float2 *d_wk = nullptr;          // [nband][Pmax]: w-plane k of band b, w0 + k dw, as a float pair
     size_t bytes = 0;
 
     BandGeom geom(int b) const {
@@ -179,6 +191,19 @@ struct Ctx {
 // colfft.cu: the FP32 column pass of the w-plane transforms over the image region (see there)
 bool colfft_fits(int Nu, int Nv, int nx, int ny);
 void colfft_planes(Ctx &ctx, float2 *data, int nplanes, int Nu, int Nv, int nx, int ny, bool inverse,
+                   cudaStream_t st);
+// twiddle table exp(-2 pi i m / n), m < n, kept in the context
+const float2 *fft_twiddles(Ctx &ctx, int n, cudaStream_t st);
+// tensor map of a plane block [nplanes][Nu][Nv] (8-byte cells) for 2 x box_rows x 1 boxes; false when the
+// driver's encoder or the layout rules of the copy do not allow one
+bool plane_tensor_map(CUtensorMap *map, float2 *data, int Nu, int Nv, int nplanes, int ny, int box_rows);
+
+// planefft.cu: pruned FP32 plane transforms (see there)
+bool pruned_fits(const Plan &p);
+void build_pruned_tables(Ctx &ctx, Plan &p, cudaStream_t st);
+void plane_forward(Ctx &ctx, const Plan &p, int b, const float *x, int k_lo, int k_hi, float2 *planes,
+                   cudaStream_t st);
+void plane_inverse(Ctx &ctx, const Plan &p, int b, int k_lo, int k_hi, float2 *planes, float *image,
                    cudaStream_t st);
 
 // Scoped timer: records events around the enclosed launches when timing is on.

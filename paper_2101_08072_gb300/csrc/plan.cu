@@ -679,6 +679,7 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
                                                   (float *)p.d_corr);
     check_launch("pixel_tables");
     build_item_records(ctx, p, st);
+    build_pruned_tables(ctx, p, st);
     // the host vectors above die with this scope: wait for the copies
     PFB_CUDA(cudaStreamSynchronize(st));
     ctx.release("sort_tmp");

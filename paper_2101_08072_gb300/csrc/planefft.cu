@@ -1,0 +1,584 @@
+// Pruned w-plane transforms of the FP32 path.
+//
+// R and R^dagger apply a 2-D DFT to every w-plane of a band (Section 2's w-stacking, Eqs. 1 and 3).  Two
+// facts make most of that work avoidable:
+//  - in image space only the image region carries data: the pixel (i, j) sits at
+//    ((i - nx/2) mod Nu, (j - ny/2) mod Nv), so the forward transform's input is zero outside the image
+//    rows and columns, and the inverse transform's output is needed only there;
+//  - in uv space only the cells that some visibility's kernel footprint touches matter: the gridding
+//    kernels leave every other cell zero, and degridding reads no other cell.  A w-plane of a wide-field
+//    plan holds the visibilities of one narrow range of w, which lie along a band of the uv plane: in the
+//    MeerKAT-like plan (4096^2 pixels of 1.5", 8192^2 planes) about 6% of the 32 x 32 tiles and 36% of the
+//    tile-rows of a plane are touched.
+// The plan records which tiles of each plane are touched (from the item counts per tile and w bucket:
+// an item of bucket kq reaches planes kq q .. kq q + q + W_w - 2) and lists the (plane, tile-row) pairs
+// that hold a touched tile.  Then
+//   forward (degridding):
+//     k_colfwd   per pair of adjacent image columns and every plane of the block: the pre-pass values
+//                x corr exp(-2 pi i w_k t) at the image rows (zero at the other rows), an N-point DFT
+//                along the column, and TMA stores of the occupied tile-rows only;
+//     k_rowfft   per occupied row: a DFT along the row from its image columns (the rest is zero), stored
+//                in the row's touched 32-cell segments only;
+//   inverse (gridding):
+//     k_rowfft   per occupied row: a DFT along the row from its touched segments (the rest is zero),
+//                stored at the image columns only;
+//     k_colinv   per image column pair and every plane: a DFT along the column from its occupied rows
+//                (the other rows are zero) and the post-pass sum over planes of Re exp(+2 pi i w_k t) H_k
+//                at the image rows, kept in shared memory and multiplied by the correction
+//                1/(n psihat) at the end.
+// The pre- and post-pass values never go through HBM, and no cell outside the touched tiles is computed
+// or read.  The per-pixel inputs of the column kernels (x corr and t = n - 1 - t_c as a float pair) are
+// first transposed into column-pair order, [q][i], so that the threads of a column read them coalesced;
+// a column kernel re-reads its share from L2 for every plane.
+//
+// The DFTs are the mixed-radix Stockham stages of fftcore.cuh on pairs of complex values (two columns,
+// or two rows, at once), N/16 threads per pair.
+#include "ctx.cuh"
+#include "fftcore.cuh"
+
+#include <algorithm>
+
+namespace pfb {
+namespace {
+using namespace fft;
+
+// The Stockham stages of an N = 2^L point DFT (10 <= L <= 13) of float4 pairs held by T = N/16 threads.
+// On entry v[r] = x[tid + r T].  On return thread tid holds output row d_b + r Ns in v[b RL + operm<RL>(r)]
+// (b < BPT, r < RL), where j = tid + b T, d_b = (j / Ns) Ns RL + (j mod Ns) and Ns is the returned value.
+// sm is the padded exchange buffer.  The function begins with a barrier (so the caller's earlier reads of
+// sm are complete) and ends after its last read of sm, without a barrier.
+template <int L>
+struct Shape {
+    static constexpr int N = 1 << L, T = N / 16;
+    static constexpr int NST16 = L / 4, RL = (L % 4) ? (1 << (L % 4)) : 16, BPT = 16 / RL;
+    static constexpr int NMID = NST16 - 1 - ((L % 4) ? 0 : 1);   // radix-16 stages between the first and last
+};
+
+template <int L, bool INV>
+__device__ __forceinline__ int fft_stages(float4 *v, float4 *sm, const float2 *__restrict__ W, int tid) {
+    using S = Shape<L>;
+    constexpr int N = S::N, T = S::T, RL = S::RL, BPT = S::BPT;
+    dft_reg<16, INV>(v);   // first stage: radix 16, Ns = 1, no twiddles
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm[spad(tid * 16 + r)] = v[operm<16>(r)];
+    __syncthreads();
+    int Ns = 16;
+#pragma unroll
+    for (int s = 0; s < S::NMID; ++s) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = sm[spad(tid + r * T)];
+        const int k = tid & (Ns - 1);
+        apply_twiddles<16, INV>(v, W, k, N / (Ns * 16));
+        dft_reg<16, INV>(v);
+        __syncthreads();
+        const int d = (tid / Ns) * Ns * 16 + k;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) sm[spad(d + r * Ns)] = v[operm<16>(r)];
+        __syncthreads();
+        Ns *= 16;
+    }
+#pragma unroll
+    for (int b = 0; b < BPT; ++b)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[b * RL + r] = sm[spad(tid + b * T + r * (N / RL))];
+    const int step = N / (Ns * RL);
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = tid + b * T, k = j & (Ns - 1);
+        apply_twiddles<RL, INV>(v + b * RL, W, k, step);
+        dft_reg<RL, INV>(v + b * RL);
+    }
+    return Ns;
+}
+
+// After fft_stages: write the outputs densely (row-major, no padding) into sm, then a barrier.
+template <int L>
+__device__ __forceinline__ void dense_to_smem(const float4 *v, float4 *sm, int tid, int Ns) {
+    using S = Shape<L>;
+    __syncthreads();   // every thread has read the exchange buffer
+#pragma unroll
+    for (int b = 0; b < S::BPT; ++b) {
+        const int j = tid + b * S::T, k = j & (Ns - 1);
+        const int d = (j / Ns) * Ns * S::RL + k;
+#pragma unroll
+        for (int r = 0; r < S::RL; ++r) sm[d + r * Ns] = v[b * S::RL + operm<S::RL>(r)];
+    }
+}
+
+__device__ __forceinline__ bool bit_set(const uint32_t *__restrict__ words, int i) {
+    return (__ldg(words + (i >> 5)) >> (i & 31)) & 1u;
+}
+
+// exp(-/+ 2 pi i w_k t) for t = (t_hi, t_lo) and w_k = (wk_hi, wk_lo): the phase frac(w_k t) in turns,
+// reduced in float-float arithmetic (frac_prod_df), then evaluated in FP32.
+__device__ __forceinline__ void screen(float2 wk, float t_hi, float t_lo, float *s, float *c) {
+    float h, l;
+    frac_prod_df(wk.x, wk.y, t_hi, t_lo, &h, &l);
+    sincos_turns(h + l, s, c);
+}
+
+// ---------------------------------------------------------------- forward column pass (fused pre-pass)
+// One CTA per pair of adjacent image columns (plane columns c, c + 1); it takes the pair through the
+// planes [k_lo, k_lo + nk) of band b.  rowocc: the band's tile-row masks [Pmax][ntu / 32].
+template <int L, bool TMA>
+__global__ void __launch_bounds__((1 << L) / 16)
+    k_colfwd(float2 *__restrict__ planes, int nk, int k_lo, int Nv, int64_t plane_sz, int nx, int ny,
+             const float2 *__restrict__ xcT, const float4 *__restrict__ tT, const float2 *__restrict__ wk,
+             int wstack, const uint32_t *__restrict__ rowocc, const float2 *__restrict__ W,
+             const __grid_constant__ CUtensorMap tmap) {
+    using S = Shape<L>;
+    constexpr int N = S::N, T = S::T;
+    extern __shared__ __align__(1024) float4 sm[];
+    const int tid = threadIdx.x;
+    const int q = blockIdx.x, hq = ny / 4;
+    const int c = q < hq ? 2 * q : Nv - ny / 2 + 2 * (q - hq);
+    const int rlo = nx / 2, rhi = N - nx / 2;
+    const int ntu = N / TILE, nw = ntu / 32;
+    const float2 *xq = xcT + (int64_t)q * nx;
+    const float4 *tq = tT + (int64_t)q * nx;
+    float4 v[16];
+
+    for (int pl = 0; pl < nk; ++pl) {
+        const int k = k_lo + pl;
+        const float2 w = wk[k];
+        const uint32_t *occ = rowocc + (int64_t)k * nw;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int row = tid + r * T;
+            float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < rlo || row >= rhi) {
+                const int i = row < rlo ? row + nx / 2 : row - rhi;
+                const float2 xc = xq[i];
+                if (wstack) {
+                    const float4 t = tq[i];
+                    float s0, c0, s1, c1;
+                    screen(w, t.x, t.y, &s0, &c0);
+                    screen(w, t.z, t.w, &s1, &c1);
+                    e = make_float4(xc.x * c0, -xc.x * s0, xc.y * c1, -xc.y * s1);
+                } else {
+                    e = make_float4(xc.x, 0.f, xc.y, 0.f);
+                }
+            }
+            v[r] = e;
+        }
+        const int Ns = fft_stages<L, false>(v, sm, W, tid);
+        if constexpr (TMA) {
+            dense_to_smem<L>(v, sm, tid, Ns);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid < 32) {
+                // the lanes of warp 0 store the occupied tile-rows: boxes of 2 cells x TILE rows
+                for (int tu = tid; tu < ntu; tu += 32) {
+                    if (!bit_set(occ, tu)) continue;
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                            reinterpret_cast<uint64_t>(&tmap)),
+                        "r"(c), "r"(tu * TILE), "r"(pl), "r"(smem_u32(sm + tu * TILE))
+                        : "memory");
+                }
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            }
+        } else {
+            float2 *base = planes + (int64_t)pl * plane_sz + c;
+#pragma unroll
+            for (int b = 0; b < S::BPT; ++b) {
+                const int j = tid + b * T, kk = j & (Ns - 1);
+                const int d = (j / Ns) * Ns * S::RL + kk;
+#pragma unroll
+                for (int r = 0; r < S::RL; ++r) {
+                    const int row = d + r * Ns;
+                    if (bit_set(occ, row / TILE))
+                        *reinterpret_cast<float4 *>(base + (int64_t)row * Nv) = v[b * S::RL + operm<S::RL>(r)];
+                }
+            }
+        }
+    }
+    if (TMA && tid < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- inverse column pass (fused post-pass)
+// One CTA per image column pair.  Shared memory: the exchange buffer, then the running post-pass sums of
+// the pair's image rows ([nx] float2, one writer per row).  image [nx][ny] of the band; accumulate adds
+// the result to it (a later plane block).
+template <int L>
+__global__ void __launch_bounds__((1 << L) / 16)
+    k_colinv(const float2 *__restrict__ planes, int nk, int k_lo, int Nv, int64_t plane_sz, int nx, int ny,
+             const float4 *__restrict__ tT, const float2 *__restrict__ wk, int wstack,
+             const uint32_t *__restrict__ rowocc, const float *__restrict__ corr, int accumulate,
+             float *__restrict__ image, const float2 *__restrict__ W) {
+    using S = Shape<L>;
+    constexpr int N = S::N, T = S::T;
+    extern __shared__ __align__(1024) float4 sm[];
+    float2 *acc = reinterpret_cast<float2 *>(sm + spad(N - 1) + 1);
+    const int tid = threadIdx.x;
+    const int q = blockIdx.x, hq = ny / 4;
+    const int c = q < hq ? 2 * q : Nv - ny / 2 + 2 * (q - hq);
+    const int j0 = q < hq ? 2 * q + ny / 2 : 2 * (q - hq);
+    const int rlo = nx / 2, rhi = N - nx / 2;
+    const int nw = (N / TILE) / 32;
+    const float4 *tq = tT + (int64_t)q * nx;
+    for (int i = tid; i < nx; i += T) acc[i] = make_float2(0.f, 0.f);
+    float4 v[16];
+
+    for (int pl = 0; pl < nk; ++pl) {
+        const int k = k_lo + pl;
+        const uint32_t *occ = rowocc + (int64_t)k * nw;
+        const float2 *base = planes + (int64_t)pl * plane_sz + c;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int row = tid + r * T;
+            v[r] = bit_set(occ, row / TILE) ? *reinterpret_cast<const float4 *>(base + (int64_t)row * Nv)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int Ns = fft_stages<L, true>(v, sm, W, tid);
+        const float2 w = wk[k];
+#pragma unroll
+        for (int b = 0; b < S::BPT; ++b) {
+            const int j = tid + b * T, kk = j & (Ns - 1);
+            const int d = (j / Ns) * Ns * S::RL + kk;
+#pragma unroll
+            for (int r = 0; r < S::RL; ++r) {
+                const int row = d + r * Ns;
+                if (row >= rlo && row < rhi) continue;
+                const int i = row < rlo ? row + nx / 2 : row - rhi;
+                const float4 h = v[b * S::RL + operm<S::RL>(r)];
+                float2 a = acc[i];
+                if (wstack) {
+                    const float4 t = tq[i];
+                    float s0, c0, s1, c1;
+                    screen(w, t.x, t.y, &s0, &c0);
+                    screen(w, t.z, t.w, &s1, &c1);
+                    a.x += h.x * c0 - h.y * s0;
+                    a.y += h.z * c1 - h.w * s1;
+                } else {
+                    a.x += h.x;
+                    a.y += h.z;
+                }
+                acc[i] = a;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < nx; i += T) {
+        const int64_t p = (int64_t)i * ny + j0;
+        const float2 cr = *reinterpret_cast<const float2 *>(corr + p);
+        float2 o = make_float2(acc[i].x * cr.x, acc[i].y * cr.y);
+        if (accumulate) {
+            const float2 prev = *reinterpret_cast<const float2 *>(image + p);
+            o.x += prev.x;
+            o.y += prev.y;
+        }
+        *reinterpret_cast<float2 *>(image + p) = o;
+    }
+}
+
+// ---------------------------------------------------------------- row pass
+// One CTA per pair of rows (u0, u0 + 1) of one occupied tile-row; list[e] = k << 16 | tu, and the CTA
+// takes rows tu TILE + 2 p, p = blockIdx.x mod 16.  occ: the band's tile masks [Pmax][ntu][ntv / 32].
+//   INV: reads the touched segments (the rest is zero), writes the image columns;
+//   forward: reads the image columns (the rest is zero), writes the touched segments.
+template <int L, bool INV>
+__global__ void __launch_bounds__((1 << L) / 16)
+    k_rowfft(float2 *__restrict__ planes, int k_lo, int ntu, int64_t plane_sz, int ny,
+             const int *__restrict__ list, const uint32_t *__restrict__ occ, const float2 *__restrict__ W) {
+    using S = Shape<L>;
+    constexpr int N = S::N, T = S::T;
+    constexpr int NW = N / TILE / 32;   // mask words per tile-row
+    extern __shared__ __align__(1024) float4 sm[];
+    const int tid = threadIdx.x;
+    const int ent = list[blockIdx.x / (TILE / 2)];
+    const int k = ent >> 16, tu = ent & 0xffff;
+    const int u0 = tu * TILE + 2 * (int)(blockIdx.x % (TILE / 2));
+    float2 *row0 = planes + (int64_t)(k - k_lo) * plane_sz + (int64_t)u0 * N;
+    float2 *row1 = row0 + N;
+    const uint32_t *segs = occ + ((int64_t)k * ntu + tu) * NW;
+    const int clo = ny / 2, chi = N - ny / 2;
+    float4 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int m = tid + r * T;
+        const bool in = INV ? bit_set(segs, m / TILE) : (m < clo || m >= chi);
+        if (in) {
+            const float2 a = row0[m], b = row1[m];
+            v[r] = make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    const int Ns = fft_stages<L, INV>(v, sm, W, tid);
+    dense_to_smem<L>(v, sm, tid, Ns);
+    __syncthreads();
+#pragma unroll 4
+    for (int m = tid; m < N; m += T) {
+        const bool out = INV ? (m < clo || m >= chi) : bit_set(segs, m / TILE);
+        if (out) {
+            const float4 e = sm[m];
+            row0[m] = make_float2(e.x, e.y);
+            row1[m] = make_float2(e.z, e.w);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- tables
+// xcT[q][i] = (x corr)(i, j0(q)), (x corr)(i, j0(q) + 1): the pre-pass inputs in column-pair order
+// (j0(q) = ny/2 + 2 q for q < ny/4, 2 (q - ny/4) after), by a 32 x 32 tile transpose.
+__global__ void k_xc_transpose(const float *__restrict__ x, const float *__restrict__ corr, int nx, int ny,
+                               float2 *__restrict__ xcT) {
+    __shared__ float2 tile[32][33];
+    const int hq = ny / 4, nq = ny / 2;
+    const int i0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
+    for (int kk = threadIdx.y; kk < 32; kk += 8) {
+        const int i = i0 + kk, q = q0 + threadIdx.x;
+        float2 e = make_float2(0.f, 0.f);
+        if (i < nx && q < nq) {
+            const int j0 = q < hq ? 2 * q + ny / 2 : 2 * (q - hq);
+            const int64_t p = (int64_t)i * ny + j0;
+            const float2 a = *reinterpret_cast<const float2 *>(x + p);
+            const float2 cr = *reinterpret_cast<const float2 *>(corr + p);
+            e = make_float2(a.x * cr.x, a.y * cr.y);
+        }
+        tile[kk][threadIdx.x] = e;
+    }
+    __syncthreads();
+    for (int kk = threadIdx.y; kk < 32; kk += 8) {
+        const int q = q0 + kk, i = i0 + threadIdx.x;
+        if (q < nq && i < nx) xcT[(int64_t)q * nx + i] = tile[threadIdx.x][kk];
+    }
+}
+
+// tT[q][i] = t(i, j0(q)), t(i, j0(q) + 1) from the per-pixel float pairs of an FP32 plan
+__global__ void k_t_transpose(const float2 *__restrict__ tp, int nx, int ny, float4 *__restrict__ tT) {
+    const int64_t n = (int64_t)nx * (ny / 2);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e / nx), i = (int)(e - (int64_t)q * nx);
+        const int hq = ny / 4;
+        const int j0 = q < hq ? 2 * q + ny / 2 : 2 * (q - hq);
+        const float2 a = tp[(int64_t)i * ny + j0], b = tp[(int64_t)i * ny + j0 + 1];
+        tT[e] = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+// Touched tiles: an item of bucket (b, tile, kq) reaches planes kq q .. kq q + q + W_w - 2 of tile.
+__global__ void k_occupancy(const int64_t *__restrict__ off, int64_t nkeys, int ntiles, int ntu, int ntv,
+                            int nkq, int q, int Ww, int Pmax, const BandGeom *__restrict__ bgs,
+                            uint32_t *__restrict__ occ) {
+    for (int64_t key = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; key < nkeys;
+         key += (int64_t)gridDim.x * blockDim.x) {
+        if (off[key + 1] <= off[key]) continue;
+        const int kq = (int)(key % nkq);
+        const int64_t bt = key / nkq;
+        const int b = (int)(bt / ntiles), t = (int)(bt - (int64_t)b * ntiles);
+        const int tu = t / ntv, tv = t - tu * ntv;
+        const int P = bgs[b].P;
+        for (int cc = 0; cc < q + Ww - 1; ++cc) {
+            const int k = kq * q + cc;
+            if (k >= P) break;
+            atomicOr(&occ[(((int64_t)b * Pmax + k) * ntu + tu) * (ntv / 32) + (tv >> 5)], 1u << (tv & 31));
+        }
+    }
+}
+
+int log2_exact(int n) {
+    int L = 0;
+    while ((1 << L) < n) ++L;
+    return (1 << L) == n ? L : -1;
+}
+
+template <int L, bool TMA>
+void launch_colfwd(unsigned grid, size_t smem, cudaStream_t st, float2 *planes, int nk, int k_lo, int Nv,
+                   int64_t plane_sz, int nx, int ny, const float2 *xcT, const float4 *tT, const float2 *wk,
+                   int wstack, const uint32_t *rowocc, const float2 *W, const CUtensorMap &map) {
+    PFB_CUDA(cudaFuncSetAttribute(k_colfwd<L, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_colfwd<L, TMA><<<grid, (1 << L) / 16, smem, st>>>(planes, nk, k_lo, Nv, plane_sz, nx, ny, xcT, tT, wk, wstack,
+                                                         rowocc, W, map);
+}
+
+template <int L>
+void launch_colinv(unsigned grid, size_t smem, cudaStream_t st, const float2 *planes, int nk, int k_lo, int Nv,
+                   int64_t plane_sz, int nx, int ny, const float4 *tT, const float2 *wk, int wstack,
+                   const uint32_t *rowocc, const float *corr, int accumulate, float *image, const float2 *W) {
+    PFB_CUDA(cudaFuncSetAttribute(k_colinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_colinv<L><<<grid, (1 << L) / 16, smem, st>>>(planes, nk, k_lo, Nv, plane_sz, nx, ny, tT, wk, wstack, rowocc,
+                                                    corr, accumulate, image, W);
+}
+
+template <int L, bool INV>
+void launch_rowfft(unsigned grid, cudaStream_t st, float2 *planes, int k_lo, int ntu, int64_t plane_sz, int ny,
+                   const int *list, const uint32_t *occ, const float2 *W) {
+    const size_t smem = (size_t)(spad((1 << L) - 1) + 1) * sizeof(float4);
+    PFB_CUDA(cudaFuncSetAttribute(k_rowfft<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_rowfft<L, INV><<<grid, (1 << L) / 16, smem, st>>>(planes, k_lo, ntu, plane_sz, ny, list, occ, W);
+}
+
+#define PFB_L_SWITCH(Lv, CALL)                                              \
+    switch (Lv) {                                                           \
+        case 10: CALL(10); break;                                           \
+        case 11: CALL(11); break;                                           \
+        case 12: CALL(12); break;                                           \
+        case 13: CALL(13); break;                                           \
+        default: throw Error(PFB_ERR_ARG, "pruned plane transform: unsupported plane size"); \
+    }
+
+}  // namespace
+
+bool pruned_fits(const Plan &p) {
+    const int Lu = log2_exact(p.Nu), Lv = log2_exact(p.Nv);
+    return p.prec == PFB_F32 && Lu >= 10 && Lu <= 13 && Lv >= 10 && Lv <= 13 && colfft_fits(p.Nu, p.Nv, p.nx, p.ny) &&
+           p.nx >= 2 && p.ny >= 4 && p.Pmax < (1 << 15) && !(p.flags & PFB_NO_PRUNED_FFT);
+}
+
+void build_pruned_tables(Ctx &ctx, Plan &p, cudaStream_t st) {
+    if (!pruned_fits(p)) return;
+    const int nw = p.ntv / 32;
+    const size_t occ_words = (size_t)p.nband * p.Pmax * p.ntu * nw;
+    const size_t need = occ_words * 4 + (size_t)p.nx * p.ny * sizeof(float2) + (size_t)p.nband * p.Pmax * 8 +
+                        (size_t)p.nband * p.Pmax * p.ntu * 4 + (16u << 20);
+    if (ctx.available() < need) return;
+    p.d_occ = (uint32_t *)ctx.dalloc(occ_words * 4);
+    p.bytes += occ_words * 4;
+    PFB_CUDA(cudaMemsetAsync(p.d_occ, 0, occ_words * 4, st));
+    const int64_t ntiles = (int64_t)p.ntu * p.ntv;
+    k_occupancy<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((p.nkeys + 255) / 256, 64LL * ctx.num_sms)), 256, 0,
+                  st>>>(p.d_off, p.nkeys, (int)ntiles, p.ntu, p.ntv, p.nkq, p.q, p.Ww, p.Pmax, p.d_bg, p.d_occ);
+    check_launch("occupancy");
+    std::vector<uint32_t> occ(occ_words);
+    PFB_CUDA(cudaMemcpyAsync(occ.data(), p.d_occ, occ_words * 4, cudaMemcpyDeviceToHost, st));
+    PFB_CUDA(cudaStreamSynchronize(st));
+    const int rw = p.ntu / 32;
+    std::vector<uint32_t> rowocc((size_t)p.nband * p.Pmax * rw, 0u);
+    std::vector<int> list;
+    p.rowlist_off.assign((size_t)p.nband * (p.Pmax + 1), 0);
+    for (int b = 0; b < p.nband; ++b) {
+        for (int k = 0; k <= p.Pmax; ++k) {
+            p.rowlist_off[(size_t)b * (p.Pmax + 1) + k] = (int64_t)list.size();
+            if (k == p.Pmax || k >= p.P[b]) continue;
+            for (int tu = 0; tu < p.ntu; ++tu) {
+                const uint32_t *wd = occ.data() + (((size_t)b * p.Pmax + k) * p.ntu + tu) * nw;
+                bool any = false;
+                for (int w = 0; w < nw; ++w) any = any || wd[w] != 0u;
+                if (!any) continue;
+                list.push_back(k << 16 | tu);
+                rowocc[((size_t)b * p.Pmax + k) * rw + tu / 32] |= 1u << (tu & 31);
+            }
+        }
+    }
+    std::vector<float2> wk((size_t)p.nband * p.Pmax, make_float2(0.f, 0.f));
+    for (int b = 0; b < p.nband; ++b)
+        for (int k = 0; k < p.P[b]; ++k) {
+            const double w = p.w0[b] + (double)k * p.dw;
+            const float hi = (float)w;
+            wk[(size_t)b * p.Pmax + k] = make_float2(hi, (float)(w - (double)hi));
+        }
+    p.d_rowocc = (uint32_t *)ctx.dalloc(rowocc.size() * 4);
+    p.d_rowlist = (int *)ctx.dalloc(std::max<size_t>(list.size(), 1) * sizeof(int));
+    p.d_wk = (float2 *)ctx.dalloc(wk.size() * sizeof(float2));
+    p.d_tT = (float4 *)ctx.dalloc((size_t)p.nx * p.ny * sizeof(float2));
+    p.bytes += rowocc.size() * 4 + list.size() * sizeof(int) + wk.size() * sizeof(float2) +
+               (size_t)p.nx * p.ny * sizeof(float2);
+    PFB_CUDA(cudaMemcpyAsync(p.d_rowocc, rowocc.data(), rowocc.size() * 4, cudaMemcpyHostToDevice, st));
+    if (!list.empty())
+        PFB_CUDA(cudaMemcpyAsync(p.d_rowlist, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    PFB_CUDA(cudaMemcpyAsync(p.d_wk, wk.data(), wk.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    const int64_t n = (int64_t)p.nx * (p.ny / 2);
+    k_t_transpose<<<(unsigned)std::min<int64_t>((n + 255) / 256, 32LL * ctx.num_sms), 256, 0, st>>>(
+        reinterpret_cast<const float2 *>(p.d_tp), p.nx, p.ny, p.d_tT);
+    check_launch("t_transpose");
+    // the host vectors die with this scope
+    PFB_CUDA(cudaStreamSynchronize(st));
+    p.pruned = true;
+}
+
+// rows (tile-rows x TILE) and touched tiles of band b over planes [k_lo, k_hi), from the list
+static void occupied_counts(const Plan &p, int b, int k_lo, int k_hi, double *rows) {
+    const int64_t e0 = p.rowlist_off[(size_t)b * (p.Pmax + 1) + k_lo];
+    const int64_t e1 = p.rowlist_off[(size_t)b * (p.Pmax + 1) + k_hi];
+    *rows = (double)(e1 - e0) * TILE;
+}
+
+void plane_forward(Ctx &ctx, const Plan &p, int b, const float *x, int k_lo, int k_hi, float2 *planes,
+                   cudaStream_t st) {
+    const int nk = k_hi - k_lo;
+    const int Lu = log2_exact(p.Nu), Lv = log2_exact(p.Nv);
+    const int64_t npix = (int64_t)p.nx * p.ny;
+    const int64_t plane_sz = (int64_t)p.Nu * p.Nv;
+    const float2 *Wu = fft_twiddles(ctx, p.Nu, st);
+    const float2 *Wv = p.Nv == p.Nu ? Wu : fft_twiddles(ctx, p.Nv, st);
+    double rows = 0;
+    occupied_counts(p, b, k_lo, k_hi, &rows);
+    float2 *xcT = (float2 *)ctx.scratch("xcT", (size_t)npix * sizeof(float));
+    {
+        KTimer t(ctx, "xc_transpose", st, 12.0 * npix);
+        const dim3 grid((unsigned)((p.nx + 31) / 32), (unsigned)((p.ny / 2 + 31) / 32));
+        k_xc_transpose<<<grid, dim3(32, 8), 0, st>>>(x, (const float *)p.d_corr, p.nx, p.ny, xcT);
+        check_launch("xc_transpose");
+    }
+    const float2 *wk = p.d_wk + (size_t)b * p.Pmax;
+    const uint32_t *rowocc = p.d_rowocc + (size_t)b * p.Pmax * (p.ntu / 32);
+    {
+        KTimer t(ctx, "col_fwd", st, 12.0 * npix + rows * p.ny * 8.0);
+        CUtensorMap map;
+        std::memset(&map, 0, sizeof(map));
+        const bool tma = plane_tensor_map(&map, planes, p.Nu, p.Nv, nk, p.ny, TILE);
+        const size_t smem = (size_t)(spad(p.Nu - 1) + 1) * sizeof(float4);
+        const unsigned grid = (unsigned)(p.ny / 2);
+#define PFB_CF(LV)                                                                                         \
+    (tma ? launch_colfwd<LV, true>(grid, smem, st, planes, nk, k_lo, p.Nv, plane_sz, p.nx, p.ny, xcT, p.d_tT, \
+                                   wk, p.wstack ? 1 : 0, rowocc, Wu, map)                                  \
+         : launch_colfwd<LV, false>(grid, smem, st, planes, nk, k_lo, p.Nv, plane_sz, p.nx, p.ny, xcT, p.d_tT, \
+                                    wk, p.wstack ? 1 : 0, rowocc, Wu, map))
+        PFB_L_SWITCH(Lu, PFB_CF)
+#undef PFB_CF
+        check_launch("col_fwd");
+    }
+    const int64_t e0 = p.rowlist_off[(size_t)b * (p.Pmax + 1) + k_lo];
+    const int64_t e1 = p.rowlist_off[(size_t)b * (p.Pmax + 1) + k_hi];
+    if (e1 > e0) {
+        KTimer t(ctx, "row_fwd", st, rows * (p.ny + p.Nv) * 8.0);
+        const uint32_t *occ = p.d_occ + (size_t)b * p.Pmax * p.ntu * (p.ntv / 32);
+        const unsigned grid = (unsigned)((e1 - e0) * (TILE / 2));
+#define PFB_RF(LV) launch_rowfft<LV, false>(grid, st, planes, k_lo, p.ntu, plane_sz, p.ny, p.d_rowlist + e0, occ, Wv)
+        PFB_L_SWITCH(Lv, PFB_RF)
+#undef PFB_RF
+        check_launch("row_fwd");
+    }
+}
+
+void plane_inverse(Ctx &ctx, const Plan &p, int b, int k_lo, int k_hi, float2 *planes, float *image,
+                   cudaStream_t st) {
+    const int nk = k_hi - k_lo;
+    const int Lu = log2_exact(p.Nu), Lv = log2_exact(p.Nv);
+    const int64_t npix = (int64_t)p.nx * p.ny;
+    const int64_t plane_sz = (int64_t)p.Nu * p.Nv;
+    const float2 *Wu = fft_twiddles(ctx, p.Nu, st);
+    const float2 *Wv = p.Nv == p.Nu ? Wu : fft_twiddles(ctx, p.Nv, st);
+    double rows = 0;
+    occupied_counts(p, b, k_lo, k_hi, &rows);
+    const int64_t e0 = p.rowlist_off[(size_t)b * (p.Pmax + 1) + k_lo];
+    const int64_t e1 = p.rowlist_off[(size_t)b * (p.Pmax + 1) + k_hi];
+    if (e1 > e0) {
+        KTimer t(ctx, "row_inv", st, rows * (p.Nv + p.ny) * 8.0);
+        const uint32_t *occ = p.d_occ + (size_t)b * p.Pmax * p.ntu * (p.ntv / 32);
+        const unsigned grid = (unsigned)((e1 - e0) * (TILE / 2));
+#define PFB_RI(LV) launch_rowfft<LV, true>(grid, st, planes, k_lo, p.ntu, plane_sz, p.ny, p.d_rowlist + e0, occ, Wv)
+        PFB_L_SWITCH(Lv, PFB_RI)
+#undef PFB_RI
+        check_launch("row_inv");
+    }
+    {
+        KTimer t(ctx, "col_inv", st, rows * p.ny * 8.0 + npix * (8.0 + 4.0 + 4.0 + (k_lo > 0 ? 4.0 : 0.0)));
+        const float2 *wk = p.d_wk + (size_t)b * p.Pmax;
+        const uint32_t *rowocc = p.d_rowocc + (size_t)b * p.Pmax * (p.ntu / 32);
+        const size_t smem = (size_t)(spad(p.Nu - 1) + 1) * sizeof(float4) + (size_t)p.nx * sizeof(float2);
+        const unsigned grid = (unsigned)(p.ny / 2);
+#define PFB_CI(LV)                                                                                              \
+    launch_colinv<LV>(grid, smem, st, planes, nk, k_lo, p.Nv, plane_sz, p.nx, p.ny, p.d_tT, wk, p.wstack ? 1 : 0, \
+                      rowocc, (const float *)p.d_corr, k_lo > 0 ? 1 : 0, image, Wu)
+        PFB_L_SWITCH(Lu, PFB_CI)
+#undef PFB_CI
+        check_launch("col_inv");
+    }
+}
+
+}  // namespace pfb

@@ -1207,7 +1207,9 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
     // room for cuFFT work areas is taken from the same budget
     const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
     cx_t<T> *planes = (cx_t<T> *)ctx.scratch("planes", (size_t)blk * p.Nu * p.Nv * cxs);
-    const bool keep = keep_zeros_fits(ctx, p, cxs, blk, 1, "dg_in");
+    // pruned transforms: one buffer, no kept zeros (cells outside the touched tiles are never read)
+    const bool pruned = sizeof(T) == 4 && p.pruned;
+    const bool keep = !pruned && keep_zeros_fits(ctx, p, cxs, blk, 1, "dg_in");
     cx_t<T> *in = keep ? kept_zero_buffer<T>(ctx, p, "dg_in0", blk, st) : planes;
     const int64_t npix = (int64_t)p.nx * p.ny;
     const double plane_bytes = (double)p.Nu * p.Nv * cxs;
@@ -1219,6 +1221,9 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
         for (int k_lo = 0; k_lo < g.P; k_lo += blk) {
             const int k_hi = std::min(g.P, k_lo + blk);
             const int nk = k_hi - k_lo;
+            if (pruned) {
+                plane_forward(ctx, p, b, (const float *)(image + b * npix), k_lo, k_hi, (float2 *)planes, st);
+            } else {
             if (!keep) {
                 KTimer t(ctx, "memset_planes", st, nk * plane_bytes, 0);
                 PFB_CUDA(cudaMemsetAsync(planes, 0, (size_t)nk * p.Nu * p.Nv * cxs, st));
@@ -1237,6 +1242,7 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
                 } else {
                     fft_planes<T>(ctx, in, nk, p.Nu, p.Nv, CUFFT_FORWARD, st, keep ? planes : nullptr);
                 }
+            }
             }
             if (i1 > i0 && sizeof(T) == 4 && degrid_tiles_fit(p)) {
                 KTimer t(ctx, "degrid_tiles", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
@@ -1264,7 +1270,9 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
     const size_t cxs = sizeof(cx_t<T>);
     const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
     cx_t<T> *planes = (cx_t<T> *)ctx.scratch("planes", (size_t)blk * p.Nu * p.Nv * cxs);
-    const bool keep = keep_zeros_fits(ctx, p, cxs, blk, p.nband, "gr_in");
+    // pruned transforms: one buffer; the tiles without items are never read, so they need no zeros
+    const bool pruned = sizeof(T) == 4 && p.pruned;
+    const bool keep = !pruned && keep_zeros_fits(ctx, p, cxs, blk, p.nband, "gr_in");
     const int64_t npix = (int64_t)p.nx * p.ny;
     const int R = p.Ww + p.q - 1;
     const size_t smem = (size_t)R * TILE * TILE * cxs;
@@ -1274,7 +1282,7 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
         const BandGeom g = p.geom(b);
         const int64_t w0 = p.work_begin[b], w1 = p.work_begin[b + 1];
         // tiles zeroed per call: the heavy ones (filled by reductions), and the empty ones unless kept
-        const int64_t h0 = p.heavy_begin[b], h1 = keep ? p.empty_begin[b] : p.heavy_begin[b + 1];
+        const int64_t h0 = p.heavy_begin[b], h1 = (keep || pruned) ? p.empty_begin[b] : p.heavy_begin[b + 1];
         const double nvb = (double)band_nvis(p, b);
         const double nit = (double)(p.band_items_end[b] - p.band_items_begin[b]);
         cx_t<T> *const out = planes;
@@ -1312,6 +1320,10 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                                                                              unit_vis ? 1 : 0, g, k_lo, k_hi, in);
                 }
                 check_launch("grid_tiles");
+            }
+            if (pruned) {
+                plane_inverse(ctx, p, b, k_lo, k_hi, (float2 *)out, (float *)(image + b * npix), st);
+                continue;
             }
             {
                 KTimer t(ctx, "fft_inv", st, 2.0 * nk * plane_bytes, split_fft<T>(p) ? 1 : 0);

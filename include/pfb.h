@@ -136,7 +136,9 @@ typedef struct {
  * Returns PFB_OK and *ctx, or an error (then *ctx is NULL). */
 int pfb_create(pfb_ctx **ctx, int device, size_t hbm_budget_bytes);
 
-/* Free every device buffer the context owns.  Waits for the context's work. */
+/* Free every device buffer the context owns.  The buffers are released in stream
+ * order after the work of the context's last call; the function does not wait for
+ * the device, and work of other contexts or streams is not held up. */
 void pfb_destroy(pfb_ctx *ctx);
 
 /* Message of the last failure on this context ("" if none).  The pointer stays
@@ -148,7 +150,11 @@ const char *pfb_last_error(const pfb_ctx *ctx);
  * like), returning their memory to the context's budget; the next call rebuilds
  * what it needs.  Call it after changing uvw/freq/band or PSF contents in place,
  * or between the phases of a solve that use different geometries (the PSF's 2x
- * field, then the image).  Synchronises the device. */
+ * field, then the image).  The buffers are released in stream order after the
+ * work of the context's last call (the context allocates from a memory pool of its
+ * own, on the stream of each call), so the function neither waits for the device
+ * nor holds up work on other streams.  Calls of one context are expected in the
+ * order of one stream (or ordered by the caller), as before. */
 int pfb_plan_reset(pfb_ctx *ctx);
 
 /* R, degridding (Section 2, Eq. 1): image [nband][nx][ny] -> vis_out [nrow][nchan].
@@ -242,8 +248,8 @@ int pfb_step(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_params
  * full R^dagger Sigma^-1 R applications: one per exact-gradient step plus one for
  * the dirty image and the PSF together (each is one half: a gridding pass without
  * the degridding).  history_out (host, [max_outer][3], may be NULL) receives each
- * step's stats as pfb_step's stats_out.  Synchronises the device (step 2) and the
- * stream after every step (the stopping test reads the update on the host).
+ * step's stats as pfb_step's stats_out.  Synchronises the stream after every step
+ * (the stopping test reads the update on the host).
  * Arrays: vis, wgt as pfb_dirty; dirty_out [nband][nx][ny]; psf_out
  * [nband][2nx][2ny]; x_inout [nband][nx][ny]; dual_inout [nbasis][nband][nx][ny]. */
 int pfb_clean(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_params *params, int32_t max_outer,

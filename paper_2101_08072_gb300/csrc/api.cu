@@ -12,19 +12,49 @@ namespace pfb {
 
 Ctx::~Ctx() {
     cudaSetDevice(device);
-    cudaDeviceSynchronize();
-    for (auto &pp : plans) free_plan(*pp);
-    plans.clear();
-    for (auto &s : spectra) cudaFree(s.spec);
-    spectra.clear();
-    for (auto &kv : bufs) cudaFree(kv.second.ptr);
-    bufs.clear();
+    release_all_buffers();
     for (auto &kv : ffts) cufftDestroy(kv.second);
     ffts.clear();
     for (cudaEvent_t e : copy_events) cudaEventDestroy(e);
     copy_events.clear();
+    // destroying a stream, event or pool with work or frees still queued returns at once; the resources
+    // go when that work is done
     if (copy_stream) cudaStreamDestroy(copy_stream);
     copy_stream = nullptr;
+    if (pool) cudaMemPoolDestroy(pool);
+    if (own) cudaStreamDestroy(own);
+    if (done) cudaEventDestroy(done);
+}
+
+void Ctx::init_memory() {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    PFB_CUDA(cudaMemPoolCreate(&pool, &props));
+    // keep released memory for the context's later plans instead of returning it at every synchronisation
+    uint64_t keep = budget;
+    PFB_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    PFB_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    PFB_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+}
+
+void Ctx::release_all_buffers() {
+    if (!own) return;
+    // the frees follow the work queued so far: inside a call the work on its stream, otherwise the last call's
+    if (in_call) cudaEventRecord(done, cur);
+    cudaStreamWaitEvent(own, done, 0);
+    const cudaStream_t saved = cur;
+    cur = own;
+    for (auto &pp : plans) free_plan(*pp);
+    plans.clear();
+    for (auto &sp : spectra) dfree(sp.spec, sp.bytes);
+    spectra.clear();
+    for (auto &b : bufs)
+        if (b.second.ptr) dfree(b.second.ptr, b.second.bytes);
+    bufs.clear();
+    zero_tag.clear();
+    cur = saved;
 }
 
 cudaStream_t Ctx::copy_stream_get() {
@@ -47,11 +77,11 @@ void *Ctx::dalloc(size_t bytes) {
         throw Error(PFB_ERR_OOM, "HBM budget exceeded: need " + std::to_string(bytes) + " more bytes, " +
                                      std::to_string(available()) + " left of " + std::to_string(budget));
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, cur);
     if (e != cudaSuccess) {
         cudaGetLastError();
         throw Error(e == cudaErrorMemoryAllocation ? PFB_ERR_OOM : PFB_ERR_CUDA,
-                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+                    std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
     }
     used += bytes;
     return p;
@@ -59,7 +89,7 @@ void *Ctx::dalloc(size_t bytes) {
 
 void Ctx::dfree(void *p, size_t bytes) {
     if (!p) return;
-    cudaFree(p);
+    cudaFreeAsync(p, cur);
     used -= std::min(used, bytes == 0 ? (size_t)16 : bytes);
 }
 
@@ -124,17 +154,7 @@ void Ctx::free_plan(Plan &p) {
     p.d_tp = nullptr; p.d_corr = nullptr; p.d_work = nullptr; p.d_heavy = nullptr;
 }
 
-void Ctx::reset() {
-    cudaDeviceSynchronize();
-    for (auto &pp : plans) free_plan(*pp);
-    plans.clear();
-    for (auto &s : spectra) dfree(s.spec, s.bytes);
-    spectra.clear();
-    for (auto &b : bufs)
-        if (b.second.ptr) dfree(b.second.ptr, b.second.bytes);
-    bufs.clear();
-    zero_tag.clear();
-}
+void Ctx::reset() { release_all_buffers(); }
 
 cufftHandle Ctx::fft(int n0, int n1, int batch, cufftType type) {
     FftKey k{n0, n1, batch, (int)type};
@@ -207,22 +227,55 @@ using namespace pfb;
 
 namespace {
 
+// Runs f on the context; a call that queues device work passes its stream, on which the context's
+// allocations and frees are then ordered and `done` is recorded at the end.
 template <typename F>
-int guarded(pfb_ctx *ctx, F &&f) {
+int guarded(pfb_ctx *ctx, void *stream, F &&f) {
     if (!ctx) return PFB_ERR_ARG;
-    ctx->impl.err.clear();
+    Ctx &c = ctx->impl;
+    c.err.clear();
+    struct Bind {
+        Ctx &c;
+        Bind(Ctx &c_, cudaStream_t s) : c(c_) {
+            c.cur = s;
+            c.in_call = true;
+        }
+        ~Bind() {
+            cudaEventRecord(c.done, c.cur);
+            c.in_call = false;
+        }
+    };
     try {
-        PFB_CUDA(cudaSetDevice(ctx->impl.device));
-        f(ctx->impl);
+        PFB_CUDA(cudaSetDevice(c.device));
+        Bind bind(c, reinterpret_cast<cudaStream_t>(stream));
+        f(c);
         return PFB_OK;
     } catch (const Error &e) {
-        ctx->impl.err = e.what();
+        c.err = e.what();
         return e.code;
     } catch (const std::bad_alloc &) {
-        ctx->impl.err = "host allocation failed";
+        c.err = "host allocation failed";
         return PFB_ERR_OOM;
     } catch (const std::exception &e) {
-        ctx->impl.err = e.what();
+        c.err = e.what();
+        return PFB_ERR_CUDA;
+    }
+}
+// calls without device work (timing, reset): the stream stays the last call's
+template <typename F>
+int guarded_host(pfb_ctx *ctx, F &&f) {
+    if (!ctx) return PFB_ERR_ARG;
+    Ctx &c = ctx->impl;
+    c.err.clear();
+    try {
+        PFB_CUDA(cudaSetDevice(c.device));
+        f(c);
+        return PFB_OK;
+    } catch (const Error &e) {
+        c.err = e.what();
+        return e.code;
+    } catch (const std::exception &e) {
+        c.err = e.what();
         return PFB_ERR_CUDA;
     }
 }
@@ -349,14 +402,14 @@ int pfb_kernel_support(double epsilon, pfb_prec prec) {
 }
 
 int pfb_timing(pfb_ctx *ctx, int enable) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded_host(ctx, [&](Ctx &c) {
         c.timing.clear();
         c.timing.on = enable != 0;
     });
 }
 
 int pfb_timing_read(pfb_ctx *ctx, const char *kernel, int64_t *launches, double *total_ms, double *bytes) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded_host(ctx, [&](Ctx &c) {
         PFB_REQUIRE(kernel && launches && total_ms, "kernel, launches and total_ms must not be NULL");
         c.timing.resolve();
         if (std::string(kernel) == "*") {
@@ -378,7 +431,7 @@ int pfb_timing_read(pfb_ctx *ctx, const char *kernel, int64_t *launches, double 
 }
 
 int pfb_timing_names(pfb_ctx *ctx, char *buf, size_t len) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded_host(ctx, [&](Ctx &c) {
         PFB_REQUIRE(buf && len > 0, "buf must hold at least one byte");
         c.timing.resolve();
         std::string s;
@@ -406,6 +459,13 @@ int pfb_create(pfb_ctx **out, int device, size_t budget) {
     cudaMemGetInfo(&fr, &tot);
     cudaDeviceGetAttribute(&c->impl.num_sms, cudaDevAttrMultiProcessorCount, device);
     c->impl.budget = budget ? budget : (size_t)(0.85 * (double)fr);
+    try {
+        c->impl.init_memory();
+    } catch (const Error &) {
+        cudaGetLastError();
+        delete c;
+        return PFB_ERR_CUDA;
+    }
     *out = c;
     return PFB_OK;
 }
@@ -415,12 +475,12 @@ void pfb_destroy(pfb_ctx *ctx) { delete ctx; }
 const char *pfb_last_error(const pfb_ctx *ctx) { return ctx ? ctx->impl.err.c_str() : pfb::g_free_error.c_str(); }
 
 int pfb_plan_reset(pfb_ctx *ctx) {
-    return guarded(ctx, [&](Ctx &c) { c.reset(); });
+    return guarded_host(ctx, [&](Ctx &c) { c.reset(); });
 }
 
 int pfb_degrid(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
                const double *freq, const int32_t *band, const void *image, void *vis_out, void *stream) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded(ctx, stream, [&](Ctx &c) {
         check_geom(g, prec);
         check_data(nrow, nchan, uvw, freq, band);
         PFB_REQUIRE(image && vis_out, "image and vis_out must not be NULL");
@@ -434,7 +494,7 @@ int pfb_degrid(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int
 int pfb_grid(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
              const double *freq, const int32_t *band, const void *vis, const void *wgt, void *image_out,
              void *stream) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded(ctx, stream, [&](Ctx &c) {
         check_geom(g, prec);
         check_data(nrow, nchan, uvw, freq, band);
         PFB_REQUIRE(vis && image_out, "vis and image_out must not be NULL");
@@ -457,7 +517,7 @@ static void wsum_to_host(Ctx &c, const Plan &p, pfb_prec prec, const void *wgt, 
 int pfb_dirty(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
               const double *freq, const int32_t *band, const void *vis, const void *wgt, void *image_out,
               double *wsum_out, void *stream) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded(ctx, stream, [&](Ctx &c) {
         check_geom(g, prec);
         check_data(nrow, nchan, uvw, freq, band);
         PFB_REQUIRE(vis && image_out, "vis and image_out must not be NULL");
@@ -473,7 +533,7 @@ int pfb_dirty(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int3
 int pfb_psf(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
             const double *freq, const int32_t *band, const void *wgt, void *psf_out, double *wsum_out,
             void *stream) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded(ctx, stream, [&](Ctx &c) {
         check_geom(g, prec);
         check_data(nrow, nchan, uvw, freq, band);
         PFB_REQUIRE(psf_out, "psf_out must not be NULL");
@@ -490,7 +550,7 @@ int pfb_psf(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_
 int pfb_hessian(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
                 const double *freq, const int32_t *band, const void *wgt, const void *x, void *y_out,
                 void *stream) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded(ctx, stream, [&](Ctx &c) {
         check_geom(g, prec);
         check_data(nrow, nchan, uvw, freq, band);
         PFB_REQUIRE(x && y_out, "x and y_out must not be NULL");
@@ -510,7 +570,7 @@ int pfb_hessian(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, in
 int pfb_hessian_host(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, int32_t nchan, const double *uvw,
                      const double *freq, const int32_t *band, const void *wgt, const void *x, void *y_out,
                      void *stream) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded(ctx, stream, [&](Ctx &c) {
         check_geom(g, prec);
         check_data(nrow, nchan, uvw, freq, band);
         PFB_REQUIRE(x && y_out, "x and y_out must not be NULL");
@@ -525,7 +585,7 @@ int pfb_hessian_host(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nro
 
 int pfb_psf_conv(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const void *psf, const void *x, void *y_out,
                  void *stream) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded(ctx, stream, [&](Ctx &c) {
         PFB_REQUIRE(g != nullptr, "geom is NULL");
         PFB_REQUIRE(prec == PFB_F32 || prec == PFB_F64, "prec must be PFB_F32 or PFB_F64");
         PFB_REQUIRE(g->nx >= 2 && g->ny >= 2 && g->nx % 2 == 0 && g->ny % 2 == 0, "nx, ny must be even");
@@ -544,7 +604,7 @@ int pfb_step(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const pfb_params *p
              const double *uvw, const double *freq, const int32_t *band, const void *wgt, const void *dirty,
              const void *psf, const double *wsum, void *x_inout, void *dual_inout, int64_t *n_hessian_out,
              double *stats_out, void *stream) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded(ctx, stream, [&](Ctx &c) {
         check_geom(g, prec);
         check_data(nrow, nchan, uvw, freq, band);
         check_params(prm, g);
@@ -560,7 +620,7 @@ int pfb_clean(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const pfb_params *
               int64_t nrow, int32_t nchan, const double *uvw, const double *freq, const int32_t *band,
               const void *vis, const void *wgt, void *dirty_out, void *psf_out, double *wsum_out, void *x_inout,
               void *dual_inout, int32_t *n_outer_out, int64_t *n_hessian_out, double *history_out, void *stream) {
-    return guarded(ctx, [&](Ctx &c) {
+    return guarded(ctx, stream, [&](Ctx &c) {
         check_geom(g, prec);
         check_data(nrow, nchan, uvw, freq, band);
         check_params(prm, g);

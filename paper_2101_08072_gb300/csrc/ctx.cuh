@@ -173,6 +173,17 @@ struct Ctx {
     int host_nchan = -1;
     cudaStream_t copy_stream_get();
     cudaEvent_t copy_event(size_t i);
+    // Stream-ordered memory: every buffer comes from the context's own pool, allocated and freed in the
+    // order of the stream of the call that needs it (cur), so neither allocation nor release waits for the
+    // device.  Each call records `done` on its stream when its work is queued; pfb_plan_reset and
+    // pfb_destroy release the buffers on the context's own stream `own` after that event.
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t own = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaStream_t cur = nullptr;
+    bool in_call = false;
+    void init_memory();                    // pool, own stream and done event (at creation)
+    void release_all_buffers();            // free plans, spectra and scratch on `own` after `done`
 
     ~Ctx();
     void *dalloc(size_t bytes);            // counted against the budget

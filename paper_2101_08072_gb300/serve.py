@@ -8,10 +8,15 @@ HBM between steps.  The scheduler thread
   * admits queued requests, in arrival order, whenever their HBM reservation fits
     the memory left by the active ones (a request larger than the whole budget is
     rejected);
+  * sets an admitted request up (uploads, PSF, plan, dirty image) on a worker
+    thread, so the scheduler keeps issuing the running requests' steps meanwhile;
+    the library allocates and frees stream-ordered, so neither the set-up nor a
+    completion stalls the other requests' work on the device;
   * keeps every admitted request on its own CUDA stream and libpfb context, and
     issues one step at a time per request, so the steps of different requests run
     concurrently on the device; a request admitted while others are mid-solve
-    joins the rotation at once (continuous batching, not a FIFO of whole solves);
+    joins the rotation once its set-up is done (continuous batching, not a FIFO of
+    whole solves);
   * completes a request when its last step's event has fired, returns its image,
     dual and per-step statistics through a Future, and records its latency
     (submit -> result).
@@ -31,7 +36,7 @@ import math
 import queue
 import threading
 import time
-from concurrent.futures import Future
+from concurrent.futures import Future, ThreadPoolExecutor
 from typing import Any, Callable
 
 import numpy as np
@@ -200,6 +205,7 @@ class Server:
         self._stop = threading.Event()
         self._t0 = None
         self._t_last = None
+        self._setup_pool = ThreadPoolExecutor(max_workers=2, thread_name_prefix="pfb-admit")
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.thread.start()
 
@@ -215,6 +221,7 @@ class Server:
     def close(self):
         self._stop.set()
         self.thread.join()
+        self._setup_pool.shutdown(wait=True)
 
     def metrics(self) -> dict:
         lat = np.array(self.latencies)
@@ -225,12 +232,21 @@ class Server:
                 "mvis_per_s": (self.vis_done / span / 1e6) if span and span > 0 else None}
 
     # ------------------------------------------------------------------ loop
+    def _setup(self, r: Request, fut: Future, reserve: int):
+        """Device set-up of an admitted request, on a worker thread."""
+        if self.slot_factory is _Slot:
+            import torch
+            torch.cuda.set_device(self.device)
+        return self.slot_factory(r, fut, self.device, reserve)
+
     def _loop(self):
         if self.slot_factory is _Slot:
             import torch
             torch.cuda.set_device(self.device)
         slots: dict[int, Any] = {}
-        while not self._stop.is_set() or slots or not self.inbox.empty() or self.sched.pending:
+        setting_up: dict[int, tuple] = {}   # id -> (set-up future, request future)
+        while (not self._stop.is_set() or slots or setting_up or not self.inbox.empty()
+               or self.sched.pending):
             while True:
                 try:
                     r = self.inbox.get_nowait()
@@ -245,10 +261,16 @@ class Server:
                 r.t_admit = time.perf_counter()
                 if self._t0 is None:
                     self._t0 = r.t_admit
+                setting_up[r.id] = (self._setup_pool.submit(self._setup, r, fut, self.sched.active[r.id]), fut)
+            for rid in list(setting_up):
+                sf, fut = setting_up[rid]
+                if not sf.done():
+                    continue
+                setting_up.pop(rid)
                 try:
-                    slots[r.id] = self.slot_factory(r, fut, self.device, self.sched.active[r.id])
+                    slots[rid] = sf.result()
                 except Exception as e:   # failed set-up: report to the caller, free the reservation
-                    self.sched.release(r.id)
+                    self.sched.release(rid)
                     fut.set_exception(e)
             idle = True
             for rid in list(slots):

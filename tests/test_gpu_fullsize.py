@@ -55,7 +55,7 @@ def test_grid_sampled_pixels(big):
     img = big["ctx"].pfb_grid(big["g"], big["uvw"], big["freq"], big["band"], torch.from_numpy(y).to(dev),
                               torch.from_numpy(w).to(dev))
     npx = obs.nband * obs.nx * obs.ny
-    pix = np.sort(np.random.default_rng(13).choice(npx, 16, replace=False))
+    pix = np.sort(np.random.default_rng(13).choice(npx, 256, replace=False))
     ref = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, y.astype(np.complex128), w.astype(np.float64),
                       obs.nx, obs.ny, obs.dl, obs.dm, obs.nband, pix=pix)
     got = img.reshape(-1)[torch.from_numpy(pix).to(dev)].cpu().numpy()
@@ -117,8 +117,60 @@ def test_fp64_path_full_size_sampled(big):
     y = synth.random_vis(rng, (obs.nrow, obs.nchan))
     img = ctx.pfb_grid(*a, torch.from_numpy(y).to(dev))
     npx = obs.nband * obs.nx * obs.ny
-    pix = np.sort(np.random.default_rng(20).choice(npx, 8, replace=False))
+    pix = np.sort(np.random.default_rng(20).choice(npx, 64, replace=False))
     ref = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, y, None, obs.nx, obs.ny, obs.dl, obs.dm, obs.nband,
                       pix=pix)
     got = img.reshape(-1)[torch.from_numpy(pix).to(dev)].cpu().numpy()
     assert rel_l2(got, ref) <= 1e-9
+
+
+def _near_and_random(rng, centres, nband, nx, ny, n_near, n_rand):
+    """Flat pixel indices: n_near within 3 pixels of the given (b, i, j) centres, n_rand uniform."""
+    out = set()
+    while len(out) < n_near:
+        b, i, j = centres[rng.integers(len(centres))]
+        di, dj = rng.integers(-3, 4, 2)
+        out.add(int(b * nx * ny + ((i + di) % nx) * ny + (j + dj) % ny))
+    while len(out) < n_near + n_rand:
+        out.add(int(rng.integers(nband * nx * ny)))
+    return np.array(sorted(out), dtype=np.int64)
+
+
+def test_psf_sampled_pixels(big):
+    """pfb_psf at the full size: the 8192^2 PSF of the 4096^2 image (16384^2 w-planes, whose transforms
+    take the full-plane path), against the oracle at pixels around the peak and at random."""
+    obs, ctx, dev = big["obs"], big["ctx"], big["dev"]
+    rng = np.random.default_rng(21)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan)).astype(np.float32)
+    psf, wsum = ctx.pfb_psf(big["g"], big["uvw"], big["freq"], big["band"], torch.from_numpy(w).to(dev))
+    n2x, n2y = 2 * obs.nx, 2 * obs.ny
+    pix = _near_and_random(rng, [(b, obs.nx, obs.ny) for b in range(obs.nband)], obs.nband, n2x, n2y, 32, 32)
+    ones = np.ones((obs.nrow, obs.nchan), dtype=np.complex128)
+    ref = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, ones, w.astype(np.float64), n2x, n2y, obs.dl, obs.dm,
+                      obs.nband, pix=pix)
+    got = psf.reshape(-1)[torch.from_numpy(pix).to(dev)].cpu().numpy()
+    assert rel_l2(got, ref) <= TOL
+    ws_ref = oracle.wsum(obs.band_of_chan, w.astype(np.float64), obs.nrow, obs.nband)
+    assert np.allclose(wsum, ws_ref, rtol=1e-9)
+    del psf
+    ctx.pfb_plan_reset()
+
+
+def test_hessian_all_rows_sampled(big):
+    """The Hessian on all 907,200 rows (the bench's plan: heavy tiles in chunks that add into zeroed
+    cells, light tiles stored whole) at pixels near the sources and at random, for a sparse sky whose
+    direct-sum evaluation stays in seconds."""
+    obs, ctx, g, dev = big["obs"], big["ctx"], big["g"], big["dev"]
+    rng = np.random.default_rng(22)
+    x = synth.point_source_image(rng, obs.nband, obs.nx, obs.ny, 16)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan)).astype(np.float32)
+    hx = ctx.pfb_hessian(g, big["uvw"], big["freq"], big["band"], torch.from_numpy(x.astype(np.float32)).to(dev),
+                         torch.from_numpy(w).to(dev))
+    src = [tuple(int(t) for t in c) for c in np.argwhere(x != 0)]
+    pix = _near_and_random(rng, src, obs.nband, obs.nx, obs.ny, 48, 16)
+    x32 = x.astype(np.float32).astype(np.float64)
+    v = oracle.degrid(obs.uvw, obs.freq, obs.band_of_chan, x32, obs.dl, obs.dm)
+    ref = oracle.grid(obs.uvw, obs.freq, obs.band_of_chan, v, w.astype(np.float64), obs.nx, obs.ny, obs.dl,
+                      obs.dm, obs.nband, pix=pix)
+    got = hx.reshape(-1)[torch.from_numpy(pix).to(dev)].cpu().numpy()
+    assert rel_l2(got, ref) <= 2 * TOL

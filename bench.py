@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-max-pix", type=int, default=4096)
     ap.add_argument("--serve-max-rows", type=int, default=1_000_000)
+    ap.add_argument("--serve-fp64-max-rows", type=int, default=200_000,
+                    help="row cap of the FP64 requests (eps 1e-9, 1331 taps per visibility in FP64: "
+                         "a 1e6-row FP64 request alone takes minutes)")
     ap.add_argument("--clean", action="store_true",
                     help="full pfb-clean workload instead: PSF, dirty image and --clean-outer steps (pfb_clean)")
     ap.add_argument("--clean-npix", type=int, default=8192)
@@ -67,6 +70,10 @@ def parse():
     ap.add_argument("--clean-sigma", type=float, default=1e-3)
     ap.add_argument("--clean-lambda", type=float, default=1e-4)
     ap.add_argument("--clean-basis", type=int, default=0b1111111, help="basis mask (bit 0 Dirac, 1..6 db1..db6)")
+    ap.add_argument("--clean-safe-gamma", action="store_true",
+                    help="cap gamma at 1.9 / lambda_max(U^-1 H), estimated by power iteration (PFB_STEP_SAFE_GAMMA)")
+    ap.add_argument("--clean-tol", type=float, default=0.0,
+                    help="stop at this relative update (0: run --clean-outer steps)")
     ap.add_argument("--facets", type=int, default=0,
                     help="faceted Hessian instead: the image split into F x F facets (R = sum of the facets' R)")
     ap.add_argument("--facets-wide", action="store_true",
@@ -524,7 +531,7 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------ serving workload
-def serve_requests(n, seed=3, max_pix=4096, max_rows=1_000_000):
+def serve_requests(n, seed=3, max_pix=4096, max_rows=1_000_000, fp64_max_rows=200_000):
     """n requests, each an independent pfb-clean solve: image 512^2..4096^2, rows 1e4..1e6,
     channels 8..128, bands 1..4 (log-uniform), half FP32 at eps 1e-5 and half FP64 at
     eps 1e-9, 10 steps each.  Visibilities are noise-like (the solver's cost does not
@@ -540,6 +547,8 @@ def serve_requests(n, seed=3, max_pix=4096, max_rows=1_000_000):
         nchan = int(synth.log_uniform_int(rng, 8, 129))
         nband = int(min(nchan, synth.log_uniform_int(rng, 1, 5)))
         prec = "f32" if i % 2 == 0 else "f64"
+        if prec == "f64":
+            nrow = min(nrow, fp64_max_rows)
         rows = np.sort(rng.choice(base.nrow, nrow, replace=False))
         freq = np.linspace(0.856e9, 1.712e9, nchan)
         cell = 1.5 * 4096 / npix * synth.ARCSEC
@@ -558,7 +567,8 @@ def run_serve(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2101_08072_gb300.serve import Server
-    reqs = serve_requests(args.serve_requests, max_pix=args.serve_max_pix, max_rows=args.serve_max_rows)
+    reqs = serve_requests(args.serve_requests, max_pix=args.serve_max_pix, max_rows=args.serve_max_rows,
+                          fp64_max_rows=args.serve_fp64_max_rows)
     # offered load: a Poisson stream at 0.8 of the sequential capacity.  The service time of a
     # request is modelled as (seconds per visibility-step of its precision) x visibilities x
     # (steps + 3, for the dirty image and the PSF); the per-precision rate comes from the first
@@ -602,8 +612,13 @@ def run_serve(args):
             "arrival_rate_per_s": rate, "predicted_sequential_s": float(np.sum(predicted)),
             "data": "synthetic (seeded)", "n_gpus": 1,
             "config": {"workload": f"Poisson stream of mixed-size requests: 512^2-{args.serve_max_pix}^2, "
-                                   f"1e4-{args.serve_max_rows:.0e} rows, 8-128 channels, 1-4 bands, "
-                                   "half FP32 eps 1e-5 / half FP64 eps 1e-9"}}
+                                   f"1e4-{args.serve_max_rows:.0e} rows (FP64 requests capped at "
+                                   f"{args.serve_fp64_max_rows:.0e}), 8-128 channels, 1-4 bands, "
+                                   "half FP32 eps 1e-5 / half FP64 eps 1e-9, 10 steps each"},
+            "requests_detail": [{"pix": q.nx, "rows": int(q.uvw.shape[0]), "chan": int(q.freq.shape[0]),
+                                 "bands": q.nband, "prec": q.precision,
+                                 "latency_s": (q.t_done - q.t_submit) if q.t_done else None}
+                                for q in reqs]}
     print(json.dumps(line))
     return 0
 
@@ -659,11 +674,12 @@ def run_clean(args):
     del sd
     ctx.pfb_plan_reset()
     prm = StepParams(gamma=args.clean_gamma, sigma=args.clean_sigma, lam=args.clean_lambda, cg_iters=args.clean_cg,
-                     pd_iters=args.clean_pd, nlevel=3, basis_mask=args.clean_basis)
+                     pd_iters=args.clean_pd, nlevel=3, basis_mask=args.clean_basis,
+                     safe_gamma=args.clean_safe_gamma)
     torch.cuda.synchronize(dev)
     ctx.lib.pfb_timing(ctx.h, 1)
     t0 = time.perf_counter()
-    r = ctx.pfb_clean(g, prm, uvw, freq, band, vis, wgt, max_outer=args.clean_outer, tol=0.0)
+    r = ctx.pfb_clean(g, prm, uvw, freq, band, vis, wgt, max_outer=args.clean_outer, tol=args.clean_tol)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
     kern = kernel_totals(ctx)
@@ -671,11 +687,14 @@ def run_clean(args):
     x = r["x"]
     model_err = float(torch.linalg.vector_norm(x - xt) / torch.linalg.vector_norm(xt))
     hist = r["history"]
+    lmax, gamma_used = ctx.pfb_last_step_bound() if args.clean_safe_gamma else (None, args.clean_gamma)
+    to_1pct = next((i + 1 for i, h in enumerate(hist) if h[1] <= 1e-2), None)
     line = {"metric": "full pfb-clean solve wall time", "value": wall, "unit": "s", "higher_is_better": False,
             "n_outer": r["n_outer"], "n_hessian": r["n_hessian"],
             "mvis_per_s_hessian_equivalent": r["n_hessian"] * obs.nvis / wall / 1e6,
             "objective_first_last": [float(hist[0, 0]), float(hist[-1, 0])] if len(hist) else None,
             "rel_update_last": float(hist[-1, 1]) if len(hist) else None,
+            "steps_to_rel_update_1e-2": to_1pct, "gamma_used": gamma_used, "lambda_max_UinvH": lmax,
             "history": [[float(v) for v in h] for h in hist],
             "rel_error_vs_true_sky": model_err,
             "kernels_ms": {k: round(v, 2) for k, v in sorted(kern.items(), key=lambda kv: -kv[1])[:16]},

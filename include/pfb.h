@@ -130,6 +130,15 @@ typedef struct {
    convolution structure); it is offered as the cheap inner gradient of a major /
    minor cycle scheme, not as a replacement for the exact step. */
 #define PFB_STEP_APPROX_GRADIENT 1u
+/* pfb_clean only: before the steps, estimate L_U = lambda_max(U^-1 H) with
+   pfb_step_bound (PFB_SAFE_GAMMA_ITERS power iterations, cg_iters CG iterations
+   each, from a constant image) and take gamma = min(gamma, 1.9 / L_U) for every step.
+   Forward-backward in the metric U (Eqs. 6-7) converges for gamma < 2 / L_U; on wide
+   fields the PSF-based U can fall short of the Hessian by more than a factor 2 in
+   some directions, so a fixed gamma = 1 may diverge.  The estimate costs
+   PFB_SAFE_GAMMA_ITERS Hessian applications, counted in n_hessian_out. */
+#define PFB_STEP_SAFE_GAMMA 2u
+#define PFB_SAFE_GAMMA_ITERS 8
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the scratch
  * (w-plane stacks, sort tables); 0 means 85% of the device memory free at creation.
@@ -257,6 +266,24 @@ int pfb_clean(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_param
               const int32_t *band_of_chan, const void *vis, const void *wgt, void *dirty_out, void *psf_out,
               double *wsum_out, void *x_inout, void *dual_inout, int32_t *n_outer_out, int64_t *n_hessian_out,
               double *history_out, void *stream);
+
+/* Step-size bound of the preconditioned forward-backward step (Eqs. 6-8):
+ * *lmax_out = an estimate of L_U = lambda_max(U^-1 H) in the step's normalised units
+ * (H and I^psf divided by wbar = mean_b wsum[b]; U = I^psf_sym * + sigma Id with
+ * params->sigma), by `iters` power iterations: rho_k = z^T H z / z^T U z, then
+ * z <- U^-1 H z (params->cg_iters CG iterations per band) normalised; the largest rho_k
+ * is returned (each is a lower bound of L_U).  The step converges for gamma < 2 / L_U.
+ * Data as pfb_hessian; psf [nband][2nx][2ny] (device), wsum [nband] (host), z0
+ * [nband][nx][ny] (device) the start vector or NULL for a constant image.  Costs `iters`
+ * Hessian applications; returns after synchronising the stream. */
+int pfb_step_bound(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_params *params, int64_t nrow,
+                   int32_t nchan, const double *uvw, const double *freq, const int32_t *band_of_chan,
+                   const void *wgt, const void *psf, const double *wsum, const void *z0, int32_t iters,
+                   double *lmax_out, void *stream);
+
+/* The bound of the context's last pfb_step_bound, or of its last pfb_clean with
+ * PFB_STEP_SAFE_GAMMA, and the step size that solve used (host doubles; 0 when none). */
+int pfb_last_step_bound(pfb_ctx *ctx, double *lmax_out, double *gamma_out);
 
 /* Per-kernel device timing (tracing; not part of the paper's method).
  * pfb_timing(ctx, 1) clears the totals and starts recording CUDA events around

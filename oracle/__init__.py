@@ -18,8 +18,9 @@ interferometric data"):
   prox        Condat-Vu primal-dual for Eq. 7 with r(x) of Eq. 9
   step        one preconditioned forward-backward step (Eqs. 6-7); optionally with
               the approximate gradient of Eq. 4 (I^psf * x in place of H x)
+  step_bound  lambda_max(U^-1 H) by power iteration (the step size bound of Eqs. 6-7)
   clean       a whole solve: PSF, dirty image, then steps until the relative update
-              reaches a tolerance
+              reaches a tolerance (optionally with gamma capped at 1.9 / lambda_max)
   daubechies  db1..db6 filters by spectral factorisation, periodised DWT (Eq. 9's Psi)
 
 Parity status: R, R^dagger, I^d, I^psf, the Hessian, the PSF convolution, CG,
@@ -37,6 +38,7 @@ and no closed form: those iterates are "parity unpinned" (their parts are pinned
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import math
 import os
 import subprocess
@@ -347,6 +349,7 @@ class Params:
     basis_mask: int = 1
     unorm: float = 0.0          # ||U||; <= 0 means max|Re spectrum| + sigma
     approx_gradient: bool = False   # Eq. 4: I^psf * x stands in for H x
+    safe_gamma: bool = False    # clean: cap gamma at SAFE_GAMMA_FACTOR / lambda_max(U^-1 H)
 
 
 def unorm_of(spec_sym, sigma):
@@ -426,6 +429,39 @@ def step(uvw, freq, band_of_chan, wgt, dirty_img, psf_img, wsum_b, x, v, dl, dm,
     return x1, v1, np.array([obj, rel, float(cgres.max()) if nband else 0.0])
 
 
+# ------------------------------------------------------------------ step-size bound
+SAFE_GAMMA_FACTOR = 1.9
+BOUND_ITERS = 8
+
+
+def step_bound(uvw, freq, band_of_chan, wgt, psf_img, wsum_b, dl, dm, sigma, iters, cg_iters, z0=None,
+               flags=0, hessian_fn=None):
+    """Estimate of L_U = lambda_max(U^-1 H) in the step's normalised units (H and the PSF
+    divided by wbar = mean_b wsum_b; U = I^psf_sym * + sigma Id, Eq. 8).  Forward-backward
+    in the metric U (Eqs. 6-7) converges for gamma < 2 / L_U.  Power iteration on U^-1 H:
+        rho_k = z_k^T H z_k / z_k^T U z_k          (generalised Rayleigh quotient, <= L_U)
+        z_{k+1} = CG(U, H z_k) / ||CG(U, H z_k)||  (cg_iters iterations per band)
+    from z_0 (ones by default); returns max_k rho_k."""
+    wbar = float(np.mean(wsum_b))
+    psfn = np.asarray(psf_img, dtype=np.float64) / wbar
+    spec_sym = np.real(psf_spectrum(psfn))
+    nband = psfn.shape[0]
+    nx, ny = psfn.shape[1] // 2, psfn.shape[2] // 2
+    z = np.ones((nband, nx, ny)) if z0 is None else np.array(z0, dtype=np.float64)
+    best = 0.0
+    for _ in range(iters):
+        hz = (hessian(uvw, freq, band_of_chan, wgt, z, dl, dm, flags) if hessian_fn is None
+              else hessian_fn(z)) / wbar
+        rho = float(np.vdot(z, hz)) / float(np.vdot(z, u_apply(spec_sym, sigma, z)))
+        best = max(best, rho)
+        z, _ = cg(spec_sym, sigma, hz, cg_iters)
+        nz = float(np.linalg.norm(z))
+        if nz == 0.0:
+            break
+        z = z / nz
+    return best
+
+
 # ------------------------------------------------------------------ whole solve
 def clean(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, p: Params, max_outer, tol,
           x0=None, v0=None, flags=0):
@@ -441,6 +477,15 @@ def clean(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, p: Params, m
     v = np.zeros((nbasis, nband, nx, ny)) if v0 is None else np.array(v0, dtype=np.float64)
     hist = []
     n_hessian = 1
+    lmax = None
+    if p.safe_gamma and not p.approx_gradient:
+        # gamma < 2 / L_U is what forward-backward in the metric U needs; the estimate costs
+        # BOUND_ITERS Hessian applications, counted
+        lmax = step_bound(uvw, freq, band_of_chan, wgt, psf_img, wsum_b, dl, dm, p.sigma, BOUND_ITERS,
+                          p.cg_iters, flags=flags)
+        n_hessian += BOUND_ITERS
+        if lmax > 0:
+            p = dataclasses.replace(p, gamma=min(p.gamma, SAFE_GAMMA_FACTOR / lmax))
     while len(hist) < max_outer:
         x, v, st = step(uvw, freq, band_of_chan, wgt, dirty_img, psf_img, wsum_b, x, v, dl, dm, p, flags)
         hist.append(st)
@@ -448,4 +493,5 @@ def clean(uvw, freq, band_of_chan, vis, wgt, nx, ny, dl, dm, nband, p: Params, m
         if tol > 0 and st[1] <= tol:
             break
     return {"x": x, "dual": v, "dirty": dirty_img, "psf": psf_img, "wsum": wsum_b, "n_outer": len(hist),
-            "n_hessian": n_hessian, "history": np.array(hist).reshape(len(hist), 3)}
+            "n_hessian": n_hessian, "history": np.array(hist).reshape(len(hist), 3), "lmax": lmax,
+            "gamma": p.gamma}

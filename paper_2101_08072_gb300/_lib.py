@@ -15,6 +15,8 @@ PFB_NO_ITEM_RECORDS = 4
 PFB_ACCUMULATE = 8
 PFB_NO_PRUNED_FFT = 16
 PFB_STEP_APPROX_GRADIENT = 1
+PFB_STEP_SAFE_GAMMA = 2
+PFB_SAFE_GAMMA_ITERS = 8
 
 ERRORS = {
     0: "PFB_OK", -1: "PFB_ERR_ARG", -2: "PFB_ERR_OOM", -3: "PFB_ERR_CUDA", -4: "PFB_ERR_EPS",
@@ -25,7 +27,8 @@ ERRORS = {
 EXPORTS = ["pfb_create", "pfb_destroy", "pfb_last_error", "pfb_plan_reset", "pfb_degrid", "pfb_grid",
            "pfb_dirty", "pfb_psf", "pfb_hessian", "pfb_hessian_host", "pfb_psf_conv", "pfb_step", "pfb_clean",
            "pfb_version",
-           "pfb_timing", "pfb_timing_read", "pfb_timing_names", "pfb_wsum_static", "pfb_kernel_support"]
+           "pfb_timing", "pfb_timing_read", "pfb_timing_names", "pfb_wsum_static", "pfb_kernel_support",
+           "pfb_step_bound", "pfb_last_step_bound"]
 
 
 class pfb_geom(ctypes.Structure):
@@ -83,6 +86,9 @@ def load(path: str = LIB_PATH):
     lib.pfb_clean.argtypes = [P, G, ctypes.c_int, ctypes.POINTER(pfb_params), I32, D, *data, P, P, P, P,
                               ctypes.POINTER(D), P, P, ctypes.POINTER(I32), ctypes.POINTER(I64),
                               ctypes.POINTER(D), P]
+    lib.pfb_step_bound.argtypes = [P, G, ctypes.c_int, ctypes.POINTER(pfb_params), *data, P, P,
+                                   ctypes.POINTER(D), P, I32, ctypes.POINTER(D), P]
+    lib.pfb_last_step_bound.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.pfb_timing.argtypes = [P, ctypes.c_int]
     lib.pfb_timing_read.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.pfb_timing_names.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]

@@ -313,7 +313,7 @@ void check_params(const pfb_params *prm, const pfb_geom *g) {
     PFB_REQUIRE(prm->gamma > 0 && prm->sigma > 0 && prm->lambda >= 0, "need gamma > 0, sigma > 0, lambda >= 0");
     PFB_REQUIRE(prm->cg_iters >= 0 && prm->pd_iters >= 0, "iteration counts must be >= 0");
     PFB_REQUIRE(prm->basis_mask >= 1u && prm->basis_mask < 128u, "basis_mask must select bits 0..6");
-    PFB_REQUIRE((prm->flags & ~PFB_STEP_APPROX_GRADIENT) == 0, "unknown params flag bits");
+    PFB_REQUIRE((prm->flags & ~(PFB_STEP_APPROX_GRADIENT | PFB_STEP_SAFE_GAMMA)) == 0, "unknown params flag bits");
     if (prm->basis_mask != 1u) {
         PFB_REQUIRE(prm->nlevel >= 1 && prm->nlevel <= 12, "nlevel must be in [1, 12]");
         PFB_REQUIRE(g->nx % (1 << prm->nlevel) == 0 && g->ny % (1 << prm->nlevel) == 0,
@@ -329,6 +329,18 @@ void run_step(Ctx &c, const Plan &p, pfb_prec prec, const pfb_params &prm, const
     else
         op_step<float>(c, p, prm, (const float *)wgt, (const float *)dirty, (const float *)psf, wsum, (float *)x,
                        (float *)dual, stats, st);
+}
+
+double run_step_bound(Ctx &c, const Plan &p, pfb_prec prec, const pfb_params &prm, const void *wgt, const void *psf,
+                      const double *wsum, const void *z0, int iters, cudaStream_t st) {
+    const double lm = prec == PFB_F64
+                          ? op_step_bound<double>(c, p, (const double *)wgt, (const double *)psf, wsum, prm.sigma,
+                                                  iters, prm.cg_iters, (const double *)z0, st)
+                          : op_step_bound<float>(c, p, (const float *)wgt, (const float *)psf, wsum, prm.sigma, iters,
+                                                 prm.cg_iters, (const float *)z0, st);
+    c.last_lmax = lm;
+    c.last_gamma = 0.0;
+    return lm;
 }
 
 }  // namespace
@@ -616,6 +628,29 @@ int pfb_step(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const pfb_params *p
     });
 }
 
+int pfb_step_bound(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const pfb_params *prm, int64_t nrow,
+                   int32_t nchan, const double *uvw, const double *freq, const int32_t *band, const void *wgt,
+                   const void *psf, const double *wsum, const void *z0, int32_t iters, double *lmax_out,
+                   void *stream) {
+    return guarded(ctx, stream, [&](Ctx &c) {
+        check_geom(g, prec);
+        check_data(nrow, nchan, uvw, freq, band);
+        check_params(prm, g);
+        PFB_REQUIRE(psf && wsum && lmax_out, "psf, wsum and lmax_out must not be NULL");
+        PFB_REQUIRE(iters >= 1, "iters must be >= 1");
+        const cudaStream_t st = S(stream);
+        Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, st);
+        *lmax_out = run_step_bound(c, p, prec, *prm, wgt, psf, wsum, z0, iters, st);
+    });
+}
+
+int pfb_last_step_bound(pfb_ctx *ctx, double *lmax_out, double *gamma_out) {
+    return guarded_host(ctx, [&](Ctx &c) {
+        if (lmax_out) *lmax_out = c.last_lmax;
+        if (gamma_out) *gamma_out = c.last_gamma;
+    });
+}
+
 int pfb_clean(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const pfb_params *prm, int32_t max_outer, double tol,
               int64_t nrow, int32_t nchan, const double *uvw, const double *freq, const int32_t *band,
               const void *vis, const void *wgt, void *dirty_out, void *psf_out, double *wsum_out, void *x_inout,
@@ -648,9 +683,16 @@ int pfb_clean(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, const pfb_params *
         const bool exact = !(prm->flags & PFB_STEP_APPROX_GRADIENT);
         int32_t k = 0;
         int64_t nh = 1;   // I^d and I^psf: one half each
+        pfb_params ps = *prm;
+        if ((prm->flags & PFB_STEP_SAFE_GAMMA) && exact) {
+            const double lm = run_step_bound(c, p, prec, *prm, wgt, psf_out, wsum_out, nullptr, PFB_SAFE_GAMMA_ITERS, st);
+            nh += PFB_SAFE_GAMMA_ITERS;
+            if (lm > 0) ps.gamma = std::min(prm->gamma, 1.9 / lm);
+            c.last_gamma = ps.gamma;
+        }
         while (k < max_outer) {
             double stats[3];
-            run_step(c, p, prec, *prm, wgt, dirty_out, psf_out, wsum_out, x_inout, dual_inout, stats, st);
+            run_step(c, p, prec, ps, wgt, dirty_out, psf_out, wsum_out, x_inout, dual_inout, stats, st);
             if (history_out) std::copy(stats, stats + 3, history_out + 3 * (size_t)k);
             ++k;
             nh += exact ? 1 : 0;

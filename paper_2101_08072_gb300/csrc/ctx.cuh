@@ -182,6 +182,7 @@ struct Ctx {
     cudaEvent_t done = nullptr;
     cudaStream_t cur = nullptr;
     bool in_call = false;
+    double last_lmax = 0.0, last_gamma = 0.0;   // pfb_last_step_bound
     void init_memory();                    // pool, own stream and done event (at creation)
     void release_all_buffers();            // free plans, spectra and scratch on `own` after `done`
 
@@ -263,6 +264,9 @@ void op_wsum(Ctx &ctx, const Plan &p, const T *wgt, double *d_wsum, cudaStream_t
 // image.cu
 template <typename T>
 void op_psf_conv(Ctx &ctx, int nx, int ny, int nband, const T *psf, const T *x, T *y, cudaStream_t st);
+template <typename T>
+double op_step_bound(Ctx &ctx, const Plan &p, const T *wgt, const T *psf, const double *wsum_h, double sigma,
+                     int iters, int cg_iters, const T *z0, cudaStream_t st);
 template <typename T>
 void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const T *dirty,
              const T *psf, const double *wsum_h, T *x, T *dual, double *stats_h, cudaStream_t st);

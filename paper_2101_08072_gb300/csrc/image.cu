@@ -1006,6 +1006,112 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
     }
 }
 
+// ------------------------------------------------------------------ step-size bound
+template <typename T>
+__global__ void k_fill(int64_t n, T v, T *__restrict__ y) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) y[e] = v;
+}
+
+template <typename T>
+__global__ void k_sumsq(int64_t n, const T *__restrict__ x, double *__restrict__ out) {
+    Acc<T> acc;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        acc.add_prod(x[e], x[e]);
+    block_sum_atomic(acc.value(), out);
+}
+
+// L_U = lambda_max(U^-1 H) in the step's normalised units (H, I^psf divided by wbar; U of Eq. 8), by
+// power iteration: rho_k = z^T H z / z^T U z (a lower bound of L_U), z <- CG(U, H z) / ||.|| with
+// cg_iters iterations per band, from z0 (ones when NULL).  Returns max_k rho_k.  Forward-backward in the
+// metric U (Eqs. 6-7) converges for gamma < 2 / L_U.  The CG runs on -H z / wbar (the residual kernel
+// with a zero dirty image), which flips the sign of z from one iteration to the next: rho is unchanged.
+template <typename T>
+double op_step_bound(Ctx &ctx, const Plan &p, const T *wgt, const T *psf, const double *wsum_h, double sigma_d,
+                     int iters, int cg_iters, const T *z0, cudaStream_t st) {
+    const int nx = p.nx, ny = p.ny, nb = p.nband;
+    const int64_t npix = (int64_t)nx * ny, n = npix * nb;
+    const int64_t NX = 2 * nx, NY = 2 * ny, nbig = nb * NX * NY;
+    double wbar = 0;
+    for (int b = 0; b < nb; ++b) wbar += wsum_h[b];
+    wbar /= nb;
+    PFB_REQUIRE(wbar > 0, "weight sums must be positive");
+    const double inv_wbar = 1.0 / wbar;
+    const size_t img = (size_t)n * sizeof(T);
+    T *z = (T *)ctx.scratch("sb_z", img);
+    T *hz = (T *)ctx.scratch("st_hx", img);
+    T *zero = (T *)ctx.scratch("sb_zero", img);
+    T *rhs = (T *)ctx.scratch("st_ir", img);
+    T *delta = (T *)ctx.scratch("st_delta", img);
+    T *r = (T *)ctx.scratch("st_r", img);
+    T *pp = (T *)ctx.scratch("st_p", img);
+    T *ap = (T *)ctx.scratch("st_ap", img);
+    const int ci = std::max(0, cg_iters);
+    const size_t nsc = S_COUNT + nb + (size_t)(ci + 1) * nb + (size_t)ci * nb + nb + 1;
+    double *sc = (double *)ctx.scratch("sb_scal", nsc * sizeof(double));
+    double *bb = sc + S_COUNT, *RR = bb + nb, *PAP = RR + (size_t)(ci + 1) * nb, *DEN = PAP + (size_t)ci * nb;
+    double *NRM = DEN + nb;
+    cx_t<T> *S = psf_spectrum<T>(ctx, nx, ny, nb, psf, st);
+    T *padded = (T *)ctx.scratch("img_pad", (size_t)nbig * sizeof(T));
+    ctx.scratch("img_spec", (size_t)nb * NX * (NY / 2 + 1) * sizeof(cx_t<T>));
+    ctx.fft((int)NX, (int)NY, nb, RFft<T>::c2r);
+    cx_t<T> *vis = (cx_t<T> *)ctx.scratch("st_vis", (size_t)p.nrow * p.nchan * sizeof(cx_t<T>));
+    const unsigned gn = (unsigned)((n + 255) / 256);
+    PFB_CUDA(cudaMemsetAsync(zero, 0, img, st));
+    if (z0) {
+        PFB_CUDA(cudaMemcpyAsync(z, z0, img, cudaMemcpyDeviceToDevice, st));
+    } else {
+        k_fill<T><<<gn, 256, 0, st>>>(n, (T)1, z);
+        check_launch("fill");
+    }
+    const T conv_scale = (T)(inv_wbar / (double)(NX * NY));
+    const T sigma = (T)sigma_d;
+    double best = 0;
+    std::vector<double> h(nsc);
+    for (int it = 0; it < iters; ++it) {
+        PFB_CUDA(cudaMemsetAsync(sc, 0, nsc * sizeof(double), st));
+        op_degrid<T>(ctx, p, z, vis, st);
+        op_grid<T>(ctx, p, vis, wgt, false, hz, st);
+        // numerator z . H z / wbar (into S_XHX) and the CG right-hand side -H z / wbar with its norms
+        k_residual<T><<<band_grid(ctx, npix, nb), 256, 0, st>>>(npix, zero, hz, z, inv_wbar, rhs, sc, bb);
+        check_launch("sb_residual");
+        // denominator z . U z
+        k_pad<T><<<row_grid(ctx, 2 * nx, nb), 256, 0, st>>>(nx, ny, z, (const T *)nullptr, padded);
+        check_launch("sb_pad");
+        conv_padded<T>(ctx, nx, ny, nb, padded, S, conv_scale, true, st);
+        k_cg_ap<T><<<row_grid(ctx, nx, nb), 256, 0, st>>>(nx, ny, padded, z, sigma, ap, DEN);
+        check_launch("sb_uz");
+        // CG for U delta = -H z / wbar
+        k_cg_init<T><<<gn, 256, 0, st>>>(n, rhs, delta, r, pp);
+        check_launch("sb_cg_init");
+        PFB_CUDA(cudaMemcpyAsync(RR, bb, nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        k_pad<T><<<row_grid(ctx, 2 * nx, nb), 256, 0, st>>>(nx, ny, pp, (const T *)nullptr, padded);
+        check_launch("sb_cg_pad");
+        for (int c = 0; c < ci; ++c) {
+            double *rr = RR + (size_t)c * nb, *rrn = RR + (size_t)(c + 1) * nb, *pap = PAP + (size_t)c * nb;
+            conv_padded<T>(ctx, nx, ny, nb, padded, S, conv_scale, true, st);
+            k_cg_ap<T><<<row_grid(ctx, nx, nb), 256, 0, st>>>(nx, ny, padded, pp, sigma, ap, pap);
+            check_launch("sb_cg_ap");
+            k_cg_update<T><<<band_grid(ctx, npix, nb), 256, 0, st>>>(npix, pp, ap, rr, pap, bb, 0.0, delta, r, rrn);
+            check_launch("sb_cg_update");
+            k_cg_dir<T><<<row_grid(ctx, 2 * nx, nb), 256, 0, st>>>(nx, ny, r, rr, rrn, bb, 0.0, pp, padded);
+            check_launch("sb_cg_dir");
+        }
+        k_sumsq<T><<<rblocks(n, 8 * ctx.num_sms), 256, 0, st>>>(n, delta, NRM);
+        check_launch("sb_norm");
+        PFB_CUDA(cudaMemcpyAsync(h.data(), sc, nsc * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PFB_CUDA(cudaStreamSynchronize(st));
+        double den = 0;
+        for (int b = 0; b < nb; ++b) den += h[S_COUNT + nb + (size_t)(ci + 1) * nb + (size_t)ci * nb + b];
+        const double num = h[S_XHX], nrm2 = h[nsc - 1];
+        if (den > 0) best = std::max(best, num / den);
+        if (!(nrm2 > 0)) break;
+        k_axpy<T><<<gn, 256, 0, st>>>(n, (T)(1.0 / std::sqrt(nrm2)), delta, 0, z);
+        check_launch("sb_scale");
+    }
+    return best;
+}
+
 template void op_psf_conv<float>(Ctx &, int, int, int, const float *, const float *, float *, cudaStream_t);
 template void op_psf_conv<double>(Ctx &, int, int, int, const double *, const double *, double *, cudaStream_t);
 template void op_step<float>(Ctx &, const Plan &, const pfb_params &, const float *, const float *, const float *,
@@ -1013,4 +1119,11 @@ template void op_step<float>(Ctx &, const Plan &, const pfb_params &, const floa
 template void op_step<double>(Ctx &, const Plan &, const pfb_params &, const double *, const double *,
                               const double *, const double *, double *, double *, double *, cudaStream_t);
 
+}  // namespace pfb
+
+namespace pfb {
+template double op_step_bound<float>(Ctx &, const Plan &, const float *, const float *, const double *, double, int,
+                                     int, const float *, cudaStream_t);
+template double op_step_bound<double>(Ctx &, const Plan &, const double *, const double *, const double *, double,
+                                      int, int, const double *, cudaStream_t);
 }  // namespace pfb

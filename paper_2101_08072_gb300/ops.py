@@ -51,11 +51,13 @@ class StepParams:
     basis_mask: int = 1
     unorm: float = 0.0
     approx_gradient: bool = False   # Eq. 4 (I^psf * x) in place of the Hessian (PFB_STEP_APPROX_GRADIENT)
+    safe_gamma: bool = False        # pfb_clean: gamma capped at 1.9 / lambda_max(U^-1 H) (PFB_STEP_SAFE_GAMMA)
 
     def c(self) -> _lib.pfb_params:
+        flags = (_lib.PFB_STEP_APPROX_GRADIENT if self.approx_gradient else 0) | \
+                (_lib.PFB_STEP_SAFE_GAMMA if self.safe_gamma else 0)
         return _lib.pfb_params(self.gamma, self.sigma, self.lam, self.cg_tol, self.pd_tol, self.cg_iters,
-                               self.pd_iters, self.nlevel, self.basis_mask, self.unorm,
-                               _lib.PFB_STEP_APPROX_GRADIENT if self.approx_gradient else 0)
+                               self.pd_iters, self.nlevel, self.basis_mask, self.unorm, flags)
 
 
 def _ptr(t):
@@ -311,6 +313,31 @@ class Context:
         return {"x": x, "dual": dual, "dirty": dirty, "psf": psf, "wsum": np.array(ws[:], dtype=np.float64),
                 "n_outer": k, "n_hessian": int(nh.value),
                 "history": np.array(hist[:3 * k], dtype=np.float64).reshape(k, 3)}
+
+    def pfb_step_bound(self, geom: Geometry, params: StepParams, uvw, freq, band_of_chan, wgt, psf, wsum,
+                       iters: int = 8, z0=None) -> float:
+        """lambda_max(U^-1 H) by `iters` power iterations (the step converges for gamma < 2 / it)."""
+        nrow, nchan = self._data(uvw, freq, band_of_chan)
+        prec = _prec_real(psf.dtype)
+        rdt = _RDT[prec]
+        if wgt is not None:
+            self._t(wgt, "wgt", rdt, (nrow, nchan))
+        self._t(psf, "psf", rdt, (geom.nband, 2 * geom.nx, 2 * geom.ny))
+        if z0 is not None:
+            self._t(z0, "z0", rdt, (geom.nband, geom.nx, geom.ny))
+        ws = (ctypes.c_double * geom.nband)(*[float(v) for v in wsum])
+        out = ctypes.c_double(0)
+        g, p = geom.c(), params.c()
+        self._check(self.lib.pfb_step_bound(self.h, ctypes.byref(g), prec, ctypes.byref(p), nrow, nchan, _ptr(uvw),
+                                            _ptr(freq), _ptr(band_of_chan), _ptr(wgt), _ptr(psf), ws, _ptr(z0),
+                                            int(iters), ctypes.byref(out), self._stream()))
+        return float(out.value)
+
+    def pfb_last_step_bound(self) -> tuple[float, float]:
+        """(lambda_max, gamma) of the last step-bound estimate / safe-gamma solve of this context."""
+        lm, ga = ctypes.c_double(0), ctypes.c_double(0)
+        self._check(self.lib.pfb_last_step_bound(self.h, ctypes.byref(lm), ctypes.byref(ga)))
+        return float(lm.value), float(ga.value)
 
     def pfb_plan_reset(self):
         """Drop cached plans (after changing uvw/freq/band_of_chan in place)."""

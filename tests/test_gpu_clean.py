@@ -172,3 +172,36 @@ def test_clean_errors(ctx):
     with pytest.raises(PfbError) as e:
         ctx.pfb_clean(g, gp, *dev_obs(obs), cx_t(V, 64), real_t(w, 64), max_outer=1)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_step_bound_against_oracle(ctx, prec):
+    """lambda_max(U^-1 H) by power iteration (pfb_step_bound) against the oracle's estimate from the
+    same start vector and iteration counts."""
+    obs, a, xt, w, V = _case(205, 0.0)
+    p, ws = oracle.psf(*a, w, 32, 32, obs.dl, obs.dm, 2)
+    z0 = np.random.default_rng(206).uniform(0.5, 1.5, (2, 32, 32))
+    gp, op = _params(sigma=0.05, cg_iters=15)
+    ref = oracle.step_bound(*a, w, p, ws, obs.dl, obs.dm, op.sigma, 4, op.cg_iters, z0=z0)
+    g = geometry(obs, EPS32 if prec == 32 else EPS64)
+    got = ctx.pfb_step_bound(g, gp, *dev_obs(obs), real_t(w, prec), real_t(p, prec), ws, iters=4,
+                             z0=real_t(z0, prec))
+    assert got == pytest.approx(ref, rel=1e-5 if prec == 32 else 1e-10)
+    assert ctx.pfb_last_step_bound()[0] == got
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_clean_safe_gamma(ctx, prec):
+    """pfb_clean with PFB_STEP_SAFE_GAMMA: the bound from a constant start, gamma capped at 1.9 / bound,
+    the bound's Hessians counted; final iterate against the oracle's solve with the same option."""
+    obs, a, xt, w, V = _case(207, 1e-4)
+    gp, op = _params(gamma=4.0, sigma=0.05, cg_iters=12, pd_iters=10, safe_gamma=True)
+    ref = oracle.clean(*a, V, w, 32, 32, obs.dl, obs.dm, 2, op, max_outer=3, tol=0.0)
+    g = geometry(obs, EPS32 if prec == 32 else EPS64)
+    out = ctx.pfb_clean(g, gp, *dev_obs(obs), cx_t(V, prec), real_t(w, prec), max_outer=3, tol=0.0)
+    lm, ga = ctx.pfb_last_step_bound()
+    tol = 1e-4 if prec == 32 else 1e-8
+    assert lm == pytest.approx(ref["lmax"], rel=tol)
+    assert ga == pytest.approx(ref["gamma"], rel=tol) and ga < 4.0
+    assert out["n_hessian"] == ref["n_hessian"] == 1 + oracle.BOUND_ITERS + 3
+    assert rel_l2(out["x"].cpu().numpy(), ref["x"]) <= tol

@@ -624,6 +624,64 @@ def test_step_equals_dense_preconditioned_step():
     assert st[2] < 1e-8
 
 
+def _dense_h_u(nx, ny, w, obs, p, ws, sigma):
+    """Dense normalised H / wbar and U = PSF_sym / wbar + sigma Id of a one-band tiny problem, built column
+    by column from unit images (H) and from the PSF samples (U), independent of the power iteration."""
+    a = (obs.uvw, obs.freq, obs.band_of_chan)
+    n = nx * ny
+    wbar = float(np.mean(ws))
+    Hd = np.zeros((n, n))
+    M = np.zeros((n, n))
+    for k in range(n):
+        i, j = divmod(k, ny)
+        Hd[:, k] = oracle.hessian(*a, w, _unit_image(nx, ny, i, j), obs.dl, obs.dm).ravel()
+        for k2 in range(n):
+            i2, j2 = divmod(k2, ny)
+            M[k2, k] = p[0, i2 - i + nx, j2 - j + ny]
+    return Hd / wbar, 0.5 * (M + M.T) / wbar + sigma * np.eye(n)
+
+
+def test_step_bound_is_generalised_eigenvalue():
+    """L_U = lambda_max(U^-1 H) (the bound gamma < 2 / L_U of forward-backward in the metric U,
+    Eqs. 6-8): the power iteration's Rayleigh quotients never exceed the largest eigenvalue of the
+    dense generalised problem H z = lambda U z, and converge to it (slowly: the gap to the second
+    eigenvalue is small, 60 iterations come within 1e-4)."""
+    import scipy.linalg
+    nx = ny = 8
+    obs = synth.tiny_observation(nx=nx, ny=ny)
+    rng = np.random.default_rng(29)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    a = (obs.uvw, obs.freq, obs.band_of_chan)
+    p, ws = oracle.psf(*a, w, nx, ny, obs.dl, obs.dm, 1)
+    sigma = 0.05
+    Hn, U = _dense_h_u(nx, ny, w, obs, p, ws, sigma)
+    lam = scipy.linalg.eigh(Hn, U, eigvals_only=True)
+    lmax = float(lam[-1])
+    est = [oracle.step_bound(*a, w, p, ws, obs.dl, obs.dm, sigma, k, cg_iters=300) for k in (1, 3, 60)]
+    assert all(e <= lmax * (1 + 1e-10) for e in est)
+    assert est[0] <= est[1] <= est[2]
+    assert est[2] == pytest.approx(lmax, rel=2e-4)
+
+
+def test_clean_safe_gamma_caps_the_step():
+    """With safe_gamma the solve takes gamma = min(gamma, 1.9 / L_U) and counts the bound's Hessians:
+    the same as a plain solve run with that gamma."""
+    nx = ny = 8
+    obs = synth.tiny_observation(nx=nx, ny=ny)
+    rng = np.random.default_rng(30)
+    w = rng.uniform(0.5, 1.5, (obs.nrow, obs.nchan))
+    a = (obs.uvw, obs.freq, obs.band_of_chan)
+    xt = synth.point_source_image(rng, 1, nx, ny, 3)
+    V = oracle.degrid(*a, xt, obs.dl, obs.dm) + synth.complex_noise(rng, (obs.nrow, obs.nchan), 1e-3)
+    prm = oracle.Params(gamma=3.0, sigma=0.05, lam=1e-3, cg_iters=20, pd_iters=10, safe_gamma=True)
+    r = oracle.clean(*a, V, w, nx, ny, obs.dl, obs.dm, 1, prm, max_outer=3, tol=0.0)
+    assert r["lmax"] > 0 and r["gamma"] == pytest.approx(oracle.SAFE_GAMMA_FACTOR / r["lmax"])
+    assert r["gamma"] < 3.0 and r["n_hessian"] == 1 + oracle.BOUND_ITERS + 3
+    p2 = oracle.Params(gamma=r["gamma"], sigma=0.05, lam=1e-3, cg_iters=20, pd_iters=10)
+    r2 = oracle.clean(*a, V, w, nx, ny, obs.dl, obs.dm, 1, p2, max_outer=3, tol=0.0)
+    assert np.abs(r["x"] - r2["x"]).max() <= 1e-12 * max(np.abs(r2["x"]).max(), 1e-30)
+
+
 def test_step_decreases_objective():
     obs = synth.tiny_observation(nx=16, ny=16)
     rng = np.random.default_rng(26)

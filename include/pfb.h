@@ -132,13 +132,15 @@ typedef struct {
 #define PFB_STEP_APPROX_GRADIENT 1u
 /* pfb_clean only: before the steps, estimate L_U = lambda_max(U^-1 H) with
    pfb_step_bound (PFB_SAFE_GAMMA_ITERS power iterations, cg_iters CG iterations
-   each, from a constant image) and take gamma = min(gamma, 1.9 / L_U) for every step.
+   each, from the image 0.5 + u_e, u_e the SplitMix64 uniform of the flat pixel index
+   e + 1 (Steele, Lea & Flood 2014): a generic positive start, since a constant one
+   can miss the modes where H exceeds U most) and take gamma = min(gamma, 1.9 / L_U).
    Forward-backward in the metric U (Eqs. 6-7) converges for gamma < 2 / L_U; on wide
    fields the PSF-based U can fall short of the Hessian by more than a factor 2 in
    some directions, so a fixed gamma = 1 may diverge.  The estimate costs
    PFB_SAFE_GAMMA_ITERS Hessian applications, counted in n_hessian_out. */
 #define PFB_STEP_SAFE_GAMMA 2u
-#define PFB_SAFE_GAMMA_ITERS 8
+#define PFB_SAFE_GAMMA_ITERS 30
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the scratch
  * (w-plane stacks, sort tables); 0 means 85% of the device memory free at creation.
@@ -274,7 +276,8 @@ int pfb_clean(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_param
  * z <- U^-1 H z (params->cg_iters CG iterations per band) normalised; the largest rho_k
  * is returned (each is a lower bound of L_U).  The step converges for gamma < 2 / L_U.
  * Data as pfb_hessian; psf [nband][2nx][2ny] (device), wsum [nband] (host), z0
- * [nband][nx][ny] (device) the start vector or NULL for a constant image.  Costs `iters`
+ * [nband][nx][ny] (device) the start vector or NULL for 0.5 + u_e (the SplitMix64 start of
+ * PFB_STEP_SAFE_GAMMA).  Costs `iters`
  * Hessian applications; returns after synchronising the stream. */
 int pfb_step_bound(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, const pfb_params *params, int64_t nrow,
                    int32_t nchan, const double *uvw, const double *freq, const int32_t *band_of_chan,

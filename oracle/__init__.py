@@ -431,7 +431,24 @@ def step(uvw, freq, band_of_chan, wgt, dirty_img, psf_img, wsum_b, x, v, dl, dm,
 
 # ------------------------------------------------------------------ step-size bound
 SAFE_GAMMA_FACTOR = 1.9
-BOUND_ITERS = 8
+BOUND_ITERS = 30
+
+
+def splitmix64_uniform(n):
+    """u_e in [0, 1) for e = 0..n-1 from SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom
+    number generators", OOPSLA 2014) applied to the counter e + 1: the top 53 bits of the mixed word."""
+    with np.errstate(over="ignore"):
+        z = (np.arange(n, dtype=np.uint64) + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+
+
+def bound_start(nband, nx, ny):
+    """Start vector of the safe-gamma bound: 0.5 + u_e over the flat index of [nband][nx][ny] (a generic
+    positive image; a constant one can miss the modes where H exceeds U most)."""
+    return 0.5 + splitmix64_uniform(nband * nx * ny).reshape(nband, nx, ny)
 
 
 def step_bound(uvw, freq, band_of_chan, wgt, psf_img, wsum_b, dl, dm, sigma, iters, cg_iters, z0=None,
@@ -441,13 +458,13 @@ def step_bound(uvw, freq, band_of_chan, wgt, psf_img, wsum_b, dl, dm, sigma, ite
     in the metric U (Eqs. 6-7) converges for gamma < 2 / L_U.  Power iteration on U^-1 H:
         rho_k = z_k^T H z_k / z_k^T U z_k          (generalised Rayleigh quotient, <= L_U)
         z_{k+1} = CG(U, H z_k) / ||CG(U, H z_k)||  (cg_iters iterations per band)
-    from z_0 (ones by default); returns max_k rho_k."""
+    from z_0 (bound_start, the library's default, when None); returns max_k rho_k."""
     wbar = float(np.mean(wsum_b))
     psfn = np.asarray(psf_img, dtype=np.float64) / wbar
     spec_sym = np.real(psf_spectrum(psfn))
     nband = psfn.shape[0]
     nx, ny = psfn.shape[1] // 2, psfn.shape[2] // 2
-    z = np.ones((nband, nx, ny)) if z0 is None else np.array(z0, dtype=np.float64)
+    z = bound_start(nband, nx, ny) if z0 is None else np.array(z0, dtype=np.float64)
     best = 0.0
     for _ in range(iters):
         hz = (hessian(uvw, freq, band_of_chan, wgt, z, dl, dm, flags) if hessian_fn is None

@@ -16,7 +16,7 @@ PFB_ACCUMULATE = 8
 PFB_NO_PRUNED_FFT = 16
 PFB_STEP_APPROX_GRADIENT = 1
 PFB_STEP_SAFE_GAMMA = 2
-PFB_SAFE_GAMMA_ITERS = 8
+PFB_SAFE_GAMMA_ITERS = 30
 
 ERRORS = {
     0: "PFB_OK", -1: "PFB_ERR_ARG", -2: "PFB_ERR_OOM", -3: "PFB_ERR_CUDA", -4: "PFB_ERR_EPS",

@@ -1007,10 +1007,17 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
 }
 
 // ------------------------------------------------------------------ step-size bound
+// 0.5 + u_e, u_e in [0, 1) from SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) of the counter e + 1: the start
+// vector of the step-size bound (a generic positive image)
 template <typename T>
-__global__ void k_fill(int64_t n, T v, T *__restrict__ y) {
+__global__ void k_bound_start(int64_t n, T *__restrict__ y) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < n) y[e] = v;
+    if (e >= n) return;
+    uint64_t z = ((uint64_t)e + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    y[e] = (T)(0.5 + (double)(z >> 11) * 0x1.0p-53);
 }
 
 template <typename T>
@@ -1023,7 +1030,7 @@ __global__ void k_sumsq(int64_t n, const T *__restrict__ x, double *__restrict__
 
 // L_U = lambda_max(U^-1 H) in the step's normalised units (H, I^psf divided by wbar; U of Eq. 8), by
 // power iteration: rho_k = z^T H z / z^T U z (a lower bound of L_U), z <- CG(U, H z) / ||.|| with
-// cg_iters iterations per band, from z0 (ones when NULL).  Returns max_k rho_k.  Forward-backward in the
+// cg_iters iterations per band, from z0 (0.5 + a SplitMix64 uniform per pixel when NULL).  Returns max_k rho_k.  Forward-backward in the
 // metric U (Eqs. 6-7) converges for gamma < 2 / L_U.  The CG runs on -H z / wbar (the residual kernel
 // with a zero dirty image), which flips the sign of z from one iteration to the next: rho is unchanged.
 template <typename T>
@@ -1061,8 +1068,8 @@ double op_step_bound(Ctx &ctx, const Plan &p, const T *wgt, const T *psf, const 
     if (z0) {
         PFB_CUDA(cudaMemcpyAsync(z, z0, img, cudaMemcpyDeviceToDevice, st));
     } else {
-        k_fill<T><<<gn, 256, 0, st>>>(n, (T)1, z);
-        check_launch("fill");
+        k_bound_start<T><<<gn, 256, 0, st>>>(n, z);
+        check_launch("bound_start");
     }
     const T conv_scale = (T)(inv_wbar / (double)(NX * NY));
     const T sigma = (T)sigma_d;

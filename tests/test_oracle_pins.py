@@ -663,6 +663,16 @@ def test_step_bound_is_generalised_eigenvalue():
     assert est[2] == pytest.approx(lmax, rel=2e-4)
 
 
+def test_bound_start_is_splitmix64():
+    """The start vector of the safe-gamma bound: 0.5 + u_e with u_e the top 53 bits of SplitMix64 of
+    e + 1.  The first word is the generator's published first output from seed 0, 0xE220A8397B1DCDAF."""
+    u = oracle.splitmix64_uniform(4)
+    assert u[0] == (0xE220A8397B1DCDAF >> 11) * 2.0 ** -53
+    assert np.all((u >= 0) & (u < 1)) and len(set(u.tolist())) == 4
+    z = oracle.bound_start(2, 4, 4)
+    assert z.shape == (2, 4, 4) and z.flat[0] == 0.5 + u[0]
+
+
 def test_clean_safe_gamma_caps_the_step():
     """With safe_gamma the solve takes gamma = min(gamma, 1.9 / L_U) and counts the bound's Hessians:
     the same as a plain solve run with that gamma."""

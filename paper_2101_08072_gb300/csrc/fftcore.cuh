@@ -16,19 +16,31 @@
 namespace pfb {
 namespace fft {
 
+// Element types: float4 holds two complex values (two columns, or two rows, transformed together), float2
+// one.  The arithmetic below is overloaded on both.
 __device__ __forceinline__ float4 c_add(float4 a, float4 b) {
     return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float4 c_sub(float4 a, float4 b) {
     return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
 }
-// both complex values of a times w
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float4 c_neg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+__device__ __forceinline__ float2 c_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// the complex value(s) of a times w
 __device__ __forceinline__ float4 c_mul(float4 a, float2 w) {
     return make_float4(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x, a.z * w.x - a.w * w.y, a.z * w.y + a.w * w.x);
+}
+__device__ __forceinline__ float2 c_mul(float2 a, float2 w) {
+    return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
 }
 // times -i (forward sign) or +i (inverse sign)
 template <bool INV> __device__ __forceinline__ float4 c_rot(float4 a) {
     return INV ? make_float4(-a.y, a.x, -a.w, a.z) : make_float4(a.y, -a.x, a.w, -a.z);
+}
+template <bool INV> __device__ __forceinline__ float2 c_rot(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
 // cos(2 pi e / 16), from cos(pi/8), sin(pi/8) and sqrt(1/2); sin(2 pi e / 16) = cos16(e - 4)
@@ -41,23 +53,23 @@ __host__ __device__ constexpr double cos16(int e) {
 }
 
 // a times exp(-/+ 2 pi i e / R), R in {8, 16}; e is a compile-time constant once the loops unroll
-template <int R, bool INV> __device__ __forceinline__ float4 c_tw(float4 a, int e) {
+template <int R, bool INV, typename E> __device__ __forceinline__ E c_tw(E a, int e) {
     const int f = (e * (16 / R)) & 15;
     if (f == 0) return a;
-    if (f == 8) return make_float4(-a.x, -a.y, -a.z, -a.w);
+    if (f == 8) return c_neg(a);
     if (f == 4) return c_rot<INV>(a);
     if (f == 12) return c_rot<!INV>(a);
     const float c = (float)cos16(f), s = (float)cos16(f - 4);
     return c_mul(a, make_float2(c, INV ? s : -s));
 }
 
-template <bool INV> __device__ __forceinline__ void dft2(float4 &x0, float4 &x1) {
-    const float4 a = c_add(x0, x1);
+template <bool INV, typename E> __device__ __forceinline__ void dft2(E &x0, E &x1) {
+    const E a = c_add(x0, x1);
     x1 = c_sub(x0, x1);
     x0 = a;
 }
-template <bool INV> __device__ __forceinline__ void dft4(float4 &x0, float4 &x1, float4 &x2, float4 &x3) {
-    const float4 a0 = c_add(x0, x2), a1 = c_sub(x0, x2), a2 = c_add(x1, x3), a3 = c_rot<INV>(c_sub(x1, x3));
+template <bool INV, typename E> __device__ __forceinline__ void dft4(E &x0, E &x1, E &x2, E &x3) {
+    const E a0 = c_add(x0, x2), a1 = c_sub(x0, x2), a2 = c_add(x1, x3), a3 = c_rot<INV>(c_sub(x1, x3));
     x0 = c_add(a0, a2);
     x1 = c_add(a1, a3);
     x2 = c_sub(a0, a2);
@@ -68,7 +80,7 @@ template <bool INV> __device__ __forceinline__ void dft4(float4 &x0, float4 &x1,
 template <int R> __device__ __forceinline__ constexpr int operm(int k) {
     return R == 16 ? 4 * (k & 3) + (k >> 2) : R == 8 ? 2 * (k & 3) + (k >> 2) : k;
 }
-template <int R, bool INV> __device__ __forceinline__ void dft_reg(float4 *x) {
+template <int R, bool INV, typename E> __device__ __forceinline__ void dft_reg(E *x) {
     if constexpr (R == 2) {
         dft2<INV>(x[0], x[1]);
     } else if constexpr (R == 4) {
@@ -108,8 +120,8 @@ __device__ __forceinline__ float2 c_mul1(float2 a, float2 b) {
 // come from the table, the other powers from products of at most three of them (w^r = w^h w^(r-h),
 // h the largest power of two below r): two gathered loads instead of R - 1, and a twiddle error of a
 // few units in the last place, about the table's own rounding.
-template <int R, bool INV>
-__device__ __forceinline__ void apply_twiddles(float4 *v, const float2 *__restrict__ W, int k, int step) {
+template <int R, bool INV, typename E>
+__device__ __forceinline__ void apply_twiddles(E *v, const float2 *__restrict__ W, int k, int step) {
     float2 w[R];
     w[1] = twiddle<INV>(W, k * step);
     if (R >= 8) w[4 % R] = twiddle<INV>(W, 4 * k * step);

@@ -31,12 +31,15 @@
 // first transposed into column-pair order, [q][i], so that the threads of a column read them coalesced;
 // a column kernel re-reads its share from L2 for every plane.
 //
-// The DFTs are the mixed-radix Stockham stages of fftcore.cuh on pairs of complex values (two columns,
-// or two rows, at once), N/16 threads per pair.
+// The DFTs are the mixed-radix Stockham stages of fftcore.cuh with N/16 threads per CTA, on pairs of complex
+// values (two columns, or two rows, at once) for N <= 8192, and on single columns or rows for N = 16384,
+// whose pairs would not fit in shared memory (those columns are stored per thread: a TMA box needs 16 bytes
+// of inner extent).
 #include "ctx.cuh"
 #include "fftcore.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace pfb {
 namespace {
@@ -54,8 +57,22 @@ struct Shape {
     static constexpr int NMID = NST16 - 1 - ((L % 4) ? 0 : 1);   // radix-16 stages between the first and last
 };
 
-template <int L, bool INV>
-__device__ __forceinline__ int fft_stages(float4 *v, float4 *sm, const float2 *__restrict__ W, int tid) {
+// What one CTA transforms: E = float4, two adjacent columns (or rows) at once (transforms of up to 8192
+// points); E = float2, one column (or row) (16384 points, whose pair would not fit in shared memory).
+template <typename E> struct Lanes;
+template <> struct Lanes<float4> {
+    static constexpr int K = 2;
+    using X = float2;   // x corr of the K pixels of an image row
+    using Tt = float4;  // t of the K pixels (float pairs)
+};
+template <> struct Lanes<float2> {
+    static constexpr int K = 1;
+    using X = float;
+    using Tt = float2;
+};
+
+template <int L, bool INV, typename E>
+__device__ __forceinline__ int fft_stages(E *v, E *sm, const float2 *__restrict__ W, int tid) {
     using S = Shape<L>;
     constexpr int N = S::N, T = S::T, RL = S::RL, BPT = S::BPT;
     dft_reg<16, INV>(v);   // first stage: radix 16, Ns = 1, no twiddles
@@ -93,8 +110,8 @@ __device__ __forceinline__ int fft_stages(float4 *v, float4 *sm, const float2 *_
 }
 
 // After fft_stages: write the outputs densely (row-major, no padding) into sm, then a barrier.
-template <int L>
-__device__ __forceinline__ void dense_to_smem(const float4 *v, float4 *sm, int tid, int Ns) {
+template <int L, typename E>
+__device__ __forceinline__ void dense_to_smem(const E *v, E *sm, int tid, int Ns) {
     using S = Shape<L>;
     __syncthreads();   // every thread has read the exchange buffer
 #pragma unroll
@@ -119,26 +136,78 @@ __device__ __forceinline__ void screen(float2 wk, float t_hi, float t_lo, float 
     __sincosf(6.28318530717958647692f * (h + l), s, c);
 }
 
+// the pre-pass value x corr exp(-2 pi i w_k t) of the CTA's pixels of one image row
+__device__ __forceinline__ float4 pre_value(float2 xc, float4 t, float2 w, int wstack) {
+    if (!wstack) return make_float4(xc.x, 0.f, xc.y, 0.f);
+    float s0, c0, s1, c1;
+    screen(w, t.x, t.y, &s0, &c0);
+    screen(w, t.z, t.w, &s1, &c1);
+    return make_float4(xc.x * c0, -xc.x * s0, xc.y * c1, -xc.y * s1);
+}
+__device__ __forceinline__ float2 pre_value(float xc, float2 t, float2 w, int wstack) {
+    if (!wstack) return make_float2(xc, 0.f);
+    float s0, c0;
+    screen(w, t.x, t.y, &s0, &c0);
+    return make_float2(xc * c0, -xc * s0);
+}
+// the post-pass term Re exp(+2 pi i w_k t) h of the CTA's pixels of one image row, added to a
+__device__ __forceinline__ void post_add(float2 &a, float4 h, float4 t, float2 w, int wstack) {
+    if (!wstack) {
+        a.x += h.x;
+        a.y += h.z;
+        return;
+    }
+    float s0, c0, s1, c1;
+    screen(w, t.x, t.y, &s0, &c0);
+    screen(w, t.z, t.w, &s1, &c1);
+    a.x += h.x * c0 - h.y * s0;
+    a.y += h.z * c1 - h.w * s1;
+}
+__device__ __forceinline__ void post_add(float &a, float2 h, float2 t, float2 w, int wstack) {
+    if (!wstack) {
+        a += h.x;
+        return;
+    }
+    float s0, c0;
+    screen(w, t.x, t.y, &s0, &c0);
+    a += h.x * c0 - h.y * s0;
+}
+__device__ __forceinline__ float2 mul_corr(float2 a, float2 c) { return make_float2(a.x * c.x, a.y * c.y); }
+__device__ __forceinline__ float mul_corr(float a, float c) { return a * c; }
+__device__ __forceinline__ float2 add_prev(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float add_prev(float a, float b) { return a + b; }
+
+// plane column and image column of the CTA's first lane: column groups q < ny / (2K) are the image columns
+// right of the centre (plane columns from 0), the rest those left of it (plane columns from Nv - ny/2)
+template <int K> __device__ __forceinline__ void column_of(int q, int Nv, int ny, int *c, int *j0) {
+    const int hq = ny / (2 * K);
+    *c = q < hq ? K * q : Nv - ny / 2 + K * (q - hq);
+    *j0 = q < hq ? K * q + ny / 2 : K * (q - hq);
+}
+
 // ---------------------------------------------------------------- forward column pass (fused pre-pass)
-// One CTA per pair of adjacent image columns (plane columns c, c + 1); it takes the pair through the
-// planes [k_lo, k_lo + nk) of band b.  rowocc: the band's tile-row masks [Pmax][ntu / 32].
-template <int L, bool TMA>
+// One CTA per group of K adjacent image columns; it takes them through the planes [k_lo, k_lo + nk) of
+// band b.  xcT, tT: x corr and t of the group's pixels by image row; rowocc: the band's tile-row masks
+// [Pmax][ntu / 32].  TMA (K = 2 only) stores boxes of 2 cells x TILE rows.
+template <int L, bool TMA, typename E>
 __global__ void __launch_bounds__((1 << L) / 16)
     k_colfwd(float2 *__restrict__ planes, int nk, int k_lo, int Nv, int64_t plane_sz, int nx, int ny,
-             const float2 *__restrict__ xcT, const float4 *__restrict__ tT, const float2 *__restrict__ wk,
-             int wstack, const uint32_t *__restrict__ rowocc, const float2 *__restrict__ W,
-             const __grid_constant__ CUtensorMap tmap) {
+             const typename Lanes<E>::X *__restrict__ xcT, const typename Lanes<E>::Tt *__restrict__ tT,
+             const float2 *__restrict__ wk, int wstack, const uint32_t *__restrict__ rowocc,
+             const float2 *__restrict__ W, const __grid_constant__ CUtensorMap tmap) {
     using S = Shape<L>;
     constexpr int N = S::N, T = S::T;
-    extern __shared__ __align__(1024) float4 sm[];
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    E *sm = reinterpret_cast<E *>(smraw);
     const int tid = threadIdx.x;
-    const int q = blockIdx.x, hq = ny / 4;
-    const int c = q < hq ? 2 * q : Nv - ny / 2 + 2 * (q - hq);
+    const int q = blockIdx.x;
+    int c, j0;
+    column_of<Lanes<E>::K>(q, Nv, ny, &c, &j0);
     const int rlo = nx / 2, rhi = N - nx / 2;
     const int ntu = N / TILE, nw = ntu / 32;
-    const float2 *xq = xcT + (int64_t)q * nx;
-    const float4 *tq = tT + (int64_t)q * nx;
-    float4 v[16];
+    const auto *xq = xcT + (int64_t)q * nx;
+    const auto *tq = tT + (int64_t)q * nx;
+    E v[16];
 
     for (int pl = 0; pl < nk; ++pl) {
         const int k = k_lo + pl;
@@ -147,19 +216,10 @@ __global__ void __launch_bounds__((1 << L) / 16)
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int row = tid + r * T;
-            float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+            E e{};
             if (row < rlo || row >= rhi) {
                 const int i = row < rlo ? row + nx / 2 : row - rhi;
-                const float2 xc = xq[i];
-                if (wstack) {
-                    const float4 t = tq[i];
-                    float s0, c0, s1, c1;
-                    screen(w, t.x, t.y, &s0, &c0);
-                    screen(w, t.z, t.w, &s1, &c1);
-                    e = make_float4(xc.x * c0, -xc.x * s0, xc.y * c1, -xc.y * s1);
-                } else {
-                    e = make_float4(xc.x, 0.f, xc.y, 0.f);
-                }
+                e = pre_value(xq[i], tq[i], w, wstack);
             }
             v[r] = e;
         }
@@ -191,7 +251,7 @@ __global__ void __launch_bounds__((1 << L) / 16)
                 for (int r = 0; r < S::RL; ++r) {
                     const int row = d + r * Ns;
                     if (bit_set(occ, row / TILE))
-                        *reinterpret_cast<float4 *>(base + (int64_t)row * Nv) = v[b * S::RL + operm<S::RL>(r)];
+                        *reinterpret_cast<E *>(base + (int64_t)row * Nv) = v[b * S::RL + operm<S::RL>(r)];
                 }
             }
         }
@@ -200,28 +260,30 @@ __global__ void __launch_bounds__((1 << L) / 16)
 }
 
 // ---------------------------------------------------------------- inverse column pass (fused post-pass)
-// One CTA per image column pair.  Shared memory: the exchange buffer, then the running post-pass sums of
-// the pair's image rows ([nx] float2, one writer per row).  image [nx][ny] of the band; accumulate adds
-// the result to it (a later plane block).
-template <int L>
+// One CTA per group of K image columns.  Shared memory: the exchange buffer, then the running post-pass
+// sums of the group's image rows ([nx] X, one writer per row).  image [nx][ny] of the band; accumulate
+// adds the result to it (a later plane block).
+template <int L, typename E>
 __global__ void __launch_bounds__((1 << L) / 16)
     k_colinv(const float2 *__restrict__ planes, int nk, int k_lo, int Nv, int64_t plane_sz, int nx, int ny,
-             const float4 *__restrict__ tT, const float2 *__restrict__ wk, int wstack,
+             const typename Lanes<E>::Tt *__restrict__ tT, const float2 *__restrict__ wk, int wstack,
              const uint32_t *__restrict__ rowocc, const float *__restrict__ corr, int accumulate,
              float *__restrict__ image, const float2 *__restrict__ W) {
     using S = Shape<L>;
+    using X = typename Lanes<E>::X;
     constexpr int N = S::N, T = S::T;
-    extern __shared__ __align__(1024) float4 sm[];
-    float2 *acc = reinterpret_cast<float2 *>(sm + spad(N - 1) + 1);
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    E *sm = reinterpret_cast<E *>(smraw);
+    X *acc = reinterpret_cast<X *>(sm + spad(N - 1) + 1);
     const int tid = threadIdx.x;
-    const int q = blockIdx.x, hq = ny / 4;
-    const int c = q < hq ? 2 * q : Nv - ny / 2 + 2 * (q - hq);
-    const int j0 = q < hq ? 2 * q + ny / 2 : 2 * (q - hq);
+    const int q = blockIdx.x;
+    int c, j0;
+    column_of<Lanes<E>::K>(q, Nv, ny, &c, &j0);
     const int rlo = nx / 2, rhi = N - nx / 2;
     const int nw = (N / TILE) / 32;
-    const float4 *tq = tT + (int64_t)q * nx;
-    for (int i = tid; i < nx; i += T) acc[i] = make_float2(0.f, 0.f);
-    float4 v[16];
+    const auto *tq = tT + (int64_t)q * nx;
+    for (int i = tid; i < nx; i += T) acc[i] = X{};
+    E v[16];
 
     for (int pl = 0; pl < nk; ++pl) {
         const int k = k_lo + pl;
@@ -230,8 +292,7 @@ __global__ void __launch_bounds__((1 << L) / 16)
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             const int row = tid + r * T;
-            v[r] = bit_set(occ, row / TILE) ? *reinterpret_cast<const float4 *>(base + (int64_t)row * Nv)
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[r] = bit_set(occ, row / TILE) ? *reinterpret_cast<const E *>(base + (int64_t)row * Nv) : E{};
         }
         const int Ns = fft_stages<L, true>(v, sm, W, tid);
         const float2 w = wk[k];
@@ -244,19 +305,8 @@ __global__ void __launch_bounds__((1 << L) / 16)
                 const int row = d + r * Ns;
                 if (row >= rlo && row < rhi) continue;
                 const int i = row < rlo ? row + nx / 2 : row - rhi;
-                const float4 h = v[b * S::RL + operm<S::RL>(r)];
-                float2 a = acc[i];
-                if (wstack) {
-                    const float4 t = tq[i];
-                    float s0, c0, s1, c1;
-                    screen(w, t.x, t.y, &s0, &c0);
-                    screen(w, t.z, t.w, &s1, &c1);
-                    a.x += h.x * c0 - h.y * s0;
-                    a.y += h.z * c1 - h.w * s1;
-                } else {
-                    a.x += h.x;
-                    a.y += h.z;
-                }
+                X a = acc[i];
+                post_add(a, v[b * S::RL + operm<S::RL>(r)], tq[i], w, wstack);
                 acc[i] = a;
             }
         }
@@ -264,49 +314,51 @@ __global__ void __launch_bounds__((1 << L) / 16)
     __syncthreads();
     for (int i = tid; i < nx; i += T) {
         const int64_t p = (int64_t)i * ny + j0;
-        const float2 cr = *reinterpret_cast<const float2 *>(corr + p);
-        float2 o = make_float2(acc[i].x * cr.x, acc[i].y * cr.y);
-        if (accumulate) {
-            const float2 prev = *reinterpret_cast<const float2 *>(image + p);
-            o.x += prev.x;
-            o.y += prev.y;
-        }
-        *reinterpret_cast<float2 *>(image + p) = o;
+        X o = mul_corr(acc[i], *reinterpret_cast<const X *>(corr + p));
+        if (accumulate) o = add_prev(o, *reinterpret_cast<const X *>(image + p));
+        *reinterpret_cast<X *>(image + p) = o;
     }
 }
 
 // ---------------------------------------------------------------- row pass
-// One CTA per pair of rows (u0, u0 + 1) of one occupied tile-row; list[e] = k << 16 | tu, and the CTA
-// takes rows tu TILE + 2 p, p = blockIdx.x mod 16.  occ: the band's tile masks [Pmax][ntu][ntv / 32].
+// One CTA per group of K rows of one occupied tile-row: list[e] = k << 16 | tu, and the CTA takes rows
+// tu TILE + K p .. + K - 1, p = blockIdx.x mod (TILE / K).  occ: the band's tile masks [Pmax][ntu][ntv / 32].
 //   INV: reads the touched segments (the rest is zero), writes the image columns;
 //   forward: reads the image columns (the rest is zero), writes the touched segments.
-template <int L, bool INV>
+template <typename E> __device__ __forceinline__ E load_rows(const float2 *r0, int64_t N, int m);
+template <> __device__ __forceinline__ float4 load_rows<float4>(const float2 *r0, int64_t N, int m) {
+    const float2 a = r0[m], b = r0[N + m];
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <> __device__ __forceinline__ float2 load_rows<float2>(const float2 *r0, int64_t N, int m) { return r0[m]; }
+__device__ __forceinline__ void store_rows(float2 *r0, int64_t N, int m, float4 e) {
+    r0[m] = make_float2(e.x, e.y);
+    r0[N + m] = make_float2(e.z, e.w);
+}
+__device__ __forceinline__ void store_rows(float2 *r0, int64_t, int m, float2 e) { r0[m] = e; }
+
+template <int L, bool INV, typename E>
 __global__ void __launch_bounds__((1 << L) / 16)
     k_rowfft(float2 *__restrict__ planes, int k_lo, int ntu, int64_t plane_sz, int ny,
              const int *__restrict__ list, const uint32_t *__restrict__ occ, const float2 *__restrict__ W) {
     using S = Shape<L>;
-    constexpr int N = S::N, T = S::T;
+    constexpr int N = S::N, T = S::T, K = Lanes<E>::K;
     constexpr int NW = N / TILE / 32;   // mask words per tile-row
-    extern __shared__ __align__(1024) float4 sm[];
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    E *sm = reinterpret_cast<E *>(smraw);
     const int tid = threadIdx.x;
-    const int ent = list[blockIdx.x / (TILE / 2)];
+    const int ent = list[blockIdx.x / (TILE / K)];
     const int k = ent >> 16, tu = ent & 0xffff;
-    const int u0 = tu * TILE + 2 * (int)(blockIdx.x % (TILE / 2));
+    const int u0 = tu * TILE + K * (int)(blockIdx.x % (TILE / K));
     float2 *row0 = planes + (int64_t)(k - k_lo) * plane_sz + (int64_t)u0 * N;
-    float2 *row1 = row0 + N;
     const uint32_t *segs = occ + ((int64_t)k * ntu + tu) * NW;
     const int clo = ny / 2, chi = N - ny / 2;
-    float4 v[16];
+    E v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int m = tid + r * T;
         const bool in = INV ? bit_set(segs, m / TILE) : (m < clo || m >= chi);
-        if (in) {
-            const float2 a = row0[m], b = row1[m];
-            v[r] = make_float4(a.x, a.y, b.x, b.y);
-        } else {
-            v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        v[r] = in ? load_rows<E>(row0, N, m) : E{};
     }
     const int Ns = fft_stages<L, INV>(v, sm, W, tid);
     dense_to_smem<L>(v, sm, tid, Ns);
@@ -314,31 +366,27 @@ __global__ void __launch_bounds__((1 << L) / 16)
 #pragma unroll 4
     for (int m = tid; m < N; m += T) {
         const bool out = INV ? (m < clo || m >= chi) : bit_set(segs, m / TILE);
-        if (out) {
-            const float4 e = sm[m];
-            row0[m] = make_float2(e.x, e.y);
-            row1[m] = make_float2(e.z, e.w);
-        }
+        if (out) store_rows(row0, N, m, sm[m]);
     }
 }
 
 // ---------------------------------------------------------------- tables
-// xcT[q][i] = (x corr)(i, j0(q)), (x corr)(i, j0(q) + 1): the pre-pass inputs in column-pair order
-// (j0(q) = ny/2 + 2 q for q < ny/4, 2 (q - ny/4) after), by a 32 x 32 tile transpose.
+// xcT[q][i] = (x corr)(i, j0(q) .. j0(q) + K - 1): the pre-pass inputs of column group q by image row
+// (j0 as in column_of), by a 32 x 32 tile transpose.
+template <int K>
 __global__ void k_xc_transpose(const float *__restrict__ x, const float *__restrict__ corr, int nx, int ny,
-                               float2 *__restrict__ xcT) {
-    __shared__ float2 tile[32][33];
-    const int hq = ny / 4, nq = ny / 2;
+                               typename Lanes<std::conditional_t<K == 2, float4, float2>>::X *__restrict__ xcT) {
+    using X = typename Lanes<std::conditional_t<K == 2, float4, float2>>::X;
+    __shared__ X tile[32][33];
+    const int hq = ny / (2 * K), nq = ny / K;
     const int i0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
     for (int kk = threadIdx.y; kk < 32; kk += 8) {
         const int i = i0 + kk, q = q0 + threadIdx.x;
-        float2 e = make_float2(0.f, 0.f);
+        X e{};
         if (i < nx && q < nq) {
-            const int j0 = q < hq ? 2 * q + ny / 2 : 2 * (q - hq);
+            const int j0 = q < hq ? K * q + ny / 2 : K * (q - hq);
             const int64_t p = (int64_t)i * ny + j0;
-            const float2 a = *reinterpret_cast<const float2 *>(x + p);
-            const float2 cr = *reinterpret_cast<const float2 *>(corr + p);
-            e = make_float2(a.x * cr.x, a.y * cr.y);
+            e = mul_corr(*reinterpret_cast<const X *>(x + p), *reinterpret_cast<const X *>(corr + p));
         }
         tile[kk][threadIdx.x] = e;
     }
@@ -349,15 +397,22 @@ __global__ void k_xc_transpose(const float *__restrict__ x, const float *__restr
     }
 }
 
-// tT[q][i] = t(i, j0(q)), t(i, j0(q) + 1) from the per-pixel float pairs of an FP32 plan
-__global__ void k_t_transpose(const float2 *__restrict__ tp, int nx, int ny, float4 *__restrict__ tT) {
-    const int64_t n = (int64_t)nx * (ny / 2);
+// tT[q][i] = t(i, j0(q) .. j0(q) + K - 1) from the per-pixel float pairs of an FP32 plan
+template <int K>
+__global__ void k_t_transpose(const float2 *__restrict__ tp, int nx, int ny,
+                              typename Lanes<std::conditional_t<K == 2, float4, float2>>::Tt *__restrict__ tT) {
+    const int64_t n = (int64_t)nx * (ny / K);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int q = (int)(e / nx), i = (int)(e - (int64_t)q * nx);
-        const int hq = ny / 4;
-        const int j0 = q < hq ? 2 * q + ny / 2 : 2 * (q - hq);
-        const float2 a = tp[(int64_t)i * ny + j0], b = tp[(int64_t)i * ny + j0 + 1];
-        tT[e] = make_float4(a.x, a.y, b.x, b.y);
+        const int hq = ny / (2 * K);
+        const int j0 = q < hq ? K * q + ny / 2 : K * (q - hq);
+        const float2 a = tp[(int64_t)i * ny + j0];
+        if constexpr (K == 2) {
+            const float2 b = tp[(int64_t)i * ny + j0 + 1];
+            tT[e] = make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            tT[e] = a;
+        }
     }
 }
 
@@ -387,30 +442,44 @@ int log2_exact(int n) {
     return (1 << L) == n ? L : -1;
 }
 
+template <int L, typename E> constexpr size_t fft_smem() { return (size_t)(spad((1 << L) - 1) + 1) * sizeof(E); }
+// column groups of K = 2 columns for transforms of up to 8192 points, single columns for 16384
+template <int L> using ColE = std::conditional_t<(L <= 13), float4, float2>;
+
 template <int L, bool TMA>
-void launch_colfwd(unsigned grid, size_t smem, cudaStream_t st, float2 *planes, int nk, int k_lo, int Nv,
-                   int64_t plane_sz, int nx, int ny, const float2 *xcT, const float4 *tT, const float2 *wk,
-                   int wstack, const uint32_t *rowocc, const float2 *W, const CUtensorMap &map) {
-    PFB_CUDA(cudaFuncSetAttribute(k_colfwd<L, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_colfwd<L, TMA><<<grid, (1 << L) / 16, smem, st>>>(planes, nk, k_lo, Nv, plane_sz, nx, ny, xcT, tT, wk, wstack,
-                                                         rowocc, W, map);
+void launch_colfwd(cudaStream_t st, float2 *planes, int nk, int k_lo, int Nv, int64_t plane_sz, int nx, int ny,
+                   const void *xcT, const void *tT, const float2 *wk, int wstack, const uint32_t *rowocc,
+                   const float2 *W, const CUtensorMap &map) {
+    using E = ColE<L>;
+    const size_t smem = fft_smem<L, E>();
+    const unsigned grid = (unsigned)(ny / Lanes<E>::K);
+    PFB_CUDA(cudaFuncSetAttribute(k_colfwd<L, TMA, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_colfwd<L, TMA, E><<<grid, (1 << L) / 16, smem, st>>>(
+        planes, nk, k_lo, Nv, plane_sz, nx, ny, (const typename Lanes<E>::X *)xcT,
+        (const typename Lanes<E>::Tt *)tT, wk, wstack, rowocc, W, map);
 }
 
 template <int L>
-void launch_colinv(unsigned grid, size_t smem, cudaStream_t st, const float2 *planes, int nk, int k_lo, int Nv,
-                   int64_t plane_sz, int nx, int ny, const float4 *tT, const float2 *wk, int wstack,
-                   const uint32_t *rowocc, const float *corr, int accumulate, float *image, const float2 *W) {
-    PFB_CUDA(cudaFuncSetAttribute(k_colinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_colinv<L><<<grid, (1 << L) / 16, smem, st>>>(planes, nk, k_lo, Nv, plane_sz, nx, ny, tT, wk, wstack, rowocc,
-                                                    corr, accumulate, image, W);
+void launch_colinv(cudaStream_t st, const float2 *planes, int nk, int k_lo, int Nv, int64_t plane_sz, int nx, int ny,
+                   const void *tT, const float2 *wk, int wstack, const uint32_t *rowocc, const float *corr,
+                   int accumulate, float *image, const float2 *W) {
+    using E = ColE<L>;
+    const size_t smem = fft_smem<L, E>() + (size_t)nx * sizeof(typename Lanes<E>::X);
+    const unsigned grid = (unsigned)(ny / Lanes<E>::K);
+    PFB_CUDA(cudaFuncSetAttribute(k_colinv<L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_colinv<L, E><<<grid, (1 << L) / 16, smem, st>>>(planes, nk, k_lo, Nv, plane_sz, nx, ny,
+                                                       (const typename Lanes<E>::Tt *)tT, wk, wstack, rowocc, corr,
+                                                       accumulate, image, W);
 }
 
 template <int L, bool INV>
-void launch_rowfft(unsigned grid, cudaStream_t st, float2 *planes, int k_lo, int ntu, int64_t plane_sz, int ny,
+void launch_rowfft(int64_t entries, cudaStream_t st, float2 *planes, int k_lo, int ntu, int64_t plane_sz, int ny,
                    const int *list, const uint32_t *occ, const float2 *W) {
-    const size_t smem = (size_t)(spad((1 << L) - 1) + 1) * sizeof(float4);
-    PFB_CUDA(cudaFuncSetAttribute(k_rowfft<L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_rowfft<L, INV><<<grid, (1 << L) / 16, smem, st>>>(planes, k_lo, ntu, plane_sz, ny, list, occ, W);
+    using E = ColE<L>;
+    const size_t smem = fft_smem<L, E>();
+    const unsigned grid = (unsigned)(entries * (TILE / Lanes<E>::K));
+    PFB_CUDA(cudaFuncSetAttribute(k_rowfft<L, INV, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_rowfft<L, INV, E><<<grid, (1 << L) / 16, smem, st>>>(planes, k_lo, ntu, plane_sz, ny, list, occ, W);
 }
 
 #define PFB_L_SWITCH(Lv, CALL)                                              \
@@ -419,15 +488,20 @@ void launch_rowfft(unsigned grid, cudaStream_t st, float2 *planes, int k_lo, int
         case 11: CALL(11); break;                                           \
         case 12: CALL(12); break;                                           \
         case 13: CALL(13); break;                                           \
+        case 14: CALL(14); break;                                           \
         default: throw Error(PFB_ERR_ARG, "pruned plane transform: unsupported plane size"); \
     }
 
 }  // namespace
 
+// columns of the column kernels per CTA for planes of Nu rows: pairs up to 8192, single columns at 16384
+static int col_group(int Nu) { return Nu <= 8192 ? 2 : 1; }
+
 bool pruned_fits(const Plan &p) {
     const int Lu = log2_exact(p.Nu), Lv = log2_exact(p.Nv);
-    return p.prec == PFB_F32 && Lu >= 10 && Lu <= 13 && Lv >= 10 && Lv <= 13 && colfft_fits(p.Nu, p.Nv, p.nx, p.ny) &&
-           p.nx >= 2 && p.ny >= 4 && p.Pmax < (1 << 15) && !(p.flags & PFB_NO_PRUNED_FFT);
+    return p.prec == PFB_F32 && Lu >= 10 && Lu <= 14 && Lv >= 10 && Lv <= 14 && p.nx % 2 == 0 && p.ny % 4 == 0 &&
+           p.nx >= 2 && p.ny >= 4 && p.nx <= p.Nu && p.ny <= p.Nv && p.Pmax < (1 << 15) &&
+           !(p.flags & PFB_NO_PRUNED_FFT);
 }
 
 void build_pruned_tables(Ctx &ctx, Plan &p, cudaStream_t st) {
@@ -482,9 +556,14 @@ void build_pruned_tables(Ctx &ctx, Plan &p, cudaStream_t st) {
     if (!list.empty())
         PFB_CUDA(cudaMemcpyAsync(p.d_rowlist, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     PFB_CUDA(cudaMemcpyAsync(p.d_wk, wk.data(), wk.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
-    const int64_t n = (int64_t)p.nx * (p.ny / 2);
-    k_t_transpose<<<(unsigned)std::min<int64_t>((n + 255) / 256, 32LL * ctx.num_sms), 256, 0, st>>>(
-        reinterpret_cast<const float2 *>(p.d_tp), p.nx, p.ny, p.d_tT);
+    const int K = col_group(p.Nu);
+    const int64_t n = (int64_t)p.nx * (p.ny / K);
+    const unsigned tb = (unsigned)std::min<int64_t>((n + 255) / 256, 32LL * ctx.num_sms);
+    if (K == 2)
+        k_t_transpose<2><<<tb, 256, 0, st>>>(reinterpret_cast<const float2 *>(p.d_tp), p.nx, p.ny, p.d_tT);
+    else
+        k_t_transpose<1><<<tb, 256, 0, st>>>(reinterpret_cast<const float2 *>(p.d_tp), p.nx, p.ny,
+                                             reinterpret_cast<float2 *>(p.d_tT));
     check_launch("t_transpose");
     // the host vectors die with this scope
     PFB_CUDA(cudaStreamSynchronize(st));
@@ -508,11 +587,15 @@ void plane_forward(Ctx &ctx, const Plan &p, int b, const float *x, int k_lo, int
     const float2 *Wv = p.Nv == p.Nu ? Wu : fft_twiddles(ctx, p.Nv, st);
     double rows = 0;
     occupied_counts(p, b, k_lo, k_hi, &rows);
-    float2 *xcT = (float2 *)ctx.scratch("xcT", (size_t)npix * sizeof(float));
+    void *xcT = ctx.scratch("xcT", (size_t)npix * sizeof(float));
+    const int K = col_group(p.Nu);
     {
         KTimer t(ctx, "xc_transpose", st, 12.0 * npix);
-        const dim3 grid((unsigned)((p.nx + 31) / 32), (unsigned)((p.ny / 2 + 31) / 32));
-        k_xc_transpose<<<grid, dim3(32, 8), 0, st>>>(x, (const float *)p.d_corr, p.nx, p.ny, xcT);
+        const dim3 grid((unsigned)((p.nx + 31) / 32), (unsigned)((p.ny / K + 31) / 32));
+        if (K == 2)
+            k_xc_transpose<2><<<grid, dim3(32, 8), 0, st>>>(x, (const float *)p.d_corr, p.nx, p.ny, (float2 *)xcT);
+        else
+            k_xc_transpose<1><<<grid, dim3(32, 8), 0, st>>>(x, (const float *)p.d_corr, p.nx, p.ny, (float *)xcT);
         check_launch("xc_transpose");
     }
     const float2 *wk = p.d_wk + (size_t)b * p.Pmax;
@@ -521,14 +604,13 @@ void plane_forward(Ctx &ctx, const Plan &p, int b, const float *x, int k_lo, int
         KTimer t(ctx, "col_fwd", st, 12.0 * npix + rows * p.ny * 8.0);
         CUtensorMap map;
         std::memset(&map, 0, sizeof(map));
-        const bool tma = plane_tensor_map(&map, planes, p.Nu, p.Nv, nk, p.ny, TILE);
-        const size_t smem = (size_t)(spad(p.Nu - 1) + 1) * sizeof(float4);
-        const unsigned grid = (unsigned)(p.ny / 2);
-#define PFB_CF(LV)                                                                                         \
-    (tma ? launch_colfwd<LV, true>(grid, smem, st, planes, nk, k_lo, p.Nv, plane_sz, p.nx, p.ny, xcT, p.d_tT, \
-                                   wk, p.wstack ? 1 : 0, rowocc, Wu, map)                                  \
-         : launch_colfwd<LV, false>(grid, smem, st, planes, nk, k_lo, p.Nv, plane_sz, p.nx, p.ny, xcT, p.d_tT, \
-                                    wk, p.wstack ? 1 : 0, rowocc, Wu, map))
+        // TMA boxes of 2 cells x TILE rows for column pairs; single columns (8-byte rows) store per thread
+        const bool tma = K == 2 && plane_tensor_map(&map, planes, p.Nu, p.Nv, nk, p.ny, TILE);
+#define PFB_CF(LV)                                                                                          \
+    (tma ? launch_colfwd<LV, (LV <= 13)>(st, planes, nk, k_lo, p.Nv, plane_sz, p.nx, p.ny, xcT, p.d_tT, wk,  \
+                                         p.wstack ? 1 : 0, rowocc, Wu, map)                                   \
+         : launch_colfwd<LV, false>(st, planes, nk, k_lo, p.Nv, plane_sz, p.nx, p.ny, xcT, p.d_tT, wk,        \
+                                    p.wstack ? 1 : 0, rowocc, Wu, map))
         PFB_L_SWITCH(Lu, PFB_CF)
 #undef PFB_CF
         check_launch("col_fwd");
@@ -538,8 +620,7 @@ void plane_forward(Ctx &ctx, const Plan &p, int b, const float *x, int k_lo, int
     if (e1 > e0) {
         KTimer t(ctx, "row_fwd", st, rows * (p.ny + p.Nv) * 8.0);
         const uint32_t *occ = p.d_occ + (size_t)b * p.Pmax * p.ntu * (p.ntv / 32);
-        const unsigned grid = (unsigned)((e1 - e0) * (TILE / 2));
-#define PFB_RF(LV) launch_rowfft<LV, false>(grid, st, planes, k_lo, p.ntu, plane_sz, p.ny, p.d_rowlist + e0, occ, Wv)
+#define PFB_RF(LV) launch_rowfft<LV, false>(e1 - e0, st, planes, k_lo, p.ntu, plane_sz, p.ny, p.d_rowlist + e0, occ, Wv)
         PFB_L_SWITCH(Lv, PFB_RF)
 #undef PFB_RF
         check_launch("row_fwd");
@@ -561,8 +642,7 @@ void plane_inverse(Ctx &ctx, const Plan &p, int b, int k_lo, int k_hi, float2 *p
     if (e1 > e0) {
         KTimer t(ctx, "row_inv", st, rows * (p.Nv + p.ny) * 8.0);
         const uint32_t *occ = p.d_occ + (size_t)b * p.Pmax * p.ntu * (p.ntv / 32);
-        const unsigned grid = (unsigned)((e1 - e0) * (TILE / 2));
-#define PFB_RI(LV) launch_rowfft<LV, true>(grid, st, planes, k_lo, p.ntu, plane_sz, p.ny, p.d_rowlist + e0, occ, Wv)
+#define PFB_RI(LV) launch_rowfft<LV, true>(e1 - e0, st, planes, k_lo, p.ntu, plane_sz, p.ny, p.d_rowlist + e0, occ, Wv)
         PFB_L_SWITCH(Lv, PFB_RI)
 #undef PFB_RI
         check_launch("row_inv");
@@ -571,11 +651,9 @@ void plane_inverse(Ctx &ctx, const Plan &p, int b, int k_lo, int k_hi, float2 *p
         KTimer t(ctx, "col_inv", st, rows * p.ny * 8.0 + npix * (8.0 + 4.0 + 4.0 + (k_lo > 0 ? 4.0 : 0.0)));
         const float2 *wk = p.d_wk + (size_t)b * p.Pmax;
         const uint32_t *rowocc = p.d_rowocc + (size_t)b * p.Pmax * (p.ntu / 32);
-        const size_t smem = (size_t)(spad(p.Nu - 1) + 1) * sizeof(float4) + (size_t)p.nx * sizeof(float2);
-        const unsigned grid = (unsigned)(p.ny / 2);
 #define PFB_CI(LV)                                                                                              \
-    launch_colinv<LV>(grid, smem, st, planes, nk, k_lo, p.Nv, plane_sz, p.nx, p.ny, p.d_tT, wk, p.wstack ? 1 : 0, \
-                      rowocc, (const float *)p.d_corr, k_lo > 0 ? 1 : 0, image, Wu)
+    launch_colinv<LV>(st, planes, nk, k_lo, p.Nv, plane_sz, p.nx, p.ny, p.d_tT, wk, p.wstack ? 1 : 0, rowocc,    \
+                      (const float *)p.d_corr, k_lo > 0 ? 1 : 0, image, Wu)
         PFB_L_SWITCH(Lu, PFB_CI)
 #undef PFB_CI
         check_launch("col_inv");

@@ -1,9 +1,9 @@
-"""Pruned plane transforms of the FP32 path (planes of 1024..8192 cells per side, powers of two): only
+"""Pruned plane transforms of the FP32 path (planes of 1024..16384 cells per side, powers of two): only
 the image region and the 32 x 32 uv tiles that some visibility touches are transformed, with the pre-
 and post-pass folded into the column transforms.  R, R^dagger and the Hessian are checked against the
 FP64 oracle and against the full-plane transforms (PFB_NO_PRUNED_FFT) on the same inputs: square and
-non-square planes, several bands with an empty one, more than one plane block per band, and repeated
-calls that reuse the plane buffer."""
+non-square planes, several bands with an empty one, more than one plane block per band, repeated calls
+that reuse the plane buffer, and the 16384-point transforms (one column or row per CTA)."""
 import ctypes
 
 import numpy as np
@@ -135,3 +135,35 @@ def test_pruned_several_plane_blocks():
         finally:
             c.close()
     assert found, "no budget split the w-stack into blocks"
+
+
+# planes of 16384 cells along one axis: the column (8192 x 512 image) or row (512 x 8192 image) transforms
+# take single columns / rows per CTA
+CASES_16K = [(8192, 512), (512, 8192)]
+
+
+@pytest.mark.parametrize("nx,ny", CASES_16K)
+def test_pruned_16384_point_transforms(ctx, nx, ny):
+    obs = _obs(nx, ny, 1, seed=13)
+    rng = np.random.default_rng(314)
+    a = (obs.uvw, obs.freq, obs.band_of_chan)
+    d = dev_obs(obs)
+    g = geometry(obs, EPS32)
+    gf = geometry(obs, EPS32, flags=_no_pruned())
+    ctx.lib.pfb_timing(ctx.h, 1)
+    x = _sky(rng, 1, nx, ny)
+    ref = oracle.degrid(*a, x, obs.dl, obs.dm)
+    v = ctx.pfb_degrid(g, *d, real_t(x, 32)).cpu().numpy()
+    vf = ctx.pfb_degrid(gf, *d, real_t(x, 32)).cpu().numpy()
+    assert rel_l2(v, ref) <= TOL32
+    assert rel_l2(v, vf) <= TOL_PATHS
+    y = synth.random_vis(rng, (obs.nrow, obs.nchan))
+    w = synth.uniform_weights(rng, (obs.nrow, obs.nchan))
+    img = ctx.pfb_grid(g, *d, cx_t(y, 32), real_t(w, 32)).cpu().numpy()
+    imf = ctx.pfb_grid(gf, *d, cx_t(y, 32), real_t(w, 32)).cpu().numpy()
+    assert rel_l2(img, imf) <= TOL_PATHS
+    pix = np.sort(rng.choice(nx * ny, 1024, replace=False))
+    ref = oracle.grid(*a, y, w, nx, ny, obs.dl, obs.dm, 1, pix=pix)
+    assert rel_l2(img.reshape(-1)[pix], ref) <= TOL32
+    assert _launches(ctx, "col_fwd") == 1 and _launches(ctx, "col_inv") == 1
+    ctx.lib.pfb_timing(ctx.h, 0)

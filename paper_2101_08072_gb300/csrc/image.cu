@@ -650,12 +650,14 @@ static void dwt2(int nx, int ny, int nband, int nlevel, const WavFilt &f, const 
     const View2<T> det{coef, full, ny};
     for (int lv = 0; lv < nlevel; ++lv) {
         const int n = nx >> lv, m = ny >> lv;
-        const View2<T> ll = lv == nlevel - 1 ? det : View2<T>{tmp + (lv & 1) * nband * quarter, quarter, m / 2};
+        // the coarse band of an intermediate level: [nband][n/2][m/2], dense, read back by the next level
+        const View2<T> ll = lv == nlevel - 1
+                                ? det
+                                : View2<T>{tmp + (lv & 1) * nband * quarter, (int64_t)(n / 2) * (m / 2), m / 2};
 #define PFB_DWT_CALL(LV) dwt_level_launch<T, LV>(nband, n, m, src, ll, det, f, st)
         PFB_TAPS_SWITCH(f.L, PFB_DWT_CALL)
 #undef PFB_DWT_CALL
         src = ll;
-        if (lv < nlevel - 1) src.bs = (int64_t)(n / 2) * (m / 2);
     }
 }
 

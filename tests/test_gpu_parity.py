@@ -191,10 +191,13 @@ def test_psf_conv(ctx, prec):
     assert rel_l2(y, ref) <= (1e-5 if prec == 32 else 1e-12)
 
 
-@pytest.mark.parametrize("prec,mask", [(32, 1), (64, 1), (32, 0b1111111), (64, 0b1111111)])
-def test_step_fixed_iterations(ctx, prec, mask):
+@pytest.mark.parametrize("prec,mask,nlevel", [(32, 1, 2), (64, 1, 2), (32, 0b1111111, 2), (64, 0b1111111, 2),
+                                              (32, 0b1111111, 3), (64, 0b1111111, 3), (64, 0b1111111, 4)])
+def test_step_fixed_iterations(ctx, prec, mask, nlevel):
     """One pfb step against the oracle's step at identical iteration counts, with the
-    Dirac basis alone and with the full dictionary of Eq. 9 (Dirac + db1..db6)."""
+    Dirac basis alone and with the full dictionary of Eq. 9 (Dirac + db1..db6), at two to
+    four wavelet levels on two bands (the coarse bands of the intermediate levels of every
+    band go through scratch between levels)."""
     from paper_2101_08072_gb300 import StepParams
     obs = synth.tiny_observation(nx=32, ny=32, nband=2)
     rng = np.random.default_rng(107)
@@ -207,12 +210,12 @@ def test_step_fixed_iterations(ctx, prec, mask):
     x0 = 0.5 * xt
     nbasis = bin(mask).count("1")
     v0 = np.zeros((nbasis, 2, 32, 32))
-    prm = oracle.Params(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=10, pd_iters=20, nlevel=2, basis_mask=mask)
+    prm = oracle.Params(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=10, pd_iters=20, nlevel=nlevel, basis_mask=mask)
     x1, v1, st = oracle.step(*a, w, d, p, ws, x0, v0, obs.dl, obs.dm, prm)
     eps = EPS32 if prec == 32 else EPS64
     g = geometry(obs, eps)
     xg, vg = real_t(x0, prec), real_t(v0, prec)
-    nh, stg = ctx.pfb_step(g, StepParams(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=10, pd_iters=20, nlevel=2,
+    nh, stg = ctx.pfb_step(g, StepParams(gamma=1.0, sigma=1e-2, lam=1e-3, cg_iters=10, pd_iters=20, nlevel=nlevel,
                                          basis_mask=mask), *dev_obs(obs),
                            real_t(w, prec), real_t(d, prec), real_t(p, prec), ws, xg, vg)
     tol = 1e-4 if prec == 32 else 1e-8

@@ -37,6 +37,9 @@ struct Plan {
     int Nu = 0, Nv = 0, Ww = 1, ntu = 0, ntv = 0, q = 1, nkq = 1, Pmax = 1;
     double beta = 0, dw = 0, tc = 0, Thalf = 0;
     bool wstack = false;
+    // FP32 tile kernels: every visibility is listed once, in the tile of its first-tap cell (no spill
+    // copies into the tiles its footprint crosses); gridding adds each tile's (TILE + W - 1)^2 region
+    bool halo = false;
     std::vector<double> w0, wlo, whi;
     std::vector<int> P;
     std::vector<double> scale;      // f / c per channel
@@ -44,8 +47,10 @@ struct Plan {
     std::vector<int64_t> band_items_begin, band_items_end;
     std::vector<int64_t> work_begin; // per band offset into d_work (size nband + 1)
     std::vector<int64_t> work_heavy_end; // per band: end of the heavy-tile chunks (they come first)
-    std::vector<int64_t> heavy_begin; // per band offset into d_heavy (size nband + 1)
-    std::vector<int64_t> empty_begin; // per band: the tiles without items follow the heavy ones in d_heavy
+    // per band offset into d_heavy (size nband + 1): the tiles that reductions fill (heavy tiles; on halo
+    // plans every tile some footprint reaches), then, from empty_begin[b], the tiles nothing writes
+    std::vector<int64_t> heavy_begin;
+    std::vector<int64_t> empty_begin;
 
     // ---- device
     double *d_scale = nullptr;
@@ -251,6 +256,7 @@ Plan &get_plan(Ctx &ctx, const pfb_geom &g, int prec, int64_t nrow, int nchan, c
 int kernel_support(double eps);
 
 // wstack.cu
+bool halo_fits(const Plan &p);
 void build_item_records(Ctx &ctx, Plan &p, cudaStream_t st);
 template <typename T>
 void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st, bool accumulate = false);

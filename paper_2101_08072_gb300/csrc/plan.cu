@@ -156,7 +156,7 @@ __global__ void k_w_range(const double *__restrict__ uvw, int64_t nrow, unsigned
 // that one atomic serves the whole group.
 template <typename T, bool SCATTER>
 __global__ void k_bucket(CoordSrc src, const int *__restrict__ band, int64_t nvis, int nchan,
-                         const BandGeom *__restrict__ bgs, int *__restrict__ counts,
+                         const BandGeom *__restrict__ bgs, int halo, int *__restrict__ counts,
                          const int64_t *__restrict__ off, uint32_t *__restrict__ items) {
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nvis;
@@ -170,8 +170,9 @@ __global__ void k_bucket(CoordSrc src, const int *__restrict__ band, int64_t nvi
             const BandGeom g = bgs[band[ch]];
             const VisCoord<T> c = vis_coord<T>(src, row, ch, g);
             const int tu = c.gu0 / TILE, tv = c.gv0 / TILE;
-            const bool su = c.gu0 - tu * TILE + g.W - 1 >= TILE;
-            const bool sv = c.gv0 - tv * TILE + g.W - 1 >= TILE;
+            // spill copies into the tiles the footprint crosses (none on halo plans)
+            const bool su = !halo && c.gu0 - tu * TILE + g.W - 1 >= TILE;
+            const bool sv = !halo && c.gv0 - tv * TILE + g.W - 1 >= TILE;
             const int tu1 = tu + 1 == g.ntu ? 0 : tu + 1, tv1 = tv + 1 == g.ntv ? 0 : tv + 1;
             const int kq = c.k0 / g.q;
             const long long bt = (long long)g.band * g.ntu * g.ntv;
@@ -520,6 +521,7 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     const size_t cxs = p.prec == PFB_F64 ? 16 : 8;
     PFB_REQUIRE((size_t)(p.Ww + p.q - 1) * TILE * TILE * cxs <= 227 * 1024,
                 "w-plane ring of the gridding kernel exceeds shared memory (reduce epsilon demands or image size)");
+    p.halo = halo_fits(p);
 
     // ---- device copies of per-channel data and band geometry
     p.d_scale = (double *)ctx.dalloc(p.nchan * sizeof(double));
@@ -560,10 +562,10 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     p.bytes += (size_t)(p.nkeys + 1) * sizeof(int64_t);
     const int bblocks = (int)std::max<int64_t>(1, std::min<int64_t>((nvis + 255) / 256, 32 * ctx.num_sms));
     if (p.prec == PFB_F64)
-        k_bucket<double, false><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, counts,
+        k_bucket<double, false><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, p.halo, counts,
                                                          nullptr, nullptr);
     else
-        k_bucket<float, false><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, counts,
+        k_bucket<float, false><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, p.halo, counts,
                                                         nullptr, nullptr);
     check_launch("bucket_count");
     exclusive_scan<int>(ctx, counts, p.nkeys, p.d_off, st);
@@ -573,10 +575,10 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     p.bytes += (size_t)std::max<int64_t>(p.nitems, 1) * sizeof(uint32_t);
     PFB_CUDA(cudaMemsetAsync(counts, 0, (size_t)p.nkeys * sizeof(int), st));
     if (p.prec == PFB_F64)
-        k_bucket<double, true><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, counts,
+        k_bucket<double, true><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, p.halo, counts,
                                                         p.d_off, p.d_items);
     else
-        k_bucket<float, true><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, counts,
+        k_bucket<float, true><<<bblocks, 256, 0, st>>>(p.coords(), p.d_band, nvis, p.nchan, p.d_bg, p.halo, counts,
                                                        p.d_off, p.d_items);
     check_launch("bucket_scatter");
 
@@ -611,22 +613,38 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
         const int64_t chunk = std::max<int64_t>(8192, (b1 - b0 + 16LL * ctx.num_sms - 1) / (16LL * ctx.num_sms));
         p.work_begin[b] = (int64_t)work.size();
         p.heavy_begin[b] = (int64_t)heavy.size();
+        const int64_t *tbb = tb.data() + b * ntiles;
+        auto has_items = [&](int tu, int tv) {
+            const int64_t t = (int64_t)tu * p.ntv + tv;
+            return tbb[t + 1] > tbb[t];
+        };
+        // on halo plans a tile's cells also receive the far edges of the regions of the tiles before it
+        // (with wrap-around): every such tile is filled by reductions into zeroed cells
+        auto reached = [&](int64_t t) {
+            const int tu = (int)(t / p.ntv), tv = (int)(t - (int64_t)tu * p.ntv);
+            const int pu = tu == 0 ? p.ntu - 1 : tu - 1, pv = tv == 0 ? p.ntv - 1 : tv - 1;
+            return has_items(tu, tv) || has_items(pu, tv) || has_items(tu, pv) || has_items(pu, pv);
+        };
         for (int64_t t = 0; t < ntiles; ++t) {
-            const int64_t s = tb[b * ntiles + t], e = tb[b * ntiles + t + 1];
+            const int64_t s = tbb[t], e = tbb[t + 1];
             if (e - s > chunk) {
-                heavy.push_back((int)t);
+                if (!p.halo) heavy.push_back((int)t);
                 for (int64_t c = s; c < e; c += chunk) work.push_back({(int)t, 1, c, std::min(e, c + chunk)});
             }
         }
         p.work_heavy_end[b] = (int64_t)work.size();
-        // owned tiles with items, largest first (no long tile starts at the end of the launch); tiles
-        // without items follow the heavy ones in the list of tiles that a plain kernel zeroes
+        // tiles with items that one CTA takes whole, largest first (no long tile starts at the end of the
+        // launch): they own their cells unless the plan is a halo plan.  Tiles that nothing writes follow
+        // the reduction-filled ones in the list of tiles that a plain kernel zeroes.
         const size_t l0 = work.size();
+        if (p.halo)
+            for (int64_t t = 0; t < ntiles; ++t)
+                if (reached(t)) heavy.push_back((int)t);
         p.empty_begin[b] = (int64_t)heavy.size();
         for (int64_t t = 0; t < ntiles; ++t) {
-            const int64_t s = tb[b * ntiles + t], e = tb[b * ntiles + t + 1];
-            if (e == s) heavy.push_back((int)t);
-            else if (e - s <= chunk) work.push_back({(int)t, 0, s, e});
+            const int64_t s = tbb[t], e = tbb[t + 1];
+            if (p.halo ? !reached(t) : e == s) heavy.push_back((int)t);
+            if (e > s && e - s <= chunk) work.push_back({(int)t, p.halo ? 1 : 0, s, e});
         }
         std::stable_sort(work.begin() + l0, work.end(), [](const WorkItem &x, const WorkItem &y) {
             return x.end - x.begin > y.end - y.begin;

@@ -416,9 +416,10 @@ __global__ void k_t_transpose(const float2 *__restrict__ tp, int nx, int ny,
     }
 }
 
-// Touched tiles: an item of bucket (b, tile, kq) reaches planes kq q .. kq q + q + W_w - 2 of tile.
+// Touched tiles: an item of bucket (b, tile, kq) reaches planes kq q .. kq q + q + W_w - 2 of tile, and on
+// plans that list items in their home tile only (halo), of the tiles after it in u, v and both.
 __global__ void k_occupancy(const int64_t *__restrict__ off, int64_t nkeys, int ntiles, int ntu, int ntv,
-                            int nkq, int q, int Ww, int Pmax, const BandGeom *__restrict__ bgs,
+                            int nkq, int q, int Ww, int Pmax, int halo, const BandGeom *__restrict__ bgs,
                             uint32_t *__restrict__ occ) {
     for (int64_t key = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; key < nkeys;
          key += (int64_t)gridDim.x * blockDim.x) {
@@ -428,10 +429,17 @@ __global__ void k_occupancy(const int64_t *__restrict__ off, int64_t nkeys, int 
         const int b = (int)(bt / ntiles), t = (int)(bt - (int64_t)b * ntiles);
         const int tu = t / ntv, tv = t - tu * ntv;
         const int P = bgs[b].P;
+        const int tu1 = tu + 1 == ntu ? 0 : tu + 1, tv1 = tv + 1 == ntv ? 0 : tv + 1;
         for (int cc = 0; cc < q + Ww - 1; ++cc) {
             const int k = kq * q + cc;
             if (k >= P) break;
-            atomicOr(&occ[(((int64_t)b * Pmax + k) * ntu + tu) * (ntv / 32) + (tv >> 5)], 1u << (tv & 31));
+            uint32_t *o = occ + ((int64_t)b * Pmax + k) * ntu * (ntv / 32);
+            atomicOr(&o[(int64_t)tu * (ntv / 32) + (tv >> 5)], 1u << (tv & 31));
+            if (halo) {
+                atomicOr(&o[(int64_t)tu1 * (ntv / 32) + (tv >> 5)], 1u << (tv & 31));
+                atomicOr(&o[(int64_t)tu * (ntv / 32) + (tv1 >> 5)], 1u << (tv1 & 31));
+                atomicOr(&o[(int64_t)tu1 * (ntv / 32) + (tv1 >> 5)], 1u << (tv1 & 31));
+            }
         }
     }
 }
@@ -516,7 +524,8 @@ void build_pruned_tables(Ctx &ctx, Plan &p, cudaStream_t st) {
     PFB_CUDA(cudaMemsetAsync(p.d_occ, 0, occ_words * 4, st));
     const int64_t ntiles = (int64_t)p.ntu * p.ntv;
     k_occupancy<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((p.nkeys + 255) / 256, 64LL * ctx.num_sms)), 256, 0,
-                  st>>>(p.d_off, p.nkeys, (int)ntiles, p.ntu, p.ntv, p.nkq, p.q, p.Ww, p.Pmax, p.d_bg, p.d_occ);
+                  st>>>(p.d_off, p.nkeys, (int)ntiles, p.ntu, p.ntv, p.nkq, p.q, p.Ww, p.Pmax, p.halo ? 1 : 0,
+                        p.d_bg, p.d_occ);
     check_launch("occupancy");
     std::vector<uint32_t> occ(occ_words);
     PFB_CUDA(cudaMemcpyAsync(occ.data(), p.d_occ, occ_words * 4, cudaMemcpyDeviceToHost, st));

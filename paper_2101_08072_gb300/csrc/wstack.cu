@@ -281,10 +281,15 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 }
 
 // ------------------------------------------------------------------ FP32 gridding by residue classes
-// Same work decomposition as k_grid_tiles (a CTA owns a tile's cells).  Items are
-// processed in chunks of at most res_ch(W) records of one w bucket; chunks run
-// across w planes with a sliding window of W_w ring planes (one plane per bucket) in
-// shared memory, which are written to HBM once complete.
+// One CTA per work item: the items of one uv tile, or a chunk of a heavy tile's
+// items.  The plan lists every visibility once, in the tile of its first-tap cell, so
+// the ring of a CTA covers the tile and the W - 1 cells past its far edges that the
+// footprints reach: (TILE + W - 1)^2 cells per plane.  Neighbouring regions overlap,
+// so every region is added to the planes with global vector reductions into cells
+// zeroed before the launch.  Items are processed in chunks of at most res_ch(W)
+// records of one w bucket; chunks run across w planes with a sliding window of W_w
+// ring planes (one plane per bucket) in shared memory, each added to HBM once
+// complete.
 //
 // The CTA is warp-specialised.  Four producer warps stage chunk i+1 (coordinates,
 // ES taps, weighted and phase-rotated value) into one of two shared buffers while
@@ -304,7 +309,10 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 // it stores the ES tap that lands on that class together with a packed cell key (u
 // cell and first plane in the u entry, v cell in the v entry), so a scatter step is
 // two 8-byte loads, an OR and a compare, one multiply and 2 W_w FMAs.
-constexpr int RSTRIDE = TILE + 6;   // padded ring row: spreads a footprint over the banks
+// ring region edge: the tile and the W - 1 cells past its far edges that footprints reach
+__host__ __device__ constexpr int res_edge(int W) { return TILE + W - 1; }
+// padded ring row: spreads a footprint over the banks
+__host__ __device__ constexpr int res_stride(int W) { return res_edge(W) + 1; }
 constexpr int GRID_NP = 128;        // producer threads (4 warps)
 constexpr int GRID_NC = 256;        // consumer threads (8 warps)
 constexpr int GRID_NT = GRID_NP + GRID_NC;
@@ -312,7 +320,7 @@ constexpr int GRID_NT = GRID_NP + GRID_NC;
 constexpr int BAR_FULL = 1, BAR_EMPTY = 3, BAR_CONS = 5;
 // packed cell key: (u + 64) << 25 | (v + 64) << 18 | first plane (18 bits)
 constexpr int KEY_PLANE_BITS = 18;
-constexpr uint32_t KEY_NONE = 0xffffffffu;   // decodes to u = 63, outside every tile
+constexpr uint32_t KEY_NONE = 0xffffffffu;   // decodes to u = 63, outside every ring region
 
 // records per chunk: two buffers and the ring fit twice in an SM's shared memory
 __host__ __device__ constexpr int res_ch(int W) { return W <= 7 ? 128 : 96; }
@@ -326,7 +334,7 @@ struct ResSmem {
 __host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
     ResSmem L;
     const int ch = res_ch(W);
-    int o = R * TILE * RSTRIDE * (int)sizeof(float2);
+    int o = R * res_edge(W) * res_stride(W) * (int)sizeof(float2);
     for (int s = 0; s < 2; ++s) {
         L.ru[s] = o; o += ch * W * (int)sizeof(float2);
         L.rv[s] = o; o += ch * W * (int)sizeof(float2);
@@ -405,7 +413,8 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
            int k_lo, int k_hi, float2 *__restrict__ planes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int R = Ww;                  // ring planes (one w bucket per plane)
-    constexpr int SLOT = TILE * RSTRIDE;
+    constexpr int E = res_edge(W), HS = res_stride(W);
+    constexpr int SLOT = E * HS;
     constexpr int WS = res_ws(Ww);
     constexpr int CH = res_ch(W);
     constexpr int G = W * W;         // consumer threads of a group (one per residue class)
@@ -414,43 +423,30 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
     const ResSmem L = res_layout(R, W, Ww);
     float2 *ring = reinterpret_cast<float2 *>(smem_raw);
     int4 *meta = reinterpret_cast<int4 *>(smem_raw + L.meta);
-    const int cells = TILE * TILE;
     const WorkItem wi = work[blockIdx.x];
+    if (wi.end <= wi.begin) return;
     const int tu = wi.tile / g.ntv, tv = wi.tile - tu * g.ntv;
     const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
-    float2 *tile0 = planes + (int64_t)(tu * TILE) * g.Nv + tv * TILE;
-
-    if (wi.end <= wi.begin) {
-        // no items: the tile's cells of every plane of the block are zero
-        if (!wi.atomic_mode) {
-            const int nk = k_hi - k_lo;
-            for (int e = threadIdx.x; e < nk * cells / 2; e += blockDim.x) {
-                const int k = e / (cells / 2), c2 = e - k * (cells / 2);
-                const int r = c2 / (TILE / 2), cc = (c2 - r * (TILE / 2)) * 2;
-                *reinterpret_cast<float4 *>(tile0 + (int64_t)k * plane_sz + (int64_t)r * g.Nv + cc) =
-                    make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-        return;
-    }
     for (int e = threadIdx.x; e < R * SLOT; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
 
-    // write planes [next, upto) from the ring to HBM and clear their slots
+    // add planes [next, upto) of the ring's region to HBM (cells past the grid's edge wrap around) and
+    // clear their slots
     int next = k_lo;
     auto flush_planes = [&](int upto, int tid, int nthr) {
         upto = min(upto, k_hi);
         for (int k = next; k < upto; ++k) {
             float2 *slot = ring + (k % R) * SLOT;
-            float2 *dst = tile0 + (int64_t)(k - k_lo) * plane_sz;
-            for (int e2 = tid; e2 < cells; e2 += nthr) {
-                const int r = e2 / TILE, cc = e2 - r * TILE;
-                const float2 val = slot[r * RSTRIDE + cc];
-                if (wi.atomic_mode) {
-                    if (val.x != 0.f || val.y != 0.f) atomicAdd(dst + (int64_t)r * g.Nv + cc, val);
-                } else {
-                    dst[(int64_t)r * g.Nv + cc] = val;
+            float2 *dst = planes + (int64_t)(k - k_lo) * plane_sz;
+            for (int e2 = tid; e2 < E * E; e2 += nthr) {
+                const int r = e2 / E, cc = e2 - r * E;
+                const float2 val = slot[r * HS + cc];
+                if (val.x != 0.f || val.y != 0.f) {
+                    int gu = tu * TILE + r, gv = tv * TILE + cc;
+                    gu -= gu >= g.Nu ? g.Nu : 0;
+                    gv -= gv >= g.Nv ? g.Nv : 0;
+                    atomicAdd(dst + (int64_t)gu * g.Nv + gv, val);
+                    slot[r * HS + cc] = make_float2(0.f, 0.f);
                 }
-                slot[r * RSTRIDE + cc] = make_float2(0.f, 0.f);
             }
         }
         if (upto > next) next = upto;
@@ -656,8 +652,8 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         auto flush_acc = [&]() {
             const int cu = (int)(ckey >> 25) - 64, cv = (int)((ckey >> KEY_PLANE_BITS) & 127u) - 64;
             const int ck = (int)(ckey & ((1u << KEY_PLANE_BITS) - 1u));
-            if ((unsigned)cu < (unsigned)TILE && (unsigned)cv < (unsigned)TILE) {
-                float2 *cell = ring + cu * RSTRIDE + cv;
+            if ((unsigned)cu < (unsigned)E && (unsigned)cv < (unsigned)E) {
+                float2 *cell = ring + cu * HS + cv;
                 const int s0 = ck % R;
 #pragma unroll
                 for (int c = 0; c < Ww; ++c) {
@@ -755,9 +751,9 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             pair_arrive<BAR_EMPTY>(sb);
             if (m.y) break;
         }
-        // remaining planes: all of the block for an owned tile, the touched ones for a chunk
+        // remaining planes: those the last bucket touched
         named_sync<BAR_CONS, GRID_NC>();
-        flush_planes(wi.atomic_mode ? min(k_hi, next + R) : k_hi, ct, GRID_NC);
+        flush_planes(min(k_hi, next + R), ct, GRID_NC);
     }
 }
 
@@ -1143,9 +1139,12 @@ static bool degrid_tiles_fit(const Plan &p) {
     const int R = p.Ww, E = TILE + p.W - 1, ES = E | 1;
     return fast_path_f32(p) && (size_t)R * E * ES * sizeof(float2) <= 227 * 1024;
 }
-static bool grid_res_fit(const Plan &p) {
-    return fast_path_f32(p) && (size_t)res_layout(p.Ww, p.W, p.Ww).total <= 227 * 1024;
+// FP32 plans whose tile kernels fit: the plan lists each visibility once, in its home tile, and the
+// gridding kernel adds the tile's region with the footprints' far edges (k_grid_res)
+bool halo_fits(const Plan &p) {
+    return fast_path_f32(p) && degrid_tiles_fit(p) && (size_t)res_layout(p.Ww, p.W, p.Ww).total <= 227 * 1024;
 }
+static bool grid_res_fit(const Plan &p) { return p.halo; }
 
 template <int W, int Ww>
 static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkItem *work, const Plan &p,
@@ -1281,7 +1280,8 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
     for (int b = 0; b < p.nband; ++b) {
         const BandGeom g = p.geom(b);
         const int64_t w0 = p.work_begin[b], w1 = p.work_begin[b + 1];
-        // tiles zeroed per call: the heavy ones (filled by reductions), and the empty ones unless kept
+        // tiles zeroed per call: those that reductions fill (heavy tiles; on plans of home items, every
+        // tile that some footprint reaches), and the rest unless kept or never read
         const int64_t h0 = p.heavy_begin[b], h1 = (keep || pruned) ? p.empty_begin[b] : p.heavy_begin[b + 1];
         const double nvb = (double)band_nvis(p, b);
         const double nit = (double)(p.band_items_end[b] - p.band_items_begin[b]);

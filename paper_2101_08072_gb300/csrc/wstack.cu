@@ -307,8 +307,11 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 // visibilities; distinct groups can meet on a cell, so the (rare) ring adds are
 // atomic.  Staging does the per-visibility index work once: for every residue class j
 // it stores the ES tap that lands on that class together with a packed cell key (u
-// cell and first plane in the u entry, v cell in the v entry), so a scatter step is
-// two 8-byte loads, an OR and a compare, one multiply and 2 W_w FMAs.
+// cell in the u entry, v cell in the v entry), so a scatter step is two 8-byte
+// loads, an OR and a compare, one multiply and 2 W_w FMAs.  All items of a bucket
+// start on the same w plane, so the ring slots of a run's planes are set once per
+// bucket, for all threads alike.
+//
 // ring region edge: the tile and the W - 1 cells past its far edges that footprints reach
 __host__ __device__ constexpr int res_edge(int W) { return TILE + W - 1; }
 // padded ring row: spreads a footprint over the banks
@@ -318,7 +321,8 @@ constexpr int GRID_NC = 256;        // consumer threads (8 warps)
 constexpr int GRID_NT = GRID_NP + GRID_NC;
 // named barriers (0 is __syncthreads)
 constexpr int BAR_FULL = 1, BAR_EMPTY = 3, BAR_CONS = 5;
-// packed cell key: (u + 64) << 25 | (v + 64) << 18 | first plane (18 bits)
+// packed cell key: (u + 64) << 25 | (v + 64) << 18 (the low bits are zero; plans of this path keep
+// their plane count below 2^18)
 constexpr int KEY_PLANE_BITS = 18;
 constexpr uint32_t KEY_NONE = 0xffffffffu;   // decodes to u = 63, outside every ring region
 
@@ -576,14 +580,13 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             }
             const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
             const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
-            const uint32_t kbits = (uint32_t)c.k0;
 #pragma unroll
             for (int j = 0; j < W; ++j) {
                 int ap = j - mu, bp = j - mv;   // taps that land on residue class j
                 ap += ap < 0 ? W : 0;
                 bp += bp < 0 ? W : 0;
                 ru[t * W + j] = make_float2(es_kernel_fast(c.ou + (float)ap, ihw, bt),
-                                            __uint_as_float(((uint32_t)(lu + ap + 64) << 25) | kbits));
+                                            __uint_as_float((uint32_t)(lu + ap + 64) << 25));
                 rv[t * W + j] = make_float2(es_kernel_fast(c.ov + (float)bp, ihw, bt),
                                             __uint_as_float((uint32_t)(lv + bp + 64) << KEY_PLANE_BITS));
             }
@@ -645,20 +648,20 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         const int grp = ct / G, lid = ct - grp * G;
         const int ta = lid / W, tb = lid - ta * W;
         const bool in_group = grp < NG;
+        // a run starts by assignment (set), so the sums need no clearing
         float2 acc[Ww];
-#pragma unroll
-        for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
-        uint32_t ckey = KEY_NONE;   // cell and first plane the accumulators belong to
+        uint32_t ckey = KEY_NONE;   // cell the accumulators belong to
+        // per bucket (uniform): ring slot of its first plane, and which of its W_w planes lie in the block
+        // (all items of a bucket share their first plane: one w plane per bucket on this path)
+        int s0 = 0;
+        uint32_t vmask = 0u;
         auto flush_acc = [&]() {
             const int cu = (int)(ckey >> 25) - 64, cv = (int)((ckey >> KEY_PLANE_BITS) & 127u) - 64;
-            const int ck = (int)(ckey & ((1u << KEY_PLANE_BITS) - 1u));
             if ((unsigned)cu < (unsigned)E && (unsigned)cv < (unsigned)E) {
                 float2 *cell = ring + cu * HS + cv;
-                const int s0 = ck % R;
 #pragma unroll
                 for (int c = 0; c < Ww; ++c) {
-                    const int k = ck + c;
-                    if (k >= k_lo && k < k_hi) {
+                    if ((vmask >> c) & 1u) {
                         const int sl = s0 + c - (s0 + c >= R ? R : 0);
                         float2 *dst = cell + sl * SLOT;
                         atomicAdd(&dst->x, acc[c].x);
@@ -666,9 +669,6 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                     }
                 }
             }
-#pragma unroll
-            for (int c = 0; c < Ww; ++c) acc[c] = make_float2(0.f, 0.f);
-            ckey = KEY_NONE;
         };
         int prev_kq = -1;
         for (int i = 0;; ++i) {
@@ -683,6 +683,11 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                 flush_planes(max(m.x * g.q, k_lo), ct, GRID_NC);
                 named_sync<BAR_CONS, GRID_NC>();
                 prev_kq = m.x;
+                const int ck = m.x * g.q;
+                s0 = ck % R;
+                vmask = 0u;
+#pragma unroll
+                for (int c = 0; c < Ww; ++c) vmask |= (ck + c >= k_lo && ck + c < k_hi) ? 1u << c : 0u;
             }
             if (in_group) {
                 const float2 *ru = reinterpret_cast<const float2 *>(smem_raw + L.ru[sb]);
@@ -700,6 +705,14 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                         const float4 v = q[c >> 1];
                         acc[c].x = fmaf(wuv, (c & 1) ? v.z : v.x, acc[c].x);
                         acc[c].y = fmaf(wuv, (c & 1) ? v.w : v.y, acc[c].y);
+                    }
+                };
+                auto set = [&](float wuv, const float4 *q) {
+#pragma unroll
+                    for (int c = 0; c < Ww; ++c) {
+                        const float4 v = q[c >> 1];
+                        acc[c].x = wuv * ((c & 1) ? v.z : v.x);
+                        acc[c].y = wuv * ((c & 1) ? v.w : v.y);
                     }
                 };
                 // two records per step (W_w <= 6: both w-tap rows fit in registers); one test covers
@@ -720,13 +733,17 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                         if (k0 != ckey) {
                             flush_acc();
                             ckey = k0;
+                            set(a0.x * b0.x, q0);
+                        } else {
+                            add(a0.x * b0.x, q0);
                         }
-                        add(a0.x * b0.x, q0);
                         if (k1 != ckey) {
                             flush_acc();
                             ckey = k1;
+                            set(a1.x * b1.x, q1);
+                        } else {
+                            add(a1.x * b1.x, q1);
                         }
-                        add(a1.x * b1.x, q1);
                     } else {
                         add(a0.x * b0.x, q0);
                         add(a1.x * b1.x, q1);
@@ -741,11 +758,16 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                     if (k0 != ckey) {
                         flush_acc();
                         ckey = k0;
+                        set(a0.x * b0.x, q0);
+                    } else {
+                        add(a0.x * b0.x, q0);
                     }
-                    add(a0.x * b0.x, q0);
                 }
                 // the sums stay in registers while the next chunk continues this bucket
-                if (m.y || m.z != m.x) flush_acc();
+                if (m.y || m.z != m.x) {
+                    flush_acc();
+                    ckey = KEY_NONE;
+                }
             }
             __threadfence_block();
             pair_arrive<BAR_EMPTY>(sb);

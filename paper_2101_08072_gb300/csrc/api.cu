@@ -389,8 +389,7 @@ static void hessian_host(Ctx &c, const pfb_geom *g, int prec, int64_t nrow, int3
     cudaEvent_t e_out = c.copy_event(2);
     Plan &p = get_plan(c, *g, prec, nrow, nchan, d_uvw, d_freq, d_band, false, st);
     cx_t<T> *vis = (cx_t<T> *)c.scratch("hess_vis", (size_t)nrow * nchan * sizeof(cx_t<T>));
-    op_degrid<T>(c, p, d_x, vis, st);
-    op_grid<T>(c, p, vis, d_w, false, d_y, st, [&](int b) {
+    op_hessian<T>(c, p, d_x, d_w, vis, d_y, st, [&](int b) {
         cudaEvent_t e = c.copy_event(3 + (size_t)b);
         PFB_CUDA(cudaEventRecord(e, st));
         PFB_CUDA(cudaStreamWaitEvent(cs, e, 0));
@@ -569,13 +568,11 @@ int pfb_hessian(pfb_ctx *ctx, const pfb_geom *g, pfb_prec prec, int64_t nrow, in
         Plan &p = get_plan(c, *g, prec, nrow, nchan, uvw, freq, band, false, S(stream));
         const size_t cxs = prec == PFB_F64 ? 16 : 8;
         void *vis = c.scratch("hess_vis", (size_t)nrow * nchan * cxs);
-        if (prec == PFB_F64) {
-            op_degrid<double>(c, p, (const double *)x, (double2 *)vis, S(stream));
-            op_grid<double>(c, p, (const double2 *)vis, (const double *)wgt, false, (double *)y_out, S(stream));
-        } else {
-            op_degrid<float>(c, p, (const float *)x, (float2 *)vis, S(stream));
-            op_grid<float>(c, p, (const float2 *)vis, (const float *)wgt, false, (float *)y_out, S(stream));
-        }
+        if (prec == PFB_F64)
+            op_hessian<double>(c, p, (const double *)x, (const double *)wgt, (double2 *)vis, (double *)y_out,
+                               S(stream));
+        else
+            op_hessian<float>(c, p, (const float *)x, (const float *)wgt, (float2 *)vis, (float *)y_out, S(stream));
     });
 }
 

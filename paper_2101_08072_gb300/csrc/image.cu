@@ -881,8 +881,7 @@ void op_step(Ctx &ctx, const Plan &p, const pfb_params &prm, const T *wgt, const
         check_launch("approx_crop");
     } else {
         cx_t<T> *vis = (cx_t<T> *)ctx.scratch("st_vis", (size_t)p.nrow * p.nchan * sizeof(cx_t<T>));
-        op_degrid<T>(ctx, p, x, vis, st);
-        op_grid<T>(ctx, p, vis, wgt, false, hx, st);
+        op_hessian<T>(ctx, p, x, wgt, vis, hx, st);
     }
     // 2. IR = (I^d - H x_k) / wbar
     {
@@ -1079,8 +1078,7 @@ double op_step_bound(Ctx &ctx, const Plan &p, const T *wgt, const T *psf, const 
     std::vector<double> h(nsc);
     for (int it = 0; it < iters; ++it) {
         PFB_CUDA(cudaMemsetAsync(sc, 0, nsc * sizeof(double), st));
-        op_degrid<T>(ctx, p, z, vis, st);
-        op_grid<T>(ctx, p, vis, wgt, false, hz, st);
+        op_hessian<T>(ctx, p, z, wgt, vis, hz, st);
         // numerator z . H z / wbar (into S_XHX) and the CG right-hand side -H z / wbar with its norms
         k_residual<T><<<band_grid(ctx, npix, nb), 256, 0, st>>>(npix, zero, hz, z, inv_wbar, rhs, sc, bb);
         check_launch("sb_residual");

@@ -413,7 +413,7 @@ template <int W, int Ww, bool REC>
 __global__ void __launch_bounds__(GRID_NT, 2)
 k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items, const int64_t *__restrict__ off,
            CoordSrc src, const float4 *__restrict__ recs, const float2 *__restrict__ rph,
-           const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, BandGeom g,
+           const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, int item_order, BandGeom g,
            int k_lo, int k_hi, float2 *__restrict__ planes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int R = Ww;                  // ring planes (one w bucket per plane)
@@ -514,7 +514,7 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                 q.v = src.rowdf[3 * row + 1];
                 q.w = src.rowdf[3 * row + 2];
             }
-            q.y = unit_vis ? make_float2(1.f, 0.f) : vis[v];
+            q.y = unit_vis ? make_float2(1.f, 0.f) : vis[item_order ? idx : (int64_t)v];
             q.wt = wgt ? wgt[v] : 1.f;
         };
         // record t of buffer sb: per residue class the tap and the packed cell key
@@ -791,6 +791,7 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
                                                       const int64_t *__restrict__ off, CoordSrc src,
                                                       const float4 *__restrict__ recs, const float2 *__restrict__ rph,
                                                       BandGeom g, int k_lo, int k_hi, const float2 *__restrict__ planes,
+                                                      const float *__restrict__ wgt, int item_order,
                                                       float2 *__restrict__ vis) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *reg = reinterpret_cast<float2 *>(smem_raw);
@@ -938,18 +939,25 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
                 ar = fmaf(kw[cw], pr, ar);
                 ai = fmaf(kw[cw], pi, ai);
             }
-            const float vr = ar * cs + ai * sn;
+            float vr = ar * cs + ai * sn;
             float vi = ai * cs - ar * sn;
             if (c.flip) vi = -vi;
+            // item order: the weighted value w_v (R x)_v at the item's position
+            const int64_t o = item_order ? it : (int64_t)v;
+            if (item_order && wgt) {
+                const float wv = wgt[v];
+                vr *= wv;
+                vi *= wv;
+            }
             float2 out;
             if (g.accumulate || c.k0 < k_lo) {
-                out = vis[v];
+                out = vis[o];
                 out.x += vr;
                 out.y += vi;
             } else {
                 out = make_float2(vr, vi);
             }
-            vis[v] = out;
+            vis[o] = out;
         }
         __syncthreads();
     }
@@ -1170,37 +1178,38 @@ static bool grid_res_fit(const Plan &p) { return p.halo; }
 
 template <int W, int Ww>
 static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkItem *work, const Plan &p,
-                              const float2 *vis, const float *wgt, int unit, const BandGeom &g, int k_lo, int k_hi,
-                              float2 *planes) {
+                              const float2 *vis, const float *wgt, int unit, int item_order, const BandGeom &g,
+                              int k_lo, int k_hi, float2 *planes) {
     const size_t smem = (size_t)res_layout(R, W, Ww).total;
     if (p.d_rec) {
         PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         k_grid_res<W, Ww, true><<<nblk, GRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), p.d_rec,
-                                                             p.d_rph, vis, wgt, unit, g, k_lo, k_hi, planes);
+                                                             p.d_rph, vis, wgt, unit, item_order, g, k_lo, k_hi, planes);
     } else {
         PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         k_grid_res<W, Ww, false><<<nblk, GRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), nullptr,
-                                                              nullptr, vis, wgt, unit, g, k_lo, k_hi, planes);
+                                                              nullptr, vis, wgt, unit, item_order, g, k_lo, k_hi, planes);
     }
 }
 
 template <int W, int Ww>
 static void launch_degrid_t(unsigned nblk, int R, cudaStream_t st, const WorkItem *work, const Plan &p,
-                            const BandGeom &g, int k_lo, int k_hi, const float2 *planes, float2 *vis) {
+                            const BandGeom &g, int k_lo, int k_hi, const float2 *planes, const float *wgt,
+                            int item_order, float2 *vis) {
     const int E = TILE + W - 1, ES = E | 1;
     const size_t smem = (size_t)R * E * ES * sizeof(float2);
     if (p.d_rec) {
         PFB_CUDA(cudaFuncSetAttribute(k_degrid_tiles<W, Ww, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         k_degrid_tiles<W, Ww, true><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), p.d_rec, p.d_rph,
-                                                             g, k_lo, k_hi, planes, vis);
+                                                             g, k_lo, k_hi, planes, wgt, item_order, vis);
     } else {
         PFB_CUDA(cudaFuncSetAttribute(k_degrid_tiles<W, Ww, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         k_degrid_tiles<W, Ww, false><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), nullptr, nullptr,
-                                                              g, k_lo, k_hi, planes, vis);
+                                                              g, k_lo, k_hi, planes, wgt, item_order, vis);
     }
 }
 
@@ -1222,8 +1231,10 @@ static int64_t band_nvis(const Plan &p, int b) {
     return nc * p.nrow;
 }
 
+// item_order: vis is in item order and receives w_v (R x)_v, w = item_wgt (halo plans, FP32 tile kernels)
 template <typename T>
-void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st, bool accumulate) {
+static void degrid_impl(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st, bool accumulate,
+                        bool item_order, const T *item_wgt) {
     const size_t cxs = sizeof(cx_t<T>);
     // room for cuFFT work areas is taken from the same budget
     const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
@@ -1271,11 +1282,12 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
                 const int R = p.Ww;
 #define PFB_DEGRID_CALL(WV, WWV)                                                                          \
     launch_degrid_t<WV, WWV>((unsigned)(w1 - w0), R, st, p.d_work + w0, p, g, k_lo, k_hi, (const float2 *)planes, \
-                             (float2 *)vis)
+                             (const float *)item_wgt, item_order ? 1 : 0, (float2 *)vis)
                 PFB_W_SWITCH(p.W, p.wstack, PFB_DEGRID_CALL)
 #undef PFB_DEGRID_CALL
                 check_launch("degrid_tiles");
             } else if (i1 > i0) {
+                PFB_REQUIRE(!item_order, "item-order visibilities need the FP32 tile kernels");
                 KTimer t(ctx, "gather", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
                 k_gather<T><<<grid_blocks(i1 - i0, 256, 64 * ctx.num_sms), 256, 0, st>>>(
                     p.d_items + i0, i1 - i0, p.coords(), g, k_lo, k_hi, planes, vis);
@@ -1286,8 +1298,14 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
 }
 
 template <typename T>
-void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool unit_vis, T *image,
-             cudaStream_t st, const std::function<void(int)> &band_done) {
+void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream_t st, bool accumulate) {
+    degrid_impl<T>(ctx, p, image, vis, st, accumulate, false, nullptr);
+}
+
+// item_order: vis is in item order with the weights applied (wgt is then NULL)
+template <typename T>
+static void grid_impl(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool unit_vis, bool item_order,
+                      T *image, cudaStream_t st, const std::function<void(int)> &band_done) {
     const size_t cxs = sizeof(cx_t<T>);
     const int blk = plane_block(ctx, p, cxs, (size_t)p.Nu * p.Nv * cxs * 2);
     cx_t<T> *planes = (cx_t<T> *)ctx.scratch("planes", (size_t)blk * p.Nu * p.Nv * cxs);
@@ -1332,11 +1350,13 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
                         KTimer tp(ctx, part == 0 ? "grid_dense" : "grid_light", st, 0.0, 0);
 #define PFB_GRID_CALL(WV, WWV)                                                                            \
     launch_grid_res_t<WV, WWV>((unsigned)(a1 - a0), R, st, p.d_work + a0, p, (const float2 *)vis,          \
-                               (const float *)wgt, unit_vis ? 1 : 0, g, k_lo, k_hi, (float2 *)in)
+                               (const float *)wgt, unit_vis ? 1 : 0, item_order ? 1 : 0, g, k_lo, k_hi,     \
+                               (float2 *)in)
                         PFB_W_SWITCH(p.W, p.wstack, PFB_GRID_CALL)
 #undef PFB_GRID_CALL
                     }
                 } else if (w1 > w0) {
+                    PFB_REQUIRE(!item_order, "item-order visibilities need the FP32 tile kernels");
                     k_grid_tiles<T><<<(unsigned)(w1 - w0), 256, smem, st>>>(p.d_work + w0, p.d_items, p.d_off,
                                                                              p.coords(), vis, wgt,
                                                                              unit_vis ? 1 : 0, g, k_lo, k_hi, in);
@@ -1369,6 +1389,24 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
 }
 
 template <typename T>
+void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool unit_vis, T *image,
+             cudaStream_t st, const std::function<void(int)> &band_done) {
+    grid_impl<T>(ctx, p, vis, wgt, unit_vis, false, image, st, band_done);
+}
+
+template <typename T>
+void op_hessian(Ctx &ctx, const Plan &p, const T *x, const T *wgt, cx_t<T> *vis, T *hx, cudaStream_t st,
+                const std::function<void(int)> &band_done) {
+    if (sizeof(T) == 4 && p.halo && p.nitems == p.nrow * (int64_t)p.nchan) {
+        degrid_impl<T>(ctx, p, x, vis, st, false, true, wgt);
+        grid_impl<T>(ctx, p, vis, nullptr, false, true, hx, st, band_done);
+    } else {
+        degrid_impl<T>(ctx, p, x, vis, st, false, false, nullptr);
+        grid_impl<T>(ctx, p, vis, wgt, false, false, hx, st, band_done);
+    }
+}
+
+template <typename T>
 void op_wsum(Ctx &ctx, const Plan &p, const T *wgt, double *d_wsum, cudaStream_t st) {
     PFB_CUDA(cudaMemsetAsync(d_wsum, 0, 32 * sizeof(double), st));
     const int64_t n = p.nrow * p.nchan;
@@ -1383,6 +1421,10 @@ template void op_grid<float>(Ctx &, const Plan &, const float2 *, const float *,
                              const std::function<void(int)> &);
 template void op_grid<double>(Ctx &, const Plan &, const double2 *, const double *, bool, double *, cudaStream_t,
                               const std::function<void(int)> &);
+template void op_hessian<float>(Ctx &, const Plan &, const float *, const float *, float2 *, float *, cudaStream_t,
+                                const std::function<void(int)> &);
+template void op_hessian<double>(Ctx &, const Plan &, const double *, const double *, double2 *, double *,
+                                 cudaStream_t, const std::function<void(int)> &);
 template void op_wsum<float>(Ctx &, const Plan &, const float *, double *, cudaStream_t);
 template void op_wsum<double>(Ctx &, const Plan &, const double *, double *, cudaStream_t);
 

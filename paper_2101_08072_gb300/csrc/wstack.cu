@@ -282,14 +282,13 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 
 // ------------------------------------------------------------------ FP32 gridding by residue classes
 // One CTA per work item: the items of one uv tile, or a chunk of a heavy tile's
-// items.  The plan lists every visibility once, in the tile of its first-tap cell, so
-// the ring of a CTA covers the tile and the W - 1 cells past its far edges that the
-// footprints reach: (TILE + W - 1)^2 cells per plane.  Neighbouring regions overlap,
-// so every region is added to the planes with global vector reductions into cells
-// zeroed before the launch.  Items are processed in chunks of at most res_ch(W)
-// records of one w bucket; chunks run across w planes with a sliding window of W_w
-// ring planes (one plane per bucket) in shared memory, each added to HBM once
-// complete.
+// items.  The plan lists every visibility once, in the tile of its first-tap cell;
+// its footprint reaches the W - 1 cells past the tile's far edges, which belong to the
+// neighbouring tiles.  Sums go straight to the planes in HBM by global vector
+// reductions (one instruction per plane and cell) into cells zeroed before the
+// launch: the tiles a CTA works on stay in L2 meanwhile, and no shared-memory copy of
+// the region is kept (floating-point adds to shared memory would be compare-and-swap
+// loops).  Items are processed in chunks of at most res_ch(W) records of one w bucket.
 //
 // The CTA is warp-specialised.  Four producer warps stage chunk i+1 (coordinates,
 // ES taps, weighted and phase-rotated value) into one of two shared buffers while
@@ -302,31 +301,28 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 // The consumers form groups of W * W threads: thread (a, b) of a group owns the
 // footprint cell whose local indices are congruent to (a, b) mod W (exactly one per
 // visibility), keeps the W_w plane sums of that cell in registers, and adds them to
-// the ring only when its cell changes.  The plan sorts every bucket by first-tap
+// the planes only when its cell changes.  The plan sorts every bucket by first-tap
 // cell, so in the dense tiles a thread stays on one cell for long runs of
-// visibilities; distinct groups can meet on a cell, so the (rare) ring adds are
-// atomic.  Staging does the per-visibility index work once: for every residue class j
-// it stores the ES tap that lands on that class together with a packed cell key (u
-// cell in the u entry, v cell in the v entry), so a scatter step is two 8-byte
-// loads, an OR and a compare, one multiply and 2 W_w FMAs.  All items of a bucket
-// start on the same w plane, so the ring slots of a run's planes are set once per
-// bucket, for all threads alike.
+// visibilities.  Staging does the per-visibility index work once: for every residue
+// class j it stores the ES tap that lands on that class together with a packed cell
+// key (u cell in the u entry, v cell in the v entry), so a scatter step is two
+// 8-byte loads, an OR and a compare, one multiply and 2 W_w FMAs.  All items of a
+// bucket start on the same w plane, so the planes of a run are set once per bucket,
+// for all threads alike.
 //
-// ring region edge: the tile and the W - 1 cells past its far edges that footprints reach
+// cells a CTA's items reach, per axis: the tile and the W - 1 cells past its far edge
 __host__ __device__ constexpr int res_edge(int W) { return TILE + W - 1; }
-// padded ring row: spreads a footprint over the banks
-__host__ __device__ constexpr int res_stride(int W) { return res_edge(W) + 1; }
 constexpr int GRID_NP = 128;        // producer threads (4 warps)
 constexpr int GRID_NC = 256;        // consumer threads (8 warps)
 constexpr int GRID_NT = GRID_NP + GRID_NC;
 // named barriers (0 is __syncthreads)
-constexpr int BAR_FULL = 1, BAR_EMPTY = 3, BAR_CONS = 5;
+constexpr int BAR_FULL = 1, BAR_EMPTY = 3;
 // packed cell key: (u + 64) << 25 | (v + 64) << 18 (the low bits are zero; plans of this path keep
 // their plane count below 2^18)
 constexpr int KEY_PLANE_BITS = 18;
-constexpr uint32_t KEY_NONE = 0xffffffffu;   // decodes to u = 63, outside every ring region
+constexpr uint32_t KEY_NONE = 0xffffffffu;   // decodes to u = 63, outside every reach
 
-// records per chunk: two buffers and the ring fit twice in an SM's shared memory
+// records per chunk
 __host__ __device__ constexpr int res_ch(int W) { return W <= 7 ? 128 : 96; }
 // w-tap row stride in float2: even, so a record's row starts on 16 bytes
 __host__ __device__ constexpr int res_ws(int Ww) { return (Ww + 1) & ~1; }
@@ -335,10 +331,10 @@ struct ResSmem {
     int ru[2], rv[2], wy[2], meta, total;
 };
 
-__host__ __device__ inline ResSmem res_layout(int R, int W, int Ww) {
+__host__ __device__ inline ResSmem res_layout(int W, int Ww) {
     ResSmem L;
     const int ch = res_ch(W);
-    int o = R * res_edge(W) * res_stride(W) * (int)sizeof(float2);
+    int o = 0;
     for (int s = 0; s < 2; ++s) {
         L.ru[s] = o; o += ch * W * (int)sizeof(float2);
         L.rv[s] = o; o += ch * W * (int)sizeof(float2);
@@ -416,46 +412,18 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
            const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, int item_order, BandGeom g,
            int k_lo, int k_hi, float2 *__restrict__ planes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int R = Ww;                  // ring planes (one w bucket per plane)
-    constexpr int E = res_edge(W), HS = res_stride(W);
-    constexpr int SLOT = E * HS;
+    constexpr int E = res_edge(W);
     constexpr int WS = res_ws(Ww);
     constexpr int CH = res_ch(W);
     constexpr int G = W * W;         // consumer threads of a group (one per residue class)
     constexpr int NG = GRID_NC / G;  // consumer groups
     constexpr int RPG = CH / NG;     // records of one group in a chunk
-    const ResSmem L = res_layout(R, W, Ww);
-    float2 *ring = reinterpret_cast<float2 *>(smem_raw);
+    const ResSmem L = res_layout(W, Ww);
     int4 *meta = reinterpret_cast<int4 *>(smem_raw + L.meta);
     const WorkItem wi = work[blockIdx.x];
     if (wi.end <= wi.begin) return;
     const int tu = wi.tile / g.ntv, tv = wi.tile - tu * g.ntv;
     const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
-    for (int e = threadIdx.x; e < R * SLOT; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
-
-    // add planes [next, upto) of the ring's region to HBM (cells past the grid's edge wrap around) and
-    // clear their slots
-    int next = k_lo;
-    auto flush_planes = [&](int upto, int tid, int nthr) {
-        upto = min(upto, k_hi);
-        for (int k = next; k < upto; ++k) {
-            float2 *slot = ring + (k % R) * SLOT;
-            float2 *dst = planes + (int64_t)(k - k_lo) * plane_sz;
-            for (int e2 = tid; e2 < E * E; e2 += nthr) {
-                const int r = e2 / E, cc = e2 - r * E;
-                const float2 val = slot[r * HS + cc];
-                if (val.x != 0.f || val.y != 0.f) {
-                    int gu = tu * TILE + r, gv = tv * TILE + cc;
-                    gu -= gu >= g.Nu ? g.Nu : 0;
-                    gv -= gv >= g.Nv ? g.Nv : 0;
-                    atomicAdd(dst + (int64_t)gu * g.Nv + gv, val);
-                    slot[r * HS + cc] = make_float2(0.f, 0.f);
-                }
-            }
-        }
-        if (upto > next) next = upto;
-    };
-    __syncthreads();
 
     if (threadIdx.x < GRID_NP) {
         // ================================================================ producers
@@ -651,23 +619,21 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
         // a run starts by assignment (set), so the sums need no clearing
         float2 acc[Ww];
         uint32_t ckey = KEY_NONE;   // cell the accumulators belong to
-        // per bucket (uniform): ring slot of its first plane, and which of its W_w planes lie in the block
-        // (all items of a bucket share their first plane: one w plane per bucket on this path)
-        int s0 = 0;
+        // per bucket (uniform): offset of the bucket's first plane in the plane block (negative when the
+        // block starts later), and which of its W_w planes lie in the block (all items of a bucket share
+        // their first plane: one w plane per bucket on this path)
+        int64_t poff = 0;
         uint32_t vmask = 0u;
         auto flush_acc = [&]() {
             const int cu = (int)(ckey >> 25) - 64, cv = (int)((ckey >> KEY_PLANE_BITS) & 127u) - 64;
             if ((unsigned)cu < (unsigned)E && (unsigned)cv < (unsigned)E) {
-                float2 *cell = ring + cu * HS + cv;
+                int gu = tu * TILE + cu, gv = tv * TILE + cv;
+                gu -= gu >= g.Nu ? g.Nu : 0;
+                gv -= gv >= g.Nv ? g.Nv : 0;
+                const int64_t cell = poff + (int64_t)gu * g.Nv + gv;
 #pragma unroll
-                for (int c = 0; c < Ww; ++c) {
-                    if ((vmask >> c) & 1u) {
-                        const int sl = s0 + c - (s0 + c >= R ? R : 0);
-                        float2 *dst = cell + sl * SLOT;
-                        atomicAdd(&dst->x, acc[c].x);
-                        atomicAdd(&dst->y, acc[c].y);
-                    }
-                }
+                for (int c = 0; c < Ww; ++c)
+                    if ((vmask >> c) & 1u) atomicAdd(planes + cell + c * plane_sz, acc[c]);
             }
         };
         int prev_kq = -1;
@@ -677,14 +643,9 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             const int4 m = meta[2 * sb];        // bucket, last chunk, bucket of the next chunk
             const int4 mc = meta[2 * sb + 1];   // part length, items of the bucket, chunk in the bucket
             if (m.x != prev_kq) {
-                // planes below this bucket's first plane are complete (the sums of the previous
-                // bucket were added to the ring at the end of its last chunk)
-                named_sync<BAR_CONS, GRID_NC>();
-                flush_planes(max(m.x * g.q, k_lo), ct, GRID_NC);
-                named_sync<BAR_CONS, GRID_NC>();
                 prev_kq = m.x;
                 const int ck = m.x * g.q;
-                s0 = ck % R;
+                poff = (int64_t)(ck - k_lo) * plane_sz;
                 vmask = 0u;
 #pragma unroll
                 for (int c = 0; c < Ww; ++c) vmask |= (ck + c >= k_lo && ck + c < k_hi) ? 1u << c : 0u;
@@ -773,9 +734,6 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             pair_arrive<BAR_EMPTY>(sb);
             if (m.y) break;
         }
-        // remaining planes: those the last bucket touched
-        named_sync<BAR_CONS, GRID_NC>();
-        flush_planes(min(k_hi, next + R), ct, GRID_NC);
     }
 }
 
@@ -1172,15 +1130,15 @@ static bool degrid_tiles_fit(const Plan &p) {
 // FP32 plans whose tile kernels fit: the plan lists each visibility once, in its home tile, and the
 // gridding kernel adds the tile's region with the footprints' far edges (k_grid_res)
 bool halo_fits(const Plan &p) {
-    return fast_path_f32(p) && degrid_tiles_fit(p) && (size_t)res_layout(p.Ww, p.W, p.Ww).total <= 227 * 1024;
+    return fast_path_f32(p) && degrid_tiles_fit(p) && (size_t)res_layout(p.W, p.Ww).total <= 227 * 1024;
 }
 static bool grid_res_fit(const Plan &p) { return p.halo; }
 
 template <int W, int Ww>
-static void launch_grid_res_t(unsigned nblk, int R, cudaStream_t st, const WorkItem *work, const Plan &p,
+static void launch_grid_res_t(unsigned nblk, cudaStream_t st, const WorkItem *work, const Plan &p,
                               const float2 *vis, const float *wgt, int unit, int item_order, const BandGeom &g,
                               int k_lo, int k_hi, float2 *planes) {
-    const size_t smem = (size_t)res_layout(R, W, Ww).total;
+    const size_t smem = (size_t)res_layout(W, Ww).total;
     if (p.d_rec) {
         PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
@@ -1341,7 +1299,6 @@ static void grid_impl(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt,
                 const double wb = wgt ? (double)sizeof(T) : 0.0;
                 KTimer t(ctx, "grid_tiles", st, 4.0 * nit + nvb * (vb + wb) + nk * plane_bytes);
                 if (sizeof(T) == 4 && grid_res_fit(p)) {
-                    const int R = p.Ww;
                     // dense (chunked) tiles first, then the owned light tiles, as two timed launches
                     const int64_t wh = p.work_heavy_end[b];
                     for (int part = 0; part < 2; ++part) {
@@ -1349,7 +1306,7 @@ static void grid_impl(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt,
                         if (a1 <= a0) continue;
                         KTimer tp(ctx, part == 0 ? "grid_dense" : "grid_light", st, 0.0, 0);
 #define PFB_GRID_CALL(WV, WWV)                                                                            \
-    launch_grid_res_t<WV, WWV>((unsigned)(a1 - a0), R, st, p.d_work + a0, p, (const float2 *)vis,          \
+    launch_grid_res_t<WV, WWV>((unsigned)(a1 - a0), st, p.d_work + a0, p, (const float2 *)vis,             \
                                (const float *)wgt, unit_vis ? 1 : 0, item_order ? 1 : 0, g, k_lo, k_hi,     \
                                (float2 *)in)
                         PFB_W_SWITCH(p.W, p.wstack, PFB_GRID_CALL)

@@ -548,15 +548,17 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             }
             const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
             const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
+            // tap i (cell lu + i) lands on residue class (mu + i) mod W; taps in natural order keep the
+            // offsets compile-time constants, and the cell keys step by one cell per tap
+            const uint32_t ku0 = (uint32_t)(lu + 64) << 25, kv0 = (uint32_t)(lv + 64) << KEY_PLANE_BITS;
+            float2 *rut = ru + t * W, *rvt = rv + t * W;
 #pragma unroll
-            for (int j = 0; j < W; ++j) {
-                int ap = j - mu, bp = j - mv;   // taps that land on residue class j
-                ap += ap < 0 ? W : 0;
-                bp += bp < 0 ? W : 0;
-                ru[t * W + j] = make_float2(es_kernel_fast(c.ou + (float)ap, ihw, bt),
-                                            __uint_as_float((uint32_t)(lu + ap + 64) << 25));
-                rv[t * W + j] = make_float2(es_kernel_fast(c.ov + (float)bp, ihw, bt),
-                                            __uint_as_float((uint32_t)(lv + bp + 64) << KEY_PLANE_BITS));
+            for (int i = 0; i < W; ++i) {
+                const int ju = mu + i - (mu + i >= W ? W : 0), jv = mv + i - (mv + i >= W ? W : 0);
+                rut[ju] = make_float2(es_kernel_fast(c.ou + (float)i, ihw, bt),
+                                      __uint_as_float(ku0 + ((uint32_t)i << 25)));
+                rvt[jv] = make_float2(es_kernel_fast(c.ov + (float)i, ihw, bt),
+                                      __uint_as_float(kv0 + ((uint32_t)i << KEY_PLANE_BITS)));
             }
             if (Ww > 1) {
 #pragma unroll

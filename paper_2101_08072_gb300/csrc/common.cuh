@@ -98,6 +98,17 @@ __device__ __forceinline__ float es_kernel_fast(float z, float inv_halfw, float 
     float t = 1.0f - x * x;
     return t > 0.0f ? __expf(beta * (t * rsqrtf(t) - 1.0f)) : 0.0f;
 }
+// The same kernel from its scaled argument x = 2z/W and b2 = beta log2(e), for taps whose arguments step by
+// a constant: exp(y) is evaluated as 2^(y log2 e) by the hardware approximation ex2.approx (relative error
+// about 2^-22), sqrt(t) as t * rsqrt(t).
+__device__ __forceinline__ float es_kernel_x(float x, float b2) {
+    const float t = fmaf(-x, x, 1.0f);
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fmaf(b2, t * rsqrtf(t), -b2)));
+    return t > 0.0f ? e : 0.0f;
+}
+// beta log2(e) for es_kernel_x
+__host__ __device__ inline float es_b2(double beta) { return (float)(beta * 1.4426950408889634); }
 __device__ __forceinline__ double es_kernel(double z, double inv_halfw, double beta) {
     double x = z * inv_halfw;
     double t = 1.0 - x * x;

@@ -547,23 +547,25 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                 yr = r0;
             }
             const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
-            const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
+            const float ihw = (float)g.inv_halfw, b2 = es_b2(g.beta);
             // tap i (cell lu + i) lands on residue class (mu + i) mod W; taps in natural order keep the
             // offsets compile-time constants, and the cell keys step by one cell per tap
             const uint32_t ku0 = (uint32_t)(lu + 64) << 25, kv0 = (uint32_t)(lv + 64) << KEY_PLANE_BITS;
+            const float xu = c.ou * ihw, xv = c.ov * ihw;
             float2 *rut = ru + t * W, *rvt = rv + t * W;
 #pragma unroll
             for (int i = 0; i < W; ++i) {
                 const int ju = mu + i - (mu + i >= W ? W : 0), jv = mv + i - (mv + i >= W ? W : 0);
-                rut[ju] = make_float2(es_kernel_fast(c.ou + (float)i, ihw, bt),
+                rut[ju] = make_float2(es_kernel_x(fmaf((float)i, ihw, xu), b2),
                                       __uint_as_float(ku0 + ((uint32_t)i << 25)));
-                rvt[jv] = make_float2(es_kernel_fast(c.ov + (float)i, ihw, bt),
+                rvt[jv] = make_float2(es_kernel_x(fmaf((float)i, ihw, xv), b2),
                                       __uint_as_float(kv0 + ((uint32_t)i << KEY_PLANE_BITS)));
             }
             if (Ww > 1) {
+                const float xw = c.ow * ihw;
 #pragma unroll
                 for (int i = 0; i < Ww; ++i) {
-                    const float kw = es_kernel_fast(c.ow + (float)i, ihw, bt);
+                    const float kw = es_kernel_x(fmaf((float)i, ihw, xw), b2);
                     rwy[t * WS + i] = make_float2(kw * yr, kw * yi);
                 }
             } else {
@@ -863,16 +865,17 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
                 if (g.tc != 0.0 || g.facet) sincos_turns(c.ph, &sn, &cs);
             }
             if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) continue;
-            const float ihw = (float)g.inv_halfw, bt = (float)g.beta;
+            const float ihw = (float)g.inv_halfw, b2 = es_b2(g.beta);
+            const float xu = c.ou * ihw, xv = c.ov * ihw, xw = c.ow * ihw;
             float ku[W], kv[W], kw[Ww];
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                ku[i] = es_kernel_fast(c.ou + (float)i, ihw, bt);
-                kv[i] = es_kernel_fast(c.ov + (float)i, ihw, bt);
+                ku[i] = es_kernel_x(fmaf((float)i, ihw, xu), b2);
+                kv[i] = es_kernel_x(fmaf((float)i, ihw, xv), b2);
             }
             if (Ww > 1) {
 #pragma unroll
-                for (int i = 0; i < Ww; ++i) kw[i] = es_kernel_fast(c.ow + (float)i, ihw, bt);
+                for (int i = 0; i < Ww; ++i) kw[i] = es_kernel_x(fmaf((float)i, ihw, xw), b2);
             } else {
                 kw[0] = 1.f;
             }

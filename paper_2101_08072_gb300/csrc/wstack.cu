@@ -485,6 +485,8 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             q.y = unit_vis ? make_float2(1.f, 0.f) : vis[item_order ? idx : (int64_t)v];
             q.wt = wgt ? wgt[v] : 1.f;
         };
+        // kernel constants in FP32, converted once (FP64 arithmetic is slow on this GPU)
+        const float ihw = (float)g.inv_halfw, b2 = es_b2(g.beta);
         // record t of buffer sb: per residue class the tap and the packed cell key
         auto stage = [&](const RawRec &q, int t, int sb) {
             float2 *ru = reinterpret_cast<float2 *>(smem_raw + L.ru[sb]);
@@ -547,7 +549,6 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                 yr = r0;
             }
             const int mu = (lu + 2 * TILE) % W, mv = (lv + 2 * TILE) % W;
-            const float ihw = (float)g.inv_halfw, b2 = es_b2(g.beta);
             // tap i (cell lu + i) lands on residue class (mu + i) mod W; taps in natural order keep the
             // offsets compile-time constants, and the cell keys step by one cell per tap
             const uint32_t ku0 = (uint32_t)(lu + 64) << 25, kv0 = (uint32_t)(lv + 64) << KEY_PLANE_BITS;
@@ -780,6 +781,8 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
         if (off[kbase + mid] <= wi.end - 1) lo = mid; else hi = mid - 1;
     }
     const int kq_last = lo;
+    // kernel constants in FP32, converted once (FP64 arithmetic is slow on this GPU)
+    const float ihw = (float)g.inv_halfw, b2 = es_b2(g.beta);
     __syncthreads();
     for (int kq = kq_first; kq <= kq_last; ++kq) {
         const int64_t s = max(off[kbase + kq], (int64_t)wi.begin), e = min(off[kbase + kq + 1], (int64_t)wi.end);
@@ -865,7 +868,6 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
                 if (g.tc != 0.0 || g.facet) sincos_turns(c.ph, &sn, &cs);
             }
             if (c.k0 >= k_hi || c.k0 + Ww <= k_lo) continue;
-            const float ihw = (float)g.inv_halfw, b2 = es_b2(g.beta);
             const float xu = c.ou * ihw, xv = c.ov * ihw, xw = c.ow * ihw;
             float ku[W], kv[W], kw[Ww];
 #pragma unroll
@@ -880,11 +882,13 @@ __global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restr
                 kw[0] = 1.f;
             }
             float ar = 0.f, ai = 0.f;
+            const int s0 = c.k0 % R;
 #pragma unroll
             for (int cw = 0; cw < Ww; ++cw) {
                 const int k = c.k0 + cw;
                 if (k < k_lo || k >= k_hi) continue;
-                const float2 *pl = reg + (k % R) * reg_sz + lu * ES + lv;
+                const int sl = s0 + cw - (s0 + cw >= R ? R : 0);
+                const float2 *pl = reg + sl * reg_sz + lu * ES + lv;
                 float pr = 0.f, pi = 0.f;
 #pragma unroll
                 for (int a = 0; a < W; ++a) {

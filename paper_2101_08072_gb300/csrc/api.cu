@@ -134,6 +134,8 @@ void Ctx::free_plan(Plan &p) {
     fr(p.d_tp, (size_t)p.nx * p.ny * sizeof(double));
     fr(p.d_corr, (size_t)p.nx * p.ny * (p.prec == PFB_F64 ? 8 : 4));
     if (p.d_work) fr(p.d_work, std::max<size_t>((size_t)p.work_begin.back(), 1) * sizeof(WorkItem));
+    if (p.d_work_dg) fr(p.d_work_dg, (size_t)p.work_dg_begin.back() * sizeof(WorkItem));
+    p.d_work_dg = nullptr;
     if (p.d_heavy) fr(p.d_heavy, (size_t)p.heavy_begin.back() * sizeof(int));
     fr(p.d_rec, (size_t)p.nitems * sizeof(float4));
     fr(p.d_rph, (size_t)p.nitems * sizeof(float2));

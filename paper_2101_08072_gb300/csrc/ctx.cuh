@@ -46,6 +46,8 @@ struct Plan {
     std::vector<int> band_h;
     std::vector<int64_t> band_items_begin, band_items_end;
     std::vector<int64_t> work_begin; // per band offset into d_work (size nband + 1)
+    // halo plans: degridding's own work list, in coarser chunks (each chunk stages its tile's region again)
+    std::vector<int64_t> work_dg_begin;
     std::vector<int64_t> work_heavy_end; // per band: end of the heavy-tile chunks (they come first)
     // per band offset into d_heavy (size nband + 1): the tiles that reductions fill (heavy tiles; on halo
     // plans every tile some footprint reaches), then, from empty_begin[b], the tiles nothing writes
@@ -65,6 +67,7 @@ struct Plan {
     double *d_tp = nullptr;   // n - 1 - tc per pixel (FP32 plans: the same 8 bytes as a float pair hi, lo)
     void *d_corr = nullptr;   // 1 / (n psi_u psi_v psi_w) per pixel, working precision
     WorkItem *d_work = nullptr;
+    WorkItem *d_work_dg = nullptr;
     int *d_heavy = nullptr;
     // FP32 tile kernels: per-item geometry records in item order (optional)
     float4 *d_rec = nullptr;

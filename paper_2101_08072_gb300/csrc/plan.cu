@@ -598,9 +598,10 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
     std::vector<int64_t> tb(ntb + 1);
     PFB_CUDA(cudaMemcpyAsync(tb.data(), d_tb, (ntb + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PFB_CUDA(cudaStreamSynchronize(st));
-    std::vector<WorkItem> work;
+    std::vector<WorkItem> work, work_dg;
     std::vector<int> heavy;
     p.work_begin.assign(p.nband + 1, 0);
+    p.work_dg_begin.assign(p.nband + 1, 0);
     p.work_heavy_end.assign(p.nband, 0);
     p.heavy_begin.assign(p.nband + 1, 0);
     p.empty_begin.assign(p.nband, 0);
@@ -610,7 +611,13 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
         const int64_t b0 = tb[b * ntiles], b1 = tb[(b + 1) * ntiles];
         p.band_items_begin[b] = b0;
         p.band_items_end[b] = b1;
-        const int64_t chunk = std::max<int64_t>(8192, (b1 - b0 + 16LL * ctx.num_sms - 1) / (16LL * ctx.num_sms));
+        // tiles above `chunk` items are split into chunks of that many (heavy tiles); the gridding kernel of
+        // halo plans balances best with finer chunks, the degridding kernel (which stages a tile's region per
+        // chunk) with coarser ones (measured on the MeerKAT-like Hessian)
+        auto chunk_of = [&](int64_t lo, int64_t per_sm) {
+            return std::max<int64_t>(lo, (b1 - b0 + per_sm * ctx.num_sms - 1) / (per_sm * ctx.num_sms));
+        };
+        const int64_t chunk = p.halo ? chunk_of(4096, 32) : chunk_of(8192, 16);
         p.work_begin[b] = (int64_t)work.size();
         p.heavy_begin[b] = (int64_t)heavy.size();
         const int64_t *tbb = tb.data() + b * ntiles;
@@ -649,8 +656,33 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
         std::stable_sort(work.begin() + l0, work.end(), [](const WorkItem &x, const WorkItem &y) {
             return x.end - x.begin > y.end - y.begin;
         });
+        // degridding's list on halo plans: heavy chunks, then whole tiles largest first
+        p.work_dg_begin[b] = (int64_t)work_dg.size();
+        if (p.halo) {
+            const int64_t cdg = chunk_of(16384, 8);
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t s = tbb[t], e = tbb[t + 1];
+                if (e - s > cdg)
+                    for (int64_t c = s; c < e; c += cdg) work_dg.push_back({(int)t, 1, c, std::min(e, c + cdg)});
+            }
+            const size_t d0 = work_dg.size();
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t s = tbb[t], e = tbb[t + 1];
+                if (e > s && e - s <= cdg) work_dg.push_back({(int)t, 1, s, e});
+            }
+            std::stable_sort(work_dg.begin() + d0, work_dg.end(), [](const WorkItem &x, const WorkItem &y) {
+                return x.end - x.begin > y.end - y.begin;
+            });
+        }
     }
     p.work_begin[p.nband] = (int64_t)work.size();
+    p.work_dg_begin[p.nband] = (int64_t)work_dg.size();
+    if (!work_dg.empty()) {
+        p.d_work_dg = (WorkItem *)ctx.dalloc(work_dg.size() * sizeof(WorkItem));
+        p.bytes += work_dg.size() * sizeof(WorkItem);
+        PFB_CUDA(cudaMemcpyAsync(p.d_work_dg, work_dg.data(), work_dg.size() * sizeof(WorkItem),
+                                 cudaMemcpyHostToDevice, st));
+    }
     p.heavy_begin[p.nband] = (int64_t)heavy.size();
     p.d_work = (WorkItem *)ctx.dalloc(std::max<size_t>(work.size(), 1) * sizeof(WorkItem));
     p.bytes += work.size() * sizeof(WorkItem);

@@ -1245,10 +1245,12 @@ static void degrid_impl(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, c
             }
             if (i1 > i0 && sizeof(T) == 4 && degrid_tiles_fit(p)) {
                 KTimer t(ctx, "degrid_tiles", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
-                const int64_t w0 = p.work_begin[b], w1 = p.work_begin[b + 1];
+                const WorkItem *wl = p.d_work_dg ? p.d_work_dg : p.d_work;
+                const std::vector<int64_t> &wb = p.d_work_dg ? p.work_dg_begin : p.work_begin;
+                const int64_t w0 = wb[b], w1 = wb[b + 1];
                 const int R = p.Ww;
 #define PFB_DEGRID_CALL(WV, WWV)                                                                          \
-    launch_degrid_t<WV, WWV>((unsigned)(w1 - w0), R, st, p.d_work + w0, p, g, k_lo, k_hi, (const float2 *)planes, \
+    launch_degrid_t<WV, WWV>((unsigned)(w1 - w0), R, st, wl + w0, p, g, k_lo, k_hi, (const float2 *)planes,   \
                              (const float *)item_wgt, item_order ? 1 : 0, (float2 *)vis)
                 PFB_W_SWITCH(p.W, p.wstack, PFB_DEGRID_CALL)
 #undef PFB_DEGRID_CALL

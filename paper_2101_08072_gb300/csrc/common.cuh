@@ -100,12 +100,14 @@ __device__ __forceinline__ float es_kernel_fast(float z, float inv_halfw, float 
 }
 // The same kernel from its scaled argument x = 2z/W and b2 = beta log2(e), for taps whose arguments step by
 // a constant: exp(y) is evaluated as 2^(y log2 e) by the hardware approximation ex2.approx (relative error
-// about 2^-22), sqrt(t) as t * rsqrt(t).
+// about 2^-22), sqrt(t) by sqrt.approx.  The taps of a visibility lie in -1 <= x < 1; t is clamped at 0, so
+// at x = -1 exactly (a first tap at -W/2) the tap is exp(-beta), about 1e-6 of the peak, instead of 0.
 __device__ __forceinline__ float es_kernel_x(float x, float b2) {
-    const float t = fmaf(-x, x, 1.0f);
-    float e;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fmaf(b2, t * rsqrtf(t), -b2)));
-    return t > 0.0f ? e : 0.0f;
+    const float t = fmaxf(fmaf(-x, x, 1.0f), 0.0f);
+    float r, e;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fmaf(b2, r, -b2)));
+    return e;
 }
 // beta log2(e) for es_kernel_x
 __host__ __device__ inline float es_b2(double beta) { return (float)(beta * 1.4426950408889634); }

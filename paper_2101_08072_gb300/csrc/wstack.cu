@@ -564,11 +564,15 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
             }
             if (Ww > 1) {
                 const float xw = c.ow * ihw;
+                float kw[Ww];
 #pragma unroll
-                for (int i = 0; i < Ww; ++i) {
-                    const float kw = es_kernel_x(fmaf((float)i, ihw, xw), b2);
-                    rwy[t * WS + i] = make_float2(kw * yr, kw * yi);
-                }
+                for (int i = 0; i < Ww; ++i) kw[i] = es_kernel_x(fmaf((float)i, ihw, xw), b2);
+                // the row starts on 16 bytes (WS even): pairs of taps as 16-byte stores
+                float4 *w4 = reinterpret_cast<float4 *>(rwy + t * WS);
+#pragma unroll
+                for (int i = 0; i + 1 < Ww; i += 2)
+                    w4[i / 2] = make_float4(kw[i] * yr, kw[i] * yi, kw[i + 1] * yr, kw[i + 1] * yi);
+                if (Ww & 1) rwy[t * WS + Ww - 1] = make_float2(kw[Ww - 1] * yr, kw[Ww - 1] * yi);
             } else {
                 rwy[t * WS] = make_float2(yr, yi);
             }

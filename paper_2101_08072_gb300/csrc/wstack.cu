@@ -406,7 +406,7 @@ __global__ void k_item_records(const uint32_t *__restrict__ items, int64_t i0, i
 }
 
 template <int W, int Ww, bool REC>
-__global__ void __launch_bounds__(GRID_NT, 2)
+__global__ void __launch_bounds__(GRID_NT, 3)
 k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items, const int64_t *__restrict__ off,
            CoordSrc src, const float4 *__restrict__ recs, const float2 *__restrict__ rph,
            const float2 *__restrict__ vis, const float *__restrict__ wgt, int unit_vis, int item_order, BandGeom g,
@@ -685,40 +685,9 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
                         acc[c].y = wuv * ((c & 1) ? v.w : v.y);
                     }
                 };
-                // two records per step (W_w <= 6: both w-tap rows fit in registers); one test covers
-                // both run breaks, which are rare in dense tiles
+                // one record per step: with 56 registers per thread three CTAs fit an SM, which hides the
+                // loads' latency better than two records per step at two CTAs
                 int n = cnt;
-                constexpr int PAIR = Ww <= 6 ? 2 : 1 << 30;
-                for (; n >= PAIR; n -= 2, pa += 2 * W, pb += 2 * W, pw += 2 * NQ) {
-                    const float2 a0 = pa[0], b0 = pb[0], a1 = pa[W], b1 = pb[W];
-                    float4 q0[NQ], q1[NQ];
-#pragma unroll
-                    for (int c2 = 0; c2 < NQ; ++c2) {
-                        q0[c2] = pw[c2];
-                        q1[c2] = pw[NQ + c2];
-                    }
-                    const uint32_t k0 = __float_as_uint(a0.y) | __float_as_uint(b0.y);
-                    const uint32_t k1 = __float_as_uint(a1.y) | __float_as_uint(b1.y);
-                    if (((k0 ^ ckey) | (k1 ^ ckey)) != 0u) {
-                        if (k0 != ckey) {
-                            flush_acc();
-                            ckey = k0;
-                            set(a0.x * b0.x, q0);
-                        } else {
-                            add(a0.x * b0.x, q0);
-                        }
-                        if (k1 != ckey) {
-                            flush_acc();
-                            ckey = k1;
-                            set(a1.x * b1.x, q1);
-                        } else {
-                            add(a1.x * b1.x, q1);
-                        }
-                    } else {
-                        add(a0.x * b0.x, q0);
-                        add(a1.x * b1.x, q1);
-                    }
-                }
                 for (; n > 0; --n, pa += W, pb += W, pw += NQ) {
                     const float2 a0 = pa[0], b0 = pb[0];
                     float4 q0[NQ];

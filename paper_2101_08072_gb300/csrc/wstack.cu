@@ -290,13 +290,14 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 // the region is kept (floating-point adds to shared memory would be compare-and-swap
 // loops).  Items are processed in chunks of at most res_ch(W) records of one w bucket.
 //
-// The CTA is warp-specialised.  Four producer warps stage chunk i+1 (coordinates,
-// ES taps, weighted and phase-rotated value) into one of two shared buffers while
-// eight consumer warps scatter chunk i from the other; named barriers hand each
-// buffer back and forth (FULL: producers -> consumers, EMPTY: consumers -> producers).
-// The producers keep their global loads two chunks ahead: item codes of chunk i+2 and
-// raw inputs (uvw, visibility, weight) of chunk i+1 are in flight while chunk i is
-// staged.
+// The CTA is warp-specialised.  Three producer warps stage chunk i+1 (one record per
+// thread: coordinates, ES taps, weighted and phase-rotated value) into one of two
+// shared buffers while nine consumer warps scatter chunk i from the other; named
+// barriers hand each buffer back and forth (FULL: producers -> consumers, EMPTY:
+// consumers -> producers).  The producers keep their global loads two chunks ahead:
+// item codes of chunk i+2 and raw inputs (record, visibility, weight) of chunk i+1 are
+// in flight while chunk i is staged.  With 56 registers per thread three CTAs share
+// an SM.
 //
 // The consumers form groups of W * W threads: thread (a, b) of a group owns the
 // footprint cell whose local indices are congruent to (a, b) mod W (exactly one per
@@ -312,8 +313,8 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const WorkItem *__restrict__
 //
 // cells a CTA's items reach, per axis: the tile and the W - 1 cells past its far edge
 __host__ __device__ constexpr int res_edge(int W) { return TILE + W - 1; }
-constexpr int GRID_NP = 128;        // producer threads (4 warps)
-constexpr int GRID_NC = 256;        // consumer threads (8 warps)
+constexpr int GRID_NP = 96;         // producer threads (3 warps)
+constexpr int GRID_NC = 288;        // consumer threads (9 warps: 8 groups of 36 at W = 6)
 constexpr int GRID_NT = GRID_NP + GRID_NC;
 // named barriers (0 is __syncthreads)
 constexpr int BAR_FULL = 1, BAR_EMPTY = 3;
@@ -322,8 +323,8 @@ constexpr int BAR_FULL = 1, BAR_EMPTY = 3;
 constexpr int KEY_PLANE_BITS = 18;
 constexpr uint32_t KEY_NONE = 0xffffffffu;   // decodes to u = 63, outside every reach
 
-// records per chunk
-__host__ __device__ constexpr int res_ch(int W) { return W <= 7 ? 128 : 96; }
+// records per chunk: one per producer thread
+__host__ __device__ constexpr int res_ch(int W) { return GRID_NP; }
 // w-tap row stride in float2: even, so a record's row starts on 16 bytes
 __host__ __device__ constexpr int res_ws(int Ww) { return (Ww + 1) & ~1; }
 

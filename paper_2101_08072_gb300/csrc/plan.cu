@@ -617,7 +617,7 @@ static void build_plan(Ctx &ctx, Plan &p, const double *uvw, cudaStream_t st) {
         auto chunk_of = [&](int64_t lo, int64_t per_sm) {
             return std::max<int64_t>(lo, (b1 - b0 + per_sm * ctx.num_sms - 1) / (per_sm * ctx.num_sms));
         };
-        const int64_t chunk = p.halo ? chunk_of(4096, 32) : chunk_of(8192, 16);
+        const int64_t chunk = p.halo ? chunk_of(2048, 64) : chunk_of(8192, 16);
         p.work_begin[b] = (int64_t)work.size();
         p.heavy_begin[b] = (int64_t)heavy.size();
         const int64_t *tbb = tb.data() + b * ntiles;

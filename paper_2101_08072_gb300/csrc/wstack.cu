@@ -1220,7 +1220,15 @@ static void degrid_impl(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, c
             }
             }
             if (i1 > i0 && sizeof(T) == 4 && degrid_tiles_fit(p)) {
-                KTimer t(ctx, "degrid_tiles", st, nk * plane_bytes + 4.0 * (i1 - i0) + nvb * cxs);
+                // algorithmic bytes: halo plans read the reached tiles of the block's planes once, and per
+                // item its code, record and rotor (when kept), output value and (item order) weight; other
+                // plans count the whole planes
+                const double nit = (double)(i1 - i0);
+                const double dg_bytes =
+                    p.halo ? (double)(p.empty_begin[b] - p.heavy_begin[b]) * nk * TILE * TILE * cxs +
+                                 nit * (4.0 + (p.d_rec ? 24.0 : 0.0) + cxs + (item_order && item_wgt ? 4.0 : 0.0))
+                           : nk * plane_bytes + 4.0 * nit + nvb * cxs;
+                KTimer t(ctx, "degrid_tiles", st, dg_bytes);
                 const WorkItem *wl = p.d_work_dg ? p.d_work_dg : p.d_work;
                 const std::vector<int64_t> &wb = p.d_work_dg ? p.work_dg_begin : p.work_begin;
                 const int64_t w0 = wb[b], w1 = wb[b + 1];
@@ -1284,7 +1292,14 @@ static void grid_impl(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt,
             {
                 const double vb = unit_vis ? 0.0 : (double)cxs;
                 const double wb = wgt ? (double)sizeof(T) : 0.0;
-                KTimer t(ctx, "grid_tiles", st, 4.0 * nit + nvb * (vb + wb) + nk * plane_bytes);
+                // algorithmic bytes: halo plans write the reached tiles of the block's planes once, and read
+                // per item its code, record and rotor (when kept) and value (item order: weighted, no
+                // weight); other plans count the whole planes and a gathered value and weight per visibility
+                const double g_bytes =
+                    p.halo ? (double)(p.empty_begin[b] - p.heavy_begin[b]) * nk * TILE * TILE * cxs +
+                                 nit * (4.0 + (p.d_rec ? 24.0 : 0.0) + vb + wb)
+                           : 4.0 * nit + nvb * (vb + wb) + nk * plane_bytes;
+                KTimer t(ctx, "grid_tiles", st, g_bytes);
                 if (sizeof(T) == 4 && grid_res_fit(p)) {
                     // dense (chunked) tiles first, then the owned light tiles, as two timed launches
                     const int64_t wh = p.work_heavy_end[b];

@@ -416,20 +416,22 @@ def run_ours(args):
         bi = sum(t.numel() * t.element_size() for t in (h_uvw, h_freq, h_band, h_wgt, h_x))
         bo = h_y.numel() * h_y.element_size()
         barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ctx.pfb_hessian_host(g, h_uvw, h_freq, h_band, h_x, h_wgt, out=h_y)   # plan on the host arrays' copies
         torch.cuda.synchronize(dev)
         lib.pfb_timing(ctx.h, 1)
-        f0.record(stream)
-        for _ in range(args.e2e_steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.e2e_steps + 1)]
+        ev[0].record(stream)
+        for i in range(args.e2e_steps):
             ctx.pfb_hessian_host(g, h_uvw, h_freq, h_band, h_x, h_wgt, out=h_y)
-        f1.record(stream)
+            ev[i + 1].record(stream)
         barrier()
-        ems = max_over_ranks(f0.elapsed_time(f1) / args.e2e_steps, world, dev)
-        # the kernel groups of the host-buffer calls, for the log (stderr)
+        ems = max_over_ranks(ev[0].elapsed_time(ev[-1]) / args.e2e_steps, world, dev)
+        # per call and kernel groups of the host-buffer calls, for the log (stderr)
+        per_call = [round(ev[i].elapsed_time(ev[i + 1]), 2) for i in range(args.e2e_steps)]
         e2e_k = {nm: round(v / args.e2e_steps, 3) for nm, v in kernel_totals(ctx).items()}
         lib.pfb_timing(ctx.h, 0)
-        print(f"e2e: {ems:.2f} ms per call; kernel groups (ms per call): {e2e_k}", file=sys.stderr)
+        print(f"e2e: {ems:.2f} ms per call (calls: {per_call}); kernel groups (ms per call): {e2e_k}",
+              file=sys.stderr)
         e2e = {"value": job_throughput(obs.nvis, world, ems), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo}
 

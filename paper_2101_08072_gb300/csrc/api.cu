@@ -384,14 +384,21 @@ static void hessian_host(Ctx &c, const pfb_geom *g, int prec, int64_t nrow, int3
     PFB_CUDA(cudaMemcpyAsync(d_freq, freq, (size_t)nchan * sizeof(double), cudaMemcpyHostToDevice, st));
     PFB_CUDA(cudaMemcpyAsync(d_band, band, (size_t)nchan * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     PFB_CUDA(cudaMemcpyAsync(d_x, x, (size_t)nimg * sizeof(T), cudaMemcpyHostToDevice, st));
-    // the weights go in before R x on the same stream: a host-to-device copy next to the transforms was
-    // measured to slow them by more than the copy takes
-    if (wgt)
-        PFB_CUDA(cudaMemcpyAsync(d_w, wgt, (size_t)nrow * nchan * sizeof(T), cudaMemcpyHostToDevice, st));
+    // the weights go in on the copy stream while R x runs (only R^dagger Sigma^-1 reads them), after the
+    // work already on the caller's stream, which may still read the previous call's weights
+    cudaEvent_t e_w = nullptr;
+    if (wgt) {
+        cudaEvent_t e_in = c.copy_event(0);
+        e_w = c.copy_event(1);
+        PFB_CUDA(cudaEventRecord(e_in, st));
+        PFB_CUDA(cudaStreamWaitEvent(cs, e_in, 0));
+        PFB_CUDA(cudaMemcpyAsync(d_w, wgt, (size_t)nrow * nchan * sizeof(T), cudaMemcpyHostToDevice, cs));
+        PFB_CUDA(cudaEventRecord(e_w, cs));
+    }
     cudaEvent_t e_out = c.copy_event(2);
     Plan &p = get_plan(c, *g, prec, nrow, nchan, d_uvw, d_freq, d_band, false, st);
     cx_t<T> *vis = (cx_t<T> *)c.scratch("hess_vis", (size_t)nrow * nchan * sizeof(cx_t<T>));
-    op_hessian<T>(c, p, d_x, d_w, vis, d_y, st, [&](int b) {
+    op_hessian<T>(c, p, d_x, d_w, vis, d_y, st, e_w, [&](int b) {
         cudaEvent_t e = c.copy_event(3 + (size_t)b);
         PFB_CUDA(cudaEventRecord(e, st));
         PFB_CUDA(cudaStreamWaitEvent(cs, e, 0));

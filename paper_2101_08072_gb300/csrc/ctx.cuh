@@ -268,11 +268,12 @@ template <typename T>
 void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool unit_vis, T *image,
              cudaStream_t st, const std::function<void(int)> &band_done = {});
 // H x = R^dagger W R x (Eq. 3) into hx; vis is scratch of nrow x nchan complex values.  On plans that list
-// every visibility once (halo plans) the intermediate W R x stays in item order: degridding writes
-// w_v (R x)_v at each item's position and gridding reads it back in the same order, without gathers.
+// every visibility once (halo plans) the intermediate R x stays in item order: degridding writes (R x)_v at
+// each item's position and gridding reads it back in the same order, with the weight w_v gathered by the
+// gridding producers.  wgt_ready (may be NULL): an event after which wgt may be read; R x does not wait.
 template <typename T>
 void op_hessian(Ctx &ctx, const Plan &p, const T *x, const T *wgt, cx_t<T> *vis, T *hx, cudaStream_t st,
-                const std::function<void(int)> &band_done = {});
+                cudaEvent_t wgt_ready = nullptr, const std::function<void(int)> &band_done = {});
 template <typename T>
 void op_wsum(Ctx &ctx, const Plan &p, const T *wgt, double *d_wsum, cudaStream_t st);
 

@@ -1255,7 +1255,7 @@ void op_degrid(Ctx &ctx, const Plan &p, const T *image, cx_t<T> *vis, cudaStream
     degrid_impl<T>(ctx, p, image, vis, st, accumulate, false, nullptr);
 }
 
-// item_order: vis is in item order with the weights applied (wgt is then NULL)
+// item_order: vis is in item order (halo plans); wgt, when given, stays in row order and is gathered per item
 template <typename T>
 static void grid_impl(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool unit_vis, bool item_order,
                       T *image, cudaStream_t st, const std::function<void(int)> &band_done) {
@@ -1355,14 +1355,12 @@ void op_grid(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt, bool uni
 
 template <typename T>
 void op_hessian(Ctx &ctx, const Plan &p, const T *x, const T *wgt, cx_t<T> *vis, T *hx, cudaStream_t st,
-                const std::function<void(int)> &band_done) {
-    if (sizeof(T) == 4 && p.halo && p.nitems == p.nrow * (int64_t)p.nchan) {
-        degrid_impl<T>(ctx, p, x, vis, st, false, true, wgt);
-        grid_impl<T>(ctx, p, vis, nullptr, false, true, hx, st, band_done);
-    } else {
-        degrid_impl<T>(ctx, p, x, vis, st, false, false, nullptr);
-        grid_impl<T>(ctx, p, vis, wgt, false, false, hx, st, band_done);
-    }
+                cudaEvent_t wgt_ready, const std::function<void(int)> &band_done) {
+    // R x needs no weights: they are read (from wgt_ready on) by R^dagger Sigma^-1 alone
+    const bool items = sizeof(T) == 4 && p.halo && p.nitems == p.nrow * (int64_t)p.nchan;
+    degrid_impl<T>(ctx, p, x, vis, st, false, items, nullptr);
+    if (wgt_ready) PFB_CUDA(cudaStreamWaitEvent(st, wgt_ready, 0));
+    grid_impl<T>(ctx, p, vis, wgt, false, items, hx, st, band_done);
 }
 
 template <typename T>
@@ -1381,9 +1379,9 @@ template void op_grid<float>(Ctx &, const Plan &, const float2 *, const float *,
 template void op_grid<double>(Ctx &, const Plan &, const double2 *, const double *, bool, double *, cudaStream_t,
                               const std::function<void(int)> &);
 template void op_hessian<float>(Ctx &, const Plan &, const float *, const float *, float2 *, float *, cudaStream_t,
-                                const std::function<void(int)> &);
+                                cudaEvent_t, const std::function<void(int)> &);
 template void op_hessian<double>(Ctx &, const Plan &, const double *, const double *, double2 *, double *,
-                                 cudaStream_t, const std::function<void(int)> &);
+                                 cudaStream_t, cudaEvent_t, const std::function<void(int)> &);
 template void op_wsum<float>(Ctx &, const Plan &, const float *, double *, cudaStream_t);
 template void op_wsum<double>(Ctx &, const Plan &, const double *, double *, cudaStream_t);
 

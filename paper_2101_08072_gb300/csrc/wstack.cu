@@ -724,8 +724,11 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
 // the planes the current w bucket needs (a ring of W_w + q - 1 planes, refilled as
 // the buckets advance), with coalesced 8-byte loads; then one thread per home item
 // interpolates from shared memory.
+// threads per CTA: three CTAs (each with its staged region) share an SM at 56 registers per thread
+constexpr int DEGRID_NT = 384;
+
 template <int W, int Ww, bool REC>
-__global__ void __launch_bounds__(256, 3) k_degrid_tiles(const WorkItem *__restrict__ work,
+__global__ void __launch_bounds__(DEGRID_NT, 3) k_degrid_tiles(const WorkItem *__restrict__ work,
                                                       const uint32_t *__restrict__ items,
                                                       const int64_t *__restrict__ off, CoordSrc src,
                                                       const float4 *__restrict__ recs, const float2 *__restrict__ rph,
@@ -1146,12 +1149,12 @@ static void launch_degrid_t(unsigned nblk, int R, cudaStream_t st, const WorkIte
     if (p.d_rec) {
         PFB_CUDA(cudaFuncSetAttribute(k_degrid_tiles<W, Ww, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-        k_degrid_tiles<W, Ww, true><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), p.d_rec, p.d_rph,
+        k_degrid_tiles<W, Ww, true><<<nblk, DEGRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), p.d_rec, p.d_rph,
                                                              g, k_lo, k_hi, planes, wgt, item_order, vis);
     } else {
         PFB_CUDA(cudaFuncSetAttribute(k_degrid_tiles<W, Ww, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-        k_degrid_tiles<W, Ww, false><<<nblk, 256, smem, st>>>(work, p.d_items, p.d_off, p.coords(), nullptr, nullptr,
+        k_degrid_tiles<W, Ww, false><<<nblk, DEGRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), nullptr, nullptr,
                                                               g, k_lo, k_hi, planes, wgt, item_order, vis);
     }
 }

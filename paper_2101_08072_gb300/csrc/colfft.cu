@@ -173,13 +173,11 @@ void launch_colfft(float2 *data, int nplanes, int Nv, int64_t plane_sz, int nx, 
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     if (plane_tensor_map(&map, data, N, Nv, nplanes, ny, 256)) {
-        PFB_CUDA(cudaFuncSetAttribute(k_colfft<L, INV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+        ensure_dynamic_smem(k_colfft<L, INV, true>, (size_t)smem);
         k_colfft<L, INV, true><<<(unsigned)(ny / 2), N / 16, smem, st>>>(data, nplanes, Nv, plane_sz, nx, ny, W,
                                                                           map);
     } else {
-        PFB_CUDA(cudaFuncSetAttribute(k_colfft<L, INV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+        ensure_dynamic_smem(k_colfft<L, INV, false>, (size_t)smem);
         k_colfft<L, INV, false><<<(unsigned)(ny / 2), N / 16, smem, st>>>(data, nplanes, Nv, plane_sz, nx, ny, W,
                                                                            map);
     }

@@ -6,12 +6,29 @@
 #include <cuda.h>
 
 #include <functional>
+#include <mutex>
+#include <utility>
 
 namespace pfb {
 
+// Raise a kernel's dynamic shared-memory limit on the current device only when a launch needs more than was set
+// before: one driver call per kernel, device and size instead of one per launch.
+template <typename K>
+inline void ensure_dynamic_smem(K *kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> set;
+    int dev = 0;
+    PFB_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &have = set[{reinterpret_cast<const void *>(kernel), dev}];
+    if (bytes <= have) return;
+    PFB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    have = bytes;
+}
+
 // One gridding work item: a uv tile of one band, either the tile's whole item
-// list (plain stores of the tile's cells) or one chunk of a heavy tile's list
-// (reduction into zeroed cells).
+// list or one chunk of a heavy tile's list; atomic_mode says how its sums reach the
+// planes (plain stores of cells the item owns, or reductions into zeroed cells).
 struct WorkItem {
     int tile;
     int atomic_mode;

@@ -612,7 +612,7 @@ static void dwt_level_launch(int nband, int n, int m, View2<T> src, View2<T> ll,
                              cudaStream_t st) {
     const int tk = (n / 2 + DWT_TO - 1) / DWT_TO, tq = (m / 2 + DWT_TO - 1) / DWT_TO;
     const size_t sm = dwt_smem<T>(L);
-    PFB_CUDA(cudaFuncSetAttribute(k_dwt2_tile<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ensure_dynamic_smem(k_dwt2_tile<T, L>, (size_t)sm);
     k_dwt2_tile<T, L><<<dim3((unsigned)(tk * tq), (unsigned)nband), 256, sm, st>>>(n, m, tq, src, ll, det,
                                                                                   WavTaps<T>(f));
     check_launch("dwt");
@@ -623,7 +623,7 @@ static void idwt_level_launch(int nband, int n, int m, View2<T> ll, View2<T> det
                               T alpha, int accumulate, cudaStream_t st) {
     const int tp = (n + DWT_TX - 1) / DWT_TX, ts = (m + DWT_TX - 1) / DWT_TX;
     const size_t sm = idwt_smem<T>(L);
-    PFB_CUDA(cudaFuncSetAttribute(k_idwt2_tile<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ensure_dynamic_smem(k_idwt2_tile<T, L>, (size_t)sm);
     k_idwt2_tile<T, L><<<dim3((unsigned)(tp * ts), (unsigned)nband), 256, sm, st>>>(n, m, ts, ll, det, dst,
                                                                                    WavTaps<T>(f), alpha, accumulate);
     check_launch("idwt");

@@ -461,7 +461,7 @@ void launch_colfwd(cudaStream_t st, float2 *planes, int nk, int k_lo, int Nv, in
     using E = ColE<L>;
     const size_t smem = fft_smem<L, E>();
     const unsigned grid = (unsigned)(ny / Lanes<E>::K);
-    PFB_CUDA(cudaFuncSetAttribute(k_colfwd<L, TMA, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_dynamic_smem(k_colfwd<L, TMA, E>, (size_t)smem);
     k_colfwd<L, TMA, E><<<grid, (1 << L) / 16, smem, st>>>(
         planes, nk, k_lo, Nv, plane_sz, nx, ny, (const typename Lanes<E>::X *)xcT,
         (const typename Lanes<E>::Tt *)tT, wk, wstack, rowocc, W, map);
@@ -474,7 +474,7 @@ void launch_colinv(cudaStream_t st, const float2 *planes, int nk, int k_lo, int 
     using E = ColE<L>;
     const size_t smem = fft_smem<L, E>() + (size_t)nx * sizeof(typename Lanes<E>::X);
     const unsigned grid = (unsigned)(ny / Lanes<E>::K);
-    PFB_CUDA(cudaFuncSetAttribute(k_colinv<L, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_dynamic_smem(k_colinv<L, E>, (size_t)smem);
     k_colinv<L, E><<<grid, (1 << L) / 16, smem, st>>>(planes, nk, k_lo, Nv, plane_sz, nx, ny,
                                                        (const typename Lanes<E>::Tt *)tT, wk, wstack, rowocc, corr,
                                                        accumulate, image, W);
@@ -486,7 +486,7 @@ void launch_rowfft(int64_t entries, cudaStream_t st, float2 *planes, int k_lo, i
     using E = ColE<L>;
     const size_t smem = fft_smem<L, E>();
     const unsigned grid = (unsigned)(entries * (TILE / Lanes<E>::K));
-    PFB_CUDA(cudaFuncSetAttribute(k_rowfft<L, INV, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_dynamic_smem(k_rowfft<L, INV, E>, (size_t)smem);
     k_rowfft<L, INV, E><<<grid, (1 << L) / 16, smem, st>>>(planes, k_lo, ntu, plane_sz, ny, list, occ, W);
 }
 

@@ -1128,13 +1128,11 @@ static void launch_grid_res_t(unsigned nblk, cudaStream_t st, const WorkItem *wo
                               int k_lo, int k_hi, float2 *planes) {
     const size_t smem = (size_t)res_layout(W, Ww).total;
     if (p.d_rec) {
-        PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+        ensure_dynamic_smem(k_grid_res<W, Ww, true>, (size_t)smem);
         k_grid_res<W, Ww, true><<<nblk, GRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), p.d_rec,
                                                              p.d_rph, vis, wgt, unit, item_order, g, k_lo, k_hi, planes);
     } else {
-        PFB_CUDA(cudaFuncSetAttribute(k_grid_res<W, Ww, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+        ensure_dynamic_smem(k_grid_res<W, Ww, false>, (size_t)smem);
         k_grid_res<W, Ww, false><<<nblk, GRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), nullptr,
                                                               nullptr, vis, wgt, unit, item_order, g, k_lo, k_hi, planes);
     }
@@ -1147,13 +1145,11 @@ static void launch_degrid_t(unsigned nblk, int R, cudaStream_t st, const WorkIte
     const int E = TILE + W - 1, ES = E | 1;
     const size_t smem = (size_t)R * E * ES * sizeof(float2);
     if (p.d_rec) {
-        PFB_CUDA(cudaFuncSetAttribute(k_degrid_tiles<W, Ww, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+        ensure_dynamic_smem(k_degrid_tiles<W, Ww, true>, (size_t)smem);
         k_degrid_tiles<W, Ww, true><<<nblk, DEGRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), p.d_rec, p.d_rph,
                                                              g, k_lo, k_hi, planes, wgt, item_order, vis);
     } else {
-        PFB_CUDA(cudaFuncSetAttribute(k_degrid_tiles<W, Ww, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+        ensure_dynamic_smem(k_degrid_tiles<W, Ww, false>, (size_t)smem);
         k_degrid_tiles<W, Ww, false><<<nblk, DEGRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), nullptr, nullptr,
                                                               g, k_lo, k_hi, planes, wgt, item_order, vis);
     }
@@ -1271,7 +1267,7 @@ static void grid_impl(Ctx &ctx, const Plan &p, const cx_t<T> *vis, const T *wgt,
     const int64_t npix = (int64_t)p.nx * p.ny;
     const int R = p.Ww + p.q - 1;
     const size_t smem = (size_t)R * TILE * TILE * cxs;
-    PFB_CUDA(cudaFuncSetAttribute(k_grid_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_dynamic_smem(k_grid_tiles<T>, (size_t)smem);
     const double plane_bytes = (double)p.Nu * p.Nv * cxs;
     for (int b = 0; b < p.nband; ++b) {
         const BandGeom g = p.geom(b);

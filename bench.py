@@ -391,7 +391,7 @@ def run_ours(args):
     names = ctypes.create_string_buffer(4096)
     lib.pfb_timing_names(ctx.h, names, 4096)
     kern = {}
-    for nm in [n for n in names.value.decode().split(",") if n]:
+    for nm in [n for n in names.value.decode().split(",") if n and n != "w_planes"]:   # w_planes: a count
         L, T, B = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
         lib.pfb_timing_read(ctx.h, nm.encode(), ctypes.byref(L), ctypes.byref(T), ctypes.byref(B))
         kern[nm] = {"launches": L.value, "ms": T.value, "bytes": B.value}
@@ -778,15 +778,20 @@ def run_facets(args):
 
     ms_full = timed(full, args.steps)
     ms_fac = timed(faceted, args.steps)
-    # planes per facet and for the whole image, from the forward-FFT bytes the library records
+    # planes per facet and for the whole image, from the plane bytes the library records per forward plane
+    # block (pruned transforms: "w_planes", one plane sweep; full-plane transforms: "fft_fwd", two sweeps)
     def planes(fn, nx, ny):
         ctx.lib.pfb_timing(ctx.h, 1)
         fn()
         import ctypes
         n, ms, by = ctypes.c_int64(0), ctypes.c_double(0), ctypes.c_double(0)
-        ctx.lib.pfb_timing_read(ctx.h, b"fft_fwd", ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by))
+        ctx.lib.pfb_timing_read(ctx.h, b"w_planes", ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by))
+        sweeps = 1.0
+        if by.value == 0:
+            ctx.lib.pfb_timing_read(ctx.h, b"fft_fwd", ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by))
+            sweeps = 2.0
         ctx.lib.pfb_timing(ctx.h, 0)
-        return by.value / (2.0 * (2 * nx) * (2 * ny) * 8)
+        return by.value / (sweeps * (2 * nx) * (2 * ny) * 8)
     pl_full = planes(lambda: ctx.pfb_degrid(g_full, uvw, freq, band, x, out=vis), obs.nx, obs.ny)
     pl_fac = [planes(lambda f=f: ctx.pfb_degrid(f[2], uvw, freq, band, f[4], out=vis), fx, fy) for f in facets]
     faceted()
@@ -817,7 +822,7 @@ def kernel_totals(ctx):
     buf = ctypes.create_string_buffer(1 << 14)
     ctx.lib.pfb_timing_names(ctx.h, buf, len(buf))
     out = {}
-    for name in filter(None, buf.value.decode().split(",")):
+    for name in (nm for nm in buf.value.decode().split(",") if nm and nm != "w_planes"):
         n, ms = ctypes.c_int64(0), ctypes.c_double(0)
         ctx.lib.pfb_timing_read(ctx.h, name.encode(), ctypes.byref(n), ctypes.byref(ms), None)
         out[name] = ms.value

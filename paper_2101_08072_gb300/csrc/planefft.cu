@@ -598,6 +598,8 @@ void plane_forward(Ctx &ctx, const Plan &p, int b, const float *x, int k_lo, int
     occupied_counts(p, b, k_lo, k_hi, &rows);
     void *xcT = ctx.scratch("xcT", (size_t)npix * sizeof(float));
     const int K = col_group(p.Nu);
+    // the w-planes of this block, as the bytes of one plane sweep (a count for the timing record, no kernel)
+    { KTimer w(ctx, "w_planes", st, (double)nk * (double)plane_sz * sizeof(float2), 0); }
     {
         KTimer t(ctx, "xc_transpose", st, 12.0 * npix);
         const dim3 grid((unsigned)((p.nx + 31) / 32), (unsigned)((p.ny / K + 31) / 32));

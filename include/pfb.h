@@ -195,16 +195,21 @@ int pfb_psf(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, int64_t nrow, int
             const double *uvw, const double *freq, const int32_t *band_of_chan,
             const void *wgt, void *psf_out, double *wsum_out, void *stream);
 
-/* Exact Hessian-vector product (Eq. 3): y_out = R^dagger Sigma^-1 R x, both [nband][nx][ny]. */
+/* Exact Hessian-vector product (Eq. 3): y_out = R^dagger Sigma^-1 R x, both [nband][nx][ny].  Arguments,
+ * layouts and errors as pfb_degrid and pfb_grid (wgt may be NULL: unit weights).  The intermediate R x lives in
+ * the context's scratch ([nrow][nchan] complex values); on FP32 plans with tile kernels it stays in the plan's
+ * item order between R and R^dagger Sigma^-1, so the result equals pfb_grid(pfb_degrid(x)) up to rounding. */
 int pfb_hessian(pfb_ctx *ctx, const pfb_geom *geom, pfb_prec prec, int64_t nrow, int32_t nchan,
                 const double *uvw, const double *freq, const int32_t *band_of_chan,
                 const void *wgt, const void *x, void *y_out, void *stream);
 
 /* The Hessian of pfb_hessian (Eq. 3) from HOST buffers: uvw, freq, band_of_chan, wgt (may be NULL:
  * unit weights) and x are read from host memory, y_out is written to host memory; layouts as in
- * pfb_hessian.  The inputs go in on `stream` before the computation; each band of y_out comes back on an
- * internal copy stream as soon as it is gridded, overlapping the later bands.  With page-locked (pinned)
- * host memory the copies are asynchronous; pageable memory works but loses the overlap.  The call enqueues work on `stream` (the copy stream is joined back to it); y_out holds the
+ * pfb_hessian.  uvw, freq, band_of_chan and x go in on `stream` before the computation; wgt goes in on an
+ * internal copy stream, issued before R x (only R^dagger Sigma^-1 reads it, and waits for it); each band
+ * of y_out comes back on the copy stream as soon as it is gridded.  With page-locked (pinned) host memory
+ * the copies are asynchronous and may overlap the computation; pageable memory works but loses that.
+ * The call enqueues work on `stream` (the copy stream is joined back to it); y_out holds the
  * result once `stream` has been synchronised, and the host buffers must stay valid until then.  The
  * device copies live in the context's scratch and the plan is built on them; it is reused while the
  * host pointers of uvw, freq and band_of_chan (and nrow, nchan) stay the same, so call

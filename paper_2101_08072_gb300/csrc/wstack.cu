@@ -719,11 +719,12 @@ k_grid_res(const WorkItem *__restrict__ work, const uint32_t *__restrict__ items
 }
 
 // ------------------------------------------------------------------ FP32 degridding from staged tiles
-// One CTA per work item (home items of a tile, or a chunk of a heavy tile).  The
-// tile's footprint region of (TILE + W - 1)^2 cells is staged in shared memory for
-// the planes the current w bucket needs (a ring of W_w + q - 1 planes, refilled as
-// the buckets advance), with coalesced 8-byte loads; then one thread per home item
-// interpolates from shared memory.
+// One CTA per work item (home items of a tile, or a chunk of a heavy tile).  For each
+// w bucket the tile's footprint region of (TILE + W - 1)^2 cells is staged in shared
+// memory for the bucket's W_w planes, with coalesced 8-byte loads, cell-major: a
+// cell's planes lie side by side, so one 16-byte load brings two of them.  Then one
+// thread per home item interpolates from shared memory, summing each cell over its
+// planes before the u and v taps.
 // threads per CTA: three CTAs (each with its staged region) share an SM at 56 registers per thread
 constexpr int DEGRID_NT = 384;
 
@@ -737,17 +738,15 @@ __global__ void __launch_bounds__(DEGRID_NT, 3) k_degrid_tiles(const WorkItem *_
                                                       float2 *__restrict__ vis) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *reg = reinterpret_cast<float2 *>(smem_raw);
-    __shared__ int slot_plane[MAX_W];
-    constexpr int R = Ww;                  // ring planes (one w bucket per plane)
-    const int E = TILE + W - 1;          // region edge
-    const int ES = E | 1;                // odd row stride: fewer bank conflicts
-    const int reg_sz = E * ES;
+    // the region of the current bucket's W_w planes, cell-major: cell (r, c) holds its planes k0 .. k0 + W_w - 1
+    // (padded to an even count) side by side, so that one 16-byte load brings two planes of a cell
+    constexpr int RP = (Ww + 1) & ~1;
+    constexpr int E = TILE + W - 1;      // region edge
     const WorkItem wi = work[blockIdx.x];
     if (wi.end <= wi.begin) return;
     const int tu = wi.tile / g.ntv, tv = wi.tile - tu * g.ntv;
     const int64_t plane_sz = (int64_t)g.Nu * g.Nv;
     const int64_t kbase = ((int64_t)g.band * g.ntu * g.ntv + wi.tile) * g.nkq;
-    for (int i = threadIdx.x; i < R; i += blockDim.x) slot_plane[i] = -1;
     int lo = 0, hi = g.nkq - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
@@ -769,25 +768,23 @@ __global__ void __launch_bounds__(DEGRID_NT, 3) k_degrid_tiles(const WorkItem *_
         // planes this bucket needs, clipped to the block
         const int pa = max(kq * g.q, k_lo), pb = min(kq * g.q + g.q + Ww - 1, k_hi);
         if (pa >= pb) continue;
-        // load missing planes into their ring slots
-        bool loaded = false;
-        for (int k = pa; k < pb; ++k) {
-            const int sl = k % R;
-            if (slot_plane[sl] == k) continue;
-            loaded = true;
-            float2 *dst = reg + sl * reg_sz;
-            const float2 *srcp = planes + (int64_t)(k - k_lo) * plane_sz;
-            for (int i = threadIdx.x; i < E * E; i += blockDim.x) {
-                const int r = i / E, c = i - r * E;
+        // stage the bucket's planes k0 .. k0 + W_w - 1 (zero outside the block [pa, pb)); the previous bucket's
+        // readers finished at the barrier that ends its item loop
+        const int k0 = kq * g.q;
+        for (int i = threadIdx.x; i < RP * E * E; i += blockDim.x) {
+            const int p = i / (E * E), rc = i - p * (E * E);
+            const int r = rc / E, c = rc - r * E;
+            const int k = k0 + p;
+            float2 val = make_float2(0.f, 0.f);
+            if (p < Ww && k >= pa && k < pb) {
                 int gu = tu * TILE + r, gv = tv * TILE + c;
                 gu -= gu >= g.Nu ? g.Nu : 0;
                 gv -= gv >= g.Nv ? g.Nv : 0;
-                dst[r * ES + c] = srcp[(int64_t)gu * g.Nv + gv];
+                val = planes[(int64_t)(k - k_lo) * plane_sz + (int64_t)gu * g.Nv + gv];
             }
+            reg[rc * RP + p] = val;
         }
         __syncthreads();
-        if (loaded && threadIdx.x == 0)
-            for (int k = pa; k < pb; ++k) slot_plane[k % R] = k;
         // the bucket lists its home items first (the plan's fine sort), then spill copies of
         // neighbours' items, which this tile does not degrid: find the end of the home items
         int64_t he = s;
@@ -860,30 +857,33 @@ __global__ void __launch_bounds__(DEGRID_NT, 3) k_degrid_tiles(const WorkItem *_
             } else {
                 kw[0] = 1.f;
             }
+            // per cell the sum over its planes first (planes outside the block are staged as zeros), then the
+            // u and v taps; the item's planes are the bucket's (one w plane per bucket on this path)
+            float kp[RP];
+#pragma unroll
+            for (int p = 0; p < RP; ++p) kp[p] = p < Ww ? kw[p < Ww ? p : 0] : 0.f;
             float ar = 0.f, ai = 0.f;
-            const int s0 = c.k0 % R;
+            const float4 *pl = reinterpret_cast<const float4 *>(reg + (lu * E + lv) * RP);
 #pragma unroll
-            for (int cw = 0; cw < Ww; ++cw) {
-                const int k = c.k0 + cw;
-                if (k < k_lo || k >= k_hi) continue;
-                const int sl = s0 + cw - (s0 + cw >= R ? R : 0);
-                const float2 *pl = reg + sl * reg_sz + lu * ES + lv;
-                float pr = 0.f, pi = 0.f;
+            for (int a = 0; a < W; ++a) {
+                float rr = 0.f, ri = 0.f;
 #pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    const float2 *prow = pl + a * ES;
-                    float rr = 0.f, ri = 0.f;
+                for (int b = 0; b < W; ++b) {
+                    const float4 *q = pl + (a * E + b) * (RP / 2);
+                    float sr = 0.f, si = 0.f;
 #pragma unroll
-                    for (int b = 0; b < W; ++b) {
-                        const float2 q = prow[b];
-                        rr = fmaf(kv[b], q.x, rr);
-                        ri = fmaf(kv[b], q.y, ri);
+                    for (int h = 0; h < RP / 2; ++h) {
+                        const float4 t = q[h];
+                        sr = fmaf(kp[2 * h], t.x, sr);
+                        si = fmaf(kp[2 * h], t.y, si);
+                        sr = fmaf(kp[2 * h + 1], t.z, sr);
+                        si = fmaf(kp[2 * h + 1], t.w, si);
                     }
-                    pr = fmaf(ku[a], rr, pr);
-                    pi = fmaf(ku[a], ri, pi);
+                    rr = fmaf(kv[b], sr, rr);
+                    ri = fmaf(kv[b], si, ri);
                 }
-                ar = fmaf(kw[cw], pr, ar);
-                ai = fmaf(kw[cw], pi, ai);
+                ar = fmaf(ku[a], rr, ar);
+                ai = fmaf(ku[a], ri, ai);
             }
             float vr = ar * cs + ai * sn;
             float vi = ai * cs - ar * sn;
@@ -1112,8 +1112,8 @@ void build_item_records(Ctx &ctx, Plan &p, cudaStream_t st) {
 }
 
 static bool degrid_tiles_fit(const Plan &p) {
-    const int R = p.Ww, E = TILE + p.W - 1, ES = E | 1;
-    return fast_path_f32(p) && (size_t)R * E * ES * sizeof(float2) <= 227 * 1024;
+    const int RP = (p.Ww + 1) & ~1, E = TILE + p.W - 1;
+    return fast_path_f32(p) && (size_t)RP * E * E * sizeof(float2) <= 227 * 1024;
 }
 // FP32 plans whose tile kernels fit: the plan lists each visibility once, in its home tile, and the
 // gridding kernel adds the tile's region with the footprints' far edges (k_grid_res)
@@ -1142,8 +1142,9 @@ template <int W, int Ww>
 static void launch_degrid_t(unsigned nblk, int R, cudaStream_t st, const WorkItem *work, const Plan &p,
                             const BandGeom &g, int k_lo, int k_hi, const float2 *planes, const float *wgt,
                             int item_order, float2 *vis) {
-    const int E = TILE + W - 1, ES = E | 1;
-    const size_t smem = (size_t)R * E * ES * sizeof(float2);
+    (void)R;
+    const int E = TILE + W - 1;
+    const size_t smem = (size_t)((Ww + 1) & ~1) * E * E * sizeof(float2);
     if (p.d_rec) {
         ensure_dynamic_smem(k_degrid_tiles<W, Ww, true>, (size_t)smem);
         k_degrid_tiles<W, Ww, true><<<nblk, DEGRID_NT, smem, st>>>(work, p.d_items, p.d_off, p.coords(), p.d_rec, p.d_rph,
